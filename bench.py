@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the sGKS hot path on one GB300 (or N independent replicas under torchrun).
+
+Workload (default): the 256 x 256 image-deblurring problem -- 9x9 Gaussian PSF (sigma 2),
+zero boundary, 2D gradient regularizer, lambda = 5e-3, 1% noise, sparse-sign sketch with
+s = 400 rows and 8 nonzeros per column, FP32 operators with FP64 sketched QR / projected
+solve and 2 refinement steps, 100 iterations.  One step = one whole solve of one right-hand
+side: sgks_reset (setup: S_A b, W_0, sketched QR of W_0, y_0, x_0) + 100 iterations.
+Metric: sGKS iterations per second (whole job, all replicas).  L2 is flushed (a 256 MiB
+write) before every step, outside the timed interval of the step.
+
+Extra keys: the plain FP64 GPU form on the same problem (iterations/s, final RRE and the
+time to reach 1.01 x its final RRE, for the FP32+refinement form too), the per-kernel profile
+and the roofline of the dominant kernel, nvidia-smi clocks during the timed region, and the
+FP64 CPU oracle timed on the host cores on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sGKS iterations/s (256x256 deblurring, FP32 operators + FP64 QR/solve + 2 refinement steps)"
+UNIT = "iterations/s"
+WORKLOAD = ("deblur2d: 256x256 image, 9x9 Gaussian PSF sigma=2 zero boundary, grad2d L, lambda=5e-3, 1% noise, "
+            "sparse-sign s=400 zeta=8, 100 iterations, FP32 + 2 refinement steps")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="deblur2d")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, profile and CPU baseline")
+    ap.add_argument("--cpu-sample-iters", type=int, default=25)
+    ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------- workload
+def make_workload(name, seed):
+    from workloads import make_problem
+    return make_problem(name, seed=seed)
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def cpu_oracle_sample(name, iters, seed=0):
+    """Time the FP64 oracle (as it stands) on `iters` iterations of the workload, one thread."""
+    import oracle as O
+    P = make_workload(name, seed)
+    t0 = time.perf_counter()
+    O.sgks(P, iters=iters)
+    dt = time.perf_counter() - t0
+    return dict(seconds=dt, iters=iters)
+
+
+def run_cpu_worker(name, iters):
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--config", name,
+           "--cpu-sample-iters", str(iters)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------------------- byte models
+def bytes_model(P, cls, d, elem):
+    """Algorithmic bytes of one launch of a kernel class at subspace size d."""
+    n, m, p, s = P.n, P.m, P.p, P.sketch.s
+    T = elem
+    if cls == "combine":
+        return d * (n + m) * T + (n + 2 * m) * T + 3 * n * T
+    if cls == "combine_refine":
+        return d * (n + m) * T + (n + 2 * m) * T
+    if cls == "gradient_refine":
+        return d * n * T + (m + n) * T
+    if cls == "gradient_append":
+        return (m + n) * T + n * T
+    if cls == "sketch_column":
+        return n * T + m * T
+    if cls == "append_solve":
+        return 8 * (2 * 2 * s * d + 2 * s + 3 * (2 * d) ** 2 + d * d)
+    if cls == "refine_solve":
+        return 8 * d * d
+    return 0
+
+
+def flops_fp64(P, cls, d):
+    s = P.sketch.s
+    if cls == "append_solve":
+        return 2.0 * (2 * 2 * 2 * s * d) + 2.0 * (4 * d * d + 4 * d * d + d * d)
+    if cls == "refine_solve":
+        return 2.0 * d * d
+    return 0.0
+
+
+# --------------------------------------------------------------------------- reference
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    name = args.config
+    iters = max(3, args.cpu_sample_iters // 5)
+    for _ in range(args.warmup):
+        run_cpu_worker(name, iters)
+    tot = 0.0
+    for _ in range(args.steps):
+        r = run_cpu_worker(name, iters)
+        tot += r["seconds"]
+    value = args.steps * iters / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{iters} iterations after the setup, per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"NumPy FP64 oracle, setup + {iters} iterations of the workload per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------------- ours
+def main():
+    args = parse()
+    if args.cpu_worker:
+        print(json.dumps(cpu_oracle_sample(args.config, args.cpu_sample_iters)))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2606_18073_gb300 as G
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    G.build()
+
+    P = make_workload(args.config, seed=rank)
+    iters = P.iters
+    kw = G.device_inputs(P, P.precision, device=dev)
+    S = G.Solver(**kw)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+
+    def one_step(solver, b):
+        solver.reset(b)
+        return solver.solve(iters)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        one_step(S, kw["b"])
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        dist.barrier()
+    clk = ClockSampler(dev.index)
+    clk.start()
+    launches0 = G.kernel_launches()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize(dev)
+    rep = None
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        rep = one_step(S, kw["b"])
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    launches = G.kernel_launches() - launches0
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    if ws > 1:
+        dist.barrier()
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.stop()
+    value = ws * args.steps * iters / (ms / 1e3)
+
+    # ---- e2e through the public API with host buffers (pinned), copies inside the timed step
+    dt = kw["b"].dtype
+    b_host = torch.from_numpy(np.asarray(P.b)).to(dt).pin_memory()
+    x_host = torch.empty(P.n, dtype=dt).pin_memory()
+    b_dev = torch.empty_like(kw["b"])
+    x_dev = torch.empty(P.n, dtype=dt, device=dev)
+    e2e_ms = 0.0
+    for k in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        b_dev.copy_(b_host, non_blocking=True)
+        S.reset(b_dev)
+        S.solve(iters, x_out=x_dev)
+        x_host.copy_(x_dev, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms += a.elapsed_time(b)
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = ws * args.steps * iters / (e2e_ms / 1e3)
+    elem = b_host.element_size()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if P.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "iterations_per_step": iters, "l2": "flushed (256 MiB write) before each step",
+                   "parallelism": "replicas" if ws > 1 else "single", "final_rre": rep["rre_last"]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": P.m * elem, "d2h_bytes_per_step": P.n * elem},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_extras:
+        line.update(extras(args, G, P, kw, S, iters, dev, flush))
+    S.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def time_solve(G, S, b, iters, flush, dev, reps=3):
+    stream = torch_stream(dev)
+    import torch
+    best = None
+    for _ in range(reps):
+        flush.zero_()
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        S.reset(b)
+        out = S.solve(iters, history=True)
+        c.record(stream)
+        torch.cuda.synchronize(dev)
+        t = a.elapsed_time(c)
+        best = (t, out) if best is None or t < best[0] else best
+    return best
+
+
+def torch_stream(dev):
+    import torch
+    return torch.cuda.current_stream(dev)
+
+
+def time_to_rre(ms_total, rre_hist, target, iters):
+    """Wall time until RRE_k <= target, assuming equal time per iteration (setup included)."""
+    for k, r in enumerate(rre_hist):
+        if r <= target:
+            return ms_total * (k + 1) / iters
+    return None
+
+
+def extras(args, G, P, kw, S, iters, dev, flush):
+    import torch
+    out = {}
+    # FP32 + refinement: per-iteration RRE history for time-to-tolerance
+    t32, h32 = time_solve(G, S, kw["b"], iters, flush, dev)
+    # plain FP64 GPU sGKS on the same problem (no refinement, as Algorithm 2)
+    P64 = make_workload(args.config, seed=0)
+    P64.n_refine = 0
+    kw64 = G.device_inputs(P64, "fp64", device=dev)
+    S64 = G.Solver(**kw64)
+    t64, h64 = time_solve(G, S64, kw64["b"], iters, flush, dev)
+    S64.close()
+    target = 1.01 * h64["rre_last"]
+    out["fp64_plain"] = {"iters_per_s": iters / (t64 / 1e3), "ms_per_solve": t64, "final_rre": h64["rre_last"]}
+    out["time_to_rre"] = {
+        "target_rre": target,
+        "fp64_plain_ms": time_to_rre(t64, h64["rre"], target, iters),
+        "fp32_refined_ms": time_to_rre(t32, h32["rre"], target, iters),
+        "fp32_refined_final_rre": h32["rre_last"],
+    }
+    # per-kernel profile (CUDA events on the library's stream, one eager solve)
+    S.reset(kw["b"])
+    prof = S.profile(iters)
+    tot = sum(v["ms"] for v in prof.values())
+    elem = 4 if P.precision == "fp32" else 8
+    kern = {}
+    for k, v in prof.items():
+        if v["launches"] == 0:
+            continue
+        davg = v["dsum"] / v["launches"]
+        bts = bytes_model(P, k, davg, elem)
+        kern[k] = {"ms_total": v["ms"], "launches": v["launches"], "share": v["ms"] / tot,
+                   "us_per_launch": 1e3 * v["ms"] / v["launches"], "avg_d": davg,
+                   "alg_bytes_per_launch": bts, "gbps": bts / (1e-3 * v["ms"] / v["launches"]) / 1e9}
+    out["kernels"] = kern
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    # dominant bandwidth kernel (largest time share among the streaming kernels)
+    stream_k = [k for k in kern if k not in ("append_solve", "refine_solve")]
+    dom = max(stream_k, key=lambda k: kern[k]["ms_total"])
+    dk = kern[dom]
+    out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": dk["gbps"], "peak": hbm, "unit": "GB/s",
+                       "frac": dk["gbps"] / hbm, "traffic": None,
+                       "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)" if peaks else
+                       "fallback 6800 GB/s"}
+    a = kern.get("append_solve")
+    if a:
+        fl = flops_fp64(P, "append_solve", a["avg_d"])
+        out["roofline_fp64_solve"] = {"kernel": "append_solve", "bound": "alu", "achieved": fl / (a["us_per_launch"] * 1e-6) / 1e12,
+                                      "peak": 1.25, "unit": "TFLOP/s (FP64)",
+                                      "frac": fl / (a["us_per_launch"] * 1e-6) / 1e12 / 1.25}
+    # CPU oracle baseline, bounded sample, one thread
+    try:
+        r = run_cpu_worker(args.config, args.cpu_sample_iters)
+        out["cpu_baseline"] = {"value": r["iters"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"FP64 NumPy oracle, setup + {r['iters']} of {iters} iterations, "
+                                         f"{r['seconds']:.1f} s, BLAS threads = 1"}
+    except Exception as exc:   # the GPU number stands without it
+        out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
+    return out
+
+
+if __name__ == "__main__":
+    main()

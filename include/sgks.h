@@ -1,0 +1,241 @@
+/*
+ * sgks.h -- C ABI of the GB300 sGKS library (sketched generalized Krylov subspace method
+ * for general-form Tikhonov regularization).
+ *
+ * Problem (paper Sec. 1, eq. tik):   min_x ||A x - b||^2 + lambda ||L x||^2,
+ * A in R^{m x n}, L in R^{p x n}, lambda > 0.  The solver is Algorithm 2 (sGKS): the basis
+ * W_k = [W_0, r_1, ..., r_k] is never orthogonalised; each new column r_{k+1} is the gradient
+ * A^T (A x_k - b) + lambda L^T L x_k (eq. gradient); the projected problem is solved through
+ * sketched QR factors S_A A W_k = Q_A R_A, S_L L W_k = Q_L R_L updated one column at a time
+ * (eq. updqr, eq. projected_sketched_bis).  W_0 spans K_l(A^T A, A^T b), l = 3 (Sec. 4).
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers (CUDA global memory of the current device) unless
+ *    the argument description says "host".  The caller owns them; the library never frees
+ *    them.  Arrays passed to sgks_create must stay valid and unchanged until sgks_destroy.
+ *  - Every function returns an int status: SGKS_OK (0), a negative error code, or a positive
+ *    warning.  No function throws across the ABI.  A handle is not thread-safe.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream); all
+ *    device work of a handle is ordered on that stream.
+ *  - Images are row-major with x fastest (pixel (iy, ix) -> iy*nx + ix); space-time unknowns
+ *    are frame-major (t*ny*nx + iy*nx + ix).
+ */
+#ifndef SGKS_H
+#define SGKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define SGKS_OK             0
+#define SGKS_BREAKDOWN      1   /* warning: new column numerically in the span of W (both sketched
+                                   residual norms <= 1e-13 of the column norm, or exactly 0);
+                                   it was not appended and the solve stopped early            */
+#define SGKS_STOPPED        2   /* info: the relative-change test RC_k < tol stopped the solve */
+#define SGKS_ERR_INVALID   -1   /* bad argument or descriptor                                  */
+#define SGKS_ERR_CUDA      -2   /* a CUDA runtime call failed (see sgks_last_error)             */
+#define SGKS_ERR_NONFINITE -3   /* NaN/Inf met in a sketched column or a residual norm         */
+#define SGKS_ERR_STATE     -4   /* call not valid in the handle's state (e.g. basis full)       */
+#define SGKS_ERR_NOMEM     -5   /* device allocation failed                                    */
+#define SGKS_ERR_SKETCH    -6   /* sparse-sign draw limit (256 draws for one column) exceeded   */
+
+/* ---- enums ------------------------------------------------------------------------------ */
+enum { SGKS_F32 = 0, SGKS_F64 = 1 };
+enum { SGKS_OP_DENSE = 1, SGKS_OP_CSR = 2, SGKS_OP_CONV2D = 3 };
+enum { SGKS_REG_FD1 = 1, SGKS_REG_GRAD2D = 2, SGKS_REG_LAPLACE2D = 3, SGKS_REG_SPACETIME = 4 };
+enum { SGKS_SKETCH_SPARSE_SIGN = 0, SGKS_SKETCH_GAUSSIAN = 1 };
+enum { SGKS_PREC_FP64 = 0, SGKS_PREC_FP32 = 1 };
+
+/* Forward operator A (m x n).
+ *  SGKS_OP_CSR:    row_ptr[m+1], col[nnz] (int32, 0-based), val[nnz] of val_dtype.  Optional
+ *                  transpose (the same matrix stored by columns): t_row_ptr[n+1], t_col[nnz]
+ *                  (row indices of A, ascending within each column), t_val[nnz]; if all three
+ *                  are NULL the library builds it on the device at sgks_create.
+ *  SGKS_OP_DENSE:  dense[m*ld], row-major, ld >= n, of val_dtype.
+ *  SGKS_OP_CONV2D: 2D convolution of an ny x nx image with the odd-sized kernel psf[kh*kw]
+ *                  (row-major, val_dtype), zero boundary, same-size output (m = n = nx*ny):
+ *                  (A x)[i,j] = sum_{a,c} psf[a*kw+c] * x[(i-a+kh/2)*nx + (j-c+kw/2)].
+ * Values are converted to the solver precision on the device (FP32 form: rounded to float;
+ * FP64 form: float values are widened exactly). */
+typedef struct sgks_op {
+    int32_t kind;
+    int32_t val_dtype;
+    int64_t m, n;
+    int64_t nnz;
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const void* val;
+    const int32_t* t_row_ptr;
+    const int32_t* t_col;
+    const void* t_val;
+    const void* dense;
+    int64_t ld;
+    int32_t nx, ny, kh, kw;
+    const void* psf;
+} sgks_op;
+
+/* Regularization operator L (p x n), a matrix-free finite-difference stencil.
+ *  SGKS_REG_FD1:       D_n (rows [-1 1]), n = nx, p = nx-1               (Sec. 4, eq. reg_matrix)
+ *  SGKS_REG_GRAD2D:    [I_ny (x) D_nx ; D_ny (x) I_nx], p = ny(nx-1)+(ny-1)nx (eq. reg_matrix)
+ *  SGKS_REG_LAPLACE2D: 5-point Laplacian 4x_p - sum of the 4 neighbours, zero outside, p = nx ny
+ *  SGKS_REG_SPACETIME: Psi of eq. spacetime_tik (Sec. 4.4), nt frames of ny x nx,
+ *                      p = nt(ny(nx-1)+(ny-1)nx) + (nt-1)nx ny */
+typedef struct sgks_reg {
+    int32_t kind;
+    int32_t nx, ny, nt;
+} sgks_reg;
+
+/* Options.  Zero-initialised fields take the defaults in brackets. */
+typedef struct sgks_options {
+    int32_t max_iters;    /* maximum number of appended columns; sizes W: d_max = ell + max_iters [100] */
+    int32_t ell;          /* dimension of the initial Krylov basis W_0 [3]                          */
+    int32_t n_refine;     /* refinement steps of the projected solve per iteration [0]              */
+    int32_t precision;    /* SGKS_PREC_FP64 or SGKS_PREC_FP32 (FP32 operators, sketch, W; FP64
+                             sketched QR, projected solve, refinement reductions) [FP64]            */
+    int32_t sketch_kind;  /* SGKS_SKETCH_SPARSE_SIGN or SGKS_SKETCH_GAUSSIAN [sparse-sign]          */
+    int32_t zeta;         /* nonzeros per sketch column, 1..16, <= sketch_rows [8]                  */
+    int32_t cgs_passes;   /* 1 = the single projection printed under eq. updqr, 2 = CGS2 [2]       */
+    int32_t reserved;
+    const double* gauss_SA; /* Gaussian sketch only: S_A, sketch_rows x m, row-major, FP64, device */
+    const double* gauss_SL; /* Gaussian sketch only: S_L, sketch_rows x p, row-major, FP64, device */
+    const void* x_true;     /* optional, n values of the solver precision: enables RRE records    */
+} sgks_options;
+
+/* Per-solve report (host memory).  rc / rre may be NULL; otherwise they receive one value per
+ * iteration performed (index k-1 for iteration k): RC_k = ||x_k - x_{k-1}|| / ||x_{k-1}||
+ * (eq. RC) and RRE_k = ||x_k - x_true|| / ||x_true|| (Sec. 4, needs opt.x_true). */
+typedef struct sgks_report {
+    int32_t iters_done;   /* iterations performed by this call                          */
+    int32_t status;       /* SGKS_OK, SGKS_STOPPED, SGKS_BREAKDOWN or an error code     */
+    int32_t subspace_dim; /* current d = ell + appended columns                         */
+    int32_t reserved;
+    double rc_last;
+    double rre_last;      /* NaN if x_true was not given                                */
+    double rre0;          /* RRE of x_0 (initial subspace)                              */
+    double* rc;           /* host array of >= iters entries, or NULL                    */
+    double* rre;          /* host array of >= iters entries, or NULL                    */
+} sgks_report;
+
+typedef struct sgks_handle sgks_handle;
+
+/* Create a solver and run the setup (Algorithm 2 inputs, Sec. 4: W_0 = orthonormal basis of
+ * K_l(A^T A, A^T b); S_A b; sketched QR of W_0; y_0; x_0).
+ *  A, L:        descriptors as above (arrays: device, caller-owned, must outlive the handle).
+ *  b:           m values of the solver precision (device).
+ *  lambda:      regularization parameter, > 0 (eq. tik).
+ *  sketch_rows: s = s_A = s_L, ell + max_iters <= s <= 2048 (Sec. 4: a small multiple of the
+ *               maximum subspace dimension).
+ *  seed:        seed of the sparse-sign sketches (S_A: stream 0, S_L: stream 1).
+ *  opt:         options (host pointer, may be NULL for defaults).
+ *  stream:      cudaStream_t (as void*) on which all work of the handle runs.
+ * On success *h receives the handle (owned by the caller; release with sgks_destroy).
+ * Errors: SGKS_ERR_INVALID (sizes, kinds, lambda <= 0, s out of range, zeta out of range,
+ * CSR row_ptr not starting at 0 / not ending at nnz), SGKS_ERR_NOMEM, SGKS_ERR_CUDA. */
+int sgks_create(sgks_handle** h, const sgks_op* A, const sgks_reg* L, const void* b,
+                double lambda, int32_t sketch_rows, uint64_t seed, const sgks_options* opt,
+                void* stream);
+
+/* Re-run the setup for a new right-hand side b_new (device, m values of the solver precision;
+ * may equal the previous pointer).  Operator preprocessing (transpose, conversions) and the
+ * workspace are reused; the basis is discarded.  Asynchronous on the handle's stream. */
+int sgks_reset(sgks_handle* h, const void* b_new);
+
+/* One sGKS iteration (Algorithm 2, one pass of the loop): r_k from x_{k-1} (eq. gradient),
+ * W_k = [W_{k-1}, r_k], sketch S_A A r_k and S_L L r_k, rank-one QR appends (eq. updqr) and
+ * the d_A entry (eq. dA_update), y_k (eq. projected_sketched_bis), n_refine refinement steps,
+ * x_k = W_k y_k, RC_k.  Asynchronous; returns SGKS_ERR_STATE if the basis is full.  Device
+ * status (breakdown, non-finite values) is read by sgks_status. */
+int sgks_step(sgks_handle* h);
+
+/* Run `iters` iterations (replaying a captured CUDA graph of sgks_step), optionally stopping
+ * when RC_k < tol (tol > 0; eq. RC), then copy x_k to x_out (device, n values of the solver
+ * precision; NULL = do not copy) and fill *rep (host, may be NULL).  Synchronises the stream. */
+int sgks_solve(sgks_handle* h, int32_t iters, double tol, void* x_out, sgks_report* rep);
+
+/* Synchronise and read the device status word into *code (SGKS_OK, SGKS_BREAKDOWN,
+ * SGKS_STOPPED, SGKS_ERR_NONFINITE or SGKS_ERR_SKETCH).  Returns SGKS_OK or an error. */
+int sgks_status(sgks_handle* h, int32_t* code);
+
+/* Human-readable description of the last error of h (or of the last failed sgks_create when h
+ * is NULL).  The string is owned by the library and valid until the next call on h. */
+const char* sgks_last_error(const sgks_handle* h);
+
+/* Release handle-owned device memory and the captured graph.  NULL-safe.  Synchronises. */
+void sgks_destroy(sgks_handle* h);
+
+/* ---- inspection and building blocks (used by the parity tests) ------------------------- */
+
+enum {
+    SGKS_BUF_X = 1,     /* x_k (n, solver precision)                                         */
+    SGKS_BUF_Y = 2,     /* y_k (d, FP64)                                                     */
+    SGKS_BUF_W = 3,     /* W column-major (d columns of n values, solver precision)          */
+    SGKS_BUF_QA = 4,    /* Q_A column-major (d columns of s, FP64)                           */
+    SGKS_BUF_RA = 5,    /* R_A column-major, leading dimension d_max (FP64)                  */
+    SGKS_BUF_QL = 6,
+    SGKS_BUF_RL = 7,
+    SGKS_BUF_DA = 8,    /* d_A (d, FP64)                                                     */
+    SGKS_BUF_SB = 9,    /* S_A b (s, FP64)                                                   */
+    SGKS_BUF_T = 10,    /* stacked triangular factor T, column-major, leading dim d_max      */
+    SGKS_BUF_AW = 11    /* A W column-major (d columns of m values, solver precision)        */
+};
+
+/* Copy an internal buffer to dst (device) after synchronising; `bytes` is the capacity of
+ * dst.  Writes the number of bytes copied to *copied.  Returns SGKS_ERR_INVALID if the buffer
+ * id is unknown or dst is too small. */
+int sgks_get_buffer(sgks_handle* h, int32_t which, void* dst, size_t bytes, size_t* copied);
+
+/* Scalar state: out[0] = d (subspace dimension), out[1] = iterations done since the setup,
+ * out[2] = device status code.  Host pointer, 3 entries.  Synchronises. */
+int sgks_get_info(sgks_handle* h, int64_t* out);
+
+enum { SGKS_APPLY_A = 1, SGKS_APPLY_AT = 2, SGKS_APPLY_L = 3, SGKS_APPLY_LT = 4,
+       SGKS_APPLY_LTL = 5, SGKS_APPLY_SA = 6, SGKS_APPLY_SL = 7 };
+
+/* Apply one operator of the handle: A (n -> m), A^T (m -> n), L (n -> p), L^T (p -> n),
+ * L^T L (n -> n, the fused stencil used inside the gradient) in the solver precision, or a
+ * sketch S_A (m -> s) / S_L (p -> s) with FP64 output.  in/out are device arrays of the sizes
+ * stated; asynchronous on the handle's stream. */
+int sgks_apply(sgks_handle* h, int32_t which, const void* in, void* out);
+
+/* Sparse-sign sketch positions (paper Sec. 2.2 allows any oblivious embedding; this one is
+ * defined here): for column j < h_cols, draws c = 0, 1, ... hash
+ * hv = mix64(mix64(2*seed + stream) ^ (j*256 + c)) with mix64 the SplitMix64 finalizer,
+ * row = ((hv >> 32) * s) >> 32, negative sign iff hv is odd; a repeated row is rejected.
+ * Writes rows_out[j*zeta + k] (int32, device) and neg_out[j*zeta + k] (uint8 0/1, device) for
+ * the k-th accepted draw.  Returns SGKS_ERR_SKETCH if some column needs more than 256 draws.
+ * Synchronises `stream`. */
+int sgks_sparse_sign_rows(uint64_t seed, int32_t stream_id, int64_t h_cols, int32_t s,
+                          int32_t zeta, int32_t* rows_out, uint8_t* neg_out, void* stream);
+
+/* Build the transpose of a CSR matrix on the device: the column-major storage of A, with
+ * row indices ascending within each column (deterministic).  Inputs row_ptr[m+1], col[nnz],
+ * val[nnz] (val_dtype); outputs t_row_ptr[n+1], t_col[nnz], t_val[nnz] (same dtype), all
+ * device, caller-allocated.  Temporary device memory is allocated and freed inside.
+ * Synchronises `stream`. */
+int sgks_csr_transpose(int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr,
+                       const int32_t* col, const void* val, int32_t val_dtype,
+                       int32_t* t_row_ptr, int32_t* t_col, void* t_val, void* stream);
+
+/* Number of kernel launches the library has enqueued in this process so far (host-side count;
+ * one replay of the captured step graph counts its kernel nodes). */
+int64_t sgks_kernel_launches(void);
+
+/* Per-kernel timing: run `iters` iterations (as sgks_step, without the graph) with a CUDA event
+ * pair on the handle's stream around every kernel launch; each launch is synchronised, so the
+ * call is for measurement only.  Host arrays of SGKS_PROFILE_CLASSES entries receive per kernel
+ * class the total milliseconds, the number of launches and the sum over launches of the
+ * subspace size d at launch (for per-launch byte models).  Classes:
+ *   0 gradient -> new basis column   1 operator apply + sketch   2 QR append + projected solve
+ *   3 combine inside refinement      4 gradient + W^T r          5 refinement solve
+ *   6 combine at the end of the iteration (x_k, e_k, RC, RRE) */
+#define SGKS_PROFILE_CLASSES 7
+int sgks_profile_steps(sgks_handle* h, int32_t iters, double* ms_out, int64_t* count_out, double* dsum_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGKS_H */

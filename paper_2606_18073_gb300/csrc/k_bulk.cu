@@ -1,0 +1,276 @@
+// Bandwidth-bound kernels of one sGKS iteration.
+//
+// k_gradient (K6, and K7's reduction when refining): r = A^T e + lam L^T L x with e = A x - b,
+//   the gradient of eq. (gradient) evaluated at x = W y.  L^T L is one fused stencil.  Without
+//   refinement r becomes the new basis column W[:, d] (Algorithm 2: W_{k+1} = [W_k, r_{k+1}],
+//   no normalisation, no reorthogonalisation).  With refinement r stays on chip and the CTA
+//   accumulates g = W^T r over its row tiles (FP64 across rows), reduced over a cluster of 8
+//   CTAs through distributed shared memory.
+//   Tiles of 256 rows: warp w computes rows [32w, 32w+32) of the tile (one row per lane for
+//   the stencil / convolution, one warp per row for CSR with the 32 rows done in turn).
+// k_combine (K4 + K5): x = W y (n rows) and e = (A W) y - b (m rows) in one launch; the stored
+//   A W columns replace a second pass over A (A (W y) = (A W) y).  In the final call of an
+//   iteration the kernel also forms ||x_k - x_{k-1}||^2, ||x_{k-1}||^2 (eq. RC) and
+//   ||x_k - x_true||^2 (RRE, Sec. 4) and the last CTA to finish reduces the CTA partials in
+//   a fixed order and records RC_k / RRE_k (no atomics on floating-point data).
+#include <math.h>
+
+#include "sgks_internal.cuh"
+
+namespace sgks {
+
+constexpr int kGradCluster = 8;
+
+template <typename T, typename V, bool WARPA>
+__device__ __forceinline__ T grad_value(const DevA<T, V>& A, const DevL& L, const T* psf_s, const T* e, const T* x,
+                                        double lam, int64_t base, int64_t n) {
+    const int lane = lane_id();
+    const int64_t i = base + lane;
+    T adj = T(0);
+    if (WARPA) {
+        for (int r = 0; r < 32; ++r) {
+            const int64_t ii = base + r;
+            if (ii >= n) break;
+            const T v = at_row_warp(A, ii, e);
+            if (lane == r) adj = v;
+        }
+    } else if (i < n) {
+        adj = at_row_conv(A, psf_s, i, e);
+    }
+    if (i >= n) return T(0);
+    return adj + (T)lam * ltl_row<T>(L, i, x);
+}
+
+// Append variant: W[:, d] = r.
+template <typename T, typename V, bool WARPA>
+__global__ void __launch_bounds__(kThreads) k_gradient_append(Dims D, DevA<T, V> A, DevL L, Bulk<T> B, Small S) {
+    __shared__ T psf_s[128];
+    DevScalars* sc = S.sc;
+    if (sc->stop) return;
+    const int d = sc->d;
+    if (d >= D.dmax) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) { sc->status = ST_FULL; sc->stop = 1; }
+        return;
+    }
+    if (!WARPA)
+        for (int i = threadIdx.x; i < A.kh * A.kw; i += kThreads) psf_s[i] = A.psf[i];
+    __syncthreads();
+    T* out = B.W + (size_t)d * D.n;
+    const int64_t ntiles = (D.n + kThreads - 1) / kThreads;
+    for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+        const int64_t base = tl * kThreads + warp_id() * 32;
+        const T r = grad_value<T, V, WARPA>(A, L, psf_s, B.e, B.x, D.lam, base, D.n);
+        const int64_t i = base + lane_id();
+        if (i < D.n) out[i] = r;
+    }
+}
+
+// Refinement variant: gpart[cluster][j] = sum over the cluster's rows of W[j][i] * r_i.
+template <typename T, typename V, bool WARPA>
+__global__ void __cluster_dims__(kGradCluster, 1, 1) __launch_bounds__(kThreads)
+    k_gradient_refine(Dims D, DevA<T, V> A, DevL L, Bulk<T> B, Small S) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* gacc = reinterpret_cast<double*>(smem_raw);       // [dmax]
+    T* rt = reinterpret_cast<T*>(gacc + D.dmax);             // [kThreads]
+    T* psf_s = rt + kThreads;                                  // [kh*kw]
+    cg::cluster_group cl = cg::this_cluster();
+    const DevScalars* sc = S.sc;
+    if (sc->stop) return;
+    const int d = sc->d;
+    const int lane = lane_id(), warp = warp_id();
+    for (int j = threadIdx.x; j < d; j += kThreads) gacc[j] = 0.0;
+    if (!WARPA)
+        for (int i = threadIdx.x; i < A.kh * A.kw; i += kThreads) psf_s[i] = A.psf[i];
+    __syncthreads();
+    const int64_t ntiles = (D.n + kThreads - 1) / kThreads;
+    for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+        const int64_t t0 = tl * kThreads;
+        const int64_t base = t0 + warp * 32;
+        rt[warp * 32 + lane] = grad_value<T, V, WARPA>(A, L, psf_s, B.e, B.x, D.lam, base, D.n);
+        __syncthreads();
+        const int64_t rows = (D.n - t0) < kThreads ? (D.n - t0) : kThreads;
+        for (int j = warp; j < d; j += kWarps) {      // column j is owned by warp j % 8
+            const T* wc = B.W + (size_t)j * D.n + t0;
+            T a = T(0);
+#pragma unroll
+            for (int k = 0; k < kThreads / 32; ++k) {
+                const int rr = lane + 32 * k;
+                if (rr < rows) a += wc[rr] * rt[rr];
+            }
+            const double s = warp_sum((double)a);
+            if (lane == 0) gacc[j] += s;
+        }
+        __syncthreads();
+    }
+    cl.sync();
+    if (cl.block_rank() == 0) {
+        double* out = S.gpart + (size_t)(blockIdx.x / kGradCluster) * D.dmax;
+        for (int j = threadIdx.x; j < d; j += kThreads) {
+            double v = gacc[j];
+            for (int r = 1; r < kGradCluster; ++r) v += cl.map_shared_rank(gacc, r)[j];
+            out[j] = v;
+        }
+    }
+    cl.sync();
+}
+
+template <typename T, typename V>
+cudaError_t launch_gradient(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B, const Small& S,
+                            bool refine, cudaStream_t st) {
+    const bool warpa = A.kind != SGKS_OP_CONV2D;
+    if (!refine) {
+        const int64_t tiles = (D.n + kThreads - 1) / kThreads;
+        const int blocks = (int)(tiles < 8 * 152 ? tiles : 8 * 152);
+        if (warpa)
+            k_gradient_append<T, V, true><<<blocks, kThreads, 0, st>>>(D, A, L, B, S);
+        else
+            k_gradient_append<T, V, false><<<blocks, kThreads, 0, st>>>(D, A, L, B, S);
+        return cudaGetLastError();
+    }
+    const size_t smem = (size_t)D.dmax * sizeof(double) + kThreads * sizeof(T) + 128 * sizeof(T);
+    if (warpa) {
+        auto k = k_gradient_refine<T, V, true>;
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<D.nbG, kThreads, smem, st>>>(D, A, L, B, S);
+    } else {
+        auto k = k_gradient_refine<T, V, false>;
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<D.nbG, kThreads, smem, st>>>(D, A, L, B, S);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ combine
+// mode 0: refinement (x, e only); 1: end of an iteration (x, e, RC / RRE record);
+// 2: end of the setup (x, e, RRE_0).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_combine(Dims D, Bulk<T> B, Small S, int mode) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* ys = reinterpret_cast<T*>(smem_raw);                       // [dmax]
+    __shared__ double red[3][kWarps];
+    __shared__ int am_last;
+    DevScalars* sc = S.sc;
+    if (sc->stop) return;
+    const int d = sc->d;
+    for (int j = threadIdx.x; j < d; j += kThreads) ys[j] = (T)S.y[j];
+    __syncthreads();
+    double q0 = 0.0, q1 = 0.0, q2 = 0.0;
+    const int tid = threadIdx.x;
+    if ((int)blockIdx.x < D.nbX) {
+        const int64_t i = (int64_t)blockIdx.x * kThreads + tid;
+        if (i < D.n) {
+            const T* w = B.W + i;
+            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+            int j = 0;
+            for (; j + 3 < d; j += 4) {
+                a0 += w[(size_t)j * D.n] * ys[j];
+                a1 += w[(size_t)(j + 1) * D.n] * ys[j + 1];
+                a2 += w[(size_t)(j + 2) * D.n] * ys[j + 2];
+                a3 += w[(size_t)(j + 3) * D.n] * ys[j + 3];
+            }
+            for (; j < d; ++j) a0 += w[(size_t)j * D.n] * ys[j];
+            const T xv = (a0 + a1) + (a2 + a3);
+            B.x[i] = xv;
+            if (mode >= 1) {
+                const T old = B.xs[i];
+                const double df = (double)xv - (double)old;
+                q0 = df * df;
+                q1 = (double)old * (double)old;
+                if (B.xtrue) {
+                    const double er = (double)xv - (double)B.xtrue[i];
+                    q2 = er * er;
+                }
+                B.xs[i] = xv;
+            }
+        }
+    } else {
+        const int64_t i = (int64_t)(blockIdx.x - D.nbX) * kThreads + tid;
+        if (i < D.m) {
+            const T* w = B.AW + i;
+            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+            int j = 0;
+            for (; j + 3 < d; j += 4) {
+                a0 += w[(size_t)j * D.m] * ys[j];
+                a1 += w[(size_t)(j + 1) * D.m] * ys[j + 1];
+                a2 += w[(size_t)(j + 2) * D.m] * ys[j + 2];
+                a3 += w[(size_t)(j + 3) * D.m] * ys[j + 3];
+            }
+            for (; j < d; ++j) a0 += w[(size_t)j * D.m] * ys[j];
+            B.e[i] = ((a0 + a1) + (a2 + a3)) - B.b[i];
+        }
+    }
+    if (mode == 0) return;
+    // block partials of the three squared norms
+    q0 = warp_sum(q0);
+    q1 = warp_sum(q1);
+    q2 = warp_sum(q2);
+    if (lane_id() == 0) { red[0][warp_id()] = q0; red[1][warp_id()] = q1; red[2][warp_id()] = q2; }
+    __syncthreads();
+    if (tid < 3) {
+        double t = 0.0;
+        for (int w = 0; w < kWarps; ++w) t += red[tid][w];
+        S.kapart[(size_t)blockIdx.x * 3 + tid] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) am_last = (atomicAdd(&sc->ka_done, 1) == (int)gridDim.x - 1);
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    // last CTA: fixed-order reduction of the partials (warp q sums quantity q)
+    if (warp_id() < 3) {
+        const int q = warp_id();
+        double t = 0.0;
+        for (int b = lane_id(); b < (int)gridDim.x; b += 32) t += __ldcg(S.kapart + (size_t)b * 3 + q);
+        t = warp_sum(t);
+        if (lane_id() == 0) red[q][0] = t;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const double dx2 = red[0][0], xo2 = red[1][0], er2 = red[2][0];
+        const double rre = B.xtrue ? sqrt(er2 / sc->xt2) : (double)NAN;
+        if (mode == 2) {
+            sc->rre0 = rre;
+            sc->rre_last = rre;
+        } else {
+            const double rc = sqrt(dx2 / xo2);
+            const int k = sc->iter;
+            if (k < D.max_iters) {
+                S.rc_hist[k] = rc;
+                S.rre_hist[k] = rre;
+            }
+            sc->rc_last = rc;
+            sc->rre_last = rre;
+            sc->iter = k + 1;
+            if (sc->tol_on && rc < sc->tol) {
+                sc->status = ST_STOPPED;
+                sc->stop = 1;
+            }
+            if (!(dx2 <= 1e300) || !(xo2 <= 1e300)) {  // NaN or Inf in the iterate
+                sc->status = ST_NONFINITE;
+                sc->stop = 1;
+            }
+        }
+        sc->ka_done = 0;
+    }
+}
+
+template <typename T>
+cudaError_t launch_combine(const Dims& D, const Bulk<T>& B, const Small& S, int mode, cudaStream_t st) {
+    const size_t smem = (size_t)D.dmax * sizeof(T);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_combine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_combine<T><<<D.nbX + D.nbE, kThreads, smem, st>>>(D, B, S, mode);
+    return cudaGetLastError();
+}
+
+#define SGKS_INST_BULK(T, V)                                                                          \
+    template cudaError_t launch_gradient<T, V>(const Dims&, const DevA<T, V>&, const DevL&,           \
+                                               const Bulk<T>&, const Small&, bool, cudaStream_t);
+SGKS_INST_BULK(float, float)
+SGKS_INST_BULK(double, float)
+SGKS_INST_BULK(double, double)
+template cudaError_t launch_combine<float>(const Dims&, const Bulk<float>&, const Small&, int, cudaStream_t);
+template cudaError_t launch_combine<double>(const Dims&, const Bulk<double>&, const Small&, int, cudaStream_t);
+
+}  // namespace sgks

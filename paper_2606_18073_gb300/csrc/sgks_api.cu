@@ -1,0 +1,786 @@
+// C ABI of the sGKS library: handle life cycle, setup and step sequencing, CUDA-graph replay.
+//
+// One sGKS iteration (Algorithm 2, one pass of the loop) is the launch sequence
+//   k_gradient_append   r_k = A^T (A x_{k-1} - b) + lam L^T L x_{k-1} -> W[:, d]     (eq. gradient)
+//   k_sketch_column     S_A A W[:, d], S_L L W[:, d] (sparse-sign, fused), A W[:, d] stored
+//   k_append_solve      CGS2 appends to (Q_A, R_A), (Q_L, R_L), d_A entry, stacked QR, y_k
+//   n_refine x { k_combine(x, e) ; k_gradient_refine(g = W^T r) ; k_refine_solve(y += dy) }
+//   k_combine           x_k = W y_k, e_k = A W y_k - b, RC_k and RRE_k
+// Every kernel reads the subspace size d from device memory, so the sequence is captured once
+// as a CUDA graph and replayed for every iteration without host synchronisation.
+// All work runs on an internal non-blocking stream that is joined to the caller's stream with
+// events at the start and end of every call.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+
+#include <atomic>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sgks_internal.cuh"
+
+using namespace sgks;
+
+namespace {
+
+thread_local std::string g_create_error;
+std::atomic<int64_t> g_launches{0};
+
+// Kernel classes of the per-kernel profile (sgks_profile_steps).
+enum { PK_GRAD_APPEND = 0, PK_SKETCH = 1, PK_APPEND_SOLVE = 2, PK_COMBINE_REFINE = 3, PK_GRAD_REFINE = 4,
+       PK_REFINE_SOLVE = 5, PK_COMBINE = 6, PK_COUNT = 7 };
+
+struct Profiler {
+    cudaEvent_t ev[2];
+    double ms[PK_COUNT] = {0};
+    int64_t count[PK_COUNT] = {0};
+    double bytes_d[PK_COUNT] = {0};   // sum over launches of the subspace size d (for byte models)
+};
+
+struct EngineBase {
+    Profiler* prof = nullptr;
+    cudaStream_t pst = nullptr;
+    int host_d = 0;      // subspace size as the host sequences it (for the profile byte models)
+    template <typename F>
+    cudaError_t timed(int cls, int dcount, F&& f) {
+        g_launches.fetch_add(cls == PK_SKETCH && gauss ? 2 : 1);
+        if (!prof) return f();
+        cudaEventRecord(prof->ev[0], pst);
+        cudaError_t e = f();
+        cudaEventRecord(prof->ev[1], pst);
+        cudaEventSynchronize(prof->ev[1]);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, prof->ev[0], prof->ev[1]);
+        prof->ms[cls] += t;
+        prof->count[cls] += 1;
+        prof->bytes_d[cls] += dcount;
+        return e;
+    }
+    bool gauss = false;
+    virtual ~EngineBase() {}
+    virtual cudaError_t setup(const void* b) = 0;
+    virtual cudaError_t step() = 0;
+    virtual cudaError_t apply(int which, const void* in, void* out) = 0;
+    virtual void* buffer(int which, size_t* elem, int64_t* rows, int64_t* cols_ld) = 0;
+    Dims D{};
+    Small S{};
+    int n_refine = 0;
+    int elem = 8;
+};
+
+template <typename T, typename V>
+struct Engine : EngineBase {
+    DevA<T, V> A{};
+    DevL L{};
+    Bulk<T> B{};
+    cudaStream_t st = nullptr;
+    const double* gSA = nullptr;
+    const double* gSL = nullptr;
+    double* part_setup = nullptr;   // [nbS][8]
+    int nbS = 1, nbSb = 8, npSb = 1;
+    int* d_err = nullptr;
+
+    cudaError_t setup(const void* bptr) override {
+        B.b = (const T*)bptr;
+        host_d = 0;
+        // kernels launched below without the `timed` wrapper are counted here
+        g_launches.fetch_add(2 + (B.xtrue ? 2 : 0) + 3 + (D.ell - 1) * 8);
+        cudaError_t e = cudaMemsetAsync(S.sc, 0, sizeof(DevScalars), st);
+        if (e != cudaSuccess) return e;
+        // S_A b (FP64)
+        e = launch_sketch_vector<T>(D, B.b, D.m, D.keyA, gSA, S.partA, nbSb, d_err, st);
+        if (e != cudaSuccess) return e;
+        e = launch_reduce_rows(S.partA, gSA ? 1 : npSb, D.s, D.sketch_scale, S.Sb, st);
+        if (e != cudaSuccess) return e;
+        if (B.xtrue) {
+            e = launch_sqnorm<T>(B.xtrue, D.n, part_setup, nbS, st);
+            if (e == cudaSuccess) e = launch_reduce_rows(part_setup, nbS, 1, 1.0, &S.sc->xt2, st);
+            if (e != cudaSuccess) return e;
+        }
+        // W_0: orthonormal basis of K_l(A^T A, A^T b) (Sec. 2.1, Sec. 4), CGS2 on n-vectors
+        T* W = B.W;
+        e = launch_apply<T, V>(D, A, L, SGKS_APPLY_AT, B.b, W, st);
+        if (e == cudaSuccess) e = launch_sqnorm<T>(W, D.n, part_setup, nbS, st);
+        if (e == cudaSuccess) e = launch_normalize<T>(W, D.n, part_setup, nbS, st);
+        for (int j = 1; j < D.ell && e == cudaSuccess; ++j) {
+            T* wj = W + (size_t)j * D.n;
+            e = launch_apply<T, V>(D, A, L, SGKS_APPLY_A, W + (size_t)(j - 1) * D.n, B.tmp_m, st);
+            if (e == cudaSuccess) e = launch_apply<T, V>(D, A, L, SGKS_APPLY_AT, B.tmp_m, wj, st);
+            for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+                e = launch_dots<T>(W, D.n, j, wj, part_setup, nbS, st);
+                if (e == cudaSuccess) e = launch_orth_update<T>(wj, W, D.n, j, part_setup, nbS, st);
+            }
+            if (e == cudaSuccess) e = launch_sqnorm<T>(wj, D.n, part_setup, nbS, st);
+            if (e == cudaSuccess) e = launch_normalize<T>(wj, D.n, part_setup, nbS, st);
+        }
+        if (e != cudaSuccess) return e;
+        // sketched QR of W_0, y_0, refinement, x_0
+        for (int j = 0; j < D.ell && e == cudaSuccess; ++j) {
+            e = timed(PK_SKETCH, j, [&] { return sketch(); });
+            if (e == cudaSuccess) e = timed(PK_APPEND_SOLVE, j, [&] { return launch_append_solve(D, S, st); });
+        }
+        host_d = D.ell;
+        for (int r = 0; r < n_refine && e == cudaSuccess; ++r) e = refine();
+        if (e == cudaSuccess) e = timed(PK_COMBINE, host_d, [&] { return launch_combine<T>(D, B, S, 2, st); });
+        return e;
+    }
+
+    cudaError_t sketch() {
+        if (gSA) return launch_gaussian_sketch<T, V>(D, A, L, B, S, gSA, gSL, st);
+        return launch_sketch_column<T, V>(D, A, L, B, S, st);
+    }
+
+    cudaError_t refine() {
+        const int d = host_d;
+        cudaError_t e = timed(PK_COMBINE_REFINE, d, [&] { return launch_combine<T>(D, B, S, 0, st); });
+        if (e == cudaSuccess) e = timed(PK_GRAD_REFINE, d, [&] { return launch_gradient<T, V>(D, A, L, B, S, true, st); });
+        if (e == cudaSuccess) e = timed(PK_REFINE_SOLVE, d, [&] { return launch_refine_solve(D, S, st); });
+        return e;
+    }
+
+    cudaError_t step() override {
+        const int d = host_d;
+        cudaError_t e = timed(PK_GRAD_APPEND, d, [&] { return launch_gradient<T, V>(D, A, L, B, S, false, st); });
+        if (e == cudaSuccess) e = timed(PK_SKETCH, d, [&] { return sketch(); });
+        if (e == cudaSuccess) e = timed(PK_APPEND_SOLVE, d, [&] { return launch_append_solve(D, S, st); });
+        host_d = d + 1;
+        for (int r = 0; r < n_refine && e == cudaSuccess; ++r) e = refine();
+        if (e == cudaSuccess) e = timed(PK_COMBINE, host_d, [&] { return launch_combine<T>(D, B, S, 1, st); });
+        return e;
+    }
+
+    cudaError_t apply(int which, const void* in, void* out) override {
+        if (which == SGKS_APPLY_SA || which == SGKS_APPLY_SL) {
+            const bool isA = which == SGKS_APPLY_SA;
+            const double* SG = isA ? gSA : gSL;
+            const int64_t len = isA ? D.m : D.p;
+            const int nb = sketch_blocks(len);
+            cudaError_t e = launch_sketch_vector<T>(D, (const T*)in, len, isA ? D.keyA : D.keyL, SG,
+                                                    isA ? S.partA : S.partL, nb, d_err, st);
+            if (e != cudaSuccess) return e;
+            return launch_reduce_rows(isA ? S.partA : S.partL, SG ? 1 : nb / 8, D.s, D.sketch_scale, (double*)out, st);
+        }
+        return launch_apply<T, V>(D, A, L, which, (const T*)in, (T*)out, st);
+    }
+
+    static int sketch_blocks(int64_t rows) {
+        const int64_t slabs = (rows + 31) / 32;
+        int64_t nb = (slabs + kWarps - 1) / kWarps;
+        if (nb > 4 * 152) nb = 4 * 152;
+        nb = (nb + 7) / 8 * 8;
+        return (int)(nb < 8 ? 8 : nb);
+    }
+
+    void* buffer(int which, size_t* elem_out, int64_t* rows, int64_t* ld) override {
+        *ld = 0;
+        switch (which) {
+            case SGKS_BUF_X: *elem_out = sizeof(T); *rows = D.n; return B.xs;
+            case SGKS_BUF_W: *elem_out = sizeof(T); *rows = D.n; return B.W;
+            case SGKS_BUF_AW: *elem_out = sizeof(T); *rows = D.m; return B.AW;
+            case SGKS_BUF_Y: *elem_out = 8; *rows = 1; return S.y;
+            case SGKS_BUF_QA: *elem_out = 8; *rows = D.s; return S.QA;
+            case SGKS_BUF_QL: *elem_out = 8; *rows = D.s; return S.QL;
+            case SGKS_BUF_RA: *elem_out = 8; *rows = D.dmax; return S.RA;
+            case SGKS_BUF_RL: *elem_out = 8; *rows = D.dmax; return S.RL;
+            case SGKS_BUF_T: *elem_out = 8; *rows = D.dmax; return S.Tm;
+            case SGKS_BUF_DA: *elem_out = 8; *rows = 1; return S.dA;
+            case SGKS_BUF_SB: *elem_out = 8; *rows = D.s; *ld = -1; return S.Sb;
+            default: return nullptr;
+        }
+    }
+};
+
+}  // namespace
+
+struct sgks_handle {
+    EngineBase* eng = nullptr;
+    cudaStream_t st = nullptr;
+    cudaStream_t user = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::vector<void*> allocs;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::string err;
+    DevScalars* sc_host = nullptr;   // pinned
+    int max_iters = 0;
+    int steps_since_setup = 0;
+    int prec = 0;
+    int64_t graph_launches = 0;   // kernel launches per replay of the step graph
+};
+
+static int fail(sgks_handle* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+static int cuda_fail(sgks_handle* h, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(h, SGKS_ERR_CUDA, m);
+}
+
+static void join_in(sgks_handle* h) {
+    cudaEventRecord(h->ev_in, h->user);
+    cudaStreamWaitEvent(h->st, h->ev_in, 0);
+}
+static void join_out(sgks_handle* h) {
+    cudaEventRecord(h->ev_out, h->st);
+    cudaStreamWaitEvent(h->user, h->ev_out, 0);
+}
+
+template <typename P>
+static cudaError_t dalloc(sgks_handle* h, P** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(P) + 16);
+    if (e != cudaSuccess) return e;
+    h->allocs.push_back(q);
+    *p = (P*)q;
+    return cudaSuccess;
+}
+
+template <typename T, typename V>
+static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, const void* b, double lambda,
+                        int s, uint64_t seed, const sgks_options& o, int cluster) {
+    Engine<T, V>* E = new (std::nothrow) Engine<T, V>();
+    if (!E) return fail(h, SGKS_ERR_NOMEM, "host allocation failed");
+    h->eng = E;
+    E->st = h->st;
+    E->pst = h->st;
+    E->gauss = o.sketch_kind == SGKS_SKETCH_GAUSSIAN;
+    E->elem = sizeof(T);
+    E->n_refine = o.n_refine;
+    Dims& D = E->D;
+    D.n = op->n;
+    D.m = op->m;
+    D.s = s;
+    D.zeta = o.zeta;
+    D.ell = o.ell;
+    D.dmax = o.ell + o.max_iters;
+    D.max_iters = o.max_iters;
+    D.lam = lambda;
+    D.cgs_passes = o.cgs_passes;
+    D.sketch_kind = o.sketch_kind;
+    D.sketch_scale = o.sketch_kind == SGKS_SKETCH_GAUSSIAN ? 1.0 : 1.0 / sqrt((double)o.zeta);
+    D.keyA = sketch_key_host_dev(seed, 0);
+    D.keyL = sketch_key_host_dev(seed, 1);
+    D.cluster = cluster;
+    D.has_xtrue = o.x_true != nullptr;
+
+    DevL& L = E->L;
+    L.kind = reg->kind;
+    L.nx = reg->nx;
+    L.ny = reg->kind == SGKS_REG_FD1 ? 1 : reg->ny;
+    L.nt = reg->kind == SGKS_REG_SPACETIME ? reg->nt : 1;
+    L.n = (int64_t)L.nx * L.ny * L.nt;
+    const int64_t nx = L.nx, ny = L.ny, nt = L.nt;
+    switch (L.kind) {
+        case SGKS_REG_FD1: L.p = nx - 1; break;
+        case SGKS_REG_GRAD2D: L.p = ny * (nx - 1) + (ny - 1) * nx; break;
+        case SGKS_REG_LAPLACE2D: L.p = nx * ny; break;
+        default: L.p = nt * (ny * (nx - 1) + (ny - 1) * nx) + (nt - 1) * nx * ny; break;
+    }
+    D.p = L.p;
+
+    const int64_t sl_m = (D.m + 31) / 32, sl_p = (D.p + 31) / 32;
+    auto nb8 = [](int64_t slabs) {
+        int64_t nb = (slabs + kWarps - 1) / kWarps;
+        if (nb > 4 * 152) nb = 4 * 152;
+        nb = (nb + 7) / 8 * 8;
+        return (int)(nb < 8 ? 8 : nb);
+    };
+    D.nbA = nb8(sl_m);
+    D.nbL = nb8(sl_p);
+    const bool gauss = o.sketch_kind == SGKS_SKETCH_GAUSSIAN;
+    D.npA = gauss ? 1 : D.nbA / 8;
+    D.npL = gauss ? 1 : D.nbL / 8;
+    const int64_t tiles = (D.n + kThreads - 1) / kThreads;
+    int64_t nbG = (tiles + 7) / 8 * 8;
+    if (nbG > 304) nbG = 304;
+    D.nbG = (int)nbG;
+    D.nbX = (int)tiles;
+    D.nbE = (int)((D.m + kThreads - 1) / kThreads);
+    E->nbS = (int)(tiles < 304 ? tiles : 304);
+    E->nbSb = Engine<T, V>::sketch_blocks(D.m);
+    E->npSb = E->nbSb / 8;
+
+    cudaError_t e = cudaSuccess;
+#define AL(ptr, cnt)                                          \
+    do {                                                      \
+        if (e == cudaSuccess) e = dalloc(h, &(ptr), (size_t)(cnt)); \
+    } while (0)
+    Bulk<T>& B = E->B;
+    Small& S = E->S;
+    const size_t dm = D.dmax;
+    T *W, *AW, *x, *xs, *ee, *tm, *tp;
+    AL(W, dm * D.n);
+    AL(AW, dm * D.m);
+    AL(x, D.n);
+    AL(xs, D.n);
+    AL(ee, D.m);
+    AL(tm, D.m);
+    AL(tp, D.p);
+    B.W = W; B.AW = AW; B.x = x; B.xs = xs; B.e = ee; B.tmp_m = tm; B.tmp_p = tp;
+    B.b = (const T*)b;
+    B.xtrue = (const T*)o.x_true;
+    AL(S.QA, dm * s);
+    AL(S.QL, dm * s);
+    AL(S.RA, dm * dm);
+    AL(S.RL, dm * dm);
+    AL(S.G, 4 * dm * dm);
+    AL(S.X, dm * dm);
+    AL(S.Tm, dm * dm);
+    AL(S.zf, 2 * dm + 2);
+    AL(S.dA, dm);
+    AL(S.y, dm);
+    AL(S.Sb, s);
+    AL(S.partA, (size_t)(D.nbA / 8 + 1) * s);
+    AL(S.partL, (size_t)(D.nbL / 8 + 1) * s);
+    AL(S.gpart, (size_t)(D.nbG / 8) * dm);
+    AL(S.kapart, (size_t)(D.nbX + D.nbE) * 3);
+    AL(S.rc_hist, (size_t)o.max_iters + 1);
+    AL(S.rre_hist, (size_t)o.max_iters + 1);
+    AL(S.sc, 1);
+    AL(E->part_setup, (size_t)E->nbS * 8);
+    AL(E->d_err, 1);
+    if (e != cudaSuccess) return fail(h, SGKS_ERR_NOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
+    e = cudaMemsetAsync(S.y, 0, sizeof(double) * dm, h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(xs, 0, sizeof(T) * D.n, h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(E->d_err, 0, sizeof(int), h->st);
+
+    // operator
+    DevA<T, V>& A = E->A;
+    A.kind = op->kind;
+    A.m = op->m;
+    A.n = op->n;
+    const int tdt = sizeof(T) == 4 ? SGKS_F32 : SGKS_F64;
+    const int vdt = sizeof(V) == 4 ? SGKS_F32 : SGKS_F64;
+    if (op->kind == SGKS_OP_CSR) {
+        // malformed CSR (indices out of range) would make the kernels read out of bounds
+        int herr = 0;
+        if (e == cudaSuccess) e = validate_csr_device(op->row_ptr, op->col, op->m, op->n, op->nnz, E->d_err, h->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, E->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        if (e == cudaSuccess && herr) return fail(h, SGKS_ERR_INVALID, "CSR arrays are malformed (row_ptr or col)");
+        if (e == cudaSuccess) e = cudaMemsetAsync(E->d_err, 0, sizeof(int), h->st);
+        if (op->t_row_ptr && op->t_col && e == cudaSuccess) {
+            e = validate_csr_device(op->t_row_ptr, op->t_col, op->n, op->m, op->nnz, E->d_err, h->st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, E->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+            if (e == cudaSuccess && herr) return fail(h, SGKS_ERR_INVALID, "transposed CSR arrays are malformed");
+            if (e == cudaSuccess) e = cudaMemsetAsync(E->d_err, 0, sizeof(int), h->st);
+        }
+        A.rp = op->row_ptr;
+        A.ci = op->col;
+        if (op->val_dtype == vdt) {
+            A.val = (const V*)op->val;
+        } else {
+            V* v;
+            AL(v, op->nnz);
+            if (e == cudaSuccess) e = convert_values(op->val, op->val_dtype, v, vdt, op->nnz, h->st);
+            A.val = v;
+        }
+        if (op->t_row_ptr && op->t_col && op->t_val) {
+            A.trp = op->t_row_ptr;
+            A.tci = op->t_col;
+            if (op->val_dtype == vdt) {
+                A.tval = (const V*)op->t_val;
+            } else {
+                V* v;
+                AL(v, op->nnz);
+                if (e == cudaSuccess) e = convert_values(op->t_val, op->val_dtype, v, vdt, op->nnz, h->st);
+                A.tval = v;
+            }
+        } else {
+            int32_t *trp, *tci;
+            V* tv;
+            AL(trp, op->n + 1);
+            AL(tci, op->nnz > 0 ? op->nnz : 1);
+            AL(tv, op->nnz > 0 ? op->nnz : 1);
+            if (e == cudaSuccess)
+                e = csr_transpose_device(op->m, op->n, op->nnz, A.rp, A.ci, A.val, vdt, trp, tci, tv, h->st);
+            A.trp = trp;
+            A.tci = tci;
+            A.tval = tv;
+        }
+    } else if (op->kind == SGKS_OP_DENSE) {
+        T* dd;
+        AL(dd, op->m * op->n);
+        if (e == cudaSuccess) {
+            if (op->ld == op->n) {
+                e = convert_values(op->dense, op->val_dtype, dd, tdt, op->m * op->n, h->st);
+            } else {
+                for (int64_t r = 0; r < op->m && e == cudaSuccess; ++r) {
+                    const size_t es = op->val_dtype == SGKS_F32 ? 4 : 8;
+                    e = convert_values((const char*)op->dense + (size_t)r * op->ld * es, op->val_dtype,
+                                       dd + (size_t)r * op->n, tdt, op->n, h->st);
+                }
+            }
+        }
+        A.dense = dd;
+        A.ld = op->n;
+    } else {
+        T* pp;
+        AL(pp, (size_t)op->kh * op->kw);
+        if (e == cudaSuccess) e = convert_values(op->psf, op->val_dtype, pp, tdt, (int64_t)op->kh * op->kw, h->st);
+        A.psf = pp;
+        A.nx = op->nx;
+        A.ny = op->ny;
+        A.kh = op->kh;
+        A.kw = op->kw;
+    }
+#undef AL
+    if (e != cudaSuccess) return cuda_fail(h, e, "operator preparation");
+    E->gSA = o.gauss_SA;
+    E->gSL = o.gauss_SL;
+    return SGKS_OK;
+}
+
+static int validate(const sgks_op* A, const sgks_reg* L, const void* b, double lambda, int s, const sgks_options& o,
+                    std::string* why) {
+    auto bad = [&](const char* m) {
+        *why = m;
+        return SGKS_ERR_INVALID;
+    };
+    if (!A || !L || !b) return bad("A, L and b must be non-NULL");
+    if (!(lambda > 0.0) || !isfinite(lambda)) return bad("lambda must be a finite positive number");
+    if (A->m <= 0 || A->n <= 0) return bad("A must have m, n > 0");
+    if (A->n > (int64_t)1 << 31 || A->m > (int64_t)1 << 31) return bad("m and n must fit int32");
+    if (A->val_dtype != SGKS_F32 && A->val_dtype != SGKS_F64) return bad("val_dtype must be SGKS_F32 or SGKS_F64");
+    if (A->kind == SGKS_OP_CSR) {
+        if (!A->row_ptr || !A->col || !A->val || A->nnz < 0) return bad("CSR arrays missing");
+        if (A->nnz >= ((int64_t)1 << 31)) return bad("nnz must fit int32");
+    } else if (A->kind == SGKS_OP_DENSE) {
+        if (!A->dense || A->ld < A->n) return bad("dense array missing or ld < n");
+    } else if (A->kind == SGKS_OP_CONV2D) {
+        if (!A->psf || A->kh <= 0 || A->kw <= 0 || (A->kh % 2) == 0 || (A->kw % 2) == 0)
+            return bad("conv2d needs an odd-sized psf");
+        if (A->kh * A->kw > 128) return bad("conv2d psf larger than 128 taps");
+        if ((int64_t)A->nx * A->ny != A->n || A->m != A->n) return bad("conv2d needs m = n = nx*ny");
+    } else {
+        return bad("unknown operator kind");
+    }
+    int64_t ln;
+    switch (L->kind) {
+        case SGKS_REG_FD1: ln = L->nx; if (L->nx < 2) return bad("fd1 needs nx >= 2"); break;
+        case SGKS_REG_GRAD2D:
+        case SGKS_REG_LAPLACE2D:
+            if (L->nx < 2 || L->ny < 2) return bad("2D stencils need nx, ny >= 2");
+            ln = (int64_t)L->nx * L->ny;
+            break;
+        case SGKS_REG_SPACETIME:
+            if (L->nx < 2 || L->ny < 2 || L->nt < 2) return bad("space-time stencil needs nx, ny, nt >= 2");
+            ln = (int64_t)L->nx * L->ny * L->nt;
+            break;
+        default: return bad("unknown regularization kind");
+    }
+    if (ln != A->n) return bad("L must act on the n unknowns of A");
+    if (o.max_iters < 1 || o.ell < 1 || o.ell > 8) return bad("need max_iters >= 1 and 1 <= ell <= 8");
+    if (o.ell > A->n) return bad("ell must not exceed n");
+    if (s > kMaxS || s < o.ell + o.max_iters) return bad("sketch_rows must satisfy ell + max_iters <= s <= 2048");
+    if (o.precision != SGKS_PREC_FP64 && o.precision != SGKS_PREC_FP32) return bad("unknown precision");
+    if (o.sketch_kind == SGKS_SKETCH_SPARSE_SIGN) {
+        if (o.zeta < 1 || o.zeta > kMaxZeta || o.zeta > s) return bad("zeta must satisfy 1 <= zeta <= min(16, s)");
+    } else if (o.sketch_kind == SGKS_SKETCH_GAUSSIAN) {
+        if (!o.gauss_SA || !o.gauss_SL) return bad("Gaussian sketch needs gauss_SA and gauss_SL");
+    } else {
+        return bad("unknown sketch kind");
+    }
+    if (o.cgs_passes != 1 && o.cgs_passes != 2) return bad("cgs_passes must be 1 or 2");
+    if (o.n_refine < 0 || o.n_refine > 64) return bad("n_refine out of range");
+    return SGKS_OK;
+}
+
+extern "C" {
+
+int sgks_create(sgks_handle** hp, const sgks_op* A, const sgks_reg* L, const void* b, double lambda,
+                int32_t sketch_rows, uint64_t seed, const sgks_options* opt, void* stream) {
+    if (!hp) return fail(nullptr, SGKS_ERR_INVALID, "h must be non-NULL");
+    *hp = nullptr;
+    sgks_options o{};
+    if (opt) o = *opt;
+    if (o.max_iters == 0) o.max_iters = 100;
+    if (o.ell == 0) o.ell = 3;
+    if (o.zeta == 0) o.zeta = 8;
+    if (o.cgs_passes == 0) o.cgs_passes = 2;
+    std::string why;
+    int rc = validate(A, L, b, lambda, sketch_rows, o, &why);
+    if (rc != SGKS_OK) return fail(nullptr, rc, why);
+
+    sgks_handle* h = new (std::nothrow) sgks_handle();
+    if (!h) return fail(nullptr, SGKS_ERR_NOMEM, "host allocation failed");
+    h->user = (cudaStream_t)stream;
+    h->max_iters = o.max_iters;
+    h->prec = o.precision;
+    cudaError_t e = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->sc_host, sizeof(DevScalars));
+    int cluster = 0;
+    if (e == cudaSuccess) {
+        const int dm = o.ell + o.max_iters;
+        e = configure_cluster_kernels(&cluster, sketch_rows, dm);
+    }
+    if (e != cudaSuccess) {
+        rc = cuda_fail(h, e, "sgks_create");
+        g_create_error = h->err;
+        sgks_destroy(h);
+        return rc;
+    }
+    join_in(h);
+    if (o.precision == SGKS_PREC_FP32)
+        rc = build_engine<float, float>(h, A, L, b, lambda, sketch_rows, seed, o, cluster);
+    else if (A->kind == SGKS_OP_CSR && A->val_dtype == SGKS_F64)
+        rc = build_engine<double, double>(h, A, L, b, lambda, sketch_rows, seed, o, cluster);
+    else
+        rc = build_engine<double, float>(h, A, L, b, lambda, sketch_rows, seed, o, cluster);
+    if (rc == SGKS_OK) {
+        e = h->eng->setup(b);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "setup");
+    }
+    if (rc == SGKS_OK) {
+        e = cudaStreamSynchronize(h->st);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "setup (synchronise)");
+    }
+    if (rc != SGKS_OK) {
+        g_create_error = h->err;
+        sgks_destroy(h);
+        return rc;
+    }
+    join_out(h);
+    *hp = h;
+    return SGKS_OK;
+}
+
+int sgks_reset(sgks_handle* h, const void* b_new) {
+    if (!h || !b_new) return fail(h, SGKS_ERR_INVALID, "handle and b_new must be non-NULL");
+    join_in(h);
+    cudaError_t e = h->eng->setup(b_new);
+    join_out(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sgks_reset");
+    h->steps_since_setup = 0;
+    return SGKS_OK;
+}
+
+int sgks_step(sgks_handle* h) {
+    if (!h) return SGKS_ERR_INVALID;
+    if (h->steps_since_setup >= h->max_iters) return fail(h, SGKS_ERR_STATE, "basis is full (max_iters reached)");
+    join_in(h);
+    cudaError_t e = h->eng->step();
+    join_out(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sgks_step");
+    h->steps_since_setup++;
+    return SGKS_OK;
+}
+
+static int map_status(int dev) {
+    switch (dev) {
+        case ST_OK: return SGKS_OK;
+        case ST_BREAKDOWN: return SGKS_BREAKDOWN;
+        case ST_STOPPED: return SGKS_STOPPED;
+        case ST_NONFINITE: return SGKS_ERR_NONFINITE;
+        case ST_SKETCH: return SGKS_ERR_SKETCH;
+        case ST_FULL: return SGKS_ERR_STATE;
+        default: return SGKS_ERR_STATE;
+    }
+}
+
+static cudaError_t ensure_graph(sgks_handle* h) {
+    if (h->gexec) return cudaSuccess;
+    cudaError_t e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    const int64_t l0 = g_launches.load();
+    const int hd = h->eng->host_d;
+    cudaError_t e2 = h->eng->step();
+    h->eng->host_d = hd;
+    h->graph_launches = g_launches.load() - l0;
+    g_launches.fetch_sub(h->graph_launches);
+    e = cudaStreamEndCapture(h->st, &h->graph);
+    if (e2 != cudaSuccess) return e2;
+    if (e != cudaSuccess) return e;
+    return cudaGraphInstantiate(&h->gexec, h->graph, 0);
+}
+
+int sgks_solve(sgks_handle* h, int32_t iters, double tol, void* x_out, sgks_report* rep) {
+    if (!h || iters < 0) return fail(h, SGKS_ERR_INVALID, "bad handle or iters < 0");
+    EngineBase* E = h->eng;
+    const int avail = h->max_iters - h->steps_since_setup;
+    if (iters > avail) return fail(h, SGKS_ERR_STATE, "iters exceeds the remaining basis capacity");
+    join_in(h);
+    cudaError_t e = ensure_graph(h);
+    if (e != cudaSuccess) {
+        join_out(h);
+        return cuda_fail(h, e, "graph capture");
+    }
+    // stopping test parameters (eq. RC), set on the stream before the replays
+    e = launch_set_tol(E->S.sc, tol, h->st);
+    g_launches.fetch_add(1);
+    const int it0 = h->steps_since_setup;
+    for (int k = 0; k < iters && e == cudaSuccess; ++k) e = cudaGraphLaunch(h->gexec, h->st);
+    g_launches.fetch_add(h->graph_launches * iters);
+    h->steps_since_setup += iters;
+    E->host_d += iters;
+    size_t es = 0;
+    int64_t rows = 0, ld = 0;
+    void* xs = E->buffer(SGKS_BUF_X, &es, &rows, &ld);
+    if (e == cudaSuccess && x_out) e = cudaMemcpyAsync(x_out, xs, es * (size_t)rows, cudaMemcpyDeviceToDevice, h->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->sc_host, E->S.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    join_out(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sgks_solve");
+    const DevScalars& sc = *h->sc_host;
+    const int done = sc.iter - it0;
+    if (rep) {
+        rep->iters_done = done;
+        rep->status = map_status(sc.status);
+        rep->subspace_dim = sc.d;
+        rep->rc_last = sc.rc_last;
+        rep->rre_last = sc.rre_last;
+        rep->rre0 = sc.rre0;
+        if (done > 0 && (rep->rc || rep->rre)) {
+            std::vector<double> tmp((size_t)done);
+            if (rep->rc) {
+                e = cudaMemcpy(tmp.data(), E->S.rc_hist + it0, sizeof(double) * done, cudaMemcpyDeviceToHost);
+                for (int k = 0; k < done; ++k) rep->rc[k] = tmp[k];
+            }
+            if (rep->rre && e == cudaSuccess) {
+                e = cudaMemcpy(tmp.data(), E->S.rre_hist + it0, sizeof(double) * done, cudaMemcpyDeviceToHost);
+                for (int k = 0; k < done; ++k) rep->rre[k] = tmp[k];
+            }
+            if (e != cudaSuccess) return cuda_fail(h, e, "sgks_solve (report)");
+        }
+    }
+    const int st = map_status(sc.status);
+    return (st < 0) ? fail(h, st, "device status: solve stopped on an error") : SGKS_OK;
+}
+
+int sgks_status(sgks_handle* h, int32_t* code) {
+    if (!h || !code) return SGKS_ERR_INVALID;
+    cudaError_t e = cudaMemcpyAsync(h->sc_host, h->eng->S.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sgks_status");
+    *code = map_status(h->sc_host->status);
+    return SGKS_OK;
+}
+
+const char* sgks_last_error(const sgks_handle* h) {
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+void sgks_destroy(sgks_handle* h) {
+    if (!h) return;
+    if (h->st) cudaStreamSynchronize(h->st);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->sc_host) cudaFreeHost(h->sc_host);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->st) cudaStreamDestroy(h->st);
+    delete h->eng;
+    delete h;
+}
+
+int sgks_get_info(sgks_handle* h, int64_t* out) {
+    if (!h || !out) return SGKS_ERR_INVALID;
+    cudaError_t e = cudaMemcpyAsync(h->sc_host, h->eng->S.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sgks_get_info");
+    out[0] = h->sc_host->d;
+    out[1] = h->sc_host->iter;
+    out[2] = map_status(h->sc_host->status);
+    return SGKS_OK;
+}
+
+int64_t sgks_kernel_launches(void) { return g_launches.load(); }
+
+int sgks_profile_steps(sgks_handle* h, int32_t iters, double* ms_out, int64_t* count_out, double* dsum_out) {
+    if (!h || iters < 0 || !ms_out || !count_out || !dsum_out) return SGKS_ERR_INVALID;
+    if (iters > h->max_iters - h->steps_since_setup) return fail(h, SGKS_ERR_STATE, "iters exceeds capacity");
+    Profiler p;
+    cudaEventCreate(&p.ev[0]);
+    cudaEventCreate(&p.ev[1]);
+    join_in(h);
+    h->eng->prof = &p;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < iters && e == cudaSuccess; ++k) e = h->eng->step();
+    h->eng->prof = nullptr;
+    h->steps_since_setup += iters;
+    join_out(h);
+    cudaEventDestroy(p.ev[0]);
+    cudaEventDestroy(p.ev[1]);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sgks_profile_steps");
+    for (int c = 0; c < PK_COUNT; ++c) {
+        ms_out[c] = p.ms[c];
+        count_out[c] = p.count[c];
+        dsum_out[c] = p.bytes_d[c];
+    }
+    return SGKS_OK;
+}
+
+int sgks_get_buffer(sgks_handle* h, int32_t which, void* dst, size_t bytes, size_t* copied) {
+    if (!h || !dst) return SGKS_ERR_INVALID;
+    int64_t info[3];
+    int rc = sgks_get_info(h, info);
+    if (rc != SGKS_OK) return rc;
+    const int64_t d = info[0];
+    size_t es = 0;
+    int64_t rows = 0, ld = 0;
+    void* src = h->eng->buffer(which, &es, &rows, &ld);
+    if (!src) return fail(h, SGKS_ERR_INVALID, "unknown buffer id");
+    size_t need;
+    if (which == SGKS_BUF_X || which == SGKS_BUF_SB) need = es * (size_t)rows;
+    else need = es * (size_t)rows * (size_t)d;
+    if (need > bytes) return fail(h, SGKS_ERR_INVALID, "destination too small");
+    cudaError_t e = cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToDevice, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sgks_get_buffer");
+    if (copied) *copied = need;
+    return SGKS_OK;
+}
+
+int sgks_apply(sgks_handle* h, int32_t which, const void* in, void* out) {
+    if (!h || !in || !out || which < SGKS_APPLY_A || which > SGKS_APPLY_SL)
+        return fail(h, SGKS_ERR_INVALID, "bad sgks_apply arguments");
+    join_in(h);
+    cudaError_t e = h->eng->apply(which, in, out);
+    join_out(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sgks_apply");
+    return SGKS_OK;
+}
+
+int sgks_sparse_sign_rows(uint64_t seed, int32_t stream_id, int64_t h_cols, int32_t s, int32_t zeta, int32_t* rows_out,
+                          uint8_t* neg_out, void* stream) {
+    if (h_cols < 0 || s < 1 || zeta < 1 || zeta > kMaxZeta || zeta > s || !rows_out || !neg_out)
+        return fail(nullptr, SGKS_ERR_INVALID, "bad sgks_sparse_sign_rows arguments");
+    if (h_cols == 0) return SGKS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* err = nullptr;
+    cudaError_t e = cudaMallocAsync(&err, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = sparse_sign_rows_device(sketch_key_host_dev(seed, stream_id), h_cols, s, zeta, rows_out, neg_out, err, st);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (err) cudaFreeAsync(err, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "sgks_sparse_sign_rows");
+    return herr ? fail(nullptr, SGKS_ERR_SKETCH, "sparse-sign draw limit exceeded") : SGKS_OK;
+}
+
+int sgks_csr_transpose(int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, const void* val,
+                       int32_t val_dtype, int32_t* t_row_ptr, int32_t* t_col, void* t_val, void* stream) {
+    if (m <= 0 || n <= 0 || nnz < 0 || !row_ptr || !col || !val || !t_row_ptr || !t_col || !t_val ||
+        (val_dtype != SGKS_F32 && val_dtype != SGKS_F64))
+        return fail(nullptr, SGKS_ERR_INVALID, "bad sgks_csr_transpose arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = csr_transpose_device(m, n, nnz, row_ptr, col, val, val_dtype, t_row_ptr, t_col, t_val, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "sgks_csr_transpose");
+    return SGKS_OK;
+}
+
+}  // extern "C"

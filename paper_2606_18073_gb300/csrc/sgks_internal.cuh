@@ -1,0 +1,453 @@
+// Internal declarations shared by the CUDA translation units of the sGKS library.
+// Device-side operator rows (A, A^T, L, L^T L), the sparse-sign hash, warp reductions,
+// and the launcher prototypes that the host orchestration (sgks_api.cu) calls.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sgks.h"
+
+namespace cg = cooperative_groups;
+
+namespace sgks {
+
+constexpr int kThreads = 256;           // threads of every bulk kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxS = 2048;             // largest sketch size supported
+constexpr int kMaxZeta = 16;
+constexpr int kClusterMax = 16;         // CTAs of the small FP64 cluster kernels
+constexpr int kMaxDraws = 256;
+
+// ------------------------------------------------------------------------------ status
+enum DevStatus : int { ST_OK = 0, ST_BREAKDOWN = 1, ST_STOPPED = 2, ST_NONFINITE = 3, ST_SKETCH = 4,
+                       ST_FULL = 5 };
+
+// Scalars that live on the device and are updated by the kernels, so that one captured
+// graph of a step replays for every iteration.
+struct DevScalars {
+    int d;          // columns of W currently in the sketched QR factors
+    int iter;       // iterations done since the setup
+    int stop;       // nonzero: later kernels of the solve do nothing
+    int status;     // DevStatus
+    int ka_done;    // block counter of the combine kernel's last-block reduction
+    int tol_on;     // RC stopping test active
+    double tol;
+    double rc_last, rre_last, rre0;
+    double xt2;     // ||x_true||^2
+};
+
+// ----------------------------------------------------------------------- operator views
+template <typename T, typename V>
+struct DevA {
+    int kind;            // SGKS_OP_*
+    int64_t m, n;
+    const int32_t* rp;   // CSR
+    const int32_t* ci;
+    const V* val;
+    const int32_t* trp;  // CSR of A^T
+    const int32_t* tci;
+    const V* tval;
+    const T* dense;      // row-major m x ld
+    int64_t ld;
+    int nx, ny, kh, kw;  // conv2d
+    const T* psf;
+};
+
+struct DevL {
+    int kind;            // SGKS_REG_*
+    int nx, ny, nt;
+    int64_t n, p;
+};
+
+// --------------------------------------------------------------------------- utilities
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// SplitMix64 output function (Steele, Lea, Flood 2014).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ uint64_t sketch_key_host_dev(uint64_t seed, int stream) {
+    uint64_t z = 2ull * seed + (uint64_t)stream;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Rows and signs of the sparse-sign column j: the k-th accepted draw is the first draw
+// c (counting on from the previous acceptance) whose row differs from rows[0..k-1].
+// Returns false when the 256-draw limit is hit.
+template <int ZMAX>
+__device__ __forceinline__ bool sparse_sign_column(uint64_t key, uint64_t j, int s, int zeta,
+                                                   int (&rows)[ZMAX], uint32_t& negmask) {
+    int c = 0;
+    bool ok = true;
+    negmask = 0u;
+#pragma unroll
+    for (int k = 0; k < ZMAX; ++k) {
+        rows[k] = -1;
+        if (k < zeta) {
+            while (true) {
+                if (c >= kMaxDraws) { ok = false; rows[k] = 0; break; }
+                const uint64_t hv = mix64(key ^ ((j << 8) | (uint64_t)c));
+                ++c;
+                const int r = (int)(((hv >> 32) * (uint64_t)s) >> 32);
+                bool dup = false;
+#pragma unroll
+                for (int t = 0; t < ZMAX; ++t)
+                    if (t < k && rows[t] == r) dup = true;
+                if (!dup) {
+                    rows[k] = r;
+                    if (hv & 1ull) negmask |= (1u << k);
+                    break;
+                }
+            }
+        }
+    }
+    return ok;
+}
+
+// --------------------------------------------------------------- rows of A (forward)
+// Warp-cooperative rows (CSR, dense): every lane returns the full row value.
+template <typename T, typename V>
+__device__ __forceinline__ T a_row_warp(const DevA<T, V>& A, int64_t j, const T* __restrict__ x) {
+    const int lane = lane_id();
+    T acc = T(0);
+    if (A.kind == SGKS_OP_CSR) {
+        const int b = A.rp[j], e = A.rp[j + 1];
+        int k = b + lane;
+        for (; k + 96 < e; k += 128) {
+            const int c0 = ldg(A.ci + k), c1 = ldg(A.ci + k + 32), c2 = ldg(A.ci + k + 64), c3 = ldg(A.ci + k + 96);
+            const T v0 = (T)ldg(A.val + k), v1 = (T)ldg(A.val + k + 32), v2 = (T)ldg(A.val + k + 64),
+                    v3 = (T)ldg(A.val + k + 96);
+            acc += v0 * ldg(x + c0);
+            acc += v1 * ldg(x + c1);
+            acc += v2 * ldg(x + c2);
+            acc += v3 * ldg(x + c3);
+        }
+        for (; k < e; k += 32) acc += (T)ldg(A.val + k) * ldg(x + ldg(A.ci + k));
+    } else {  // dense row-major
+        const T* row = A.dense + j * A.ld;
+        for (int64_t k = lane; k < A.n; k += 32) acc += ldg(row + k) * ldg(x + k);
+    }
+    return warp_sum(acc);
+}
+
+// Thread-level rows (2D convolution).
+template <typename T, typename V>
+__device__ __forceinline__ T a_row_conv(const DevA<T, V>& A, const T* __restrict__ psf_s, int64_t j,
+                                        const T* __restrict__ x) {
+    const int nx = A.nx, ny = A.ny, kh = A.kh, kw = A.kw;
+    const int iy = (int)(j / nx), ix = (int)(j - (int64_t)iy * nx);
+    T acc = T(0);
+    for (int a = 0; a < kh; ++a) {
+        const int yy = iy - a + kh / 2;
+        if (yy < 0 || yy >= ny) continue;
+        const T* xr = x + (int64_t)yy * nx;
+        const T* pr = psf_s + a * kw;
+        for (int c = 0; c < kw; ++c) {
+            const int xx = ix - c + kw / 2;
+            if (xx >= 0 && xx < nx) acc += pr[c] * ldg(xr + xx);
+        }
+    }
+    return acc;
+}
+
+// --------------------------------------------------------------- rows of A^T (adjoint)
+template <typename T, typename V>
+__device__ __forceinline__ T at_row_warp(const DevA<T, V>& A, int64_t i, const T* __restrict__ e) {
+    const int lane = lane_id();
+    T acc = T(0);
+    if (A.kind == SGKS_OP_CSR) {
+        const int b = A.trp[i], en = A.trp[i + 1];
+        int k = b + lane;
+        for (; k + 96 < en; k += 128) {
+            const int c0 = ldg(A.tci + k), c1 = ldg(A.tci + k + 32), c2 = ldg(A.tci + k + 64),
+                      c3 = ldg(A.tci + k + 96);
+            const T v0 = (T)ldg(A.tval + k), v1 = (T)ldg(A.tval + k + 32), v2 = (T)ldg(A.tval + k + 64),
+                    v3 = (T)ldg(A.tval + k + 96);
+            acc += v0 * ldg(e + c0);
+            acc += v1 * ldg(e + c1);
+            acc += v2 * ldg(e + c2);
+            acc += v3 * ldg(e + c3);
+        }
+        for (; k < en; k += 32) acc += (T)ldg(A.tval + k) * ldg(e + ldg(A.tci + k));
+    } else {  // dense: column i
+        for (int64_t k = lane; k < A.m; k += 32) acc += ldg(A.dense + k * A.ld + i) * ldg(e + k);
+    }
+    return warp_sum(acc);
+}
+
+template <typename T, typename V>
+__device__ __forceinline__ T at_row_conv(const DevA<T, V>& A, const T* __restrict__ psf_s, int64_t i,
+                                         const T* __restrict__ e) {
+    const int nx = A.nx, ny = A.ny, kh = A.kh, kw = A.kw;
+    const int iy = (int)(i / nx), ix = (int)(i - (int64_t)iy * nx);
+    T acc = T(0);
+    for (int a = 0; a < kh; ++a) {
+        const int yy = iy + a - kh / 2;
+        if (yy < 0 || yy >= ny) continue;
+        const T* er = e + (int64_t)yy * nx;
+        const T* pr = psf_s + a * kw;
+        for (int c = 0; c < kw; ++c) {
+            const int xx = ix + c - kw / 2;
+            if (xx >= 0 && xx < nx) acc += pr[c] * ldg(er + xx);
+        }
+    }
+    return acc;
+}
+
+// -------------------------------------------------------------- rows of L and of L^T L
+template <typename T>
+__device__ __forceinline__ T l_row(const DevL& L, int64_t k, const T* __restrict__ x) {
+    const int nx = L.nx, ny = L.ny;
+    switch (L.kind) {
+        case SGKS_REG_FD1:
+            return ldg(x + k + 1) - ldg(x + k);
+        case SGKS_REG_GRAD2D: {
+            const int64_t nh = (int64_t)ny * (nx - 1);
+            if (k < nh) {
+                const int64_t iy = k / (nx - 1), ix = k - iy * (nx - 1);
+                const int64_t q = iy * nx + ix;
+                return ldg(x + q + 1) - ldg(x + q);
+            }
+            const int64_t q = k - nh;  // (iy, ix) with iy < ny-1
+            return ldg(x + q + nx) - ldg(x + q);
+        }
+        case SGKS_REG_LAPLACE2D: {
+            const int iy = (int)(k / nx), ix = (int)(k - (int64_t)iy * nx);
+            T v = T(4) * ldg(x + k);
+            if (ix > 0) v -= ldg(x + k - 1);
+            if (ix < nx - 1) v -= ldg(x + k + 1);
+            if (iy > 0) v -= ldg(x + k - nx);
+            if (iy < ny - 1) v -= ldg(x + k + nx);
+            return v;
+        }
+        default: {  // SPACETIME
+            const int64_t per = (int64_t)ny * (nx - 1), per2 = (int64_t)(ny - 1) * nx;
+            const int64_t n1 = per * L.nt, n2 = per2 * L.nt;
+            const int64_t fr = (int64_t)nx * ny;
+            if (k < n1) {
+                const int64_t t = k / per, r = k - t * per;
+                const int64_t iy = r / (nx - 1), ix = r - iy * (nx - 1);
+                const int64_t q = t * fr + iy * nx + ix;
+                return ldg(x + q + 1) - ldg(x + q);
+            }
+            if (k < n1 + n2) {
+                const int64_t kk = k - n1;
+                const int64_t t = kk / per2, r = kk - t * per2;
+                const int64_t q = t * fr + r;
+                return ldg(x + q + nx) - ldg(x + q);
+            }
+            const int64_t q = k - n1 - n2;
+            return ldg(x + q + fr) - ldg(x + q);
+        }
+    }
+}
+
+// (L^T L x)_i, fused: for a first-difference block D along one axis, (D^T D x)_i =
+// [i not last](x_i - x_{i+1}) + [i not first](x_i - x_{i-1}).
+template <typename T>
+__device__ __forceinline__ T fd_pair(const T* __restrict__ x, int64_t i, int64_t stride, int pos, int len) {
+    const T xi = ldg(x + i);
+    T v = T(0);
+    if (pos < len - 1) v += xi - ldg(x + i + stride);
+    if (pos > 0) v += xi - ldg(x + i - stride);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T lap5(const T* __restrict__ x, int iy, int ix, int nx, int ny) {
+    const int64_t q = (int64_t)iy * nx + ix;
+    T v = T(4) * ldg(x + q);
+    if (ix > 0) v -= ldg(x + q - 1);
+    if (ix < nx - 1) v -= ldg(x + q + 1);
+    if (iy > 0) v -= ldg(x + q - nx);
+    if (iy < ny - 1) v -= ldg(x + q + nx);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T ltl_row(const DevL& L, int64_t i, const T* __restrict__ x) {
+    const int nx = L.nx, ny = L.ny;
+    switch (L.kind) {
+        case SGKS_REG_FD1:
+            return fd_pair(x, i, 1, (int)i, nx);
+        case SGKS_REG_GRAD2D: {
+            const int iy = (int)(i / nx), ix = (int)(i - (int64_t)iy * nx);
+            return fd_pair(x, i, 1, ix, nx) + fd_pair(x, i, nx, iy, ny);
+        }
+        case SGKS_REG_LAPLACE2D: {  // L symmetric: L^T L = L^2, 13-point stencil
+            const int iy = (int)(i / nx), ix = (int)(i - (int64_t)iy * nx);
+            T v = T(4) * lap5(x, iy, ix, nx, ny);
+            if (ix > 0) v -= lap5(x, iy, ix - 1, nx, ny);
+            if (ix < nx - 1) v -= lap5(x, iy, ix + 1, nx, ny);
+            if (iy > 0) v -= lap5(x, iy - 1, ix, nx, ny);
+            if (iy < ny - 1) v -= lap5(x, iy + 1, ix, nx, ny);
+            return v;
+        }
+        default: {  // SPACETIME
+            const int64_t fr = (int64_t)nx * ny;
+            const int t = (int)(i / fr);
+            const int64_t r = i - (int64_t)t * fr;
+            const int iy = (int)(r / nx), ix = (int)(r - (int64_t)iy * nx);
+            return fd_pair(x, i, 1, ix, nx) + fd_pair(x, i, nx, iy, ny) + fd_pair(x, i, fr, t, L.nt);
+        }
+    }
+}
+
+// (L^T v)_i for v of length p (used by sgks_apply only).
+template <typename T>
+__device__ __forceinline__ T lt_row(const DevL& L, int64_t i, const T* __restrict__ v) {
+    const int nx = L.nx, ny = L.ny;
+    switch (L.kind) {
+        case SGKS_REG_FD1: {
+            T a = T(0);
+            if (i < nx - 1) a -= ldg(v + i);
+            if (i > 0) a += ldg(v + i - 1);
+            return a;
+        }
+        case SGKS_REG_GRAD2D: {
+            const int iy = (int)(i / nx), ix = (int)(i - (int64_t)iy * nx);
+            const int64_t nh = (int64_t)ny * (nx - 1);
+            T a = T(0);
+            const int64_t h = (int64_t)iy * (nx - 1) + ix;
+            if (ix < nx - 1) a -= ldg(v + h);
+            if (ix > 0) a += ldg(v + h - 1);
+            if (iy < ny - 1) a -= ldg(v + nh + i);
+            if (iy > 0) a += ldg(v + nh + i - nx);
+            return a;
+        }
+        case SGKS_REG_LAPLACE2D: {
+            const int iy = (int)(i / nx), ix = (int)(i - (int64_t)iy * nx);
+            return lap5(v, iy, ix, nx, ny);
+        }
+        default: {
+            const int64_t fr = (int64_t)nx * ny;
+            const int t = (int)(i / fr);
+            const int64_t r = i - (int64_t)t * fr;
+            const int iy = (int)(r / nx), ix = (int)(r - (int64_t)iy * nx);
+            const int64_t per = (int64_t)ny * (nx - 1), per2 = (int64_t)(ny - 1) * nx;
+            const int64_t n1 = per * L.nt, n2 = per2 * L.nt;
+            T a = T(0);
+            const int64_t h = (int64_t)t * per + (int64_t)iy * (nx - 1) + ix;
+            if (ix < nx - 1) a -= ldg(v + h);
+            if (ix > 0) a += ldg(v + h - 1);
+            const int64_t g = n1 + (int64_t)t * per2 + r;
+            if (iy < ny - 1) a -= ldg(v + g);
+            if (iy > 0) a += ldg(v + g - nx);
+            const int64_t q = n1 + n2 + i;
+            if (t < L.nt - 1) a -= ldg(v + q);
+            if (t > 0) a += ldg(v + q - fr);
+            return a;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------- workspace
+template <typename T>
+struct Bulk {                 // solver-precision arrays
+    T* W;                     // [dmax][n]
+    T* AW;                    // [dmax][m]
+    T* x;                     // working x = W y (n)
+    T* xs;                    // last accepted iterate x_k (n)
+    T* e;                     // A x - b (m)
+    const T* b;               // (m), caller-owned
+    const T* xtrue;           // (n) or null
+    T* tmp_m;                 // scratch (m)
+    T* tmp_p;                 // scratch (p)
+};
+
+struct Small {                // FP64 state of the sketched QR and projected solve
+    double *QA, *QL, *RA, *RL;
+    double *G, *X, *Tm, *zf, *dA, *y, *Sb;
+    double *partA, *partL;    // sketch partials [nb][s]
+    double *gpart;            // refinement partials [nb][dmax]
+    double *kapart;           // combine-kernel norm partials [nb][4]
+    double *rc_hist, *rre_hist;
+    DevScalars* sc;
+};
+
+// ------------------------------------------------------------------------ launchers
+struct Dims {
+    int64_t n, m, p;
+    int s, zeta, dmax, ell;
+    int nbA, nbL;             // blocks of the sketch kernel for the A rows and the L rows (multiples of 8)
+    int npA, npL;             // sketch partials (one per cluster of 8 blocks; 1 for the dense sketch)
+    int nbG;                  // blocks of the gradient kernels (n / kThreads tiles)
+    int nbX, nbE;             // blocks of the combine kernel (x rows, e rows)
+    int cluster;              // CTAs of the small kernels
+    int sketch_kind;
+    double sketch_scale;      // 1/sqrt(zeta) for sparse-sign, 1 for Gaussian
+    uint64_t keyA, keyL;
+    double lam;
+    int cgs_passes;
+    int has_xtrue;
+    int max_iters;
+};
+
+template <typename T, typename V>
+cudaError_t launch_sketch_column(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
+                                 const Small& S, cudaStream_t st);
+template <typename T, typename V>
+cudaError_t launch_gaussian_sketch(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
+                                   const Small& S, const double* SA, const double* SL, cudaStream_t st);
+template <typename T>
+cudaError_t launch_sketch_vector(const Dims& D, const T* v, int64_t len, uint64_t key, const double* SG,
+                                 double* part, int nb, int* err, cudaStream_t st);
+template <typename T, typename V>
+cudaError_t launch_gradient(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
+                            const Small& S, bool refine, cudaStream_t st);
+template <typename T>
+cudaError_t launch_combine(const Dims& D, const Bulk<T>& B, const Small& S, int mode, cudaStream_t st);
+cudaError_t launch_append_solve(const Dims& D, const Small& S, cudaStream_t st);
+cudaError_t launch_refine_solve(const Dims& D, const Small& S, cudaStream_t st);
+cudaError_t launch_reduce_rows(const double* part, int nb, int len, double scale, double* out, cudaStream_t st);
+cudaError_t configure_cluster_kernels(int* cluster_out, int s, int dmax);
+
+// setup helpers (sgks_setup.cu)
+template <typename T, typename V>
+cudaError_t launch_apply(const Dims& D, const DevA<T, V>& A, const DevL& L, int which, const T* in, T* out,
+                         cudaStream_t st);
+template <typename T>
+cudaError_t launch_dots(const T* V0, int64_t n, int k, const T* w, double* part, int nb, cudaStream_t st);
+template <typename T>
+cudaError_t launch_orth_update(T* w, const T* V0, int64_t n, int k, const double* part, int nb,
+                               cudaStream_t st);
+template <typename T>
+cudaError_t launch_normalize(T* w, int64_t n, const double* part, int nb, cudaStream_t st);
+template <typename T>
+cudaError_t launch_sqnorm(const T* w, int64_t n, double* part, int nb, cudaStream_t st);
+
+// transpose and sketch rows (sgks_util.cu)
+cudaError_t csr_transpose_device(int64_t m, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
+                                 const void* val, int vdt, int32_t* trp, int32_t* tci, void* tval,
+                                 cudaStream_t st);
+cudaError_t sparse_sign_rows_device(uint64_t key, int64_t h, int s, int zeta, int32_t* rows, uint8_t* neg,
+                                    int* err, cudaStream_t st);
+cudaError_t convert_values(const void* in, int in_dt, void* out, int out_dt, int64_t count, cudaStream_t st);
+cudaError_t launch_set_tol(DevScalars* sc, double tol, cudaStream_t st);
+cudaError_t validate_csr_device(const int32_t* rp, const int32_t* ci, int64_t m, int64_t n, int64_t nnz, int* err,
+                                cudaStream_t st);
+
+// Host-side count of kernel launches enqueued by the library (graph replays add the number of
+// kernel nodes of the step graph).
+int64_t launches_total();
+void launches_add(int64_t k);
+
+}  // namespace sgks

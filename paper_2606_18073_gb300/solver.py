@@ -1,0 +1,279 @@
+"""Thin Python front end of the C ABI: operator descriptors holding torch device tensors and a
+``Solver`` whose methods map one-to-one onto sgks_create / sgks_reset / sgks_step /
+sgks_solve / sgks_destroy.  Every step of the method runs in the CUDA library; this module
+only builds the descriptor structs and passes device pointers and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import Optional
+
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _need_cuda(t, name):
+    if t is not None and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t is not None and not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+@dataclass
+class CSR:
+    """A (m x n) as CSR: row_ptr[m+1], col[nnz] int32; val[nnz] float32/float64 (device)."""
+    row_ptr: torch.Tensor
+    col: torch.Tensor
+    val: torch.Tensor
+    m: int
+    n: int
+    t_row_ptr: Optional[torch.Tensor] = None
+    t_col: Optional[torch.Tensor] = None
+    t_val: Optional[torch.Tensor] = None
+
+    def desc(self):
+        for nm in ("row_ptr", "col", "val", "t_row_ptr", "t_col", "t_val"):
+            _need_cuda(getattr(self, nm), nm)
+        d = L.sgks_op()
+        d.kind, d.m, d.n = L.SGKS_OP_CSR, self.m, self.n
+        d.val_dtype = L.SGKS_F64 if self.val.dtype == torch.float64 else L.SGKS_F32
+        d.nnz = int(self.col.numel())
+        d.row_ptr, d.col, d.val = _ptr(self.row_ptr), _ptr(self.col), _ptr(self.val)
+        d.t_row_ptr, d.t_col, d.t_val = _ptr(self.t_row_ptr), _ptr(self.t_col), _ptr(self.t_val)
+        return d
+
+    def transposed(self, stream=None):
+        """Build the column storage of A on the device (sgks_csr_transpose) and keep it."""
+        lib = L.load()
+        dev = self.col.device
+        self.t_row_ptr = torch.empty(self.n + 1, dtype=torch.int32, device=dev)
+        self.t_col = torch.empty_like(self.col)
+        self.t_val = torch.empty_like(self.val)
+        vd = L.SGKS_F64 if self.val.dtype == torch.float64 else L.SGKS_F32
+        st = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream
+        L.check(lib.sgks_csr_transpose(self.m, self.n, int(self.col.numel()), _ptr(self.row_ptr), _ptr(self.col),
+                                       _ptr(self.val), vd, _ptr(self.t_row_ptr), _ptr(self.t_col),
+                                       _ptr(self.t_val), C.c_void_p(st)))
+        return self
+
+
+@dataclass
+class Dense:
+    """A (m x n) dense, row-major, float32/float64 (device)."""
+    mat: torch.Tensor
+
+    def desc(self):
+        _need_cuda(self.mat, "mat")
+        d = L.sgks_op()
+        d.kind = L.SGKS_OP_DENSE
+        d.m, d.n = self.mat.shape
+        d.ld = self.mat.shape[1]
+        d.val_dtype = L.SGKS_F64 if self.mat.dtype == torch.float64 else L.SGKS_F32
+        d.dense = _ptr(self.mat)
+        return d
+
+
+@dataclass
+class Conv2D:
+    """2D convolution of an (ny, nx) image with the odd-sized psf (kh, kw), zero boundary."""
+    psf: torch.Tensor
+    nx: int
+    ny: int
+
+    def desc(self):
+        _need_cuda(self.psf, "psf")
+        d = L.sgks_op()
+        d.kind = L.SGKS_OP_CONV2D
+        d.m = d.n = self.nx * self.ny
+        d.nx, d.ny = self.nx, self.ny
+        d.kh, d.kw = self.psf.shape
+        d.val_dtype = L.SGKS_F64 if self.psf.dtype == torch.float64 else L.SGKS_F32
+        d.psf = _ptr(self.psf)
+        return d
+
+
+_REG = {"fd1": L.SGKS_REG_FD1, "grad2d": L.SGKS_REG_GRAD2D, "laplace2d": L.SGKS_REG_LAPLACE2D,
+        "spacetime": L.SGKS_REG_SPACETIME}
+
+
+@dataclass
+class Reg:
+    """Matrix-free finite-difference L: kind in fd1 / grad2d / laplace2d / spacetime."""
+    kind: str
+    nx: int
+    ny: int = 1
+    nt: int = 1
+
+    def desc(self):
+        r = L.sgks_reg()
+        r.kind, r.nx, r.ny, r.nt = _REG[self.kind], self.nx, self.ny, self.nt
+        return r
+
+
+class Solver:
+    """sGKS solver (Algorithm 2) on the current CUDA device and stream.
+
+    A: CSR | Dense | Conv2D; L: Reg; b: device tensor (float64 for precision="fp64", float32
+    for "fp32"); lam > 0; sketch_rows = s.  Tensors passed here must outlive the solver.
+    """
+
+    def __init__(self, A, reg: Reg, b: torch.Tensor, lam: float, sketch_rows: int, seed: int = 0, *,
+                 max_iters: int = 100, ell: int = 3, n_refine: int = 0, precision: str = "fp64",
+                 sketch: str = "sparse_sign", zeta: int = 8, cgs_passes: int = 2,
+                 gauss_SA: Optional[torch.Tensor] = None, gauss_SL: Optional[torch.Tensor] = None,
+                 x_true: Optional[torch.Tensor] = None, stream=None):
+        self._lib = L.load()
+        self.dtype = torch.float32 if precision == "fp32" else torch.float64
+        for nm, t in (("b", b), ("x_true", x_true)):
+            _need_cuda(t, nm)
+            if t is not None and t.dtype != self.dtype:
+                raise ValueError(f"{nm} must be {self.dtype} for precision={precision}")
+        for nm, t in (("gauss_SA", gauss_SA), ("gauss_SL", gauss_SL)):
+            _need_cuda(t, nm)
+            if t is not None and t.dtype != torch.float64:
+                raise ValueError(f"{nm} must be float64")
+        self._keep = [A, b, x_true, gauss_SA, gauss_SL]
+        self.A, self.reg = A, reg
+        self.n = A.desc().n
+        self.max_iters = max_iters
+        o = L.sgks_options()
+        o.max_iters, o.ell, o.n_refine, o.zeta, o.cgs_passes = max_iters, ell, n_refine, zeta, cgs_passes
+        o.precision = L.SGKS_PREC_FP32 if precision == "fp32" else L.SGKS_PREC_FP64
+        o.sketch_kind = L.SGKS_SKETCH_GAUSSIAN if sketch == "gaussian" else L.SGKS_SKETCH_SPARSE_SIGN
+        o.gauss_SA, o.gauss_SL, o.x_true = _ptr(gauss_SA), _ptr(gauss_SL), _ptr(x_true)
+        self._stream = torch.cuda.current_stream(b.device).cuda_stream if stream is None else stream
+        self.device = b.device
+        h = C.c_void_p()
+        self._adesc, self._rdesc = A.desc(), reg.desc()
+        rc = self._lib.sgks_create(C.byref(h), C.byref(self._adesc), C.byref(self._rdesc), _ptr(b), float(lam),
+                                   int(sketch_rows), int(seed), C.byref(o), C.c_void_p(self._stream))
+        L.check(rc, None)
+        self._h = h
+
+    # -- Algorithm 2 -----------------------------------------------------------------
+    def reset(self, b: torch.Tensor):
+        _need_cuda(b, "b")
+        self._keep[1] = b
+        L.check(self._lib.sgks_reset(self._h, _ptr(b)), self._h)
+
+    def step(self):
+        L.check(self._lib.sgks_step(self._h), self._h)
+
+    def solve(self, iters: int, tol: float = 0.0, x_out: Optional[torch.Tensor] = None, history: bool = False):
+        rep = L.sgks_report()
+        rc_arr = (C.c_double * max(iters, 1))() if history else None
+        rre_arr = (C.c_double * max(iters, 1))() if history else None
+        if history:
+            rep.rc = C.cast(rc_arr, C.POINTER(C.c_double))
+            rep.rre = C.cast(rre_arr, C.POINTER(C.c_double))
+        if x_out is not None:
+            _need_cuda(x_out, "x_out")
+        L.check(self._lib.sgks_solve(self._h, int(iters), float(tol), _ptr(x_out), C.byref(rep)), self._h)
+        out = dict(iters_done=rep.iters_done, status=rep.status, d=rep.subspace_dim, rc_last=rep.rc_last,
+                   rre_last=rep.rre_last, rre0=rep.rre0)
+        if history:
+            out["rc"] = list(rc_arr[:rep.iters_done])
+            out["rre"] = list(rre_arr[:rep.iters_done])
+        return out
+
+    def status(self):
+        c = C.c_int32()
+        L.check(self._lib.sgks_status(self._h, C.byref(c)), self._h)
+        return c.value
+
+    def info(self):
+        a = (C.c_int64 * 3)()
+        L.check(self._lib.sgks_get_info(self._h, a), self._h)
+        return dict(d=a[0], iter=a[1], status=a[2])
+
+    # -- inspection -------------------------------------------------------------------
+    def buffer(self, which: int, count: int, dtype=torch.float64):
+        out = torch.empty(count, dtype=dtype, device=self.device)
+        n = C.c_size_t()
+        L.check(self._lib.sgks_get_buffer(self._h, which, _ptr(out), out.numel() * out.element_size(),
+                                          C.byref(n)), self._h)
+        return out[: n.value // out.element_size()]
+
+    def x(self):
+        return self.buffer(L.SGKS_BUF_X, self.n, self.dtype)
+
+    def apply(self, which: int, x: torch.Tensor, out: torch.Tensor):
+        L.check(self._lib.sgks_apply(self._h, which, _ptr(x), _ptr(out)), self._h)
+        return out
+
+    def profile(self, iters: int):
+        """Per-kernel CUDA-event timing of `iters` eager iterations (sgks_profile_steps)."""
+        n = L.SGKS_PROFILE_CLASSES
+        ms, cnt, ds = (C.c_double * n)(), (C.c_int64 * n)(), (C.c_double * n)()
+        L.check(self._lib.sgks_profile_steps(self._h, int(iters), ms, cnt, ds), self._h)
+        return {L.PROFILE_CLASS_NAMES[i]: dict(ms=ms[i], launches=cnt[i], dsum=ds[i]) for i in range(n)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sgks_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kernel_launches() -> int:
+    """Kernel launches enqueued by the library in this process (sgks_kernel_launches)."""
+    return int(L.load().sgks_kernel_launches())
+
+
+def sparse_sign_rows(seed: int, stream_id: int, h: int, s: int, zeta: int, device="cuda"):
+    """Device-generated sparse-sign positions (rows[h, zeta] int32) and negative flags (uint8)."""
+    lib = L.load()
+    rows = torch.empty((h, zeta), dtype=torch.int32, device=device)
+    neg = torch.empty((h, zeta), dtype=torch.uint8, device=device)
+    st = torch.cuda.current_stream(rows.device).cuda_stream
+    L.check(lib.sgks_sparse_sign_rows(int(seed), int(stream_id), int(h), int(s), int(zeta), _ptr(rows), _ptr(neg),
+                                      C.c_void_p(st)))
+    return rows, neg
+
+
+def device_inputs(problem, precision: Optional[str] = None, device="cuda", transpose: bool = True):
+    """Copy a problem description (fields as in workloads.Problem: A, L, b, x_true, lam, sketch,
+    iters, n_refine) to the device and return the keyword arguments of ``Solver``.
+
+    A's values, the PSF and the dense matrix are passed as float32 (the problem data are
+    float32-representable); b and x_true in the solver precision; a Gaussian sketch in float64.
+    """
+    import numpy as np
+
+    prec = precision or problem.precision
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    A = problem.A
+    if A.kind == "csr":
+        op = CSR(torch.from_numpy(np.ascontiguousarray(A.row_ptr)).to(device),
+                 torch.from_numpy(np.ascontiguousarray(A.col)).to(device),
+                 torch.from_numpy(np.ascontiguousarray(A.val, dtype=np.float32)).to(device), A.m, A.n)
+        if transpose:
+            op.transposed()
+    elif A.kind == "dense":
+        op = Dense(torch.from_numpy(np.ascontiguousarray(A.dense, dtype=np.float32)).to(device))
+    elif A.kind == "conv2d":
+        op = Conv2D(torch.from_numpy(np.ascontiguousarray(A.psf, dtype=np.float32)).to(device), A.nx, A.ny)
+    else:
+        raise ValueError(A.kind)
+    Lr = problem.L
+    reg = Reg(Lr.kind, Lr.nx, Lr.ny, Lr.nt)
+    sk = problem.sketch
+    kw = dict(A=op, reg=reg, b=torch.from_numpy(np.asarray(problem.b)).to(device, dt), lam=float(problem.lam),
+              sketch_rows=int(sk.s), seed=int(sk.seed), max_iters=int(problem.iters),
+              n_refine=int(problem.n_refine), precision=prec, sketch=sk.kind, zeta=int(sk.zeta),
+              x_true=torch.from_numpy(np.asarray(problem.x_true)).to(device, dt))
+    if sk.kind == "gaussian":
+        kw["gauss_SA"] = torch.from_numpy(np.ascontiguousarray(sk.SA, dtype=np.float64)).to(device)
+        kw["gauss_SL"] = torch.from_numpy(np.ascontiguousarray(sk.SL, dtype=np.float64)).to(device)
+    return kw

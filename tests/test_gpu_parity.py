@@ -1,0 +1,294 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative 2-norm): 1e-10 for FP64 iterates, 1e-4 for the FP32 form with
+refinement; sparse-sign indices, CSR transposes and integer state bit-exact."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import torch
+
+import oracle as O
+from oracle import sgks_oracle as OS
+from workloads import make_problem, small_problem
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2606_18073_gb300 as G
+    G.build()
+    return G
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gpu_iterates(G, P, iters, precision=None, **over):
+    kw = G.device_inputs(P, precision)
+    kw.update(over)
+    kw["max_iters"] = max(kw["max_iters"], iters)
+    S = G.Solver(**kw)
+    xs = [S.x().double().cpu().numpy()]
+    for _ in range(iters):
+        S.step()
+        xs.append(S.x().double().cpu().numpy())
+    return S, xs
+
+
+# ------------------------------------------------------------------------ building blocks
+
+@pytest.mark.parametrize("seed,stream,h,s,zeta", [(0, 0, 1000, 400, 8), (0, 1, 70001, 600, 8), (7, 0, 513, 9, 9),
+                                                  (123456789, 1, 4097, 2048, 16), (3, 0, 333, 17, 1)])
+def test_sparse_sign_indices_bit_exact(G, seed, stream, h, s, zeta):
+    rows, neg = G.sparse_sign_rows(seed, stream, h, s, zeta)
+    r_ref, s_ref = O.sparse_sign_rows(seed, stream, h, s, zeta)
+    assert np.array_equal(rows.cpu().numpy().astype(np.int64), r_ref)
+    assert np.array_equal(neg.cpu().numpy().astype(bool), s_ref < 0)
+
+
+def test_csr_transpose_bit_exact(G):
+    P = small_problem("ct2d")
+    A = G.device_inputs(P, "fp64", transpose=True)["A"]
+    M = sp.csr_matrix((P.A.val, P.A.col, P.A.row_ptr), shape=(P.m, P.n)).tocsc()
+    M.sort_indices()
+    assert np.array_equal(A.t_row_ptr.cpu().numpy(), M.indptr)
+    assert np.array_equal(A.t_col.cpu().numpy(), M.indices)
+    assert np.array_equal(A.t_val.cpu().numpy(), M.data)
+
+
+@pytest.mark.parametrize("kind", ["deconv1d", "deblur2d", "ct2d", "seismic2d", "dynct"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_operators_match_oracle(G, kind, precision):
+    P = small_problem(kind)
+    S = G.Solver(**G.device_inputs(P, precision))
+    Aop, Lop = O.make_operators(P)
+    dt = S.dtype
+    tol = 1e-13 if precision == "fp64" else 2e-6
+    rng = np.random.default_rng(1)
+    cases = [(G._lib.SGKS_APPLY_A, P.n, Aop.apply), (G._lib.SGKS_APPLY_AT, P.m, Aop.adjoint),
+             (G._lib.SGKS_APPLY_L, P.n, Lop.apply), (G._lib.SGKS_APPLY_LT, P.p, Lop.adjoint),
+             (G._lib.SGKS_APPLY_LTL, P.n, lambda v: Lop.adjoint(Lop.apply(v)))]
+    for which, nin, ref in cases:
+        v = rng.standard_normal(nin)
+        if precision == "fp32":
+            v = v.astype(np.float32).astype(np.float64)
+        want = ref(v)
+        out = torch.empty(len(want), dtype=dt, device="cuda")
+        S.apply(which, torch.from_numpy(v).to("cuda", dt), out)
+        assert rel(out.cpu().numpy(), want) < tol, which
+    if P.sketch.kind == "sparse_sign":
+        for which, h, stream in ((G._lib.SGKS_APPLY_SA, P.m, 0), (G._lib.SGKS_APPLY_SL, P.p, 1)):
+            v = rng.standard_normal(h).astype(np.float32).astype(np.float64)
+            want = O.sketch_operator(P.sketch, stream, h) @ v
+            out = torch.empty(P.sketch.s, dtype=torch.float64, device="cuda")
+            S.apply(which, torch.from_numpy(v).to("cuda", dt), out)
+            assert rel(out.cpu().numpy(), want) < (1e-13 if precision == "fp64" else 2e-6)
+    S.close()
+
+
+def test_setup_state_matches_oracle(G):
+    """W_0, S_A b and the sketched QR factors of W_0 (eq. updqr) after sgks_create."""
+    P = small_problem("deblur2d", precision="fp64", n_refine=0)
+    S = G.Solver(**G.device_inputs(P, "fp64"))
+    ref = O.sgks(P, iters=0, record_state=True)
+    d = 3
+    W = S.buffer(G._lib.SGKS_BUF_W, d * P.n).cpu().numpy().reshape(d, P.n).T
+    assert rel(W, ref["W"]) < 1e-13
+    assert rel(S.buffer(G._lib.SGKS_BUF_SB, P.sketch.s).cpu().numpy(), ref["Sb"]) < 1e-14
+    for buf, key, rows in ((G._lib.SGKS_BUF_QA, "QA", P.sketch.s), (G._lib.SGKS_BUF_QL, "QL", P.sketch.s)):
+        Q = S.buffer(buf, d * rows).cpu().numpy().reshape(d, rows).T
+        assert rel(Q, ref[key]) < 1e-12
+    dm = P.iters + 3
+    RA = S.buffer(G._lib.SGKS_BUF_RA, d * dm).cpu().numpy().reshape(d, dm).T[:d]
+    assert rel(np.triu(RA), ref["RA"]) < 1e-12
+    assert rel(S.buffer(G._lib.SGKS_BUF_DA, d).cpu().numpy(), ref["dA"]) < 1e-12
+    S.close()
+
+
+# --------------------------------------------------------------------------- iterates
+
+@pytest.mark.parametrize("kind", ["deconv1d", "deblur2d", "ct2d", "seismic2d", "dynct"])
+def test_fp64_iterates_match_oracle(G, kind):
+    P = small_problem(kind, precision="fp64") if kind in ("deblur2d", "seismic2d", "ct2d") else small_problem(kind)
+    P.precision = "fp64"
+    iters = P.iters
+    ref = O.sgks(P, iters=iters, record_x=True)
+    S, xs = gpu_iterates(G, P, iters, "fp64")
+    errs = [rel(a, b) for a, b in zip(xs, ref["xs"])]
+    assert max(errs) < TOL64, errs
+    S.close()
+
+
+def test_fp64_iterates_cgs1_and_gaussian(G):
+    P = small_problem("deconv1d")                       # Gaussian sketch
+    ref = O.sgks(P, iters=P.iters, record_x=True, cgs_passes=1)
+    S, xs = gpu_iterates(G, P, P.iters, "fp64", cgs_passes=1)
+    assert max(rel(a, b) for a, b in zip(xs, ref["xs"])) < TOL64
+    S.close()
+
+
+@pytest.mark.parametrize("kind", ["deblur2d", "dynct"])
+def test_fp32_refined_iterates_match_oracle(G, kind):
+    P = small_problem(kind)
+    ref = O.sgks(P, record_x=True)
+    S, xs = gpu_iterates(G, P, P.iters, "fp32")
+    errs = [rel(a, b) for a, b in zip(xs, ref["xs"])]
+    assert max(errs) < TOL32, errs
+    S.close()
+
+
+def test_ragged_sizes_and_extreme_sketch(G):
+    """n not a multiple of the 32-row slab or 256-row tile; zeta = 1 and zeta = s."""
+    for nx, ny, s, zeta in ((37, 23, 64, 1), (19, 41, 40, 16), (33, 7, 30, 8)):
+        P = small_problem("deblur2d", nx=nx, ny=ny, s=s, zeta=zeta, iters=15, precision="fp64", n_refine=1)
+        ref = O.sgks(P, record_x=True)
+        S, xs = gpu_iterates(G, P, P.iters, "fp64")
+        assert max(rel(a, b) for a, b in zip(xs, ref["xs"])) < TOL64, (nx, ny, s, zeta)
+        S.close()
+
+
+def test_solve_graph_replay_equals_steps_and_is_deterministic(G):
+    P = small_problem("ct2d", iters=15)
+    kw = G.device_inputs(P, "fp64")
+    S1 = G.Solver(**kw)
+    for _ in range(15):
+        S1.step()
+    x1 = S1.x().cpu().numpy()
+    S2 = G.Solver(**kw)
+    out = S2.solve(15, history=True)
+    x2 = S2.x().cpu().numpy()
+    assert np.array_equal(x1, x2)
+    assert out["iters_done"] == 15 and out["d"] == 18 and len(out["rc"]) == 15
+    ref = O.sgks(P, iters=15)
+    assert np.allclose(out["rc"], ref["rc"], rtol=1e-8, atol=0)
+    assert np.allclose(out["rre"], ref["rre"][1:], rtol=1e-9, atol=0)
+    S3 = G.Solver(**kw)
+    S3.solve(15)
+    assert np.array_equal(S3.x().cpu().numpy(), x2)
+    # reset with a new right-hand side equals a fresh solver on that b
+    P2 = small_problem("ct2d", seed=5, iters=15)
+    b2 = torch.from_numpy(P2.b).cuda()
+    S3.reset(b2)
+    S3.solve(15)
+    kw2 = dict(kw)
+    kw2["b"] = b2
+    S4 = G.Solver(**kw2)
+    S4.solve(15)
+    assert np.array_equal(S3.x().cpu().numpy(), S4.x().cpu().numpy())
+    for s in (S1, S2, S3, S4):
+        s.close()
+
+
+def test_rc_tolerance_stops(G):
+    P = small_problem("deblur2d", precision="fp64", n_refine=0, iters=40)
+    S = G.Solver(**G.device_inputs(P, "fp64"))
+    ref = O.sgks(P, tol=1e-3)
+    out = S.solve(40, tol=1e-3)
+    assert out["status"] == G._lib.SGKS_STOPPED
+    assert out["iters_done"] == ref["iters"]
+    assert rel(S.x().cpu().numpy(), ref["x"]) < TOL64
+    S.close()
+
+
+def test_basis_full_is_an_error(G):
+    P = small_problem("deconv1d", iters=4)
+    S = G.Solver(**G.device_inputs(P, "fp64"))
+    S.solve(4)
+    with pytest.raises(G._lib.SGKSError) as ei:
+        S.step()
+    assert ei.value.code == G._lib.SGKS_ERR_STATE
+    S.close()
+
+
+def test_breakdown_when_basis_spans_space(G):
+    """Tiny n: once W spans R^n the next gradient is (numerically) in its span."""
+    P = small_problem("deconv1d", n=6, s=40, iters=30, lam=1e-1)
+    S = G.Solver(**G.device_inputs(P, "fp64"))
+    out = S.solve(30)
+    assert out["status"] == G._lib.SGKS_BREAKDOWN
+    assert out["d"] <= 6 + 1
+    Aop, Lop = O.make_operators(P)
+    SA, SL = O.sketch_operator(P.sketch, 0, P.m), O.sketch_operator(P.sketch, 1, P.p)
+    xs = O.direct_solve(Aop, Lop, P.b, P.lam, SA, SL)
+    assert rel(S.x().cpu().numpy(), xs) < 1e-8
+    S.close()
+
+
+def test_invalid_arguments(G):
+    P = small_problem("deblur2d", precision="fp64")
+    kw = G.device_inputs(P, "fp64")
+    for bad in (dict(lam=-1.0), dict(sketch_rows=5), dict(zeta=17), dict(sketch_rows=4096)):
+        k = dict(kw)
+        k.update(bad)
+        with pytest.raises(G._lib.SGKSError) as ei:
+            G.Solver(**k)
+        assert ei.value.code == G._lib.SGKS_ERR_INVALID
+
+
+def test_nonfinite_rhs_is_reported(G):
+    P = small_problem("deblur2d", precision="fp64", n_refine=0)
+    kw = G.device_inputs(P, "fp64")
+    kw["b"] = kw["b"].clone()
+    kw["b"][3] = float("nan")
+    S = G.Solver(**kw)
+    with pytest.raises(G._lib.SGKSError) as ei:
+        S.solve(3)
+    assert ei.value.code == G._lib.SGKS_ERR_NONFINITE
+    S.close()
+
+
+# ----------------------------------------------------------------------- full-size configs
+
+@pytest.mark.slow
+def test_deconv1d_full_size_fp64(G):
+    P = make_problem("deconv1d")
+    ref = O.sgks(P, record_x=True)
+    S, xs = gpu_iterates(G, P, P.iters, "fp64")
+    assert max(rel(a, b) for a, b in zip(xs, ref["xs"])) < TOL64
+    S.close()
+
+
+@pytest.mark.slow
+def test_deblur2d_full_size_fp32_refined(G):
+    P = make_problem("deblur2d")
+    ref = O.sgks(P)
+    kw = G.device_inputs(P, "fp32")
+    S = G.Solver(**kw)
+    out = S.solve(P.iters, history=True)
+    assert out["iters_done"] == P.iters
+    assert rel(S.x().double().cpu().numpy(), ref["x"]) < TOL32
+    assert np.allclose(out["rre"], ref["rre"][1:], rtol=1e-4)
+    S.close()
+
+
+@pytest.mark.slow
+def test_deblur2d_full_size_fp64(G):
+    P = make_problem("deblur2d")
+    P.n_refine = 0
+    ref = O.sgks(P, iters=40)
+    S = G.Solver(**G.device_inputs(P, "fp64"))
+    S.solve(40)
+    assert rel(S.x().cpu().numpy(), ref["x"]) < TOL64
+    S.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", ["ct2d", "seismic2d", "dynct"])
+def test_csr_configs_full_size_fp64(G, name):
+    """Full-size operators and sketch sizes, 20 iterations (the oracle's cost bound)."""
+    P = make_problem(name)
+    P.n_refine = 0
+    ref = O.sgks(P, iters=20)
+    S = G.Solver(**G.device_inputs(P, "fp64"))
+    S.solve(20)
+    assert rel(S.x().cpu().numpy(), ref["x"]) < TOL64
+    S.close()
