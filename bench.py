@@ -143,8 +143,10 @@ def bytes_model(P, cls, d, elem):
         return (m + n) * T + n * T
     if cls == "sketch_column":
         return n * T + m * T
-    if cls == "append_solve":
-        return 8 * (2 * 2 * s * d + 2 * s + 3 * (2 * d) ** 2 + d * d)
+    if cls == "qr_append":
+        return 8 * (2 * s * d + 2 * s + 2 * d)
+    if cls == "stacked_solve":
+        return 8 * (2 * d * d + 2 * d * d + 2 * d)
     if cls == "refine_solve":
         return 8 * d * d
     return 0
@@ -152,8 +154,10 @@ def bytes_model(P, cls, d, elem):
 
 def flops_fp64(P, cls, d):
     s = P.sketch.s
-    if cls == "append_solve":
-        return 2.0 * (2 * 2 * 2 * s * d) + 2.0 * (4 * d * d + 4 * d * d + d * d)
+    if cls == "qr_append":       # 2 factors x 2 passes x (dot + update) over s x d
+        return 2.0 * 2 * 2 * 2 * s * d
+    if cls == "stacked_solve":   # 2 passes x (dot + update) over 2d x d, X t and X z
+        return 2.0 * (2 * 2 * 2 * d * d + d * d)
     if cls == "refine_solve":
         return 2.0 * d * d
     return 0.0
@@ -364,19 +368,20 @@ def extras(args, G, P, kw, S, iters, dev, flush):
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     # dominant bandwidth kernel (largest time share among the streaming kernels)
-    stream_k = [k for k in kern if k not in ("append_solve", "refine_solve")]
+    stream_k = [k for k in kern if k not in ("qr_append", "stacked_solve", "refine_solve")]
     dom = max(stream_k, key=lambda k: kern[k]["ms_total"])
     dk = kern[dom]
     out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": dk["gbps"], "peak": hbm, "unit": "GB/s",
                        "frac": dk["gbps"] / hbm, "traffic": None,
                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)" if peaks else
                        "fallback 6800 GB/s"}
-    a = kern.get("append_solve")
-    if a:
-        fl = flops_fp64(P, "append_solve", a["avg_d"])
-        out["roofline_fp64_solve"] = {"kernel": "append_solve", "bound": "alu", "achieved": fl / (a["us_per_launch"] * 1e-6) / 1e12,
-                                      "peak": 1.25, "unit": "TFLOP/s (FP64)",
-                                      "frac": fl / (a["us_per_launch"] * 1e-6) / 1e12 / 1.25}
+    small = {}
+    for k in ("qr_append", "stacked_solve", "refine_solve"):
+        a = kern.get(k)
+        if a:
+            fl = flops_fp64(P, k, a["avg_d"]) / (a["us_per_launch"] * 1e-6) / 1e12
+            small[k] = {"bound": "alu", "achieved": fl, "peak": 1.25, "unit": "TFLOP/s (FP64)", "frac": fl / 1.25}
+    out["fp64_small_phase"] = small
     # CPU oracle baseline, bounded sample, one thread
     try:
         r = run_cpu_worker(args.config, args.cpu_sample_iters)

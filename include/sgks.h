@@ -48,7 +48,8 @@ enum { SGKS_F32 = 0, SGKS_F64 = 1 };
 enum { SGKS_OP_DENSE = 1, SGKS_OP_CSR = 2, SGKS_OP_CONV2D = 3 };
 enum { SGKS_REG_FD1 = 1, SGKS_REG_GRAD2D = 2, SGKS_REG_LAPLACE2D = 3, SGKS_REG_SPACETIME = 4 };
 enum { SGKS_SKETCH_SPARSE_SIGN = 0, SGKS_SKETCH_GAUSSIAN = 1 };
-enum { SGKS_PREC_FP64 = 0, SGKS_PREC_FP32 = 1 };
+enum { SGKS_PREC_FP64 = 0, SGKS_PREC_FP32 = 1, SGKS_PREC_FP32X = 2 };
+enum { SGKS_FLAG_GLOBAL_SMALL = 1 };
 
 /* Forward operator A (m x n).
  *  SGKS_OP_CSR:    row_ptr[m+1], col[nnz] (int32, 0-based), val[nnz] of val_dtype.  Optional
@@ -94,12 +95,21 @@ typedef struct sgks_options {
     int32_t max_iters;    /* maximum number of appended columns; sizes W: d_max = ell + max_iters [100] */
     int32_t ell;          /* dimension of the initial Krylov basis W_0 [3]                          */
     int32_t n_refine;     /* refinement steps of the projected solve per iteration [0]              */
-    int32_t precision;    /* SGKS_PREC_FP64 or SGKS_PREC_FP32 (FP32 operators, sketch, W; FP64
-                             sketched QR, projected solve, refinement reductions) [FP64]            */
+    int32_t precision;    /* SGKS_PREC_FP64: everything FP64.
+                             SGKS_PREC_FP32: FP32 operators, sketch and W with FP32 accumulation;
+                             FP64 sketched QR, projected solve and refinement reductions.
+                             SGKS_PREC_FP32X: FP32 storage of W, A and b; A W, x, e and every
+                             sum feeding the sketch or the gradient in compensated float-float
+                             arithmetic (TwoProd/TwoSum, Dot2); FP64 small phase.
+                             b, x_true and x_out are FP64 for FP64 and FP32 otherwise; for FP32X
+                             sgks_get_buffer(SGKS_BUF_X / SGKS_BUF_AW) returns (hi, lo) float
+                             pairs [FP64]                                                        */
     int32_t sketch_kind;  /* SGKS_SKETCH_SPARSE_SIGN or SGKS_SKETCH_GAUSSIAN [sparse-sign]          */
     int32_t zeta;         /* nonzeros per sketch column, 1..16, <= sketch_rows [8]                  */
     int32_t cgs_passes;   /* 1 = the single projection printed under eq. updqr, 2 = CGS2 [2]       */
-    int32_t reserved;
+    int32_t flags;        /* bit 0 (SGKS_FLAG_GLOBAL_SMALL): run the FP64 QR append and projected
+                             solve with the global-memory kernels instead of the on-chip cluster
+                             kernels (chosen automatically when the on-chip slices do not fit) [0] */
     const double* gauss_SA; /* Gaussian sketch only: S_A, sketch_rows x m, row-major, FP64, device */
     const double* gauss_SL; /* Gaussian sketch only: S_L, sketch_rows x p, row-major, FP64, device */
     const void* x_true;     /* optional, n values of the solver precision: enables RRE records    */
@@ -229,10 +239,11 @@ int64_t sgks_kernel_launches(void);
  * call is for measurement only.  Host arrays of SGKS_PROFILE_CLASSES entries receive per kernel
  * class the total milliseconds, the number of launches and the sum over launches of the
  * subspace size d at launch (for per-launch byte models).  Classes:
- *   0 gradient -> new basis column   1 operator apply + sketch   2 QR append + projected solve
- *   3 combine inside refinement      4 gradient + W^T r          5 refinement solve
- *   6 combine at the end of the iteration (x_k, e_k, RC, RRE) */
-#define SGKS_PROFILE_CLASSES 7
+ *   0 gradient -> new basis column   1 operator apply + sketch   2 sketched QR appends (K2)
+ *   3 stacked QR + projected solve (K3; with SGKS_FLAG_GLOBAL_SMALL: K2 and K3 in one kernel)
+ *   4 combine inside refinement      5 gradient + W^T r          6 refinement solve
+ *   7 combine at the end of the iteration (x_k, e_k, RC, RRE) */
+#define SGKS_PROFILE_CLASSES 8
 int sgks_profile_steps(sgks_handle* h, int32_t iters, double* ms_out, int64_t* count_out, double* dsum_out);
 
 #ifdef __cplusplus

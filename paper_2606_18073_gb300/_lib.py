@@ -19,7 +19,7 @@ SGKS_F32, SGKS_F64 = 0, 1
 SGKS_OP_DENSE, SGKS_OP_CSR, SGKS_OP_CONV2D = 1, 2, 3
 SGKS_REG_FD1, SGKS_REG_GRAD2D, SGKS_REG_LAPLACE2D, SGKS_REG_SPACETIME = 1, 2, 3, 4
 SGKS_SKETCH_SPARSE_SIGN, SGKS_SKETCH_GAUSSIAN = 0, 1
-SGKS_PREC_FP64, SGKS_PREC_FP32 = 0, 1
+SGKS_PREC_FP64, SGKS_PREC_FP32, SGKS_PREC_FP32X = 0, 1, 2
 (SGKS_BUF_X, SGKS_BUF_Y, SGKS_BUF_W, SGKS_BUF_QA, SGKS_BUF_RA, SGKS_BUF_QL, SGKS_BUF_RL,
  SGKS_BUF_DA, SGKS_BUF_SB, SGKS_BUF_T, SGKS_BUF_AW) = range(1, 12)
 (SGKS_APPLY_A, SGKS_APPLY_AT, SGKS_APPLY_L, SGKS_APPLY_LT, SGKS_APPLY_LTL, SGKS_APPLY_SA,
@@ -52,7 +52,7 @@ class sgks_options(C.Structure):
     _fields_ = [
         ("max_iters", C.c_int32), ("ell", C.c_int32), ("n_refine", C.c_int32),
         ("precision", C.c_int32), ("sketch_kind", C.c_int32), ("zeta", C.c_int32),
-        ("cgs_passes", C.c_int32), ("reserved", C.c_int32),
+        ("cgs_passes", C.c_int32), ("flags", C.c_int32),
         ("gauss_SA", C.c_void_p), ("gauss_SL", C.c_void_p), ("x_true", C.c_void_p),
     ]
 
@@ -85,9 +85,10 @@ _SIGNATURES = {
     "sgks_profile_steps": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                      C.POINTER(C.c_double)]),
 }
-SGKS_PROFILE_CLASSES = 7
-PROFILE_CLASS_NAMES = ["gradient_append", "sketch_column", "append_solve", "combine_refine", "gradient_refine",
-                       "refine_solve", "combine"]
+SGKS_PROFILE_CLASSES = 8
+PROFILE_CLASS_NAMES = ["gradient_append", "sketch_column", "qr_append", "stacked_solve", "combine_refine",
+                       "gradient_refine", "refine_solve", "combine"]
+SGKS_FLAG_GLOBAL_SMALL = 1
 
 _lib = None
 

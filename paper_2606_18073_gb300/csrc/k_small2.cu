@@ -1,0 +1,429 @@
+// Latency-optimised FP64 small phase of one sGKS iteration (the default path).
+//
+// k_qr_append (K2): rank-one append to the sketched QR factors S_A A W = Q_A R_A and
+//   S_L L W = Q_L R_L (eq. updqr and the formulas under it; classical Gram-Schmidt applied
+//   `cgs_passes` times), plus the new d_A entry q_A^T S_A b (eq. dA_update).  Grid = two
+//   thread-block clusters: cluster 0 appends to (Q_A, R_A), cluster 1 to (Q_L, R_L).  CTA r of
+//   a cluster owns rows [r R, (r+1) R) of the s-dimensional sketch space and stages its slice
+//   of Q (all d columns) in shared memory with coalesced loads, so each projection pass is
+//   one local matrix-vector product, one all-to-all push of d partial dot products through
+//   distributed shared memory, one cluster barrier and one local update.
+// k_stacked_solve (K3): the projected problem of eq. (projected_sketched_bis),
+//   y = argmin ||[R_A; sqrt(lam) R_L] y - [d_A; 0]||, by the same classical Gram-Schmidt
+//   append on the stacked 2d x d matrix M (rows in creation order: A-row j, L-row j).  An
+//   explicit orthonormal factor Q_T (2d x d) gives M = Q_T T with T upper triangular;
+//   z = Q_T^T [d_A; 0] gains one entry per step.  T^{-1} is bordered one column at a time
+//   (X' = [[X, -X t / theta], [0, 1 / theta]]) and kept in both column- and row-major order,
+//   so y = X z and the refinement's X X^T g are warp-per-row products.
+// k_refine_solve2: y -= X X^T g with g the FP64 sum of the refinement partials.
+//
+// All cluster-wide scalars are reduced in the same order in every CTA (deterministic).  The
+// two clusters of k_qr_append never wait on each other and never write the shared `stop` /
+// `status` words; k_stacked_solve (one cluster) reads their per-launch results and decides.
+#include <math.h>
+
+#include "sgks_internal.cuh"
+
+namespace sgks {
+
+__device__ __forceinline__ double block_sum2(double v, double* scratch) {
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane_id() == 0) scratch[warp_id()] = v;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) t += scratch[w];
+    __syncthreads();
+    return t;
+}
+
+template <int CS>
+__device__ __forceinline__ void push(cg::cluster_group& cl, double* local, int idx, double v) {
+#pragma unroll
+    for (int r = 0; r < CS; ++r) cl.map_shared_rank(local, r)[idx] = v;
+}
+
+// Shared-memory plan of k_qr_append (doubles): Qs[dq_max * RP] | v[R] | sb[R] | cbuf[CS*dm] |
+// c[dm] | p[dm] | red[4*CS] | scratch[kWarps]
+__host__ __device__ inline size_t qr_append_smem(int s, int dm, int cs) {
+    const int R = (s + cs - 1) / cs, RP = R | 1;
+    return sizeof(double) * ((size_t)dm * RP + 2 * (size_t)R + (size_t)cs * dm + 2 * (size_t)dm + 4 * cs + kWarps);
+}
+
+// k_stacked_solve (doubles): QTs[dm * RP2] | v[R2] | cbuf[CS*dm] | c[dm] | tau[dm] | red[4*CS] |
+// scal[8] | scratch[kWarps]
+__host__ __device__ inline size_t stacked_smem(int dm, int cs) {
+    const int R2 = (2 * dm + cs - 1) / cs, RP2 = R2 | 1;
+    return sizeof(double) * ((size_t)dm * RP2 + (size_t)R2 + (size_t)cs * dm + 2 * (size_t)dm + 4 * cs + 8 + kWarps);
+}
+
+template <int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads) k_qr_append(Dims D, Small S) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int fac = blockIdx.x / CS;  // 0: S_A A W, 1: S_L L W
+    const int tid = threadIdx.x, lane = lane_id(), warp = warp_id();
+    const int s = D.s, dm = D.dmax;
+    const int R = (s + CS - 1) / CS, RP = R | 1;
+    const int i0 = rank * R;
+    const int nr = max(0, min(s, i0 + R) - i0);
+
+    const DevScalars* sc = S.sc;
+    if (sc->stop) return;
+    const int dq = sc->d;
+    if (sc->status == ST_SKETCH || dq >= dm) return;   // k_stacked_solve reports it
+
+    extern __shared__ __align__(16) double sm[];
+    double* Qs = sm;                               // [dq][RP]
+    double* v = Qs + (size_t)dm * RP;              // [R]
+    double* sb = v + R;                            // [R]
+    double* cbuf = sb + R;                         // [CS][dm]
+    double* c = cbuf + (size_t)CS * dm;            // [dm]
+    double* p = c + dm;                            // [dm]
+    double* red = p + dm;                          // [4][CS]
+    double* scratch = red + 4 * CS;                // [kWarps]
+
+    double* Q = fac ? S.QL : S.QA;
+    double* Rm = fac ? S.RL : S.RA;
+    const double* part = fac ? S.partL : S.partA;
+    const int np = fac ? D.npL : D.npA;
+
+    // stage the Q slice (coalesced along rows of each column)
+    for (int idx = tid; idx < dq * nr; idx += kThreads) {
+        const int j = idx / nr, li = idx - j * nr;
+        Qs[(size_t)j * RP + li] = Q[(size_t)j * s + i0 + li];
+    }
+    // sketch partials -> own rows of the new sketched column; warp per row, lanes over partials
+    for (int li = warp; li < nr; li += kWarps) {
+        double a = 0.0;
+        for (int b = lane; b < np; b += 32) a += part[(size_t)b * s + i0 + li];
+        a = warp_sum(a);
+        if (lane == 0) v[li] = a * D.sketch_scale;
+    }
+    if (fac == 0)
+        for (int li = tid; li < nr; li += kThreads) sb[li] = S.Sb[i0 + li];
+    for (int j = tid; j < dq; j += kThreads) p[j] = 0.0;
+    __syncthreads();
+    double un = 0.0;
+    for (int li = tid; li < nr; li += kThreads) un += v[li] * v[li];
+    un = block_sum2(un, scratch);
+    if (tid == 0) push<CS>(cl, red, rank, un);
+
+    double rr = 0.0;
+    for (int pass = 0; pass < D.cgs_passes; ++pass) {
+        for (int j = tid; j < dq; j += kThreads) {          // partial c_j over own rows
+            const double* q = Qs + (size_t)j * RP;
+            double a = 0.0;
+            for (int li = 0; li < nr; ++li) a += q[li] * v[li];
+            push<CS>(cl, cbuf + (size_t)rank * dm, j, a);
+        }
+        cl.sync();
+        for (int j = tid; j < dq; j += kThreads) {
+            double a = 0.0;
+            for (int r = 0; r < CS; ++r) a += cbuf[(size_t)r * dm + j];
+            c[j] = a;
+            p[j] += a;
+        }
+        __syncthreads();
+        const bool last = pass == D.cgs_passes - 1;
+        for (int li = tid; li < nr; li += kThreads) {       // v -= Q c over own rows
+            double a = v[li];
+            for (int j = 0; j < dq; ++j) a -= Qs[(size_t)j * RP + li] * c[j];
+            v[li] = a;
+            if (last) rr += a * a;
+        }
+        if (last) {
+            rr = block_sum2(rr, scratch);
+            if (tid == 0) push<CS>(cl, red + CS, rank, rr);
+        }
+        cl.sync();   // also separates this pass's reads of cbuf from the next pass's pushes
+    }
+    if (D.cgs_passes == 0) cl.sync();
+    double un2 = 0.0, r2 = 0.0;
+    for (int r = 0; r < CS; ++r) { un2 += red[r]; r2 += red[CS + r]; }
+    double rho = sqrt(r2);
+    const bool finite = isfinite(un2) && isfinite(r2);
+    const bool broke = !(rho > 1e-13 * sqrt(un2));
+    if (broke) rho = 0.0;
+    // new Q column over own rows, d_A partial
+    double dp = 0.0;
+    for (int li = tid; li < nr; li += kThreads) {
+        const double q = rho == 0.0 ? 0.0 : v[li] / rho;
+        Q[(size_t)dq * s + i0 + li] = q;
+        if (fac == 0) dp += q * sb[li];
+    }
+    if (fac == 0) {
+        dp = block_sum2(dp, scratch);
+        if (tid == 0) push<CS>(cl, red + 2 * CS, rank, dp);
+        cl.sync();
+    }
+    if (rank == 0) {
+        for (int j = tid; j <= dq; j += kThreads) Rm[(size_t)dq * dm + j] = j < dq ? p[j] : rho;
+        if (tid == 0) {
+            double dn = 0.0;
+            if (fac == 0)
+                for (int r = 0; r < CS; ++r) dn += red[2 * CS + r];
+            double* out = S.qr_out + 4 * fac;
+            out[0] = rho;
+            out[1] = broke ? 1.0 : 0.0;
+            out[2] = finite ? 1.0 : 0.0;
+            out[3] = dn;
+        }
+    }
+}
+
+template <int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads) k_stacked_solve(Dims D, Small S) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int tid = threadIdx.x, lane = lane_id(), warp = warp_id();
+    const int gw = rank * kWarps + warp, GW = CS * kWarps;
+    const int dm = D.dmax, ldT = 2 * dm;
+    DevScalars* sc = S.sc;
+    if (sc->stop) return;
+    const int dq = sc->d;
+    const double rhoA = S.qr_out[0], rhoL = S.qr_out[4];
+    const bool brA = S.qr_out[1] != 0.0, brL = S.qr_out[5] != 0.0;
+    const bool finite = S.qr_out[2] != 0.0 && S.qr_out[6] != 0.0;
+    const int bad = (sc->status == ST_SKETCH) ? ST_SKETCH : (dq >= dm ? ST_FULL : (!finite ? ST_NONFINITE : (brA && brL ? ST_BREAKDOWN : 0)));
+    if (bad) {
+        cl.sync();   // every CTA has read stop / d / status before they change
+        if (rank == 0 && tid == 0) {
+            sc->status = bad;
+            sc->stop = 1;
+        }
+        return;
+    }
+    const double dnew = S.qr_out[3];
+    const double sl = sqrt(D.lam);
+    const int N2 = 2 * dq + 2;
+    const int R2 = (2 * dm + CS - 1) / CS, RP2 = R2 | 1;
+    const int r0 = rank * R2;
+    const int nr = max(0, min(N2, r0 + R2) - r0);
+
+    extern __shared__ __align__(16) double sm[];
+    double* Qs = sm;                                // [dq][RP2]
+    double* v = Qs + (size_t)dm * RP2;              // [R2]
+    double* cbuf = v + R2;                          // [CS][dm]
+    double* c = cbuf + (size_t)CS * dm;             // [dm]
+    double* tau = c + dm;                           // [dm]
+    double* red = tau + dm;                         // [4][CS]
+    double* scal = red + 4 * CS;                    // [8]
+    double* scratch = scal + 8;                     // [kWarps]
+
+    // stage the Q_T slice; column j is zero below row 2j+2
+    for (int idx = tid; idx < dq * nr; idx += kThreads) {
+        const int j = idx / nr, lr = idx - j * nr, row = r0 + lr;
+        Qs[(size_t)j * RP2 + lr] = row < 2 * j + 2 ? S.QT[(size_t)j * ldT + row] : 0.0;
+    }
+    // own rows of the new stacked column [p_A; sqrt(lam) p_L] in creation order
+    for (int lr = tid; lr < nr; lr += kThreads) {
+        const int row = r0 + lr, j = row >> 1;
+        double val;
+        if (j < dq) val = (row & 1) ? sl * S.RL[(size_t)dq * dm + j] : S.RA[(size_t)dq * dm + j];
+        else val = (row & 1) ? sl * rhoL : rhoA;
+        v[lr] = val;
+    }
+    for (int j = tid; j < dq; j += kThreads) tau[j] = 0.0;
+    __syncthreads();
+    double rr = 0.0;
+    for (int pass = 0; pass < D.cgs_passes; ++pass) {
+        for (int j = tid; j < dq; j += kThreads) {
+            const double* q = Qs + (size_t)j * RP2;
+            double a = 0.0;
+            for (int lr = 0; lr < nr; ++lr) a += q[lr] * v[lr];
+            push<CS>(cl, cbuf + (size_t)rank * dm, j, a);
+        }
+        cl.sync();
+        for (int j = tid; j < dq; j += kThreads) {
+            double a = 0.0;
+            for (int r = 0; r < CS; ++r) a += cbuf[(size_t)r * dm + j];
+            c[j] = a;
+            tau[j] += a;
+        }
+        __syncthreads();
+        const bool last = pass == D.cgs_passes - 1;
+        for (int lr = tid; lr < nr; lr += kThreads) {
+            double a = v[lr];
+            for (int j = 0; j < dq; ++j) a -= Qs[(size_t)j * RP2 + lr] * c[j];
+            v[lr] = a;
+            if (last) rr += a * a;
+        }
+        if (last) {
+            rr = block_sum2(rr, scratch);
+            if (tid == 0) push<CS>(cl, red, rank, rr);
+        }
+        cl.sync();
+    }
+    double t2 = 0.0;
+    for (int r = 0; r < CS; ++r) t2 += red[r];
+    const double theta = sqrt(t2);   // > 0: at least one of rho_A, rho_L is nonzero
+    // new Q_T column and the new entry of z = Q_T^T [d_A; 0]
+    double zp = 0.0;
+    for (int lr = tid; lr < nr; lr += kThreads) {
+        const int row = r0 + lr;
+        const double q = v[lr] / theta;
+        S.QT[(size_t)dq * ldT + row] = q;
+        if (!(row & 1)) {
+            const int j = row >> 1;
+            zp += q * (j < dq ? S.dA[j] : dnew);
+        }
+    }
+    zp = block_sum2(zp, scratch);
+    if (tid == 0) push<CS>(cl, red + CS, rank, zp);
+    cl.sync();
+    double zn = 0.0;
+    for (int r = 0; r < CS; ++r) zn += red[CS + r];
+    if (rank == 0) {
+        for (int j = tid; j <= dq; j += kThreads) S.Tm[(size_t)dq * dm + j] = j < dq ? tau[j] : theta;
+        if (tid == 0) {
+            S.dA[dq] = dnew;
+            S.z[dq] = zn;
+        }
+    }
+    // X = T^{-1}: new column -X tau / theta (row i of X in the row-major copy), X[dq][dq] = 1/theta;
+    // then y_i = sum_{j >= i} X(i, j) z_j with the same warp per row.
+    for (int i = gw; i <= dq; i += GW) {
+        double xn;
+        if (i < dq) {
+            const double* xr = S.Xr + (size_t)i * dm;
+            double a = 0.0;
+            for (int j = i + lane; j < dq; j += 32) a += xr[j] * tau[j];
+            xn = -warp_sum(a) / theta;
+        } else {
+            xn = 1.0 / theta;
+        }
+        const double* xr = S.Xr + (size_t)i * dm;
+        double a = 0.0;
+        for (int j = i + lane; j < dq; j += 32) a += xr[j] * S.z[j];
+        a = warp_sum(a) + xn * zn;
+        if (lane == 0) {
+            S.X[(size_t)dq * dm + i] = xn;
+            S.Xr[(size_t)i * dm + dq] = xn;
+            S.y[i] = a;
+        }
+    }
+    if (rank == 0 && tid == 0) sc->d = dq + 1;
+}
+
+template <int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads) k_refine_solve2(Dims D, Small S, int npart) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int tid = threadIdx.x, lane = lane_id(), warp = warp_id();
+    const int gw = rank * kWarps + warp, GW = CS * kWarps;
+    const int dm = D.dmax;
+    extern __shared__ __align__(16) double sm[];
+    double* g = sm;        // [dm]
+    double* h = g + dm;    // [dm]
+    const DevScalars* sc = S.sc;
+    if (sc->stop) return;
+    const int d = sc->d;
+    // g_j: warp per j over the cluster, lanes over the partials; pushed to every CTA
+    for (int j = gw; j < d; j += GW) {
+        double a = 0.0;
+        for (int b = lane; b < npart; b += 32) a += S.gpart[(size_t)b * dm + j];
+        a = warp_sum(a);
+        if (lane < CS) cl.map_shared_rank(g, lane)[j] = a;
+    }
+    cl.sync();
+    for (int i = gw; i < d; i += GW) {     // h = X^T g: column i of X (contiguous) with g[0..i]
+        const double* xc = S.X + (size_t)i * dm;
+        double a = 0.0;
+        for (int j = lane; j <= i; j += 32) a += xc[j] * g[j];
+        a = warp_sum(a);
+        if (lane < CS) cl.map_shared_rank(h, lane)[i] = a;
+    }
+    cl.sync();
+    for (int i = gw; i < d; i += GW) {     // y_i -= (X h)_i: row i of X (row-major copy)
+        const double* xr = S.Xr + (size_t)i * dm;
+        double a = 0.0;
+        for (int j = i + lane; j < d; j += 32) a += xr[j] * h[j];
+        a = warp_sum(a);
+        if (lane == 0) S.y[i] -= a;
+    }
+    (void)tid;
+}
+
+// ----------------------------------------------------------------------------- launchers
+template <int CS>
+static cudaError_t config2(int s, int dm, size_t limit) {
+    if (qr_append_smem(s, dm, CS) > limit || stacked_smem(dm, CS) > limit) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (CS > 8) {
+        e = cudaFuncSetAttribute(k_qr_append<CS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stacked_solve<CS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_refine_solve2<CS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaFuncSetAttribute(k_qr_append<CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr_append_smem(s, dm, CS));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_stacked_solve<CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stacked_smem(dm, CS));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_refine_solve2<CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(2 * sizeof(double) * (size_t)dm));
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * CS);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = qr_append_smem(s, dm, CS);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    e = cudaOccupancyMaxActiveClusters(&ncl, (void*)k_qr_append<CS>, &cfg);
+    if (e != cudaSuccess) return e;
+    return ncl >= 2 ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+// Chooses the cluster size of the fast small path; returns an error if it cannot be used
+// (the caller then falls back to the global-memory path of k_small.cu).
+cudaError_t configure_small_fast(int* cluster_out, int s, int dm) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t limit = (size_t)optin;
+    cudaError_t e = config2<16>(s, dm, limit);
+    if (e == cudaSuccess) {
+        *cluster_out = 16;
+        return e;
+    }
+    cudaGetLastError();
+    e = config2<8>(s, dm, limit);
+    if (e == cudaSuccess) *cluster_out = 8;
+    else cudaGetLastError();
+    return e;
+}
+
+cudaError_t launch_qr_append(const Dims& D, const Small& S, cudaStream_t st) {
+    if (D.cluster2 == 16)
+        k_qr_append<16><<<32, kThreads, qr_append_smem(D.s, D.dmax, 16), st>>>(D, S);
+    else
+        k_qr_append<8><<<16, kThreads, qr_append_smem(D.s, D.dmax, 8), st>>>(D, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stacked_solve(const Dims& D, const Small& S, cudaStream_t st) {
+    if (D.cluster2 == 16)
+        k_stacked_solve<16><<<16, kThreads, stacked_smem(D.dmax, 16), st>>>(D, S);
+    else
+        k_stacked_solve<8><<<8, kThreads, stacked_smem(D.dmax, 8), st>>>(D, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_solve2(const Dims& D, const Small& S, cudaStream_t st) {
+    const int np = D.nbG / 8;
+    const size_t smem = 2 * sizeof(double) * (size_t)D.dmax;
+    if (D.cluster2 == 16)
+        k_refine_solve2<16><<<16, kThreads, smem, st>>>(D, S, np);
+    else
+        k_refine_solve2<8><<<8, kThreads, smem, st>>>(D, S, np);
+    return cudaGetLastError();
+}
+
+}  // namespace sgks

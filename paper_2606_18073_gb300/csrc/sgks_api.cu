@@ -15,6 +15,7 @@
 #include <stdio.h>
 
 #include <atomic>
+#include <type_traits>
 #include <new>
 #include <string>
 #include <vector>
@@ -29,8 +30,8 @@ thread_local std::string g_create_error;
 std::atomic<int64_t> g_launches{0};
 
 // Kernel classes of the per-kernel profile (sgks_profile_steps).
-enum { PK_GRAD_APPEND = 0, PK_SKETCH = 1, PK_APPEND_SOLVE = 2, PK_COMBINE_REFINE = 3, PK_GRAD_REFINE = 4,
-       PK_REFINE_SOLVE = 5, PK_COMBINE = 6, PK_COUNT = 7 };
+enum { PK_GRAD_APPEND = 0, PK_SKETCH = 1, PK_QR_APPEND = 2, PK_STACKED_SOLVE = 3, PK_COMBINE_REFINE = 4,
+       PK_GRAD_REFINE = 5, PK_REFINE_SOLVE = 6, PK_COMBINE = 7, PK_COUNT = 8 };
 
 struct Profiler {
     cudaEvent_t ev[2];
@@ -64,6 +65,13 @@ struct EngineBase {
     virtual cudaError_t step() = 0;
     virtual cudaError_t apply(int which, const void* in, void* out) = 0;
     virtual void* buffer(int which, size_t* elem, int64_t* rows, int64_t* cols_ld) = 0;
+    // copy x_k in the public precision (FP64 for the FP64 form, FP32 otherwise)
+    virtual cudaError_t copy_x(void* out, cudaStream_t st) {
+        size_t es = 0;
+        int64_t rows = 0, ld = 0;
+        void* xs = buffer(SGKS_BUF_X, &es, &rows, &ld);
+        return cudaMemcpyAsync(out, xs, es * (size_t)rows, cudaMemcpyDeviceToDevice, st);
+    }
     Dims D{};
     Small S{};
     int n_refine = 0;
@@ -82,8 +90,13 @@ struct Engine : EngineBase {
     int nbS = 1, nbSb = 8, npSb = 1;
     int* d_err = nullptr;
 
+    T* b_own = nullptr;
+
     cudaError_t setup(const void* bptr) override {
-        B.b = (const T*)bptr;
+        // the kernels (and the captured step graph) always read the handle's own copy of b
+        cudaError_t e0 = cudaMemcpyAsync(b_own, bptr, sizeof(T) * (size_t)D.m, cudaMemcpyDeviceToDevice, st);
+        if (e0 != cudaSuccess) return e0;
+        B.b = b_own;
         host_d = 0;
         // kernels launched below without the `timed` wrapper are counted here
         g_launches.fetch_add(2 + (B.xtrue ? 2 : 0) + 3 + (D.ell - 1) * 8);
@@ -119,7 +132,7 @@ struct Engine : EngineBase {
         // sketched QR of W_0, y_0, refinement, x_0
         for (int j = 0; j < D.ell && e == cudaSuccess; ++j) {
             e = timed(PK_SKETCH, j, [&] { return sketch(); });
-            if (e == cudaSuccess) e = timed(PK_APPEND_SOLVE, j, [&] { return launch_append_solve(D, S, st); });
+            if (e == cudaSuccess) e = small_append(j);
         }
         host_d = D.ell;
         for (int r = 0; r < n_refine && e == cudaSuccess; ++r) e = refine();
@@ -132,11 +145,23 @@ struct Engine : EngineBase {
         return launch_sketch_column<T, V>(D, A, L, B, S, st);
     }
 
+    cudaError_t small_append(int d) {
+        if (D.fast_small) {
+            cudaError_t e = timed(PK_QR_APPEND, d, [&] { return launch_qr_append(D, S, st); });
+            if (e == cudaSuccess) e = timed(PK_STACKED_SOLVE, d, [&] { return launch_stacked_solve(D, S, st); });
+            return e;
+        }
+        return timed(PK_STACKED_SOLVE, d, [&] { return launch_append_solve(D, S, st); });
+    }
+
     cudaError_t refine() {
         const int d = host_d;
         cudaError_t e = timed(PK_COMBINE_REFINE, d, [&] { return launch_combine<T>(D, B, S, 0, st); });
         if (e == cudaSuccess) e = timed(PK_GRAD_REFINE, d, [&] { return launch_gradient<T, V>(D, A, L, B, S, true, st); });
-        if (e == cudaSuccess) e = timed(PK_REFINE_SOLVE, d, [&] { return launch_refine_solve(D, S, st); });
+        if (e == cudaSuccess)
+            e = timed(PK_REFINE_SOLVE, d, [&] {
+                return D.fast_small ? launch_refine_solve2(D, S, st) : launch_refine_solve(D, S, st);
+            });
         return e;
     }
 
@@ -144,7 +169,7 @@ struct Engine : EngineBase {
         const int d = host_d;
         cudaError_t e = timed(PK_GRAD_APPEND, d, [&] { return launch_gradient<T, V>(D, A, L, B, S, false, st); });
         if (e == cudaSuccess) e = timed(PK_SKETCH, d, [&] { return sketch(); });
-        if (e == cudaSuccess) e = timed(PK_APPEND_SOLVE, d, [&] { return launch_append_solve(D, S, st); });
+        if (e == cudaSuccess) e = small_append(d);
         host_d = d + 1;
         for (int r = 0; r < n_refine && e == cudaSuccess; ++r) e = refine();
         if (e == cudaSuccess) e = timed(PK_COMBINE, host_d, [&] { return launch_combine<T>(D, B, S, 1, st); });
@@ -189,6 +214,107 @@ struct Engine : EngineBase {
             case SGKS_BUF_SB: *elem_out = 8; *rows = D.s; *ld = -1; return S.Sb;
             default: return nullptr;
         }
+    }
+};
+
+// fp32x: FP32 storage of W, compensated arithmetic for A W, x, e and the gradient (k_fp32x.cu).
+struct EngineX : Engine<float, float> {
+    BulkX X{};
+
+    cudaError_t sketchx() {
+        if (gSA) return launchx_gaussian_sketch(D, A, L, X, S, gSA, gSL, st);
+        return launchx_sketch_column(D, A, L, X, S, st);
+    }
+
+    cudaError_t refinex() {
+        const int d = host_d;
+        cudaError_t e = timed(PK_COMBINE_REFINE, d, [&] { return launchx_combine(D, X, S, 0, st); });
+        if (e == cudaSuccess) e = timed(PK_GRAD_REFINE, d, [&] { return launchx_gradient(D, A, L, X, S, true, st); });
+        if (e == cudaSuccess)
+            e = timed(PK_REFINE_SOLVE, d, [&] {
+                return D.fast_small ? launch_refine_solve2(D, S, st) : launch_refine_solve(D, S, st);
+            });
+        return e;
+    }
+
+    cudaError_t setup(const void* bptr) override {
+        cudaError_t e = cudaMemcpyAsync(b_own, bptr, sizeof(float) * (size_t)D.m, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+        B.b = b_own;
+        X.b = b_own;
+        host_d = 0;
+        g_launches.fetch_add(2 + (B.xtrue ? 2 : 0) + 3 + (D.ell - 1) * 8);
+        e = cudaMemsetAsync(S.sc, 0, sizeof(DevScalars), st);
+        if (e != cudaSuccess) return e;
+        if (gSA) e = launch_sketch_vector<float>(D, b_own, D.m, D.keyA, gSA, S.partA, nbSb, d_err, st);
+        else e = launchx_sketch_vector(D, b_own, D.m, D.keyA, S.partA, nbSb, st);
+        if (e == cudaSuccess) e = launch_reduce_rows(S.partA, gSA ? 1 : npSb, D.s, D.sketch_scale, S.Sb, st);
+        if (e != cudaSuccess) return e;
+        if (B.xtrue) {
+            e = launch_sqnorm<float>(B.xtrue, D.n, part_setup, nbS, st);
+            if (e == cudaSuccess) e = launch_reduce_rows(part_setup, nbS, 1, 1.0, &S.sc->xt2, st);
+            if (e != cudaSuccess) return e;
+        }
+        float* W = B.W;
+        e = launch_apply<float, float>(D, A, L, SGKS_APPLY_AT, b_own, W, st);
+        if (e == cudaSuccess) e = launch_sqnorm<float>(W, D.n, part_setup, nbS, st);
+        if (e == cudaSuccess) e = launch_normalize<float>(W, D.n, part_setup, nbS, st);
+        for (int j = 1; j < D.ell && e == cudaSuccess; ++j) {
+            float* wj = W + (size_t)j * D.n;
+            e = launch_apply<float, float>(D, A, L, SGKS_APPLY_A, W + (size_t)(j - 1) * D.n, B.tmp_m, st);
+            if (e == cudaSuccess) e = launch_apply<float, float>(D, A, L, SGKS_APPLY_AT, B.tmp_m, wj, st);
+            for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+                e = launch_dots<float>(W, D.n, j, wj, part_setup, nbS, st);
+                if (e == cudaSuccess) e = launch_orth_update<float>(wj, W, D.n, j, part_setup, nbS, st);
+            }
+            if (e == cudaSuccess) e = launch_sqnorm<float>(wj, D.n, part_setup, nbS, st);
+            if (e == cudaSuccess) e = launch_normalize<float>(wj, D.n, part_setup, nbS, st);
+        }
+        if (e != cudaSuccess) return e;
+        for (int j = 0; j < D.ell && e == cudaSuccess; ++j) {
+            e = timed(PK_SKETCH, j, [&] { return sketchx(); });
+            if (e == cudaSuccess) e = small_append(j);
+        }
+        host_d = D.ell;
+        for (int r = 0; r < n_refine && e == cudaSuccess; ++r) e = refinex();
+        if (e == cudaSuccess) e = timed(PK_COMBINE, host_d, [&] { return launchx_combine(D, X, S, 2, st); });
+        return e;
+    }
+
+    cudaError_t step() override {
+        const int d = host_d;
+        cudaError_t e = timed(PK_GRAD_APPEND, d, [&] { return launchx_gradient(D, A, L, X, S, false, st); });
+        if (e == cudaSuccess) e = timed(PK_SKETCH, d, [&] { return sketchx(); });
+        if (e == cudaSuccess) e = small_append(d);
+        host_d = d + 1;
+        for (int r = 0; r < n_refine && e == cudaSuccess; ++r) e = refinex();
+        if (e == cudaSuccess) e = timed(PK_COMBINE, host_d, [&] { return launchx_combine(D, X, S, 1, st); });
+        return e;
+    }
+
+    cudaError_t apply(int which, const void* in, void* out) override {
+        if ((which == SGKS_APPLY_SA || which == SGKS_APPLY_SL) && !gSA) {
+            const bool isA = which == SGKS_APPLY_SA;
+            const int64_t len = isA ? D.m : D.p;
+            const int nb = sketch_blocks(len);
+            cudaError_t e = launchx_sketch_vector(D, (const float*)in, len, isA ? D.keyA : D.keyL,
+                                                  isA ? S.partA : S.partL, nb, st);
+            if (e != cudaSuccess) return e;
+            return launch_reduce_rows(isA ? S.partA : S.partL, nb / 8, D.s, D.sketch_scale, (double*)out, st);
+        }
+        return Engine<float, float>::apply(which, in, out);
+    }
+
+    cudaError_t copy_x(void* out, cudaStream_t stream) override {
+        g_launches.fetch_add(1);
+        return launchx_to_float(X.xs, (float*)out, D.n, stream);
+    }
+
+    void* buffer(int which, size_t* elem_out, int64_t* rows, int64_t* ld) override {
+        *ld = 0;
+        if (which == SGKS_BUF_X) { *elem_out = sizeof(float2); *rows = D.n; return X.xs; }
+        if (which == SGKS_BUF_AW) { *elem_out = sizeof(float2); *rows = D.m; return X.AW; }
+        return Engine<float, float>::buffer(which, elem_out, rows, ld);
     }
 };
 
@@ -243,7 +369,14 @@ static cudaError_t dalloc(sgks_handle* h, P** p, size_t count) {
 template <typename T, typename V>
 static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, const void* b, double lambda,
                         int s, uint64_t seed, const sgks_options& o, int cluster) {
-    Engine<T, V>* E = new (std::nothrow) Engine<T, V>();
+    constexpr bool kF32 = std::is_same<T, float>::value && std::is_same<V, float>::value;
+    const bool xform = kF32 && o.precision == SGKS_PREC_FP32X;
+    Engine<T, V>* E = nullptr;
+    EngineX* EX = nullptr;
+    if constexpr (kF32) {
+        if (xform) E = EX = new (std::nothrow) EngineX();
+    }
+    if (!E) E = new (std::nothrow) Engine<T, V>();
     if (!E) return fail(h, SGKS_ERR_NOMEM, "host allocation failed");
     h->eng = E;
     E->st = h->st;
@@ -266,6 +399,14 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     D.keyA = sketch_key_host_dev(seed, 0);
     D.keyL = sketch_key_host_dev(seed, 1);
     D.cluster = cluster;
+    {
+        int c2 = 0;
+        cudaError_t ef = (o.flags & SGKS_FLAG_GLOBAL_SMALL) ? cudaErrorNotSupported
+                                                            : configure_small_fast(&c2, s, o.ell + o.max_iters);
+        D.fast_small = ef == cudaSuccess ? 1 : 0;
+        D.cluster2 = c2;
+        if (ef != cudaSuccess) cudaGetLastError();
+    }
     D.has_xtrue = o.x_true != nullptr;
 
     DevL& L = E->L;
@@ -313,14 +454,25 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     Bulk<T>& B = E->B;
     Small& S = E->S;
     const size_t dm = D.dmax;
-    T *W, *AW, *x, *xs, *ee, *tm, *tp;
+    T *W = nullptr, *AW = nullptr, *x = nullptr, *xs = nullptr, *ee = nullptr, *tm = nullptr, *tp = nullptr;
     AL(W, dm * D.n);
-    AL(AW, dm * D.m);
-    AL(x, D.n);
-    AL(xs, D.n);
-    AL(ee, D.m);
     AL(tm, D.m);
-    AL(tp, D.p);
+    if (!xform) {
+        AL(AW, dm * D.m);
+        AL(x, D.n);
+        AL(xs, D.n);
+        AL(ee, D.m);
+        AL(tp, D.p);
+    } else {
+        AL(EX->X.AW, dm * D.m);
+        AL(EX->X.x, D.n);
+        AL(EX->X.xs, D.n);
+        AL(EX->X.e, D.m);
+        AL(EX->X.tmp_p, D.p);
+        EX->X.W = (float*)W;
+        EX->X.tmp_m = (float*)tm;
+        EX->X.xtrue = (const float*)o.x_true;
+    }
     B.W = W; B.AW = AW; B.x = x; B.xs = xs; B.e = ee; B.tmp_m = tm; B.tmp_p = tp;
     B.b = (const T*)b;
     B.xtrue = (const T*)o.x_true;
@@ -328,10 +480,18 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     AL(S.QL, dm * s);
     AL(S.RA, dm * dm);
     AL(S.RL, dm * dm);
-    AL(S.G, 4 * dm * dm);
+    if (D.fast_small) {
+        AL(S.QT, 2 * dm * dm);
+        AL(S.Xr, dm * dm);
+        AL(S.z, dm);
+        AL(S.qr_out, 8);
+    } else {
+        AL(S.G, 4 * dm * dm);
+        AL(S.zf, 2 * dm + 2);
+    }
     AL(S.X, dm * dm);
     AL(S.Tm, dm * dm);
-    AL(S.zf, 2 * dm + 2);
+    AL(E->b_own, D.m);
     AL(S.dA, dm);
     AL(S.y, dm);
     AL(S.Sb, s);
@@ -346,7 +506,8 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     AL(E->d_err, 1);
     if (e != cudaSuccess) return fail(h, SGKS_ERR_NOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
     e = cudaMemsetAsync(S.y, 0, sizeof(double) * dm, h->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(xs, 0, sizeof(T) * D.n, h->st);
+    if (e == cudaSuccess && xs) e = cudaMemsetAsync(xs, 0, sizeof(T) * D.n, h->st);
+    if (e == cudaSuccess && xform) e = cudaMemsetAsync(EX->X.xs, 0, 8 * D.n, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(E->d_err, 0, sizeof(int), h->st);
 
     // operator
@@ -479,7 +640,8 @@ static int validate(const sgks_op* A, const sgks_reg* L, const void* b, double l
     if (o.max_iters < 1 || o.ell < 1 || o.ell > 8) return bad("need max_iters >= 1 and 1 <= ell <= 8");
     if (o.ell > A->n) return bad("ell must not exceed n");
     if (s > kMaxS || s < o.ell + o.max_iters) return bad("sketch_rows must satisfy ell + max_iters <= s <= 2048");
-    if (o.precision != SGKS_PREC_FP64 && o.precision != SGKS_PREC_FP32) return bad("unknown precision");
+    if (o.precision != SGKS_PREC_FP64 && o.precision != SGKS_PREC_FP32 && o.precision != SGKS_PREC_FP32X)
+        return bad("unknown precision");
     if (o.sketch_kind == SGKS_SKETCH_SPARSE_SIGN) {
         if (o.zeta < 1 || o.zeta > kMaxZeta || o.zeta > s) return bad("zeta must satisfy 1 <= zeta <= min(16, s)");
     } else if (o.sketch_kind == SGKS_SKETCH_GAUSSIAN) {
@@ -529,7 +691,7 @@ int sgks_create(sgks_handle** hp, const sgks_op* A, const sgks_reg* L, const voi
         return rc;
     }
     join_in(h);
-    if (o.precision == SGKS_PREC_FP32)
+    if (o.precision == SGKS_PREC_FP32 || o.precision == SGKS_PREC_FP32X)
         rc = build_engine<float, float>(h, A, L, b, lambda, sketch_rows, seed, o, cluster);
     else if (A->kind == SGKS_OP_CSR && A->val_dtype == SGKS_F64)
         rc = build_engine<double, double>(h, A, L, b, lambda, sketch_rows, seed, o, cluster);
@@ -621,10 +783,7 @@ int sgks_solve(sgks_handle* h, int32_t iters, double tol, void* x_out, sgks_repo
     g_launches.fetch_add(h->graph_launches * iters);
     h->steps_since_setup += iters;
     E->host_d += iters;
-    size_t es = 0;
-    int64_t rows = 0, ld = 0;
-    void* xs = E->buffer(SGKS_BUF_X, &es, &rows, &ld);
-    if (e == cudaSuccess && x_out) e = cudaMemcpyAsync(x_out, xs, es * (size_t)rows, cudaMemcpyDeviceToDevice, h->st);
+    if (e == cudaSuccess && x_out) e = E->copy_x(x_out, h->st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->sc_host, E->S.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);

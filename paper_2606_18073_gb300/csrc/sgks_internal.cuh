@@ -367,15 +367,30 @@ struct Bulk {                 // solver-precision arrays
     T* x;                     // working x = W y (n)
     T* xs;                    // last accepted iterate x_k (n)
     T* e;                     // A x - b (m)
-    const T* b;               // (m), caller-owned
+    const T* b;               // (m), handle-owned copy of the right-hand side
     const T* xtrue;           // (n) or null
     T* tmp_m;                 // scratch (m)
     T* tmp_p;                 // scratch (p)
 };
 
+// fp32x form: FP32 storage of W and b, float-float pairs (hi, lo) for A W, x, e.
+struct BulkX {
+    float* W;                 // [dmax][n]
+    float2* AW;               // [dmax][m]
+    float2* x;                // working x = W y
+    float2* xs;               // last accepted iterate x_k
+    float2* e;                // A x - b
+    const float* b;           // handle-owned copy
+    const float* xtrue;       // or null
+    float* tmp_m;
+    double* tmp_p;            // L w for the Gaussian sketch
+};
+
 struct Small {                // FP64 state of the sketched QR and projected solve
     double *QA, *QL, *RA, *RL;
     double *G, *X, *Tm, *zf, *dA, *y, *Sb;
+    double *QT, *Xr, *z;      // fast path: orthonormal factor of [R_A; sqrt(lam) R_L], row-major T^{-1}, z
+    double *qr_out;           // [8] per-launch results of k_qr_append (rho, breakdown, finite, d_A entry)
     double *partA, *partL;    // sketch partials [nb][s]
     double *gpart;            // refinement partials [nb][dmax]
     double *kapart;           // combine-kernel norm partials [nb][4]
@@ -391,7 +406,9 @@ struct Dims {
     int npA, npL;             // sketch partials (one per cluster of 8 blocks; 1 for the dense sketch)
     int nbG;                  // blocks of the gradient kernels (n / kThreads tiles)
     int nbX, nbE;             // blocks of the combine kernel (x rows, e rows)
-    int cluster;              // CTAs of the small kernels
+    int cluster;              // CTAs of the small kernels (global-memory fallback path)
+    int cluster2;             // CTAs per cluster of the fast small path
+    int fast_small;           // 1: k_qr_append + k_stacked_solve; 0: k_append_solve (fallback)
     int sketch_kind;
     double sketch_scale;      // 1/sqrt(zeta) for sparse-sign, 1 for Gaussian
     uint64_t keyA, keyL;
@@ -417,8 +434,24 @@ template <typename T>
 cudaError_t launch_combine(const Dims& D, const Bulk<T>& B, const Small& S, int mode, cudaStream_t st);
 cudaError_t launch_append_solve(const Dims& D, const Small& S, cudaStream_t st);
 cudaError_t launch_refine_solve(const Dims& D, const Small& S, cudaStream_t st);
+cudaError_t launch_qr_append(const Dims& D, const Small& S, cudaStream_t st);
+cudaError_t launch_stacked_solve(const Dims& D, const Small& S, cudaStream_t st);
+cudaError_t launch_refine_solve2(const Dims& D, const Small& S, cudaStream_t st);
+cudaError_t configure_small_fast(int* cluster_out, int s, int dm);
 cudaError_t launch_reduce_rows(const double* part, int nb, int len, double scale, double* out, cudaStream_t st);
 cudaError_t configure_cluster_kernels(int* cluster_out, int s, int dmax);
+
+// fp32x form (k_fp32x.cu)
+cudaError_t launchx_sketch_column(const Dims& D, const DevA<float, float>& A, const DevL& L, const BulkX& B,
+                                  const Small& S, cudaStream_t st);
+cudaError_t launchx_sketch_vector(const Dims& D, const float* v, int64_t len, uint64_t key, double* part, int nb,
+                                  cudaStream_t st);
+cudaError_t launchx_combine(const Dims& D, const BulkX& B, const Small& S, int mode, cudaStream_t st);
+cudaError_t launchx_gradient(const Dims& D, const DevA<float, float>& A, const DevL& L, const BulkX& B,
+                             const Small& S, bool refine, cudaStream_t st);
+cudaError_t launchx_to_float(const float2* in, float* out, int64_t n, cudaStream_t st);
+cudaError_t launchx_gaussian_sketch(const Dims& D, const DevA<float, float>& A, const DevL& L, const BulkX& B,
+                                    const Small& S, const double* SA, const double* SL, cudaStream_t st);
 
 // setup helpers (sgks_setup.cu)
 template <typename T, typename V>

@@ -127,9 +127,10 @@ class Solver:
                  max_iters: int = 100, ell: int = 3, n_refine: int = 0, precision: str = "fp64",
                  sketch: str = "sparse_sign", zeta: int = 8, cgs_passes: int = 2,
                  gauss_SA: Optional[torch.Tensor] = None, gauss_SL: Optional[torch.Tensor] = None,
-                 x_true: Optional[torch.Tensor] = None, stream=None):
+                 x_true: Optional[torch.Tensor] = None, stream=None, flags: int = 0):
         self._lib = L.load()
-        self.dtype = torch.float32 if precision == "fp32" else torch.float64
+        self.precision = precision
+        self.dtype = torch.float32 if precision in ("fp32", "fp32x") else torch.float64
         for nm, t in (("b", b), ("x_true", x_true)):
             _need_cuda(t, nm)
             if t is not None and t.dtype != self.dtype:
@@ -144,9 +145,10 @@ class Solver:
         self.max_iters = max_iters
         o = L.sgks_options()
         o.max_iters, o.ell, o.n_refine, o.zeta, o.cgs_passes = max_iters, ell, n_refine, zeta, cgs_passes
-        o.precision = L.SGKS_PREC_FP32 if precision == "fp32" else L.SGKS_PREC_FP64
+        o.precision = {"fp64": L.SGKS_PREC_FP64, "fp32": L.SGKS_PREC_FP32, "fp32x": L.SGKS_PREC_FP32X}[precision]
         o.sketch_kind = L.SGKS_SKETCH_GAUSSIAN if sketch == "gaussian" else L.SGKS_SKETCH_SPARSE_SIGN
         o.gauss_SA, o.gauss_SL, o.x_true = _ptr(gauss_SA), _ptr(gauss_SL), _ptr(x_true)
+        o.flags = int(flags)
         self._stream = torch.cuda.current_stream(b.device).cuda_stream if stream is None else stream
         self.device = b.device
         h = C.c_void_p()
@@ -201,6 +203,10 @@ class Solver:
         return out[: n.value // out.element_size()]
 
     def x(self):
+        """Current iterate x_k; for fp32x the float-float pairs are summed in float64."""
+        if self.precision == "fp32x":
+            v = self.buffer(L.SGKS_BUF_X, 2 * self.n, torch.float32).view(self.n, 2).double()
+            return v[:, 0] + v[:, 1]
         return self.buffer(L.SGKS_BUF_X, self.n, self.dtype)
 
     def apply(self, which: int, x: torch.Tensor, out: torch.Tensor):
@@ -252,7 +258,7 @@ def device_inputs(problem, precision: Optional[str] = None, device="cuda", trans
     import numpy as np
 
     prec = precision or problem.precision
-    dt = torch.float32 if prec == "fp32" else torch.float64
+    dt = torch.float32 if prec in ("fp32", "fp32x") else torch.float64
     A = problem.A
     if A.kind == "csr":
         op = CSR(torch.from_numpy(np.ascontiguousarray(A.row_ptr)).to(device),
