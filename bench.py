@@ -54,6 +54,26 @@ def dist_env():
     return ws, rank, local
 
 
+# ------------------------------------------------------------------------- multi-rank
+def max_over_ranks(value: float, device=None) -> float:
+    """Max of a per-rank scalar over all ranks (the job time is the slowest replica's).
+
+    Replicas only: sGKS has no exchange step, so each rank solves its own right-hand side and
+    this reduction of one timing scalar is the only cross-rank communication."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, ms_max: float, world_size: int) -> float:
+    """Whole-job units per second: all ranks' units over the slowest rank's time."""
+    return world_size * units_per_rank / (ms_max / 1e3)
+
+
 # ----------------------------------------------------------------------------- workload
 def make_workload(name, seed):
     from workloads import make_problem
@@ -245,11 +265,9 @@ def main():
     ms = sum(a.elapsed_time(b) for a, b in evs)
     if ws > 1:
         dist.barrier()
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     clocks = clk.stop()
-    value = ws * args.steps * iters / (ms / 1e3)
+    value = job_throughput(args.steps * iters, ms, ws)
 
     # ---- e2e through the public API with host buffers (pinned), copies inside the timed step
     dt = kw["b"].dtype
@@ -269,11 +287,8 @@ def main():
         b.record(stream)
         torch.cuda.synchronize(dev)
         e2e_ms += a.elapsed_time(b)
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = ws * args.steps * iters / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e2e_ms, dev)
+    e2e_value = job_throughput(args.steps * iters, e2e_ms, ws)
     elem = b_host.element_size()
 
     line = {
@@ -339,6 +354,14 @@ def extras(args, G, P, kw, S, iters, dev, flush):
     S64.close()
     target = 1.01 * h64["rre_last"]
     out["fp64_plain"] = {"iters_per_s": iters / (t64 / 1e3), "ms_per_solve": t64, "final_rre": h64["rre_last"]}
+    # fp32x: FP32 storage with compensated arithmetic, same refinement steps as the headline form
+    Px = make_workload(args.config, seed=0)
+    kwx = G.device_inputs(Px, "fp32x", device=dev)
+    Sx = G.Solver(**kwx)
+    tx, hx = time_solve(G, Sx, kwx["b"], iters, flush, dev)
+    Sx.close()
+    out["fp32x_refined"] = {"iters_per_s": iters / (tx / 1e3), "ms_per_solve": tx, "final_rre": hx["rre_last"],
+                            "time_to_target_ms": time_to_rre(tx, hx["rre"], target, iters)}
     out["time_to_rre"] = {
         "target_rre": target,
         "fp64_plain_ms": time_to_rre(t64, h64["rre"], target, iters),

@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         list(ex.map(run, jobs))
     objs = [os.path.join(objdir, s.replace(".cu", ".o")) for s in SOURCES]
     if force or jobs or _stale(LIB, objs):
-        run([nvcc, *ARCH, "-shared", *objs, "-o", LIB + ".tmp"])
+        run([nvcc, *ARCH, "-shared", "-Xlinker", "--no-undefined", *objs, "-o", LIB + ".tmp"])
         os.replace(LIB + ".tmp", LIB)
     return LIB
 

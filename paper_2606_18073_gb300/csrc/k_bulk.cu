@@ -97,7 +97,7 @@ __global__ void __cluster_dims__(kGradCluster, 1, 1) __launch_bounds__(kThreads)
                 const int rr = lane + 32 * k;
                 if (rr < rows) a += wc[rr] * rt[rr];
             }
-            const double s = warp_sum((double)a);
+            const double s = warp_sum_acc(a);
             if (lane == 0) gacc[j] += s;
         }
         __syncthreads();
@@ -106,9 +106,10 @@ __global__ void __cluster_dims__(kGradCluster, 1, 1) __launch_bounds__(kThreads)
     if (cl.block_rank() == 0) {
         double* out = S.gpart + (size_t)(blockIdx.x / kGradCluster) * D.dmax;
         for (int j = threadIdx.x; j < d; j += kThreads) {
-            double v = gacc[j];
-            for (int r = 1; r < kGradCluster; ++r) v += cl.map_shared_rank(gacc, r)[j];
-            out[j] = v;
+            double v[kGradCluster];
+#pragma unroll
+            for (int r = 0; r < kGradCluster; ++r) v[r] = cl.map_shared_rank(gacc, r)[j];
+            out[j] = tree_sumd<kGradCluster>(v);
         }
     }
     cl.sync();
@@ -121,20 +122,26 @@ cudaError_t launch_gradient(const Dims& D, const DevA<T, V>& A, const DevL& L, c
     if (!refine) {
         const int64_t tiles = (D.n + kThreads - 1) / kThreads;
         const int blocks = (int)(tiles < 8 * 152 ? tiles : 8 * 152);
-        if (warpa)
+        if (warpa) {
+            carveout_once((const void*)k_gradient_append<T, V, true>);
             k_gradient_append<T, V, true><<<blocks, kThreads, 0, st>>>(D, A, L, B, S);
-        else
+        }
+        else {
+            carveout_once((const void*)k_gradient_append<T, V, false>);
             k_gradient_append<T, V, false><<<blocks, kThreads, 0, st>>>(D, A, L, B, S);
+        }
         return cudaGetLastError();
     }
     const size_t smem = (size_t)D.dmax * sizeof(double) + kThreads * sizeof(T) + 128 * sizeof(T);
     if (warpa) {
         auto k = k_gradient_refine<T, V, true>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        carveout_once((const void*)k);
         k<<<D.nbG, kThreads, smem, st>>>(D, A, L, B, S);
     } else {
         auto k = k_gradient_refine<T, V, false>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        carveout_once((const void*)k);
         k<<<D.nbG, kThreads, smem, st>>>(D, A, L, B, S);
     }
     return cudaGetLastError();
@@ -154,7 +161,7 @@ __global__ void __launch_bounds__(kThreads) k_combine(Dims D, Bulk<T> B, Small S
     const int d = sc->d;
     for (int j = threadIdx.x; j < d; j += kThreads) ys[j] = (T)S.y[j];
     __syncthreads();
-    double q0 = 0.0, q1 = 0.0, q2 = 0.0;
+    T q0 = T(0), q1 = T(0), q2 = T(0);   // per-element statistics in the solver precision
     const int tid = threadIdx.x;
     if ((int)blockIdx.x < D.nbX) {
         const int64_t i = (int64_t)blockIdx.x * kThreads + tid;
@@ -173,11 +180,11 @@ __global__ void __launch_bounds__(kThreads) k_combine(Dims D, Bulk<T> B, Small S
             B.x[i] = xv;
             if (mode >= 1) {
                 const T old = B.xs[i];
-                const double df = (double)xv - (double)old;
+                const T df = xv - old;
                 q0 = df * df;
-                q1 = (double)old * (double)old;
+                q1 = old * old;
                 if (B.xtrue) {
-                    const double er = (double)xv - (double)B.xtrue[i];
+                    const T er = xv - B.xtrue[i];
                     q2 = er * er;
                 }
                 B.xs[i] = xv;
@@ -200,17 +207,12 @@ __global__ void __launch_bounds__(kThreads) k_combine(Dims D, Bulk<T> B, Small S
         }
     }
     if (mode == 0) return;
-    // block partials of the three squared norms
-    q0 = warp_sum(q0);
-    q1 = warp_sum(q1);
-    q2 = warp_sum(q2);
-    if (lane_id() == 0) { red[0][warp_id()] = q0; red[1][warp_id()] = q1; red[2][warp_id()] = q2; }
+    // block partials of the three squared norms: warp sums in the solver precision, the
+    // 8 warp values combined in FP64 by three threads
+    const T w0 = warp_sum(q0), w1 = warp_sum(q1), w2 = warp_sum(q2);
+    if (lane_id() == 0) { red[0][warp_id()] = (double)w0; red[1][warp_id()] = (double)w1; red[2][warp_id()] = (double)w2; }
     __syncthreads();
-    if (tid < 3) {
-        double t = 0.0;
-        for (int w = 0; w < kWarps; ++w) t += red[tid][w];
-        S.kapart[(size_t)blockIdx.x * 3 + tid] = t;
-    }
+    if (tid < 3) S.kapart[(size_t)blockIdx.x * 3 + tid] = tree_sumd<kWarps>(red[tid]);
     __threadfence();
     __syncthreads();
     if (tid == 0) am_last = (atomicAdd(&sc->ka_done, 1) == (int)gridDim.x - 1);
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(kThreads) k_combine(Dims D, Bulk<T> B, Small S
     if (!am_last) return;
     __threadfence();
     // last CTA: fixed-order reduction of the partials (warp q sums quantity q)
-    if (warp_id() < 3) {
+    if (warp_id() < 3) {   // warp q reduces quantity q over the CTA partials (fixed order)
         const int q = warp_id();
         double t = 0.0;
         for (int b = lane_id(); b < (int)gridDim.x; b += 32) t += __ldcg(S.kapart + (size_t)b * 3 + q);
@@ -260,6 +262,7 @@ cudaError_t launch_combine(const Dims& D, const Bulk<T>& B, const Small& S, int 
     const size_t smem = (size_t)D.dmax * sizeof(T);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_combine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    carveout_once((const void*)k_combine<T>);
     k_combine<T><<<D.nbX + D.nbE, kThreads, smem, st>>>(D, B, S, mode);
     return cudaGetLastError();
 }

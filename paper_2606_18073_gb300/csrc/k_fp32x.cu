@@ -250,118 +250,6 @@ __device__ __forceinline__ double xltl_row(const DevL& L, int64_t i, const float
 }
 
 // ------------------------------------------------------------------------------- kernels
-template <int ZMAX>
-__device__ bool scatter_slab_d(uint64_t key, int s, int zeta, int64_t j, bool valid, double val, double* accw,
-                               double* stw);
-
-// K1 (fp32x): u = A w accumulated with Dot2 -> AW column (float-float); S_A u and S_L L w
-// scattered into FP64 warp accumulators.
-template <int ZMAX, bool WARPA>
-__global__ void __cluster_dims__(kXCluster, 1, 1) __launch_bounds__(kThreads)
-    kx_sketch_column(Dims D, DevA<float, float> A, DevL L, BulkX B, Small S) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* blk = reinterpret_cast<double*>(smem_raw);
-    double* acc = blk + D.s;
-    double* stage = acc + (size_t)kWarps * D.s;
-    float* psf_s = reinterpret_cast<float*>(stage + kWarps * 32);
-    const DevScalars* sc = S.sc;
-    if (sc->stop) return;
-    const int d = sc->d;
-    if (d >= D.dmax) return;
-    const bool isA = (int)blockIdx.x < D.nbA;
-    const int blk_id = isA ? blockIdx.x : blockIdx.x - D.nbA;
-    const int nblk = isA ? D.nbA : D.nbL;
-    const int64_t rows = isA ? D.m : D.p;
-    const uint64_t key = isA ? D.keyA : D.keyL;
-    const float* w = B.W + (size_t)d * D.n;
-    float2* u_out = B.AW + (size_t)d * D.m;
-    const int lane = lane_id(), warp = warp_id();
-    for (int i = threadIdx.x; i < kWarps * D.s; i += kThreads) acc[i] = 0.0;
-    if (!WARPA && isA)
-        for (int i = threadIdx.x; i < A.kh * A.kw; i += kThreads) psf_s[i] = A.psf[i];
-    __syncthreads();
-    double* accw = acc + (size_t)warp * D.s;
-    double* stw = stage + warp * 32;
-    bool ok = true;
-    const int64_t nslab = (rows + 31) / 32;
-    for (int64_t sl = (int64_t)blk_id * kWarps + warp; sl < nslab; sl += (int64_t)nblk * kWarps) {
-        const int64_t base = sl * 32, j = base + lane;
-        const bool valid = j < rows;
-        double val = 0.0;
-        if (isA) {
-            float2 uv = make_float2(0.f, 0.f);
-            if (WARPA) {
-                for (int r = 0; r < 32; ++r) {
-                    const int64_t jj = base + r;
-                    if (jj >= rows) break;
-                    const float2 t = xa_row_warp(A, jj, w).value();
-                    if (lane == r) uv = t;
-                }
-            } else if (valid) {
-                uv = xa_row_conv(A, psf_s, j, w).value();
-            }
-            if (valid) {
-                u_out[j] = uv;
-                val = dval(uv);
-            }
-        } else if (valid) {
-            val = xl_row(L, j, w);
-        }
-        ok &= scatter_slab_d<ZMAX>(key, D.s, D.zeta, j, valid, val, accw, stw);
-    }
-    if (!ok) S.sc->status = ST_SKETCH;
-    // block + cluster reduction of the FP64 warp accumulators
-    cg::cluster_group cl = cg::this_cluster();
-    __syncthreads();
-    for (int i = threadIdx.x; i < D.s; i += kThreads) {
-        double v = 0.0;
-#pragma unroll
-        for (int ww = 0; ww < kWarps; ++ww) v += acc[ww * D.s + i];
-        blk[i] = v;
-    }
-    cl.sync();
-    if (cl.block_rank() == 0) {
-        double* out = (isA ? S.partA : S.partL) + (size_t)(blk_id / kXCluster) * D.s;
-        for (int i = threadIdx.x; i < D.s; i += kThreads) {
-            double v = blk[i];
-            for (int r = 1; r < kXCluster; ++r) v += cl.map_shared_rank(blk, r)[i];
-            out[i] = v;
-        }
-    }
-    cl.sync();
-}
-
-template <int ZMAX>
-__device__ bool scatter_slab_d(uint64_t key, int s, int zeta, int64_t j, bool valid, double val, double* accw,
-                               double* stw) {
-    const int lane = lane_id();
-    int rows[ZMAX];
-    uint32_t neg = 0u;
-    bool ok = true;
-    if (valid) ok = sparse_sign_column<ZMAX>(key, (uint64_t)j, s, zeta, rows, neg);
-#pragma unroll
-    for (int k = 0; k < ZMAX; ++k) {
-        if (k >= zeta) break;
-        const int r = valid ? rows[k] : -1;
-        const double v = ((neg >> k) & 1u) ? -val : val;
-        const unsigned peers = __match_any_sync(0xffffffffu, r);
-        stw[lane] = v;
-        __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) {
-            double sum = 0.0;
-            unsigned mm = peers;
-            while (mm) {
-                const int b = __ffs(mm) - 1;
-                sum += stw[b];
-                mm &= mm - 1u;
-            }
-            accw[r] += sum;
-        }
-        __syncwarp();
-    }
-    return ok;
-}
-
 // Combine (fp32x): x = W y, e = (A W) y - b with Dot2; RC / RRE record in mode 1, RRE_0 in mode 2.
 __global__ void __launch_bounds__(kThreads) kx_combine(Dims D, BulkX B, Small S, int mode) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -542,41 +430,6 @@ __global__ void __cluster_dims__(kXCluster, 1, 1) __launch_bounds__(kThreads)
     cl.sync();
 }
 
-// Sketch of an FP32 vector with FP64 accumulation (S_A b at the setup of the fp32x form).
-template <int ZMAX>
-__global__ void __cluster_dims__(kXCluster, 1, 1) __launch_bounds__(kThreads)
-    kx_sketch_vector(const float* __restrict__ v, int64_t len, uint64_t key, int s, int zeta, double* part) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* blk = reinterpret_cast<double*>(smem_raw);
-    double* acc = blk + s;
-    double* stage = acc + (size_t)kWarps * s;
-    const int lane = lane_id(), warp = warp_id();
-    for (int i = threadIdx.x; i < kWarps * s; i += kThreads) acc[i] = 0.0;
-    __syncthreads();
-    const int64_t nslab = (len + 31) / 32;
-    for (int64_t sl = (int64_t)blockIdx.x * kWarps + warp; sl < nslab; sl += (int64_t)gridDim.x * kWarps) {
-        const int64_t j = sl * 32 + lane;
-        const bool valid = j < len;
-        scatter_slab_d<ZMAX>(key, s, zeta, j, valid, valid ? (double)v[j] : 0.0, acc + (size_t)warp * s,
-                             stage + warp * 32);
-    }
-    cg::cluster_group cl = cg::this_cluster();
-    __syncthreads();
-    for (int i = threadIdx.x; i < s; i += kThreads) {
-        double t = 0.0;
-        for (int ww = 0; ww < kWarps; ++ww) t += acc[ww * s + i];
-        blk[i] = t;
-    }
-    cl.sync();
-    if (cl.block_rank() == 0)
-        for (int i = threadIdx.x; i < s; i += kThreads) {
-            double t = blk[i];
-            for (int r = 1; r < kXCluster; ++r) t += cl.map_shared_rank(blk, r)[i];
-            part[(size_t)(blockIdx.x / kXCluster) * s + i] = t;
-        }
-    cl.sync();
-}
-
 // Gaussian sketch (fp32x): u = A w (float-float, into the A W column) and t = L w (FP64), then
 // dense FP64 products with S_A and S_L.
 template <bool WARPA>
@@ -633,15 +486,15 @@ __global__ void kx_dense_sketch_pair(Dims D, BulkX B, Small S, const double* __r
     if (lane_id() == 0) (isA ? S.partA : S.partL)[r] = a;
 }
 
+static int x_apply_blocks(const Dims& D);
+
 cudaError_t launchx_gaussian_sketch(const Dims& D, const DevA<float, float>& A, const DevL& L, const BulkX& B,
                                     const Small& S, const double* SA, const double* SL, cudaStream_t st) {
-    const int64_t slabs = (D.m + 31) / 32 + (D.p + 31) / 32;
-    int64_t blocks = (slabs + kWarps - 1) / kWarps;
-    if (blocks > 8 * 152) blocks = 8 * 152;
-    if (A.kind == SGKS_OP_CONV2D) kx_apply_column<false><<<(int)blocks, kThreads, 0, st>>>(D, A, L, B, S);
-    else kx_apply_column<true><<<(int)blocks, kThreads, 0, st>>>(D, A, L, B, S);
+    if (A.kind == SGKS_OP_CONV2D) { carveout_once((const void*)kx_apply_column<false>); kx_apply_column<false><<<x_apply_blocks(D), kThreads, 0, st>>>(D, A, L, B, S); }
+    else { carveout_once((const void*)kx_apply_column<true>); kx_apply_column<true><<<x_apply_blocks(D), kThreads, 0, st>>>(D, A, L, B, S); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    carveout_once((const void*)kx_dense_sketch_pair);
     kx_dense_sketch_pair<<<(2 * D.s + kWarps - 1) / kWarps, kThreads, 0, st>>>(D, B, S, SA, SL);
     return cudaGetLastError();
 }
@@ -653,48 +506,39 @@ __global__ void kx_to_float(const float2* __restrict__ in, float* out, int64_t n
 
 cudaError_t launchx_to_float(const float2* in, float* out, int64_t n, cudaStream_t st) {
     const int64_t blocks = (n + 255) / 256 < 2432 ? (n + 255) / 256 : 2432;
+    carveout_once((const void*)kx_to_float);
     kx_to_float<<<(int)(blocks > 0 ? blocks : 1), 256, 0, st>>>(in, out, n);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------ launchers
-static size_t x_sketch_smem(int s) { return sizeof(double) * ((size_t)s + (size_t)kWarps * s + kWarps * 32) + 128 * 4; }
-
 template <typename K>
 static void maybe_smem(K k, size_t bytes) {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-cudaError_t launchx_sketch_column(const Dims& D, const DevA<float, float>& A, const DevL& L, const BulkX& B,
-                                  const Small& S, cudaStream_t st) {
-    const size_t smem = x_sketch_smem(D.s);
-    const bool warpa = A.kind != SGKS_OP_CONV2D;
-    if (D.zeta <= 8) {
-        if (warpa) { maybe_smem(kx_sketch_column<8, true>, smem); kx_sketch_column<8, true><<<D.nbA + D.nbL, kThreads, smem, st>>>(D, A, L, B, S); }
-        else { maybe_smem(kx_sketch_column<8, false>, smem); kx_sketch_column<8, false><<<D.nbA + D.nbL, kThreads, smem, st>>>(D, A, L, B, S); }
-    } else {
-        if (warpa) { maybe_smem(kx_sketch_column<16, true>, smem); kx_sketch_column<16, true><<<D.nbA + D.nbL, kThreads, smem, st>>>(D, A, L, B, S); }
-        else { maybe_smem(kx_sketch_column<16, false>, smem); kx_sketch_column<16, false><<<D.nbA + D.nbL, kThreads, smem, st>>>(D, A, L, B, S); }
-    }
-    return cudaGetLastError();
+static int x_apply_blocks(const Dims& D) {
+    const int64_t slabs = (D.m + 31) / 32 + (D.p + 31) / 32;
+    int64_t blocks = (slabs + kWarps - 1) / kWarps;
+    if (blocks > 8 * 152) blocks = 8 * 152;
+    return (int)(blocks < 1 ? 1 : blocks);
 }
 
-cudaError_t launchx_sketch_vector(const Dims& D, const float* v, int64_t len, uint64_t key, double* part, int nb,
-                                  cudaStream_t st) {
-    const size_t smem = sizeof(double) * ((size_t)D.s + (size_t)kWarps * D.s + kWarps * 32);
-    if (D.zeta <= 8) {
-        maybe_smem(kx_sketch_vector<8>, smem);
-        kx_sketch_vector<8><<<nb, kThreads, smem, st>>>(v, len, key, D.s, D.zeta, part);
-    } else {
-        maybe_smem(kx_sketch_vector<16>, smem);
-        kx_sketch_vector<16><<<nb, kThreads, smem, st>>>(v, len, key, D.s, D.zeta, part);
-    }
-    return cudaGetLastError();
+// K1 (fp32x): u = A w with Dot2 into the A W column (float-float), L w in FP64, then the sparse
+// sketch gathers in FP64.
+cudaError_t launchx_sketch_column(const Dims& D, const DevA<float, float>& A, const DevL& L, const BulkX& B,
+                                  const Small& S, const SketchCSR& SK, cudaStream_t st) {
+    if (A.kind == SGKS_OP_CONV2D) { carveout_once((const void*)kx_apply_column<false>); kx_apply_column<false><<<x_apply_blocks(D), kThreads, 0, st>>>(D, A, L, B, S); }
+    else { carveout_once((const void*)kx_apply_column<true>); kx_apply_column<true><<<x_apply_blocks(D), kThreads, 0, st>>>(D, A, L, B, S); }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launchx_sketch_gather_col(D, B.AW, B.tmp_p, SK, S, st);
 }
 
 cudaError_t launchx_combine(const Dims& D, const BulkX& B, const Small& S, int mode, cudaStream_t st) {
     const size_t smem = (size_t)D.dmax * sizeof(float2);
     maybe_smem(kx_combine, smem);
+    carveout_once((const void*)kx_combine);
     kx_combine<<<D.nbX + D.nbE, kThreads, smem, st>>>(D, B, S, mode);
     return cudaGetLastError();
 }
@@ -705,13 +549,13 @@ cudaError_t launchx_gradient(const Dims& D, const DevA<float, float>& A, const D
     if (!refine) {
         const int64_t tiles = (D.n + kThreads - 1) / kThreads;
         const int blocks = (int)(tiles < 8 * 152 ? tiles : 8 * 152);
-        if (warpa) kx_gradient_append<true><<<blocks, kThreads, 0, st>>>(D, A, L, B, S);
-        else kx_gradient_append<false><<<blocks, kThreads, 0, st>>>(D, A, L, B, S);
+        if (warpa) { carveout_once((const void*)kx_gradient_append<true>); kx_gradient_append<true><<<blocks, kThreads, 0, st>>>(D, A, L, B, S); }
+        else { carveout_once((const void*)kx_gradient_append<false>); kx_gradient_append<false><<<blocks, kThreads, 0, st>>>(D, A, L, B, S); }
         return cudaGetLastError();
     }
     const size_t smem = (size_t)D.dmax * sizeof(double) + kThreads * sizeof(float2) + 128 * sizeof(float);
-    if (warpa) { maybe_smem(kx_gradient_refine<true>, smem); kx_gradient_refine<true><<<D.nbG, kThreads, smem, st>>>(D, A, L, B, S); }
-    else { maybe_smem(kx_gradient_refine<false>, smem); kx_gradient_refine<false><<<D.nbG, kThreads, smem, st>>>(D, A, L, B, S); }
+    if (warpa) { maybe_smem(kx_gradient_refine<true>, smem); carveout_once((const void*)kx_gradient_refine<true>); kx_gradient_refine<true><<<D.nbG, kThreads, smem, st>>>(D, A, L, B, S); }
+    else { maybe_smem(kx_gradient_refine<false>, smem); carveout_once((const void*)kx_gradient_refine<false>); kx_gradient_refine<false><<<D.nbG, kThreads, smem, st>>>(D, A, L, B, S); }
     return cudaGetLastError();
 }
 

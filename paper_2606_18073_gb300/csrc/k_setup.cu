@@ -8,9 +8,27 @@
 //  * a deterministic CSR transpose: column counts, exclusive scan, slot fill, then each column
 //    is put in ascending row order by rank sort (keys are distinct), so A^T e sums in the same
 //    row order on every run.
+#include <stdlib.h>
+
+#include <mutex>
+#include <set>
+
 #include "sgks_internal.cuh"
 
 namespace sgks {
+
+void carveout_once(const void* kernel) {
+    static std::mutex mu;
+    static std::set<const void*> done;
+    static int pref = [] {
+        const char* e = getenv("SGKS_CARVEOUT");
+        return e ? atoi(e) : -1;
+    }();
+    if (pref < 0) return;
+    std::lock_guard<std::mutex> g(mu);
+    if (done.insert(kernel).second)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pref);
+}
 
 // ---------------------------------------------------------------------------- applies
 template <typename T, typename V, bool WARPA>
@@ -59,10 +77,14 @@ cudaError_t launch_apply(const Dims& D, const DevA<T, V>& A, const DevL& L, int 
     int64_t blocks = (slabs + kWarps - 1) / kWarps;
     if (blocks > 8 * 152) blocks = 8 * 152;
     if (blocks < 1) blocks = 1;
-    if (A.kind == SGKS_OP_CONV2D)
+    if (A.kind == SGKS_OP_CONV2D) {
+        carveout_once((const void*)k_apply<T, V, false>);
         k_apply<T, V, false><<<(int)blocks, kThreads, 0, st>>>(A, L, which, in, out, rows);
-    else
+    }
+    else {
+        carveout_once((const void*)k_apply<T, V, true>);
         k_apply<T, V, true><<<(int)blocks, kThreads, 0, st>>>(A, L, which, in, out, rows);
+    }
     return cudaGetLastError();
 }
 
@@ -121,21 +143,25 @@ __global__ void __launch_bounds__(kThreads) k_normalize(T* w, int64_t n, const d
 
 template <typename T>
 cudaError_t launch_dots(const T* V0, int64_t n, int k, const T* w, double* part, int nb, cudaStream_t st) {
+    carveout_once((const void*)k_dots<T>);
     k_dots<T><<<nb, kThreads, 0, st>>>(V0, n, k, w, part);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_orth_update(T* w, const T* V0, int64_t n, int k, const double* part, int nb, cudaStream_t st) {
+    carveout_once((const void*)k_orth_update<T>);
     k_orth_update<T><<<nb, kThreads, 0, st>>>(w, V0, n, k, part, nb);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_sqnorm(const T* w, int64_t n, double* part, int nb, cudaStream_t st) {
+    carveout_once((const void*)k_dots<T>);
     k_dots<T><<<nb, kThreads, 0, st>>>(w, n, 1, w, part);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_normalize(T* w, int64_t n, const double* part, int nb, cudaStream_t st) {
+    carveout_once((const void*)k_normalize<T>);
     k_normalize<T><<<nb, kThreads, 0, st>>>(w, n, part, nb);
     return cudaGetLastError();
 }
@@ -159,6 +185,7 @@ __global__ void k_sparse_sign_rows(uint64_t key, int64_t h, int s, int zeta, int
 
 cudaError_t sparse_sign_rows_device(uint64_t key, int64_t h, int s, int zeta, int32_t* rows, uint8_t* neg, int* err,
                                     cudaStream_t st) {
+    carveout_once((const void*)k_sparse_sign_rows);
     k_sparse_sign_rows<<<(unsigned)((h + 255) / 256), 256, 0, st>>>(key, h, s, zeta, rows, neg, err);
     return cudaGetLastError();
 }
@@ -234,19 +261,23 @@ static cudaError_t transpose_impl(int64_t m, int64_t n, int64_t nnz, const int32
     if (e == cudaSuccess) e = cudaMallocAsync(&valtmp, sizeof(V) * (size_t)(nnz > 0 ? nnz : 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)(n + 1), st);
     if (e == cudaSuccess && nnz > 0) {
+        carveout_once((const void*)k_col_count);
         k_col_count<<<1216, 256, 0, st>>>(ci, nnz, cnt);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
+        carveout_once((const void*)k_scan);
         k_scan<<<1, 1024, 0, st>>>(cnt, n, trp);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)(n + 1), st);
     if (e == cudaSuccess && m > 0) {
+        carveout_once((const void*)k_fill<V>);
         k_fill<V><<<(unsigned)((m + kWarps - 1) / kWarps), kThreads, 0, st>>>(rp, ci, val, m, trp, cnt, rowtmp, valtmp);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && n > 0) {
+        carveout_once((const void*)k_rank_sort<V>);
         k_rank_sort<V><<<(unsigned)((n + kWarps - 1) / kWarps), kThreads, 0, st>>>(trp, n, rowtmp, valtmp, tci, tval);
         e = cudaGetLastError();
     }
@@ -277,10 +308,14 @@ cudaError_t convert_values(const void* in, int in_dt, void* out, int out_dt, int
         return cudaMemcpyAsync(out, in, sizeof(float) * (size_t)count, cudaMemcpyDeviceToDevice, st);
     if (in_dt == SGKS_F64 && out_dt == SGKS_F64)
         return cudaMemcpyAsync(out, in, sizeof(double) * (size_t)count, cudaMemcpyDeviceToDevice, st);
-    if (in_dt == SGKS_F32)
+    if (in_dt == SGKS_F32) {
+        carveout_once((const void*)k_convert<float, double>);
         k_convert<float, double><<<blocks, 256, 0, st>>>((const float*)in, (double*)out, count);
-    else
+    }
+    else {
+        carveout_once((const void*)k_convert<double, float>);
         k_convert<double, float><<<blocks, 256, 0, st>>>((const double*)in, (float*)out, count);
+    }
     return cudaGetLastError();
 }
 
@@ -300,6 +335,7 @@ __global__ void k_validate_csr(const int32_t* __restrict__ rp, const int32_t* __
 
 cudaError_t validate_csr_device(const int32_t* rp, const int32_t* ci, int64_t m, int64_t n, int64_t nnz, int* err,
                                 cudaStream_t st) {
+    carveout_once((const void*)k_validate_csr);
     k_validate_csr<<<1216, 256, 0, st>>>(rp, ci, m, n, nnz, err);
     return cudaGetLastError();
 }
@@ -310,6 +346,7 @@ __global__ void k_set_tol(DevScalars* sc, double tol) {
 }
 
 cudaError_t launch_set_tol(DevScalars* sc, double tol, cudaStream_t st) {
+    carveout_once((const void*)k_set_tol);
     k_set_tol<<<1, 1, 0, st>>>(sc, tol);
     return cudaGetLastError();
 }

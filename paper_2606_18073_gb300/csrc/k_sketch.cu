@@ -1,180 +1,107 @@
-// K1: apply A and L to the newest basis column and sketch both results in the same pass.
+// K1: apply A and L to the newest basis column, then sketch both results.
 //
 // Paper: Algorithm 2, first line of the loop -- the QR factors of S_A A W_k and S_L L W_k are
-// updated with the new column S_A A r_k, S_L L r_k (Sec. 3); the sketches are oblivious
-// embeddings (Sec. 2.2), here the sparse-sign sketch whose positions are re-generated from a
-// counter hash inside the kernel and never stored.
+// updated with the new column S_A A r_k, S_L L r_k (Sec. 3).  The sketches are oblivious
+// embeddings (Sec. 2.2): the sparse-sign sketch (rows from a counter hash, see
+// sparse_sign_column) or a dense Gaussian sketch passed in by the caller.
 //
-// Layout: one CTA = 8 warps; a warp owns 32 consecutive rows (a "slab") of A (m rows) or of L
-// (p rows); lane l ends with the value of row base + l.  Each lane draws the zeta sketch rows of
-// its column of S and the warp scatters its 32 values into a warp-private shared-memory
-// accumulator of length s.  Lanes of one warp that hit the same sketch row are merged with
-// __match_any_sync and summed by the lowest lane in lane order, so the result does not depend
-// on scheduling (bit-reproducible).  The 8 warp accumulators are summed in warp order, and the
-// 8 CTAs of a thread-block cluster are summed in rank order through distributed shared
-// memory; one FP64 partial of length s per cluster goes to global memory.  The small FP64
-// kernel reduces those partials (in cluster order).
+// k_apply_column: one pass over the new column w -- u = A w (kept as the column d of A W, used
+//   again by the combine kernel) and t = L w (scratch).  A warp owns 32 consecutive rows; CSR
+//   and dense rows are warp-cooperative, convolution and stencil rows one per lane.
+// k_sketch_gather: S u for the sparse-sign sketch, with S stored once per handle as a CSR by
+//   sketch rows (column indices ascending, sign in bit 31).  One CTA per sketch row gathers its
+//   ~h zeta / s entries from the L2-resident u and reduces them in a fixed order, so the result
+//   is bit-reproducible and no floating-point atomics are used.  (A fused scatter into shared
+//   memory accumulators was measured first: resolving lane collisions with __match_any_sync
+//   made it latency-bound at ~34 us per column for the 256^2 deblurring problem.)
+// k_dense_sketch_pair: S_A u and S_L t for the Gaussian sketch, one warp per sketch row.
 #include "sgks_internal.cuh"
 
 namespace sgks {
 
-constexpr int kSketchCluster = 8;
-
-// Scatter one warp slab into the warp accumulator accw[s].  `val` is lane's row value,
-// `valid` whether the lane's row exists, `j` its column index of S.
-template <typename T, int ZMAX>
-__device__ __forceinline__ bool scatter_slab(uint64_t key, int s, int zeta, int64_t j, bool valid, T val,
-                                             T* accw, T* stw) {
-    const int lane = lane_id();
-    int rows[ZMAX];
-    uint32_t neg = 0u;
-    bool ok = true;
-    if (valid) ok = sparse_sign_column<ZMAX>(key, (uint64_t)j, s, zeta, rows, neg);
-#pragma unroll
-    for (int k = 0; k < ZMAX; ++k) {
-        if (k >= zeta) break;
-        const int r = valid ? rows[k] : -1;
-        const T v = ((neg >> k) & 1u) ? -val : val;
-        const unsigned peers = __match_any_sync(0xffffffffu, r);
-        stw[lane] = v;
-        __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) {
-            T sum = T(0);
-            unsigned mm = peers;
-            while (mm) {
-                const int b = __ffs(mm) - 1;
-                sum += stw[b];
-                mm &= mm - 1u;
-            }
-            accw[r] += sum;
-        }
-        __syncwarp();
-    }
-    return ok;
-}
-
-// Sum the 8 warp accumulators of every CTA of the cluster and write one FP64 partial per
-// cluster: out[cluster][0..s).  Must be called by all threads of all CTAs of the cluster.
-template <typename T>
-__device__ __forceinline__ void cluster_reduce_partial(const T* acc, double* blk, int s, int cid, double* out) {
-    cg::cluster_group cl = cg::this_cluster();
-    __syncthreads();
-    for (int i = threadIdx.x; i < s; i += kThreads) {
-        double v = 0.0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) v += (double)acc[w * s + i];
-        blk[i] = v;
-    }
-    cl.sync();
-    if (cl.block_rank() == 0) {
-        for (int i = threadIdx.x; i < s; i += kThreads) {
-            double v = blk[i];
-            for (int r = 1; r < (int)cl.num_blocks(); ++r) v += cl.map_shared_rank(blk, r)[i];
-            out[(size_t)cid * s + i] = v;
-        }
-    }
-    cl.sync();
-}
-
-// SPARSE = true: sparse-sign scatter; false (Gaussian sketch): write A w to AW[:, d] and L w
-// to tmp_p, the dense sketch kernel runs afterwards.
-template <typename T, typename V, int ZMAX, bool WARPA, bool SPARSE>
-__global__ void __cluster_dims__(kSketchCluster, 1, 1) __launch_bounds__(kThreads)
-    k_sketch_column(Dims D, DevA<T, V> A, DevL L, Bulk<T> B, Small S) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* blk = reinterpret_cast<double*>(smem_raw);                 // [s]
-    T* acc = reinterpret_cast<T*>(blk + D.s);                         // [kWarps][s]
-    T* stage = acc + (size_t)kWarps * D.s;                            // [kWarps][32]
-    T* psf_s = stage + kWarps * 32;                                   // [kh*kw]
-
+template <typename T, typename V, bool WARPA>
+__global__ void __launch_bounds__(kThreads) k_apply_column(Dims D, DevA<T, V> A, DevL L, Bulk<T> B, Small S) {
+    __shared__ T psf_s[128];
     const DevScalars* sc = S.sc;
     if (sc->stop) return;
     const int d = sc->d;
     if (d >= D.dmax) return;
-    const bool isA = (int)blockIdx.x < D.nbA;
-    const int blk_id = isA ? blockIdx.x : blockIdx.x - D.nbA;
-    const int nblk = isA ? D.nbA : D.nbL;
-    const int64_t rows = isA ? D.m : D.p;
-    const uint64_t key = isA ? D.keyA : D.keyL;
-    const T* w = B.W + (size_t)d * D.n;
-    T* u_out = B.AW + (size_t)d * D.m;
-    const int lane = lane_id(), warp = warp_id();
-
-    if (SPARSE)
-        for (int i = threadIdx.x; i < kWarps * D.s; i += kThreads) acc[i] = T(0);
-    if (!WARPA && isA)
+    if (!WARPA)
         for (int i = threadIdx.x; i < A.kh * A.kw; i += kThreads) psf_s[i] = A.psf[i];
     __syncthreads();
-    T* accw = acc + (size_t)warp * D.s;
-    T* stw = stage + warp * 32;
-
-    bool ok = true;
-    const int64_t nslab = (rows + 31) / 32;
-    for (int64_t sl = (int64_t)blk_id * kWarps + warp; sl < nslab; sl += (int64_t)nblk * kWarps) {
-        const int64_t base = sl * 32;
-        const int64_t j = base + lane;
-        const bool valid = j < rows;
-        T val = T(0);
-        if (isA) {
+    const T* w = B.W + (size_t)d * D.n;
+    T* u = B.AW + (size_t)d * D.m;
+    const int lane = lane_id();
+    const int64_t slA = (D.m + 31) / 32, slL = (D.p + 31) / 32;
+    for (int64_t sl = (int64_t)blockIdx.x * kWarps + warp_id(); sl < slA + slL; sl += (int64_t)gridDim.x * kWarps) {
+        if (sl < slA) {
+            const int64_t base = sl * 32, j = base + lane;
+            T val = T(0);
             if (WARPA) {
                 for (int r = 0; r < 32; ++r) {
-                    const int64_t jj = base + r;
-                    if (jj >= rows) break;
-                    const T v = a_row_warp(A, jj, w);
-                    if (lane == r) val = v;
+                    if (base + r >= D.m) break;
+                    const T t = a_row_warp(A, base + r, w);
+                    if (lane == r) val = t;
                 }
-            } else if (valid) {
+            } else if (j < D.m) {
                 val = a_row_conv(A, psf_s, j, w);
             }
-            if (valid) u_out[j] = val;
-        } else if (valid) {
-            val = l_row<T>(L, j, w);
-            if (!SPARSE) B.tmp_p[j] = val;
+            if (j < D.m) u[j] = val;
+        } else {
+            const int64_t j = (sl - slA) * 32 + lane;
+            if (j < D.p) B.tmp_p[j] = l_row<T>(L, j, w);
         }
-        if (SPARSE) ok &= scatter_slab<T, ZMAX>(key, D.s, D.zeta, j, valid, val, accw, stw);
-    }
-    if (SPARSE) {
-        // only the status word is written here: other CTAs of the cluster may still be
-        // reading `stop`, and an early exit of one CTA would leave the others at the barrier
-        if (!ok) S.sc->status = ST_SKETCH;
-        cluster_reduce_partial(acc, blk, D.s, blk_id / kSketchCluster, isA ? S.partA : S.partL);
     }
 }
 
-// Sketch of a plain vector v (length len): S_A b at the setup, and sgks_apply(S_A / S_L).
-template <typename T, int ZMAX>
-__global__ void __cluster_dims__(kSketchCluster, 1, 1) __launch_bounds__(kThreads)
-    k_sketch_vector(const T* __restrict__ v, int64_t len, uint64_t key, int s, int zeta, double* part,
-                    int* err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* blk = reinterpret_cast<double*>(smem_raw);
-    T* acc = reinterpret_cast<T*>(blk + s);
-    T* stage = acc + (size_t)kWarps * s;
-    const int lane = lane_id(), warp = warp_id();
-    for (int i = threadIdx.x; i < kWarps * s; i += kThreads) acc[i] = T(0);
-    __syncthreads();
-    bool ok = true;
-    const int64_t nslab = (len + 31) / 32;
-    for (int64_t sl = (int64_t)blockIdx.x * kWarps + warp; sl < nslab; sl += (int64_t)gridDim.x * kWarps) {
-        const int64_t j = sl * 32 + lane;
-        const bool valid = j < len;
-        const T val = valid ? v[j] : T(0);
-        ok &= scatter_slab<T, ZMAX>(key, s, zeta, j, valid, val, acc + (size_t)warp * s, stage + warp * 32);
-    }
-    if (!ok && err) *err = 1;
-    cluster_reduce_partial(acc, blk, s, (int)(blockIdx.x / kSketchCluster), part);
-}
-
-// Dense (Gaussian) sketch: part[i] = sum_j SG[i*len + j] v[j], one warp per sketch row.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_dense_sketch(const double* __restrict__ SG, const T* __restrict__ v,
-                                                           int64_t len, int s, double* part) {
-    const int row = blockIdx.x * kWarps + warp_id();
-    if (row >= s) return;
-    double a = 0.0;
-    for (int64_t j = lane_id(); j < len; j += 32) a += SG[(size_t)row * len + j] * (double)v[j];
-    a = warp_sum(a);
-    if (lane_id() == 0) part[row] = a;
+__device__ __forceinline__ double as_double(T v) { return (double)v; }
+template <>
+__device__ __forceinline__ double as_double<float2>(float2 v) { return (double)v.x + (double)v.y; }
+
+// Sum of sign_k v[col_k] over the entries [b, e) of one sketch row; CTA-wide, fixed order.
+template <typename Acc, typename TV>
+__device__ __forceinline__ double gather_row(const uint32_t* __restrict__ idx, int b, int e, const TV* __restrict__ v,
+                                             double* red) {
+    Acc a = Acc(0);
+    for (int k = b + (int)threadIdx.x; k < e; k += kThreads) {
+        const uint32_t u = __ldg(idx + k);
+        const Acc val = (Acc)as_double(v[u & 0x7fffffffu]);
+        a += (u >> 31) ? -val : val;
+    }
+    const double t = warp_sum_acc(a);
+    if (lane_id() == 0) red[warp_id()] = t;
+    __syncthreads();
+    return threadIdx.x == 0 ? tree_sumd<kWarps>(red) : 0.0;   // valid in thread 0
+}
+
+// S_A (A W[:, d]) and S_L (L W[:, d]): CTA r < s gathers sketch row r of S_A from the column d of
+// A W, CTA s + r row r of S_L from the scratch L w.  d is read on the device (graph replay).
+template <typename TA, typename TL, typename Acc>
+__global__ void __launch_bounds__(kThreads) k_sketch_gather_col(Dims D, const TA* __restrict__ AW, const TL* __restrict__ lw,
+                                                                SketchCSR SK, Small S) {
+    __shared__ double red[kWarps];
+    const DevScalars* sc = S.sc;
+    if (sc->stop) return;
+    const int d = sc->d;
+    if (d >= D.dmax) return;
+    const bool isA = (int)blockIdx.x < D.s;
+    const int r = isA ? blockIdx.x : blockIdx.x - D.s;
+    double v;
+    if (isA) v = gather_row<Acc>(SK.idxA, SK.ptrA[r], SK.ptrA[r + 1], AW + (size_t)d * D.m, red);
+    else v = gather_row<Acc>(SK.idxL, SK.ptrL[r], SK.ptrL[r + 1], lw, red);
+    if (threadIdx.x == 0) (isA ? S.partA : S.partL)[r] = v;
+}
+
+// Sketch of a plain vector (S_A b at the setup, sgks_apply): out[r] for r < s.
+template <typename TV, typename Acc>
+__global__ void __launch_bounds__(kThreads) k_sketch_gather_vec(const int32_t* __restrict__ ptr,
+                                                                const uint32_t* __restrict__ idx,
+                                                                const TV* __restrict__ v, double* out) {
+    __shared__ double red[kWarps];
+    const int r = blockIdx.x;
+    const double t = gather_row<Acc>(idx, ptr[r], ptr[r + 1], v, red);
+    if (threadIdx.x == 0) out[r] = t;
 }
 
 template <typename T, typename V>
@@ -196,76 +123,87 @@ __global__ void k_dense_sketch_pair(Dims D, Bulk<T> B, Small S, const double* __
     if (lane_id() == 0) (isA ? S.partA : S.partL)[r] = a;
 }
 
-// --------------------------------------------------------------------------- launchers
+// Dense (Gaussian) sketch of a plain vector: part[i] = sum_j SG[i*len + j] v[j].
 template <typename T>
-static size_t sketch_smem(int s, int pk) {
-    return (size_t)s * sizeof(double) + (size_t)kWarps * s * sizeof(T) + kWarps * 32 * sizeof(T) +
-           (size_t)pk * sizeof(T);
+__global__ void __launch_bounds__(kThreads) k_dense_sketch(const double* __restrict__ SG, const T* __restrict__ v,
+                                                           int64_t len, int s, double* part) {
+    const int row = blockIdx.x * kWarps + warp_id();
+    if (row >= s) return;
+    double a = 0.0;
+    for (int64_t j = lane_id(); j < len; j += 32) a += SG[(size_t)row * len + j] * (double)v[j];
+    a = warp_sum(a);
+    if (lane_id() == 0) part[row] = a;
 }
 
-template <typename K>
-static cudaError_t set_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-template <typename T, typename V, int ZMAX, bool WARPA, bool SPARSE>
-static cudaError_t launch_sketch_impl(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
-                                      const Small& S, cudaStream_t st) {
-    const int pk = (A.kind == SGKS_OP_CONV2D) ? A.kh * A.kw : 0;
-    const size_t smem = sketch_smem<T>(D.s, pk);
-    auto kern = k_sketch_column<T, V, ZMAX, WARPA, SPARSE>;
-    cudaError_t e = set_smem(kern, smem);
-    if (e != cudaSuccess) return e;
-    kern<<<D.nbA + D.nbL, kThreads, smem, st>>>(D, A, L, B, S);
-    return cudaGetLastError();
+// --------------------------------------------------------------------------- launchers
+static int apply_blocks(const Dims& D) {
+    const int64_t slabs = (D.m + 31) / 32 + (D.p + 31) / 32;
+    int64_t blocks = (slabs + kWarps - 1) / kWarps;
+    if (blocks > 8 * 152) blocks = 8 * 152;
+    return (int)(blocks < 1 ? 1 : blocks);
 }
 
 template <typename T, typename V>
-cudaError_t launch_sketch_column(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
-                                 const Small& S, cudaStream_t st) {
-    const bool warpa = A.kind != SGKS_OP_CONV2D;
-    if (D.zeta <= 8) {
-        return warpa ? launch_sketch_impl<T, V, 8, true, true>(D, A, L, B, S, st)
-                     : launch_sketch_impl<T, V, 8, false, true>(D, A, L, B, S, st);
+static cudaError_t launch_apply_column(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
+                                       const Small& S, cudaStream_t st) {
+    if (A.kind == SGKS_OP_CONV2D) {
+        carveout_once((const void*)k_apply_column<T, V, false>);
+        k_apply_column<T, V, false><<<apply_blocks(D), kThreads, 0, st>>>(D, A, L, B, S);
     }
-    return warpa ? launch_sketch_impl<T, V, 16, true, true>(D, A, L, B, S, st)
-                 : launch_sketch_impl<T, V, 16, false, true>(D, A, L, B, S, st);
+    else {
+        carveout_once((const void*)k_apply_column<T, V, true>);
+        k_apply_column<T, V, true><<<apply_blocks(D), kThreads, 0, st>>>(D, A, L, B, S);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T> struct GatherAcc { using type = T; };
+
+template <typename T, typename V>
+cudaError_t launch_sketch_column(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
+                                 const Small& S, const SketchCSR& SK, cudaStream_t st) {
+    cudaError_t e = launch_apply_column<T, V>(D, A, L, B, S, st);
+    if (e != cudaSuccess) return e;
+    carveout_once((const void*)k_sketch_gather_col<T, T, T>);
+    k_sketch_gather_col<T, T, T><<<2 * D.s, kThreads, 0, st>>>(D, B.AW, B.tmp_p, SK, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launchx_sketch_gather_col(const Dims& D, const float2* AW, const double* lw, const SketchCSR& SK,
+                                      const Small& S, cudaStream_t st) {
+    carveout_once((const void*)k_sketch_gather_col<float2, double, double>);
+    k_sketch_gather_col<float2, double, double><<<2 * D.s, kThreads, 0, st>>>(D, AW, lw, SK, S);
+    return cudaGetLastError();
+}
+
+// v: float or double; acc_f32 selects FP32 accumulation (the FP32 form).
+cudaError_t launch_sketch_vec(const int32_t* ptr, const uint32_t* idx, const void* v, int vdt, bool acc_f32, int s,
+                              double* out, cudaStream_t st) {
+    if (vdt == SGKS_F32) {
+        if (acc_f32) { carveout_once((const void*)k_sketch_gather_vec<float, float>); k_sketch_gather_vec<float, float><<<s, kThreads, 0, st>>>(ptr, idx, (const float*)v, out); }
+        else { carveout_once((const void*)k_sketch_gather_vec<float, double>); k_sketch_gather_vec<float, double><<<s, kThreads, 0, st>>>(ptr, idx, (const float*)v, out); }
+    } else {
+        carveout_once((const void*)k_sketch_gather_vec<double, double>);
+        k_sketch_gather_vec<double, double><<<s, kThreads, 0, st>>>(ptr, idx, (const double*)v, out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_sketch(const double* SG, const void* v, int vdt, int64_t len, int s, double* part,
+                                cudaStream_t st) {
+    if (vdt == SGKS_F32) { carveout_once((const void*)k_dense_sketch<float>); k_dense_sketch<float><<<(s + kWarps - 1) / kWarps, kThreads, 0, st>>>(SG, (const float*)v, len, s, part); }
+    else { carveout_once((const void*)k_dense_sketch<double>); k_dense_sketch<double><<<(s + kWarps - 1) / kWarps, kThreads, 0, st>>>(SG, (const double*)v, len, s, part); }
+    return cudaGetLastError();
 }
 
 template <typename T, typename V>
 cudaError_t launch_gaussian_sketch(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
                                    const Small& S, const double* SA, const double* SL, cudaStream_t st) {
-    const bool warpa = A.kind != SGKS_OP_CONV2D;
-    cudaError_t e = warpa ? launch_sketch_impl<T, V, 8, true, false>(D, A, L, B, S, st)
-                          : launch_sketch_impl<T, V, 8, false, false>(D, A, L, B, S, st);
+    cudaError_t e = launch_apply_column<T, V>(D, A, L, B, S, st);
     if (e != cudaSuccess) return e;
     const int blocks = (2 * D.s + kWarps - 1) / kWarps;
+    carveout_once((const void*)k_dense_sketch_pair<T, V>);
     k_dense_sketch_pair<T, V><<<blocks, kThreads, 0, st>>>(D, B, S, SA, SL);
-    return cudaGetLastError();
-}
-
-// part must hold ceil(nb / 8) * s doubles (nb rounded up to a multiple of 8), or s doubles for
-// the dense sketch.  nb = number of CTAs.
-template <typename T>
-cudaError_t launch_sketch_vector(const Dims& D, const T* v, int64_t len, uint64_t key, const double* SG,
-                                 double* part, int nb, int* err, cudaStream_t st) {
-    if (SG) {
-        k_dense_sketch<T><<<(D.s + kWarps - 1) / kWarps, kThreads, 0, st>>>(SG, v, len, D.s, part);
-        return cudaGetLastError();
-    }
-    const size_t smem = sketch_smem<T>(D.s, 0);
-    if (D.zeta <= 8) {
-        auto kern = k_sketch_vector<T, 8>;
-        cudaError_t e = set_smem(kern, smem);
-        if (e != cudaSuccess) return e;
-        kern<<<nb, kThreads, smem, st>>>(v, len, key, D.s, D.zeta, part, err);
-    } else {
-        auto kern = k_sketch_vector<T, 16>;
-        cudaError_t e = set_smem(kern, smem);
-        if (e != cudaSuccess) return e;
-        kern<<<nb, kThreads, smem, st>>>(v, len, key, D.s, D.zeta, part, err);
-    }
     return cudaGetLastError();
 }
 
@@ -279,22 +217,114 @@ __global__ void k_reduce_rows(const double* __restrict__ part, int nb, int len, 
 }
 
 cudaError_t launch_reduce_rows(const double* part, int nb, int len, double scale, double* out, cudaStream_t st) {
+    carveout_once((const void*)k_reduce_rows);
     k_reduce_rows<<<(len + kThreads - 1) / kThreads, kThreads, 0, st>>>(part, nb, len, scale, out);
     return cudaGetLastError();
 }
 
+// -------------------------------------------------------------- sketch CSR by sketch rows
+// S (s x h) by rows from the hashed column lists, with a stable chunked counting sort so that
+// every row lists its columns in ascending order (deterministic, linear in h zeta):
+//   count:  chunk c of the columns counts its entries per sketch row (shared-memory counters);
+//   scan:   off[c][r] = ptr[r] + entries of row r in chunks < c;  ptr = scan of the row totals;
+//   fill:   one warp per chunk walks its entries in column order; lanes with the same row are
+//           ranked by lane index (__match_any_sync), so the order within a row is the column order.
+constexpr int kSkChunks = 1024;
+
+__global__ void k_sk_count(const int32_t* __restrict__ rows, int64_t h, int zeta, int s, int64_t ch, int32_t* cnt) {
+    extern __shared__ int32_t cs[];
+    for (int r = threadIdx.x; r < s; r += blockDim.x) cs[r] = 0;
+    __syncthreads();
+    const int64_t j0 = (int64_t)blockIdx.x * ch, j1 = j0 + ch < h ? j0 + ch : h;
+    for (int64_t e = j0 * zeta + threadIdx.x; e < j1 * zeta; e += blockDim.x) atomicAdd(cs + rows[e], 1);
+    __syncthreads();
+    for (int r = threadIdx.x; r < s; r += blockDim.x) cnt[(size_t)blockIdx.x * s + r] = cs[r];
+}
+
+__global__ void __launch_bounds__(1024) k_sk_scan(int32_t* cnt, int s, int nch, int32_t* ptr) {
+    __shared__ int32_t tot[kMaxS];
+    for (int r = threadIdx.x; r < s; r += blockDim.x) {
+        int32_t run = 0;
+        for (int c = 0; c < nch; ++c) {
+            const int32_t v = cnt[(size_t)c * s + r];
+            cnt[(size_t)c * s + r] = run;
+            run += v;
+        }
+        tot[r] = run;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t run = 0;
+        for (int r = 0; r < s; ++r) {
+            ptr[r] = run;
+            run += tot[r];
+        }
+        ptr[s] = run;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < s; r += blockDim.x) {
+        const int32_t base = ptr[r];
+        for (int c = 0; c < nch; ++c) cnt[(size_t)c * s + r] += base;
+    }
+}
+
+__global__ void k_sk_fill(const int32_t* __restrict__ rows, const uint8_t* __restrict__ neg, int64_t h, int zeta, int s,
+                          int64_t ch, const int32_t* __restrict__ off, uint32_t* idx) {
+    extern __shared__ int32_t pos[];
+    const int lane = threadIdx.x;
+    for (int r = lane; r < s; r += 32) pos[r] = off[(size_t)blockIdx.x * s + r];
+    __syncwarp();
+    const int64_t j0 = (int64_t)blockIdx.x * ch, j1 = j0 + ch < h ? j0 + ch : h;
+    for (int64_t e0 = j0 * zeta; e0 < j1 * zeta; e0 += 32) {
+        const int64_t e = e0 + lane;
+        const bool act = e < j1 * zeta;
+        const int r = act ? rows[e] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, r);
+        if (act) {
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            const int p = pos[r] + rank;
+            idx[p] = (uint32_t)(e / zeta) | (neg[e] ? 0x80000000u : 0u);
+        }
+        __syncwarp();
+        if (act && lane == 31 - __clz(peers)) pos[r] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+cudaError_t build_sketch_csr(uint64_t key, int64_t h, int s, int zeta, int32_t* ptr, uint32_t* idx, int* err,
+                             cudaStream_t st) {
+    const int64_t cnt = h * zeta;
+    const int nch = (int)(h < kSkChunks ? (h > 0 ? h : 1) : kSkChunks);
+    const int64_t ch = (h + nch - 1) / nch;
+    int32_t *rows = nullptr, *cc = nullptr;
+    uint8_t* neg = nullptr;
+    cudaError_t e = cudaMallocAsync(&rows, sizeof(int32_t) * (cnt > 0 ? cnt : 1), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&neg, cnt > 0 ? cnt : 1, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&cc, sizeof(int32_t) * (size_t)nch * s, st);
+    if (e == cudaSuccess && cnt > 0) e = sparse_sign_rows_device(key, h, s, zeta, rows, neg, err, st);
+    if (e == cudaSuccess) {
+        carveout_once((const void*)k_sk_count);
+        k_sk_count<<<nch, 256, sizeof(int32_t) * s, st>>>(rows, h, zeta, s, ch, cc);
+        carveout_once((const void*)k_sk_scan);
+        k_sk_scan<<<1, 1024, 0, st>>>(cc, s, nch, ptr);
+        carveout_once((const void*)k_sk_fill);
+        k_sk_fill<<<nch, 32, sizeof(int32_t) * s, st>>>(rows, neg, h, zeta, s, ch, cc, idx);
+        e = cudaGetLastError();
+    }
+    for (void* q : {(void*)rows, (void*)neg, (void*)cc})
+        if (q) cudaFreeAsync(q, st);
+    return e;
+}
+
 #define SGKS_INST_SK(T, V)                                                                                  \
     template cudaError_t launch_sketch_column<T, V>(const Dims&, const DevA<T, V>&, const DevL&,            \
-                                                    const Bulk<T>&, const Small&, cudaStream_t);            \
+                                                    const Bulk<T>&, const Small&, const SketchCSR&,         \
+                                                    cudaStream_t);                                          \
     template cudaError_t launch_gaussian_sketch<T, V>(const Dims&, const DevA<T, V>&, const DevL&,          \
                                                       const Bulk<T>&, const Small&, const double*,          \
                                                       const double*, cudaStream_t);
 SGKS_INST_SK(float, float)
 SGKS_INST_SK(double, float)
 SGKS_INST_SK(double, double)
-template cudaError_t launch_sketch_vector<float>(const Dims&, const float*, int64_t, uint64_t, const double*,
-                                                 double*, int, int*, cudaStream_t);
-template cudaError_t launch_sketch_vector<double>(const Dims&, const double*, int64_t, uint64_t, const double*,
-                                                  double*, int, int*, cudaStream_t);
 
 }  // namespace sgks

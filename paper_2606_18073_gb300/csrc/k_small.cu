@@ -345,19 +345,27 @@ cudaError_t configure_cluster_kernels(int* cluster_out, int s, int dm) {
 }
 
 cudaError_t launch_append_solve(const Dims& D, const Small& S, cudaStream_t st) {
-    if (D.cluster == 16)
+    if (D.cluster == 16) {
+        carveout_once((const void*)k_append_solve<16>);
         k_append_solve<16><<<16, kThreads, append_smem(D.s, D.dmax, 16), st>>>(D, S);
-    else
+    }
+    else {
+        carveout_once((const void*)k_append_solve<8>);
         k_append_solve<8><<<8, kThreads, append_smem(D.s, D.dmax, 8), st>>>(D, S);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_refine_solve(const Dims& D, const Small& S, cudaStream_t st) {
     const int np = D.nbG / 8;
-    if (D.cluster == 16)
+    if (D.cluster == 16) {
+        carveout_once((const void*)k_refine_solve<16>);
         k_refine_solve<16><<<16, kThreads, refine_smem(D.dmax), st>>>(D, S, np);
-    else
+    }
+    else {
+        carveout_once((const void*)k_refine_solve<8>);
         k_refine_solve<8><<<8, kThreads, refine_smem(D.dmax), st>>>(D, S, np);
+    }
     return cudaGetLastError();
 }
 

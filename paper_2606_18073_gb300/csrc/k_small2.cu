@@ -26,16 +26,42 @@
 
 namespace sgks {
 
+// On GB300 a dependent FP64 add costs ~68 cycles, so every cluster- or block-wide sum below is
+// a fixed pairwise tree (log2 depth) instead of a running sum; the order is the same in every
+// CTA, so all CTAs obtain bit-identical values.
+template <int N>
+__device__ __forceinline__ double tree_sum(const double* a, int stride = 1) {
+    if constexpr (N == 1) {
+        return a[0];
+    } else {
+        return tree_sum<N / 2>(a, stride) + tree_sum<N / 2>(a + (N / 2) * stride, stride);
+    }
+}
+
+// Sum of one double per thread: partials staged in shared memory and reduced by warp 0 only
+// (each warp-wide FP64 instruction occupies the SM's FP64 pipe for ~16 cycles on GB300, so the
+// reduction must not be replicated in every warp).  Result valid in every thread.
+// scratch: >= kThreads + 1 doubles.
 __device__ __forceinline__ double block_sum2(double v, double* scratch) {
-    v = warp_sum(v);
     __syncthreads();
-    if (lane_id() == 0) scratch[warp_id()] = v;
+    scratch[threadIdx.x] = v;
     __syncthreads();
-    double t = 0.0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) t += scratch[w];
+    if (warp_id() == 0) {
+        double a = tree_sum<kWarps>(scratch + lane_id(), 32);
+        a = warp_sum(a);
+        if (lane_id() == 0) scratch[kThreads] = a;
+    }
     __syncthreads();
-    return t;
+    return scratch[kThreads];
+}
+
+constexpr int kGrp = 4;   // lanes that share one dot product or one row update
+
+// Sum over the 4 lanes of an aligned lane group (fixed xor tree, result in every lane).
+__device__ __forceinline__ double group_sum(double v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
 }
 
 template <int CS>
@@ -48,14 +74,14 @@ __device__ __forceinline__ void push(cg::cluster_group& cl, double* local, int i
 // c[dm] | p[dm] | red[4*CS] | scratch[kWarps]
 __host__ __device__ inline size_t qr_append_smem(int s, int dm, int cs) {
     const int R = (s + cs - 1) / cs, RP = R | 1;
-    return sizeof(double) * ((size_t)dm * RP + 2 * (size_t)R + (size_t)cs * dm + 2 * (size_t)dm + 4 * cs + kWarps);
+    return sizeof(double) * ((size_t)dm * RP + 2 * (size_t)R + (size_t)cs * dm + 2 * (size_t)dm + 4 * cs + kThreads + 8);
 }
 
 // k_stacked_solve (doubles): QTs[dm * RP2] | v[R2] | cbuf[CS*dm] | c[dm] | tau[dm] | red[4*CS] |
 // scal[8] | scratch[kWarps]
 __host__ __device__ inline size_t stacked_smem(int dm, int cs) {
     const int R2 = (2 * dm + cs - 1) / cs, RP2 = R2 | 1;
-    return sizeof(double) * ((size_t)dm * RP2 + (size_t)R2 + (size_t)cs * dm + 2 * (size_t)dm + 4 * cs + 8 + kWarps);
+    return sizeof(double) * ((size_t)dm * RP2 + (size_t)R2 + (size_t)cs * dm + 2 * (size_t)dm + 4 * cs + 8 + kThreads + 8);
 }
 
 template <int CS>
@@ -82,7 +108,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads) k_qr_appe
     double* c = cbuf + (size_t)CS * dm;            // [dm]
     double* p = c + dm;                            // [dm]
     double* red = p + dm;                          // [4][CS]
-    double* scratch = red + 4 * CS;                // [kWarps]
+    double* scratch = red + 4 * CS;                // [kThreads + 1]
 
     double* Q = fac ? S.QL : S.QA;
     double* Rm = fac ? S.RL : S.RA;
@@ -105,34 +131,51 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads) k_qr_appe
         for (int li = tid; li < nr; li += kThreads) sb[li] = S.Sb[i0 + li];
     for (int j = tid; j < dq; j += kThreads) p[j] = 0.0;
     __syncthreads();
-    double un = 0.0;
-    for (int li = tid; li < nr; li += kThreads) un += v[li] * v[li];
-    un = block_sum2(un, scratch);
-    if (tid == 0) push<CS>(cl, red, rank, un);
+    if (warp == 0) {
+        double un = 0.0;
+        for (int li = lane; li < nr; li += 32) un += v[li] * v[li];
+        un = warp_sum(un);
+        if (lane == 0) push<CS>(cl, red, rank, un);
+    }
 
     double rr = 0.0;
+    const int gl = tid & (kGrp - 1);
     for (int pass = 0; pass < D.cgs_passes; ++pass) {
-        for (int j = tid; j < dq; j += kThreads) {          // partial c_j over own rows
-            const double* q = Qs + (size_t)j * RP;
+        // partial c_j over own rows: 8 lanes per column, each over every 8th row
+        for (int base = 0; base < dq * kGrp; base += kThreads) {
+            const int t = base + tid, j = t / kGrp;
+            const bool act = t < dq * kGrp;
             double a = 0.0;
-            for (int li = 0; li < nr; ++li) a += q[li] * v[li];
-            push<CS>(cl, cbuf + (size_t)rank * dm, j, a);
+            if (act) {
+                const double* q = Qs + (size_t)j * RP;
+                for (int li = gl; li < nr; li += kGrp) a += q[li] * v[li];
+            }
+            a = group_sum(a);
+            if (act && gl == 0) push<CS>(cl, cbuf + (size_t)rank * dm, j, a);
         }
         cl.sync();
         for (int j = tid; j < dq; j += kThreads) {
-            double a = 0.0;
-            for (int r = 0; r < CS; ++r) a += cbuf[(size_t)r * dm + j];
+            const double a = tree_sum<CS>(cbuf + j, dm);
             c[j] = a;
             p[j] += a;
         }
         __syncthreads();
         const bool last = pass == D.cgs_passes - 1;
-        for (int li = tid; li < nr; li += kThreads) {       // v -= Q c over own rows
-            double a = v[li];
-            for (int j = 0; j < dq; ++j) a -= Qs[(size_t)j * RP + li] * c[j];
-            v[li] = a;
-            if (last) rr += a * a;
+        // v -= Q c over own rows: 8 lanes per row, each over every 8th column
+        for (int base = 0; base < nr * kGrp; base += kThreads) {
+            const int t = base + tid, li = t / kGrp;
+            const bool act = t < nr * kGrp;
+            double a = 0.0;
+            if (act)
+                for (int j = gl; j < dq; j += kGrp) a += Qs[(size_t)j * RP + li] * c[j];
+            a = group_sum(a);
+            if (act && gl == 0) {
+                const double nv = v[li] - a;
+                v[li] = nv;
+                if (last) rr += nv * nv;
+            }
         }
+        __syncthreads();
         if (last) {
             rr = block_sum2(rr, scratch);
             if (tid == 0) push<CS>(cl, red + CS, rank, rr);
@@ -140,16 +183,26 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads) k_qr_appe
         cl.sync();   // also separates this pass's reads of cbuf from the next pass's pushes
     }
     if (D.cgs_passes == 0) cl.sync();
-    double un2 = 0.0, r2 = 0.0;
-    for (int r = 0; r < CS; ++r) { un2 += red[r]; r2 += red[CS + r]; }
-    double rho = sqrt(r2);
-    const bool finite = isfinite(un2) && isfinite(r2);
-    const bool broke = !(rho > 1e-13 * sqrt(un2));
-    if (broke) rho = 0.0;
+    // scalar tail on one thread (FP64 pipe), broadcast through shared memory
+    if (tid == 0) {
+        const double un2 = tree_sum<CS>(red), r2 = tree_sum<CS>(red + CS);
+        double rho = sqrt(r2);
+        const bool fin = isfinite(un2) && isfinite(r2);
+        const bool brk = !(rho > 1e-13 * sqrt(un2));
+        if (brk) rho = 0.0;
+        scratch[0] = rho;
+        scratch[1] = rho == 0.0 ? 0.0 : 1.0 / rho;
+        scratch[2] = fin ? 1.0 : 0.0;
+        scratch[3] = brk ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const double rho = scratch[0], inv = scratch[1];
+    const bool finite = scratch[2] != 0.0, broke = scratch[3] != 0.0;
+    __syncthreads();
     // new Q column over own rows, d_A partial
     double dp = 0.0;
     for (int li = tid; li < nr; li += kThreads) {
-        const double q = rho == 0.0 ? 0.0 : v[li] / rho;
+        const double q = v[li] * inv;
         Q[(size_t)dq * s + i0 + li] = q;
         if (fac == 0) dp += q * sb[li];
     }
@@ -161,9 +214,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads) k_qr_appe
     if (rank == 0) {
         for (int j = tid; j <= dq; j += kThreads) Rm[(size_t)dq * dm + j] = j < dq ? p[j] : rho;
         if (tid == 0) {
-            double dn = 0.0;
-            if (fac == 0)
-                for (int r = 0; r < CS; ++r) dn += red[2 * CS + r];
+            const double dn = fac == 0 ? tree_sum<CS>(red + 2 * CS) : 0.0;
             double* out = S.qr_out + 4 * fac;
             out[0] = rho;
             out[1] = broke ? 1.0 : 0.0;
@@ -210,7 +261,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads) k_stacked
     double* tau = c + dm;                           // [dm]
     double* red = tau + dm;                         // [4][CS]
     double* scal = red + 4 * CS;                    // [8]
-    double* scratch = scal + 8;                     // [kWarps]
+    double* scratch = scal + 8;                     // [kThreads + 1]
 
     // stage the Q_T slice; column j is zero below row 2j+2
     for (int idx = tid; idx < dq * nr; idx += kThreads) {
@@ -228,42 +279,60 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads) k_stacked
     for (int j = tid; j < dq; j += kThreads) tau[j] = 0.0;
     __syncthreads();
     double rr = 0.0;
+    const int gl = tid & (kGrp - 1);
     for (int pass = 0; pass < D.cgs_passes; ++pass) {
-        for (int j = tid; j < dq; j += kThreads) {
-            const double* q = Qs + (size_t)j * RP2;
+        for (int base = 0; base < dq * kGrp; base += kThreads) {
+            const int t = base + tid, j = t / kGrp;
+            const bool act = t < dq * kGrp;
             double a = 0.0;
-            for (int lr = 0; lr < nr; ++lr) a += q[lr] * v[lr];
-            push<CS>(cl, cbuf + (size_t)rank * dm, j, a);
+            if (act) {
+                const double* q = Qs + (size_t)j * RP2;
+                for (int lr = gl; lr < nr; lr += kGrp) a += q[lr] * v[lr];
+            }
+            a = group_sum(a);
+            if (act && gl == 0) push<CS>(cl, cbuf + (size_t)rank * dm, j, a);
         }
         cl.sync();
         for (int j = tid; j < dq; j += kThreads) {
-            double a = 0.0;
-            for (int r = 0; r < CS; ++r) a += cbuf[(size_t)r * dm + j];
+            const double a = tree_sum<CS>(cbuf + j, dm);
             c[j] = a;
             tau[j] += a;
         }
         __syncthreads();
         const bool last = pass == D.cgs_passes - 1;
-        for (int lr = tid; lr < nr; lr += kThreads) {
-            double a = v[lr];
-            for (int j = 0; j < dq; ++j) a -= Qs[(size_t)j * RP2 + lr] * c[j];
-            v[lr] = a;
-            if (last) rr += a * a;
+        for (int base = 0; base < nr * kGrp; base += kThreads) {
+            const int t = base + tid, lr = t / kGrp;
+            const bool act = t < nr * kGrp;
+            double a = 0.0;
+            if (act)
+                for (int j = gl; j < dq; j += kGrp) a += Qs[(size_t)j * RP2 + lr] * c[j];
+            a = group_sum(a);
+            if (act && gl == 0) {
+                const double nv = v[lr] - a;
+                v[lr] = nv;
+                if (last) rr += nv * nv;
+            }
         }
+        __syncthreads();
         if (last) {
             rr = block_sum2(rr, scratch);
             if (tid == 0) push<CS>(cl, red, rank, rr);
         }
         cl.sync();
     }
-    double t2 = 0.0;
-    for (int r = 0; r < CS; ++r) t2 += red[r];
-    const double theta = sqrt(t2);   // > 0: at least one of rho_A, rho_L is nonzero
+    if (tid == 0) {
+        const double th = sqrt(tree_sum<CS>(red));   // > 0: at least one of rho_A, rho_L is nonzero
+        scratch[0] = th;
+        scratch[1] = 1.0 / th;
+    }
+    __syncthreads();
+    const double theta = scratch[0], itheta = scratch[1];
+    __syncthreads();
     // new Q_T column and the new entry of z = Q_T^T [d_A; 0]
     double zp = 0.0;
     for (int lr = tid; lr < nr; lr += kThreads) {
         const int row = r0 + lr;
-        const double q = v[lr] / theta;
+        const double q = v[lr] * itheta;
         S.QT[(size_t)dq * ldT + row] = q;
         if (!(row & 1)) {
             const int j = row >> 1;
@@ -273,8 +342,9 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads) k_stacked
     zp = block_sum2(zp, scratch);
     if (tid == 0) push<CS>(cl, red + CS, rank, zp);
     cl.sync();
-    double zn = 0.0;
-    for (int r = 0; r < CS; ++r) zn += red[CS + r];
+    if (tid == 0) scratch[0] = tree_sum<CS>(red + CS);
+    __syncthreads();
+    const double zn = scratch[0];
     if (rank == 0) {
         for (int j = tid; j <= dq; j += kThreads) S.Tm[(size_t)dq * dm + j] = j < dq ? tau[j] : theta;
         if (tid == 0) {
@@ -290,9 +360,9 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads) k_stacked
             const double* xr = S.Xr + (size_t)i * dm;
             double a = 0.0;
             for (int j = i + lane; j < dq; j += 32) a += xr[j] * tau[j];
-            xn = -warp_sum(a) / theta;
+            xn = -warp_sum(a) * itheta;
         } else {
-            xn = 1.0 / theta;
+            xn = itheta;
         }
         const double* xr = S.Xr + (size_t)i * dm;
         double a = 0.0;
@@ -401,28 +471,40 @@ cudaError_t configure_small_fast(int* cluster_out, int s, int dm) {
 }
 
 cudaError_t launch_qr_append(const Dims& D, const Small& S, cudaStream_t st) {
-    if (D.cluster2 == 16)
+    if (D.cluster2 == 16) {
+        carveout_once((const void*)k_qr_append<16>);
         k_qr_append<16><<<32, kThreads, qr_append_smem(D.s, D.dmax, 16), st>>>(D, S);
-    else
+    }
+    else {
+        carveout_once((const void*)k_qr_append<8>);
         k_qr_append<8><<<16, kThreads, qr_append_smem(D.s, D.dmax, 8), st>>>(D, S);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_stacked_solve(const Dims& D, const Small& S, cudaStream_t st) {
-    if (D.cluster2 == 16)
+    if (D.cluster2 == 16) {
+        carveout_once((const void*)k_stacked_solve<16>);
         k_stacked_solve<16><<<16, kThreads, stacked_smem(D.dmax, 16), st>>>(D, S);
-    else
+    }
+    else {
+        carveout_once((const void*)k_stacked_solve<8>);
         k_stacked_solve<8><<<8, kThreads, stacked_smem(D.dmax, 8), st>>>(D, S);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_refine_solve2(const Dims& D, const Small& S, cudaStream_t st) {
     const int np = D.nbG / 8;
     const size_t smem = 2 * sizeof(double) * (size_t)D.dmax;
-    if (D.cluster2 == 16)
+    if (D.cluster2 == 16) {
+        carveout_once((const void*)k_refine_solve2<16>);
         k_refine_solve2<16><<<16, kThreads, smem, st>>>(D, S, np);
-    else
+    }
+    else {
+        carveout_once((const void*)k_refine_solve2<8>);
         k_refine_solve2<8><<<8, kThreads, smem, st>>>(D, S, np);
+    }
     return cudaGetLastError();
 }
 

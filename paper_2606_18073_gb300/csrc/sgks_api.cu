@@ -46,7 +46,7 @@ struct EngineBase {
     int host_d = 0;      // subspace size as the host sequences it (for the profile byte models)
     template <typename F>
     cudaError_t timed(int cls, int dcount, F&& f) {
-        g_launches.fetch_add(cls == PK_SKETCH && gauss ? 2 : 1);
+        g_launches.fetch_add(cls == PK_SKETCH ? 2 : 1);
         if (!prof) return f();
         cudaEventRecord(prof->ev[0], pst);
         cudaError_t e = f();
@@ -87,8 +87,9 @@ struct Engine : EngineBase {
     const double* gSA = nullptr;
     const double* gSL = nullptr;
     double* part_setup = nullptr;   // [nbS][8]
-    int nbS = 1, nbSb = 8, npSb = 1;
+    int nbS = 1;
     int* d_err = nullptr;
+    SketchCSR SK{};                 // sparse-sign sketches by rows (built at create)
 
     T* b_own = nullptr;
 
@@ -102,10 +103,11 @@ struct Engine : EngineBase {
         g_launches.fetch_add(2 + (B.xtrue ? 2 : 0) + 3 + (D.ell - 1) * 8);
         cudaError_t e = cudaMemsetAsync(S.sc, 0, sizeof(DevScalars), st);
         if (e != cudaSuccess) return e;
-        // S_A b (FP64)
-        e = launch_sketch_vector<T>(D, B.b, D.m, D.keyA, gSA, S.partA, nbSb, d_err, st);
-        if (e != cudaSuccess) return e;
-        e = launch_reduce_rows(S.partA, gSA ? 1 : npSb, D.s, D.sketch_scale, S.Sb, st);
+        // S_A b
+        const int tdt = sizeof(T) == 4 ? SGKS_F32 : SGKS_F64;
+        if (gSA) e = launch_dense_sketch(gSA, B.b, tdt, D.m, D.s, S.partA, st);
+        else e = launch_sketch_vec(SK.ptrA, SK.idxA, B.b, tdt, sizeof(T) == 4, D.s, S.partA, st);
+        if (e == cudaSuccess) e = launch_reduce_rows(S.partA, 1, D.s, D.sketch_scale, S.Sb, st);
         if (e != cudaSuccess) return e;
         if (B.xtrue) {
             e = launch_sqnorm<T>(B.xtrue, D.n, part_setup, nbS, st);
@@ -142,7 +144,7 @@ struct Engine : EngineBase {
 
     cudaError_t sketch() {
         if (gSA) return launch_gaussian_sketch<T, V>(D, A, L, B, S, gSA, gSL, st);
-        return launch_sketch_column<T, V>(D, A, L, B, S, st);
+        return launch_sketch_column<T, V>(D, A, L, B, S, SK, st);
     }
 
     cudaError_t small_append(int d) {
@@ -176,26 +178,22 @@ struct Engine : EngineBase {
         return e;
     }
 
-    cudaError_t apply(int which, const void* in, void* out) override {
-        if (which == SGKS_APPLY_SA || which == SGKS_APPLY_SL) {
-            const bool isA = which == SGKS_APPLY_SA;
-            const double* SG = isA ? gSA : gSL;
-            const int64_t len = isA ? D.m : D.p;
-            const int nb = sketch_blocks(len);
-            cudaError_t e = launch_sketch_vector<T>(D, (const T*)in, len, isA ? D.keyA : D.keyL, SG,
-                                                    isA ? S.partA : S.partL, nb, d_err, st);
-            if (e != cudaSuccess) return e;
-            return launch_reduce_rows(isA ? S.partA : S.partL, SG ? 1 : nb / 8, D.s, D.sketch_scale, (double*)out, st);
-        }
-        return launch_apply<T, V>(D, A, L, which, (const T*)in, (T*)out, st);
+    // S v for a plain vector v (sgks_apply): FP32 accumulation only for the FP32 form
+    cudaError_t sketch_vector(bool isA, const void* in, int vdt, bool acc_f32, double* out) {
+        const double* SG = isA ? gSA : gSL;
+        double* part = isA ? S.partA : S.partL;
+        cudaError_t e;
+        if (SG) e = launch_dense_sketch(SG, in, vdt, isA ? D.m : D.p, D.s, part, st);
+        else e = launch_sketch_vec(isA ? SK.ptrA : SK.ptrL, isA ? SK.idxA : SK.idxL, in, vdt, acc_f32, D.s, part, st);
+        if (e != cudaSuccess) return e;
+        return launch_reduce_rows(part, 1, D.s, D.sketch_scale, out, st);
     }
 
-    static int sketch_blocks(int64_t rows) {
-        const int64_t slabs = (rows + 31) / 32;
-        int64_t nb = (slabs + kWarps - 1) / kWarps;
-        if (nb > 4 * 152) nb = 4 * 152;
-        nb = (nb + 7) / 8 * 8;
-        return (int)(nb < 8 ? 8 : nb);
+    cudaError_t apply(int which, const void* in, void* out) override {
+        if (which == SGKS_APPLY_SA || which == SGKS_APPLY_SL)
+            return sketch_vector(which == SGKS_APPLY_SA, in, sizeof(T) == 4 ? SGKS_F32 : SGKS_F64, sizeof(T) == 4,
+                                 (double*)out);
+        return launch_apply<T, V>(D, A, L, which, (const T*)in, (T*)out, st);
     }
 
     void* buffer(int which, size_t* elem_out, int64_t* rows, int64_t* ld) override {
@@ -223,7 +221,7 @@ struct EngineX : Engine<float, float> {
 
     cudaError_t sketchx() {
         if (gSA) return launchx_gaussian_sketch(D, A, L, X, S, gSA, gSL, st);
-        return launchx_sketch_column(D, A, L, X, S, st);
+        return launchx_sketch_column(D, A, L, X, S, SK, st);
     }
 
     cudaError_t refinex() {
@@ -246,9 +244,7 @@ struct EngineX : Engine<float, float> {
         g_launches.fetch_add(2 + (B.xtrue ? 2 : 0) + 3 + (D.ell - 1) * 8);
         e = cudaMemsetAsync(S.sc, 0, sizeof(DevScalars), st);
         if (e != cudaSuccess) return e;
-        if (gSA) e = launch_sketch_vector<float>(D, b_own, D.m, D.keyA, gSA, S.partA, nbSb, d_err, st);
-        else e = launchx_sketch_vector(D, b_own, D.m, D.keyA, S.partA, nbSb, st);
-        if (e == cudaSuccess) e = launch_reduce_rows(S.partA, gSA ? 1 : npSb, D.s, D.sketch_scale, S.Sb, st);
+        e = sketch_vector(true, b_own, SGKS_F32, false, S.Sb);
         if (e != cudaSuccess) return e;
         if (B.xtrue) {
             e = launch_sqnorm<float>(B.xtrue, D.n, part_setup, nbS, st);
@@ -293,15 +289,8 @@ struct EngineX : Engine<float, float> {
     }
 
     cudaError_t apply(int which, const void* in, void* out) override {
-        if ((which == SGKS_APPLY_SA || which == SGKS_APPLY_SL) && !gSA) {
-            const bool isA = which == SGKS_APPLY_SA;
-            const int64_t len = isA ? D.m : D.p;
-            const int nb = sketch_blocks(len);
-            cudaError_t e = launchx_sketch_vector(D, (const float*)in, len, isA ? D.keyA : D.keyL,
-                                                  isA ? S.partA : S.partL, nb, st);
-            if (e != cudaSuccess) return e;
-            return launch_reduce_rows(isA ? S.partA : S.partL, nb / 8, D.s, D.sketch_scale, (double*)out, st);
-        }
+        if (which == SGKS_APPLY_SA || which == SGKS_APPLY_SL)
+            return sketch_vector(which == SGKS_APPLY_SA, in, SGKS_F32, false, (double*)out);
         return Engine<float, float>::apply(which, in, out);
     }
 
@@ -434,8 +423,8 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     D.nbA = nb8(sl_m);
     D.nbL = nb8(sl_p);
     const bool gauss = o.sketch_kind == SGKS_SKETCH_GAUSSIAN;
-    D.npA = gauss ? 1 : D.nbA / 8;
-    D.npL = gauss ? 1 : D.nbL / 8;
+    D.npA = 1;
+    D.npL = 1;
     const int64_t tiles = (D.n + kThreads - 1) / kThreads;
     int64_t nbG = (tiles + 7) / 8 * 8;
     if (nbG > 304) nbG = 304;
@@ -443,8 +432,6 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     D.nbX = (int)tiles;
     D.nbE = (int)((D.m + kThreads - 1) / kThreads);
     E->nbS = (int)(tiles < 304 ? tiles : 304);
-    E->nbSb = Engine<T, V>::sketch_blocks(D.m);
-    E->npSb = E->nbSb / 8;
 
     cudaError_t e = cudaSuccess;
 #define AL(ptr, cnt)                                          \
@@ -590,6 +577,24 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
         A.ny = op->ny;
         A.kh = op->kh;
         A.kw = op->kw;
+    }
+    if (!gauss && e == cudaSuccess) {
+        int32_t *pa, *pl;
+        uint32_t *ia, *il;
+        AL(pa, s + 1);
+        AL(pl, s + 1);
+        AL(ia, (size_t)D.m * o.zeta);
+        AL(il, (size_t)D.p * o.zeta);
+        if (e == cudaSuccess) e = build_sketch_csr(D.keyA, D.m, s, o.zeta, pa, ia, E->d_err, h->st);
+        if (e == cudaSuccess) e = build_sketch_csr(D.keyL, D.p, s, o.zeta, pl, il, E->d_err, h->st);
+        int herr = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, E->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        if (e == cudaSuccess && herr) return fail(h, SGKS_ERR_SKETCH, "sparse-sign draw limit exceeded");
+        E->SK.ptrA = pa;
+        E->SK.idxA = ia;
+        E->SK.ptrL = pl;
+        E->SK.idxL = il;
     }
 #undef AL
     if (e != cudaSuccess) return cuda_fail(h, e, "operator preparation");

@@ -75,6 +75,25 @@ __device__ __forceinline__ T warp_sum(T v) {
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
+// Warp sum of a per-lane partial: FP32 shuffles for the FP32 form (FP32 accumulation),
+// FP64 for the FP64 form; the cross-warp and cross-CTA sums are FP64 in both.
+template <typename T>
+__device__ __forceinline__ double warp_sum_acc(T v) { return (double)warp_sum(v); }
+
+// Fixed pairwise tree over N values with a stride (deterministic, log2 depth).
+template <int N>
+__device__ __forceinline__ double tree_sumd(const double* a, int stride = 1) {
+    if constexpr (N == 1) {
+        return a[0];
+    } else {
+        return tree_sumd<N / 2>(a, stride) + tree_sumd<N / 2>(a + (N / 2) * stride, stride);
+    }
+}
+
+// Shared-memory carveout: when SGKS_CARVEOUT (0..100) is set, every library kernel gets that
+// preferred carveout on its first launch, so consecutive kernels need no SM reconfiguration.
+void carveout_once(const void* kernel);
+
 // SplitMix64 output function (Steele, Lea, Flood 2014).
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -398,6 +417,15 @@ struct Small {                // FP64 state of the sketched QR and projected sol
     DevScalars* sc;
 };
 
+// Sparse-sign sketches stored by sketch rows: entries [ptr[r], ptr[r+1]) of idx hold the
+// column index of S with the sign in bit 31 (set = -1), columns ascending.
+struct SketchCSR {
+    const int32_t* ptrA;
+    const uint32_t* idxA;
+    const int32_t* ptrL;
+    const uint32_t* idxL;
+};
+
 // ------------------------------------------------------------------------ launchers
 struct Dims {
     int64_t n, m, p;
@@ -420,13 +448,18 @@ struct Dims {
 
 template <typename T, typename V>
 cudaError_t launch_sketch_column(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
-                                 const Small& S, cudaStream_t st);
+                                 const Small& S, const SketchCSR& SK, cudaStream_t st);
 template <typename T, typename V>
 cudaError_t launch_gaussian_sketch(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
                                    const Small& S, const double* SA, const double* SL, cudaStream_t st);
-template <typename T>
-cudaError_t launch_sketch_vector(const Dims& D, const T* v, int64_t len, uint64_t key, const double* SG,
-                                 double* part, int nb, int* err, cudaStream_t st);
+cudaError_t launch_sketch_vec(const int32_t* ptr, const uint32_t* idx, const void* v, int vdt, bool acc_f32, int s,
+                              double* out, cudaStream_t st);
+cudaError_t launch_dense_sketch(const double* SG, const void* v, int vdt, int64_t len, int s, double* part,
+                                cudaStream_t st);
+cudaError_t build_sketch_csr(uint64_t key, int64_t h, int s, int zeta, int32_t* ptr, uint32_t* idx, int* err,
+                             cudaStream_t st);
+cudaError_t launchx_sketch_gather_col(const Dims& D, const float2* AW, const double* lw, const SketchCSR& SK,
+                                      const Small& S, cudaStream_t st);
 template <typename T, typename V>
 cudaError_t launch_gradient(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
                             const Small& S, bool refine, cudaStream_t st);
@@ -443,9 +476,7 @@ cudaError_t configure_cluster_kernels(int* cluster_out, int s, int dmax);
 
 // fp32x form (k_fp32x.cu)
 cudaError_t launchx_sketch_column(const Dims& D, const DevA<float, float>& A, const DevL& L, const BulkX& B,
-                                  const Small& S, cudaStream_t st);
-cudaError_t launchx_sketch_vector(const Dims& D, const float* v, int64_t len, uint64_t key, double* part, int nb,
-                                  cudaStream_t st);
+                                  const Small& S, const SketchCSR& SK, cudaStream_t st);
 cudaError_t launchx_combine(const Dims& D, const BulkX& B, const Small& S, int mode, cudaStream_t st);
 cudaError_t launchx_gradient(const Dims& D, const DevA<float, float>& A, const DevL& L, const BulkX& B,
                              const Small& S, bool refine, cudaStream_t st);

@@ -46,7 +46,7 @@ CONFIG_NAMES = ("deconv1d", "deblur2d", "ct2d", "seismic2d", "dynct")
 # lambda for the configs that do not state one, chosen by a grid search of 15 log-spaced
 # values with the FP64 oracle on the seed-0 instance (minimum RRE), as in Sec. 4 (lambda*
 # hand-tuned to minimise the RRE).
-LAMBDA_SEISMIC = 3.0e1
+LAMBDA_SEISMIC = 2.683
 LAMBDA_DYNCT = 1.0
 
 
