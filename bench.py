@@ -172,6 +172,25 @@ def bytes_model(P, cls, d, elem):
     return 0
 
 
+def traffic_record(kernel_class):
+    """DRAM bytes per launch of a kernel from the committed ncu summaries in profiles/, or None
+    when no record exists or the kernel's source changed since the counters were taken."""
+    import glob
+    import hashlib
+    name = "k_" + kernel_class
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for line in open(path):
+            f = line.split()
+            if len(f) == 5 and f[0] == "traffic-record:" and f[1] == name:
+                src = os.path.join(ROOT, "paper_2606_18073_gb300", "csrc", f[2])
+                try:
+                    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+                except OSError:
+                    return None
+                return float(f[4]) if sha == f[3] else None
+    return None
+
+
 def flops_fp64(P, cls, d):
     s = P.sketch.s
     if cls == "qr_append":       # 2 factors x 2 passes x (dot + update) over s x d
@@ -395,7 +414,7 @@ def extras(args, G, P, kw, S, iters, dev, flush):
     dom = max(stream_k, key=lambda k: kern[k]["ms_total"])
     dk = kern[dom]
     out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": dk["gbps"], "peak": hbm, "unit": "GB/s",
-                       "frac": dk["gbps"] / hbm, "traffic": None,
+                       "frac": dk["gbps"] / hbm, "traffic": traffic_record(dom),
                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)" if peaks else
                        "fallback 6800 GB/s"}
     small = {}
