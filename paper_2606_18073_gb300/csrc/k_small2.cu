@@ -85,10 +85,12 @@ __host__ __device__ inline size_t stacked_smem(int dm, int cs) {
 }
 
 template <int CS>
-__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads) k_qr_append(Dims D, Small S) {
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads)
+    k_qr_append(Dims D, Small S0, const Small* __restrict__ Sarr) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    const int fac = blockIdx.x / CS;  // 0: S_A A W, 1: S_L L W
+    const int fac = (blockIdx.x / CS) & 1;  // 0: S_A A W, 1: S_L L W
+    const Small S = Sarr ? Sarr[blockIdx.x / (2 * CS)] : S0;
     const int tid = threadIdx.x, lane = lane_id(), warp = warp_id();
     const int s = D.s, dm = D.dmax;
     const int R = (s + CS - 1) / CS, RP = R | 1;
@@ -225,8 +227,10 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads) k_qr_appe
 }
 
 template <int CS>
-__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads) k_stacked_solve(Dims D, Small S) {
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads)
+    k_stacked_solve(Dims D, Small S0, const Small* __restrict__ Sarr) {
     cg::cluster_group cl = cg::this_cluster();
+    const Small S = Sarr ? Sarr[blockIdx.x / CS] : S0;
     const int rank = (int)cl.block_rank();
     const int tid = threadIdx.x, lane = lane_id(), warp = warp_id();
     const int gw = rank * kWarps + warp, GW = CS * kWarps;
@@ -247,7 +251,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads) k_stacked
         return;
     }
     const double dnew = S.qr_out[3];
-    const double sl = sqrt(D.lam);
+    const double sl = sqrt(S.lam);
     const int N2 = 2 * dq + 2;
     const int R2 = (2 * dm + CS - 1) / CS, RP2 = R2 | 1;
     const int r0 = rank * R2;
@@ -378,8 +382,10 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads) k_stacked
 }
 
 template <int CS>
-__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads) k_refine_solve2(Dims D, Small S, int npart) {
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads)
+    k_refine_solve2(Dims D, Small S0, const Small* __restrict__ Sarr, int npart) {
     cg::cluster_group cl = cg::this_cluster();
+    const Small S = Sarr ? Sarr[blockIdx.x / CS] : S0;
     const int rank = (int)cl.block_rank();
     const int tid = threadIdx.x, lane = lane_id(), warp = warp_id();
     const int gw = rank * kWarps + warp, GW = CS * kWarps;
@@ -470,40 +476,38 @@ cudaError_t configure_small_fast(int* cluster_out, int s, int dm) {
     return e;
 }
 
-cudaError_t launch_qr_append(const Dims& D, const Small& S, cudaStream_t st) {
+cudaError_t launch_qr_append(const Dims& D, const Small& S, cudaStream_t st, const Small* Sarr, int ninst) {
     if (D.cluster2 == 16) {
         carveout_once((const void*)k_qr_append<16>);
-        k_qr_append<16><<<32, kThreads, qr_append_smem(D.s, D.dmax, 16), st>>>(D, S);
-    }
-    else {
+        k_qr_append<16><<<32 * ninst, kThreads, qr_append_smem(D.s, D.dmax, 16), st>>>(D, S, Sarr);
+    } else {
         carveout_once((const void*)k_qr_append<8>);
-        k_qr_append<8><<<16, kThreads, qr_append_smem(D.s, D.dmax, 8), st>>>(D, S);
+        k_qr_append<8><<<16 * ninst, kThreads, qr_append_smem(D.s, D.dmax, 8), st>>>(D, S, Sarr);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_stacked_solve(const Dims& D, const Small& S, cudaStream_t st) {
+cudaError_t launch_stacked_solve(const Dims& D, const Small& S, cudaStream_t st, const Small* Sarr, int ninst) {
     if (D.cluster2 == 16) {
         carveout_once((const void*)k_stacked_solve<16>);
-        k_stacked_solve<16><<<16, kThreads, stacked_smem(D.dmax, 16), st>>>(D, S);
-    }
-    else {
+        k_stacked_solve<16><<<16 * ninst, kThreads, stacked_smem(D.dmax, 16), st>>>(D, S, Sarr);
+    } else {
         carveout_once((const void*)k_stacked_solve<8>);
-        k_stacked_solve<8><<<8, kThreads, stacked_smem(D.dmax, 8), st>>>(D, S);
+        k_stacked_solve<8><<<8 * ninst, kThreads, stacked_smem(D.dmax, 8), st>>>(D, S, Sarr);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_refine_solve2(const Dims& D, const Small& S, cudaStream_t st) {
-    const int np = D.nbG / 8;
+cudaError_t launch_refine_solve2(const Dims& D, const Small& S, cudaStream_t st, const Small* Sarr, int ninst,
+                                 int npart) {
+    const int np = npart >= 0 ? npart : D.nbG / 8;
     const size_t smem = 2 * sizeof(double) * (size_t)D.dmax;
     if (D.cluster2 == 16) {
         carveout_once((const void*)k_refine_solve2<16>);
-        k_refine_solve2<16><<<16, kThreads, smem, st>>>(D, S, np);
-    }
-    else {
+        k_refine_solve2<16><<<16 * ninst, kThreads, smem, st>>>(D, S, Sarr, np);
+    } else {
         carveout_once((const void*)k_refine_solve2<8>);
-        k_refine_solve2<8><<<8, kThreads, smem, st>>>(D, S, np);
+        k_refine_solve2<8><<<8 * ninst, kThreads, smem, st>>>(D, S, Sarr, np);
     }
     return cudaGetLastError();
 }

@@ -490,6 +490,7 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     AL(S.rre_hist, (size_t)o.max_iters + 1);
     AL(S.sc, 1);
     AL(E->part_setup, (size_t)E->nbS * 8);
+    S.lam = lambda;
     AL(E->d_err, 1);
     if (e != cudaSuccess) return fail(h, SGKS_ERR_NOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
     e = cudaMemsetAsync(S.y, 0, sizeof(double) * dm, h->st);

@@ -232,29 +232,44 @@ __device__ __forceinline__ T at_row_conv(const DevA<T, V>& A, const T* __restric
 }
 
 // -------------------------------------------------------------- rows of L and of L^T L
+// The stencil rows read the vector through an accessor X(q) (element q of the vector), so the
+// same definitions serve the single-instance layout (X(q) = x[q]) and the instance-interleaved
+// batched layout (X(q) = x[q * B + b]).
 template <typename T>
-__device__ __forceinline__ T l_row(const DevL& L, int64_t k, const T* __restrict__ x) {
+struct Unit {
+    const T* __restrict__ p;
+    __device__ __forceinline__ T operator()(int64_t q) const { return ldg(p + q); }
+};
+template <typename T>
+struct Strided {
+    const T* __restrict__ p;
+    int64_t st;
+    __device__ __forceinline__ T operator()(int64_t q) const { return ldg(p + q * st); }
+};
+
+template <typename T, typename X>
+__device__ __forceinline__ T l_row_x(const DevL& L, int64_t k, const X& x) {
     const int nx = L.nx, ny = L.ny;
     switch (L.kind) {
         case SGKS_REG_FD1:
-            return ldg(x + k + 1) - ldg(x + k);
+            return x(k + 1) - x(k);
         case SGKS_REG_GRAD2D: {
             const int64_t nh = (int64_t)ny * (nx - 1);
             if (k < nh) {
                 const int64_t iy = k / (nx - 1), ix = k - iy * (nx - 1);
                 const int64_t q = iy * nx + ix;
-                return ldg(x + q + 1) - ldg(x + q);
+                return x(q + 1) - x(q);
             }
             const int64_t q = k - nh;  // (iy, ix) with iy < ny-1
-            return ldg(x + q + nx) - ldg(x + q);
+            return x(q + nx) - x(q);
         }
         case SGKS_REG_LAPLACE2D: {
             const int iy = (int)(k / nx), ix = (int)(k - (int64_t)iy * nx);
-            T v = T(4) * ldg(x + k);
-            if (ix > 0) v -= ldg(x + k - 1);
-            if (ix < nx - 1) v -= ldg(x + k + 1);
-            if (iy > 0) v -= ldg(x + k - nx);
-            if (iy < ny - 1) v -= ldg(x + k + nx);
+            T v = T(4) * x(k);
+            if (ix > 0) v -= x(k - 1);
+            if (ix < nx - 1) v -= x(k + 1);
+            if (iy > 0) v -= x(k - nx);
+            if (iy < ny - 1) v -= x(k + nx);
             return v;
         }
         default: {  // SPACETIME
@@ -265,59 +280,59 @@ __device__ __forceinline__ T l_row(const DevL& L, int64_t k, const T* __restrict
                 const int64_t t = k / per, r = k - t * per;
                 const int64_t iy = r / (nx - 1), ix = r - iy * (nx - 1);
                 const int64_t q = t * fr + iy * nx + ix;
-                return ldg(x + q + 1) - ldg(x + q);
+                return x(q + 1) - x(q);
             }
             if (k < n1 + n2) {
                 const int64_t kk = k - n1;
                 const int64_t t = kk / per2, r = kk - t * per2;
                 const int64_t q = t * fr + r;
-                return ldg(x + q + nx) - ldg(x + q);
+                return x(q + nx) - x(q);
             }
             const int64_t q = k - n1 - n2;
-            return ldg(x + q + fr) - ldg(x + q);
+            return x(q + fr) - x(q);
         }
     }
 }
 
 // (L^T L x)_i, fused: for a first-difference block D along one axis, (D^T D x)_i =
 // [i not last](x_i - x_{i+1}) + [i not first](x_i - x_{i-1}).
-template <typename T>
-__device__ __forceinline__ T fd_pair(const T* __restrict__ x, int64_t i, int64_t stride, int pos, int len) {
-    const T xi = ldg(x + i);
+template <typename T, typename X>
+__device__ __forceinline__ T fd_pair_x(const X& x, int64_t i, int64_t stride, int pos, int len) {
+    const T xi = x(i);
     T v = T(0);
-    if (pos < len - 1) v += xi - ldg(x + i + stride);
-    if (pos > 0) v += xi - ldg(x + i - stride);
+    if (pos < len - 1) v += xi - x(i + stride);
+    if (pos > 0) v += xi - x(i - stride);
     return v;
 }
 
-template <typename T>
-__device__ __forceinline__ T lap5(const T* __restrict__ x, int iy, int ix, int nx, int ny) {
+template <typename T, typename X>
+__device__ __forceinline__ T lap5_x(const X& x, int iy, int ix, int nx, int ny) {
     const int64_t q = (int64_t)iy * nx + ix;
-    T v = T(4) * ldg(x + q);
-    if (ix > 0) v -= ldg(x + q - 1);
-    if (ix < nx - 1) v -= ldg(x + q + 1);
-    if (iy > 0) v -= ldg(x + q - nx);
-    if (iy < ny - 1) v -= ldg(x + q + nx);
+    T v = T(4) * x(q);
+    if (ix > 0) v -= x(q - 1);
+    if (ix < nx - 1) v -= x(q + 1);
+    if (iy > 0) v -= x(q - nx);
+    if (iy < ny - 1) v -= x(q + nx);
     return v;
 }
 
-template <typename T>
-__device__ __forceinline__ T ltl_row(const DevL& L, int64_t i, const T* __restrict__ x) {
+template <typename T, typename X>
+__device__ __forceinline__ T ltl_row_x(const DevL& L, int64_t i, const X& x) {
     const int nx = L.nx, ny = L.ny;
     switch (L.kind) {
         case SGKS_REG_FD1:
-            return fd_pair(x, i, 1, (int)i, nx);
+            return fd_pair_x<T>(x, i, 1, (int)i, nx);
         case SGKS_REG_GRAD2D: {
             const int iy = (int)(i / nx), ix = (int)(i - (int64_t)iy * nx);
-            return fd_pair(x, i, 1, ix, nx) + fd_pair(x, i, nx, iy, ny);
+            return fd_pair_x<T>(x, i, 1, ix, nx) + fd_pair_x<T>(x, i, nx, iy, ny);
         }
         case SGKS_REG_LAPLACE2D: {  // L symmetric: L^T L = L^2, 13-point stencil
             const int iy = (int)(i / nx), ix = (int)(i - (int64_t)iy * nx);
-            T v = T(4) * lap5(x, iy, ix, nx, ny);
-            if (ix > 0) v -= lap5(x, iy, ix - 1, nx, ny);
-            if (ix < nx - 1) v -= lap5(x, iy, ix + 1, nx, ny);
-            if (iy > 0) v -= lap5(x, iy - 1, ix, nx, ny);
-            if (iy < ny - 1) v -= lap5(x, iy + 1, ix, nx, ny);
+            T v = T(4) * lap5_x<T>(x, iy, ix, nx, ny);
+            if (ix > 0) v -= lap5_x<T>(x, iy, ix - 1, nx, ny);
+            if (ix < nx - 1) v -= lap5_x<T>(x, iy, ix + 1, nx, ny);
+            if (iy > 0) v -= lap5_x<T>(x, iy - 1, ix, nx, ny);
+            if (iy < ny - 1) v -= lap5_x<T>(x, iy + 1, ix, nx, ny);
             return v;
         }
         default: {  // SPACETIME
@@ -325,20 +340,20 @@ __device__ __forceinline__ T ltl_row(const DevL& L, int64_t i, const T* __restri
             const int t = (int)(i / fr);
             const int64_t r = i - (int64_t)t * fr;
             const int iy = (int)(r / nx), ix = (int)(r - (int64_t)iy * nx);
-            return fd_pair(x, i, 1, ix, nx) + fd_pair(x, i, nx, iy, ny) + fd_pair(x, i, fr, t, L.nt);
+            return fd_pair_x<T>(x, i, 1, ix, nx) + fd_pair_x<T>(x, i, nx, iy, ny) + fd_pair_x<T>(x, i, fr, t, L.nt);
         }
     }
 }
 
 // (L^T v)_i for v of length p (used by sgks_apply only).
-template <typename T>
-__device__ __forceinline__ T lt_row(const DevL& L, int64_t i, const T* __restrict__ v) {
+template <typename T, typename X>
+__device__ __forceinline__ T lt_row_x(const DevL& L, int64_t i, const X& v) {
     const int nx = L.nx, ny = L.ny;
     switch (L.kind) {
         case SGKS_REG_FD1: {
             T a = T(0);
-            if (i < nx - 1) a -= ldg(v + i);
-            if (i > 0) a += ldg(v + i - 1);
+            if (i < nx - 1) a -= v(i);
+            if (i > 0) a += v(i - 1);
             return a;
         }
         case SGKS_REG_GRAD2D: {
@@ -346,15 +361,15 @@ __device__ __forceinline__ T lt_row(const DevL& L, int64_t i, const T* __restric
             const int64_t nh = (int64_t)ny * (nx - 1);
             T a = T(0);
             const int64_t h = (int64_t)iy * (nx - 1) + ix;
-            if (ix < nx - 1) a -= ldg(v + h);
-            if (ix > 0) a += ldg(v + h - 1);
-            if (iy < ny - 1) a -= ldg(v + nh + i);
-            if (iy > 0) a += ldg(v + nh + i - nx);
+            if (ix < nx - 1) a -= v(h);
+            if (ix > 0) a += v(h - 1);
+            if (iy < ny - 1) a -= v(nh + i);
+            if (iy > 0) a += v(nh + i - nx);
             return a;
         }
         case SGKS_REG_LAPLACE2D: {
             const int iy = (int)(i / nx), ix = (int)(i - (int64_t)iy * nx);
-            return lap5(v, iy, ix, nx, ny);
+            return lap5_x<T>(v, iy, ix, nx, ny);
         }
         default: {
             const int64_t fr = (int64_t)nx * ny;
@@ -365,17 +380,30 @@ __device__ __forceinline__ T lt_row(const DevL& L, int64_t i, const T* __restric
             const int64_t n1 = per * L.nt, n2 = per2 * L.nt;
             T a = T(0);
             const int64_t h = (int64_t)t * per + (int64_t)iy * (nx - 1) + ix;
-            if (ix < nx - 1) a -= ldg(v + h);
-            if (ix > 0) a += ldg(v + h - 1);
+            if (ix < nx - 1) a -= v(h);
+            if (ix > 0) a += v(h - 1);
             const int64_t g = n1 + (int64_t)t * per2 + r;
-            if (iy < ny - 1) a -= ldg(v + g);
-            if (iy > 0) a += ldg(v + g - nx);
+            if (iy < ny - 1) a -= v(g);
+            if (iy > 0) a += v(g - nx);
             const int64_t q = n1 + n2 + i;
-            if (t < L.nt - 1) a -= ldg(v + q);
-            if (t > 0) a += ldg(v + q - fr);
+            if (t < L.nt - 1) a -= v(q);
+            if (t > 0) a += v(q - fr);
             return a;
         }
     }
+}
+
+template <typename T>
+__device__ __forceinline__ T l_row(const DevL& L, int64_t k, const T* __restrict__ x) {
+    return l_row_x<T>(L, k, Unit<T>{x});
+}
+template <typename T>
+__device__ __forceinline__ T ltl_row(const DevL& L, int64_t i, const T* __restrict__ x) {
+    return ltl_row_x<T>(L, i, Unit<T>{x});
+}
+template <typename T>
+__device__ __forceinline__ T lt_row(const DevL& L, int64_t i, const T* __restrict__ v) {
+    return lt_row_x<T>(L, i, Unit<T>{v});
 }
 
 // ------------------------------------------------------------------------- workspace
@@ -415,6 +443,7 @@ struct Small {                // FP64 state of the sketched QR and projected sol
     double *kapart;           // combine-kernel norm partials [nb][4]
     double *rc_hist, *rre_hist;
     DevScalars* sc;
+    double lam;               // regularization parameter of this instance
 };
 
 // Sparse-sign sketches stored by sketch rows: entries [ptr[r], ptr[r+1]) of idx hold the
@@ -467,9 +496,13 @@ template <typename T>
 cudaError_t launch_combine(const Dims& D, const Bulk<T>& B, const Small& S, int mode, cudaStream_t st);
 cudaError_t launch_append_solve(const Dims& D, const Small& S, cudaStream_t st);
 cudaError_t launch_refine_solve(const Dims& D, const Small& S, cudaStream_t st);
-cudaError_t launch_qr_append(const Dims& D, const Small& S, cudaStream_t st);
-cudaError_t launch_stacked_solve(const Dims& D, const Small& S, cudaStream_t st);
-cudaError_t launch_refine_solve2(const Dims& D, const Small& S, cudaStream_t st);
+// Sarr (device, ninst entries) selects per-instance state for batched handles; null = S only.
+cudaError_t launch_qr_append(const Dims& D, const Small& S, cudaStream_t st, const Small* Sarr = nullptr,
+                             int ninst = 1);
+cudaError_t launch_stacked_solve(const Dims& D, const Small& S, cudaStream_t st, const Small* Sarr = nullptr,
+                                 int ninst = 1);
+cudaError_t launch_refine_solve2(const Dims& D, const Small& S, cudaStream_t st, const Small* Sarr = nullptr,
+                                 int ninst = 1, int npart = -1);
 cudaError_t configure_small_fast(int* cluster_out, int s, int dm);
 cudaError_t launch_reduce_rows(const double* part, int nb, int len, double scale, double* out, cudaStream_t st);
 cudaError_t configure_cluster_kernels(int* cluster_out, int s, int dmax);
