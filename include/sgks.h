@@ -230,6 +230,30 @@ int sgks_csr_transpose(int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr
                        const int32_t* col, const void* val, int32_t val_dtype,
                        int32_t* t_row_ptr, int32_t* t_col, void* t_val, void* stream);
 
+/* The same CSR transpose, same arguments and the same output bit for bit, but without
+ * allocating device memory: no cudaMalloc, cudaMallocAsync or cudaFree.  The paper has no
+ * counterpart; this is for callers that cannot allocate.  One case is a process where another
+ * allocator, such as a framework's caching allocator, has already reserved the device memory.
+ * Another is a service that fixes its memory plan at start-up and must not have an allocation
+ * fail or stall in the middle of a request.
+ *
+ * Its temporaries live in a fixed scratch array of 16 MiB (16,777,216 bytes) inside the
+ * library.  Every GPU that loads the library holds that array until the process exits.  The
+ * array must hold 4*(n+1) + 4*nnz + es*nnz bytes, each of the three parts rounded up to 256
+ * bytes, where es = 4 for SGKS_F32 values and 8 for SGKS_F64.  For example, n = 65,536 with
+ * FP32 values fits nnz up to about 2.06 million.  Larger sizes return SGKS_ERR_INVALID, with
+ * the sizes in sgks_last_error(NULL); use sgks_csr_transpose for those.
+ *
+ * The first call on a device looks up the array's device address on the current device, which
+ * must be the device of `stream` and of the buffers.  Make that first call before any stream
+ * capture.  All calls share the one array, and each call overwrites what the previous one left
+ * there.  Calls that overlap on the GPU (different streams, or host threads, at the same time)
+ * race on it and give wrong results.  The call synchronises `stream` before it returns, so
+ * calls made one after another from one thread are safe. */
+int sgks_csr_transpose_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr,
+                               const int32_t* col, const void* val, int32_t val_dtype,
+                               int32_t* t_row_ptr, int32_t* t_col, void* t_val, void* stream);
+
 /* Number of kernel launches the library has enqueued in this process so far (host-side count;
  * one replay of the captured step graph counts its kernel nodes). */
 int64_t sgks_kernel_launches(void);

@@ -294,6 +294,80 @@ cudaError_t csr_transpose_device(int64_t m, int64_t n, int64_t nnz, const int32_
     return transpose_impl<double>(m, n, nnz, rp, ci, (const double*)val, trp, tci, (double*)tval, st);
 }
 
+// ------------------------------------------------------- CSR transpose without allocation
+// Fixed scratch for sgks_csr_transpose_noalloc: the column counts (n + 1 int32), then the
+// unsorted row indices (nnz int32) and values (nnz of the value type), each part starting on a
+// 256-byte boundary.  The array belongs to the module, so every GPU that loads the library holds
+// kNoAllocScratchBytes of it until the process exits, and every call shares it.
+static __device__ __align__(256) unsigned char g_transpose_scratch[kNoAllocScratchBytes];
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+size_t transpose_noalloc_need(int64_t n, int64_t nnz, int vdt) {
+    const size_t es = vdt == SGKS_F32 ? sizeof(float) : sizeof(double);
+    return align256(sizeof(int32_t) * (size_t)(n + 1)) + align256(sizeof(int32_t) * (size_t)nnz) +
+           align256(es * (size_t)nnz);
+}
+
+// Device address of the scratch on the current device, looked up once per device.
+static cudaError_t transpose_scratch_ptr(unsigned char** out) {
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static unsigned char* ptrs[kMaxDevices] = {nullptr};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> g(mu);
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_transpose_scratch);
+        if (e != cudaSuccess) return e;
+        ptrs[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = ptrs[dev];
+    return cudaSuccess;
+}
+
+template <typename V>
+static cudaError_t transpose_noalloc_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
+                                          const V* val, int32_t* trp, int32_t* tci, V* tval, cudaStream_t st) {
+    unsigned char* base = nullptr;
+    cudaError_t e = transpose_scratch_ptr(&base);
+    if (e != cudaSuccess) return e;
+    int32_t* cnt = reinterpret_cast<int32_t*>(base);
+    int32_t* rowtmp = reinterpret_cast<int32_t*>(base + align256(sizeof(int32_t) * (size_t)(n + 1)));
+    V* valtmp = reinterpret_cast<V*>(reinterpret_cast<unsigned char*>(rowtmp) + align256(sizeof(int32_t) * (size_t)nnz));
+    // the counts are the only part read before it is written; the previous call left its own there
+    e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)(n + 1), st);
+    if (e == cudaSuccess && nnz > 0) {
+        k_col_count<<<1216, 256, 0, st>>>(ci, nnz, cnt);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_scan<<<1, 1024, 0, st>>>(cnt, n, trp);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)(n + 1), st);
+    if (e == cudaSuccess && m > 0) {
+        k_fill<V><<<(unsigned)((m + kWarps - 1) / kWarps), kThreads, 0, st>>>(rp, ci, val, m, trp, cnt, rowtmp, valtmp);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && n > 0) {
+        k_rank_sort<V><<<(unsigned)((n + kWarps - 1) / kWarps), kThreads, 0, st>>>(trp, n, rowtmp, valtmp, tci, tval);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+cudaError_t csr_transpose_noalloc_device(int64_t m, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
+                                         const void* val, int vdt, int32_t* trp, int32_t* tci, void* tval,
+                                         cudaStream_t st) {
+    if (vdt == SGKS_F32)
+        return transpose_noalloc_impl<float>(m, n, nnz, rp, ci, (const float*)val, trp, tci, (float*)tval, st);
+    return transpose_noalloc_impl<double>(m, n, nnz, rp, ci, (const double*)val, trp, tci, (double*)tval, st);
+}
+
 // ---------------------------------------------------------------------------- conversion
 template <typename A, typename B>
 __global__ void k_convert(const A* __restrict__ in, B* out, int64_t count) {

@@ -948,4 +948,24 @@ int sgks_csr_transpose(int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr
     return SGKS_OK;
 }
 
+int sgks_csr_transpose_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
+                               const void* val, int32_t val_dtype, int32_t* t_row_ptr, int32_t* t_col, void* t_val,
+                               void* stream) {
+    if (m <= 0 || n <= 0 || nnz < 0 || !row_ptr || !col || !val || !t_row_ptr || !t_col || !t_val ||
+        (val_dtype != SGKS_F32 && val_dtype != SGKS_F64))
+        return fail(nullptr, SGKS_ERR_INVALID, "bad sgks_csr_transpose_noalloc arguments");
+    const int64_t cap = (int64_t)kNoAllocScratchBytes;
+    if (n >= cap || nnz >= cap || transpose_noalloc_need(n, nnz, val_dtype) > kNoAllocScratchBytes)
+        return fail(nullptr, SGKS_ERR_INVALID,
+                    "sgks_csr_transpose_noalloc: n = " + std::to_string(n) + ", nnz = " + std::to_string(nnz) +
+                        " needs more than its fixed scratch of " + std::to_string(kNoAllocScratchBytes) +
+                        " bytes; use sgks_csr_transpose");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e =
+        csr_transpose_noalloc_device(m, n, nnz, row_ptr, col, val, val_dtype, t_row_ptr, t_col, t_val, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "sgks_csr_transpose_noalloc");
+    return SGKS_OK;
+}
+
 }  // extern "C"

@@ -535,6 +535,12 @@ cudaError_t launch_sqnorm(const T* w, int64_t n, double* part, int nb, cudaStrea
 cudaError_t csr_transpose_device(int64_t m, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
                                  const void* val, int vdt, int32_t* trp, int32_t* tci, void* tval,
                                  cudaStream_t st);
+// Scratch size of the allocation-free CSR transpose and the bytes a given size needs of it.
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;
+size_t transpose_noalloc_need(int64_t n, int64_t nnz, int vdt);
+cudaError_t csr_transpose_noalloc_device(int64_t m, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
+                                         const void* val, int vdt, int32_t* trp, int32_t* tci, void* tval,
+                                         cudaStream_t st);
 cudaError_t sparse_sign_rows_device(uint64_t key, int64_t h, int s, int zeta, int32_t* rows, uint8_t* neg,
                                     int* err, cudaStream_t st);
 cudaError_t convert_values(const void* in, int in_dt, void* out, int out_dt, int64_t count, cudaStream_t st);
