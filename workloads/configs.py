@@ -47,7 +47,7 @@ CONFIG_NAMES = ("deconv1d", "deblur2d", "ct2d", "seismic2d", "dynct")
 # values with the FP64 oracle on the seed-0 instance (minimum RRE), as in Sec. 4 (lambda*
 # hand-tuned to minimise the RRE).
 LAMBDA_SEISMIC = 2.683
-LAMBDA_DYNCT = 1.0
+LAMBDA_DYNCT = 26.83
 
 
 def _f32(a):
