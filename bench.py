@@ -11,8 +11,10 @@ write) before every step, outside the timed interval of the step.
 
 Extra keys: the plain FP64 GPU form on the same problem (iterations/s, final RRE and the
 time to reach 1.01 x its final RRE, for the FP32+refinement form too), the per-kernel profile
-and the roofline of the dominant kernel, nvidia-smi clocks during the timed region, and the
-FP64 CPU oracle timed on the host cores on a bounded sample.
+and the roofline of the dominant kernel, nvidia-smi clocks during the timed region, the
+FP64 CPU oracle timed on the host cores on a bounded sample, and the batched form on the CT
+(64 right-hand sides x lambdas sharing one CSR) and ragged dynamic-CT (16 instances of 8 to
+32 frames) workloads, each next to plain FP64 GPU sGKS on one of its instances.
 """
 from __future__ import annotations
 
@@ -42,6 +44,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="deblur2d")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, profile and CPU baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched CT and dynamic-CT measurements")
     ap.add_argument("--cpu-sample-iters", type=int, default=25)
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -424,6 +427,8 @@ def extras(args, G, P, kw, S, iters, dev, flush):
             fl = flops_fp64(P, k, a["avg_d"]) / (a["us_per_launch"] * 1e-6) / 1e12
             small[k] = {"bound": "alu", "achieved": fl, "peak": 1.25, "unit": "TFLOP/s (FP64)", "frac": fl / 1.25}
     out["fp64_small_phase"] = small
+    if not args.no_batch:
+        out["batched"] = {"ct2d_64rhs": bench_ct_batch(G, dev, flush), "dynct_ragged16": bench_dynct_batch(G, dev, flush)}
     # CPU oracle baseline, bounded sample, one thread
     try:
         r = run_cpu_worker(args.config, args.cpu_sample_iters)
@@ -432,6 +437,127 @@ def extras(args, G, P, kw, S, iters, dev, flush):
                                          f"{r['seconds']:.1f} s, BLAS threads = 1"}
     except Exception as exc:   # the GPU number stands without it
         out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
+    return out
+
+
+# ------------------------------------------------------------------------- batched form
+def _dev_tensor(a, dt, dev):
+    import numpy as np
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+
+
+def time_batch(Bt, bs, iters, flush, dev, reps=2):
+    """Best of `reps` (reset + solve(iters)) of a batch; the first call also warms up."""
+    import torch
+    stream = torch_stream(dev)
+    Bt.reset(bs)
+    Bt.solve(iters)
+    best = None
+    for _ in range(reps):
+        flush.zero_()
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        Bt.reset(bs)
+        out = Bt.solve(iters, history=True)
+        c.record(stream)
+        torch.cuda.synchronize(dev)
+        t = a.elapsed_time(c)
+        best = (t, out) if best is None or t < best[0] else best
+    return best
+
+
+def batch_profile(Bt, bs, iters):
+    """Per-kernel times of one eager solve of the batch (each launch timed and synchronised)."""
+    Bt.reset(bs)
+    prof = Bt.profile(iters)
+    tot = sum(v["ms"] for v in prof.values()) or 1.0
+    return {k: {"ms_total": v["ms"], "launches": v["launches"], "share": v["ms"] / tot,
+                "us_per_launch": 1e3 * v["ms"] / v["launches"]} for k, v in prof.items() if v["launches"]}
+
+
+def batch_report(ms, reps, iters, count, P64, ref_idx, G, dev, flush):
+    """Instance-iterations/s of the batch next to plain FP64 GPU sGKS on instance ref_idx."""
+    import numpy as np
+    P64.n_refine = 0
+    kw64 = G.device_inputs(P64, "fp64", device=dev)
+    S64 = G.Solver(**kw64)
+    t64, h64 = time_solve(G, S64, kw64["b"], iters, flush, dev)
+    S64.close()
+    rre = [r["rre_last"] for r in reps]
+    target = 1.01 * h64["rre_last"]
+    return {"instances": count, "iterations": iters, "ms_per_solve": ms,
+            "instance_iters_per_s": count * iters / (ms / 1e3),
+            "final_rre": {"min": float(np.min(rre)), "median": float(np.median(rre)), "max": float(np.max(rre))},
+            "fp64_plain_single": {"instance": ref_idx, "iters_per_s": iters / (t64 / 1e3), "ms_per_solve": t64,
+                                  "final_rre": h64["rre_last"]},
+            "batched_instance_final_rre": rre[ref_idx],
+            "batched_instance_time_to_target_ms": time_to_rre(ms, reps[ref_idx]["rre"], target, iters),
+            "fp64_time_to_target_ms": time_to_rre(t64, h64["rre"], target, iters)}
+
+
+def bench_ct_batch(G, dev, flush, count=64):
+    """Parallel-beam CT 512 x 512, 180 angles x 725 bins: 64 right-hand sides (noise seed i,
+    lambda_i = 10^(-4 + 3 i / 63)) sharing one CSR, FP32, 150 iterations, s = 600."""
+    import numpy as np
+    import torch
+    from workloads.configs import ct_op, make_ct2d
+    A0 = ct_op(512, np.arange(180) * 1.0, 725)
+    probs = [make_ct2d(instance=i, A=A0, precision="fp32") for i in range(count)]
+    kw = G.device_inputs(probs[0], "fp32", device=dev)
+    insts = [dict(A=kw["A"], reg=kw["reg"], lam=P.lam, b=_dev_tensor(P.b, torch.float32, dev),
+                  x_true=_dev_tensor(P.x_true, torch.float32, dev)) for P in probs]
+    P0 = probs[0]
+    Bt = G.Batch(insts, P0.sketch.s, P0.sketch.seed, max_iters=P0.iters, n_refine=0, precision="fp32",
+                 zeta=P0.sketch.zeta)
+    ms, reps = time_batch(Bt, [i["b"] for i in insts], P0.iters, flush, dev)
+    prof = batch_profile(Bt, [i["b"] for i in insts], P0.iters)
+    Bt.close()
+    del insts, kw
+    torch.cuda.empty_cache()
+    out = batch_report(ms, reps, P0.iters, count, make_ct2d(instance=42, A=A0), 42, G, dev, flush)
+    out["kernels"] = prof
+    out["workload"] = ("ct2d: 512x512, 180 angles x 725 bins, CSR FP32 (nnz %d), grad2d L, 2%% noise, "
+                       "lambda_i = 10^(-4+3i/63), sparse-sign s=600 zeta=8, 150 iterations, FP32, 64 RHS" % len(A0.col))
+    return out
+
+
+def bench_dynct_batch(G, dev, flush):
+    """Dynamic CT 128 x 128 x F frames, 16 instances, F in {8, 16, 24, 32} (4 each, seeds 0..15):
+    ragged sizes in four groups, FP32 + 3 refinement steps, 200 iterations, s = 800."""
+    import torch
+    from workloads.configs import dynct_frame_ops, make_dynct
+    ops = dynct_frame_ops(128, 32)
+    frames = [8, 16, 24, 32] * 4
+    probs, shared = [], {}
+    for i, F in enumerate(frames):
+        P = make_dynct(seed=i, frames=F, frame_ops=ops)
+        P.A = shared.setdefault(F, P.A)
+        probs.append(P)
+    dev_ops = {}
+    insts = []
+    for P in probs:
+        if id(P.A) not in dev_ops:
+            kw = G.device_inputs(P, "fp32", device=dev)
+            dev_ops[id(P.A)] = (kw["A"], kw["reg"])
+        A, reg = dev_ops[id(P.A)]
+        insts.append(dict(A=A, reg=reg, lam=P.lam, b=_dev_tensor(P.b, torch.float32, dev),
+                          x_true=_dev_tensor(P.x_true, torch.float32, dev)))
+    P0 = probs[0]
+    Bt = G.Batch(insts, P0.sketch.s, P0.sketch.seed, max_iters=P0.iters, n_refine=P0.n_refine, precision="fp32",
+                 zeta=P0.sketch.zeta)
+    groups = Bt.layout()[0]
+    ms, reps = time_batch(Bt, [i["b"] for i in insts], P0.iters, flush, dev)
+    prof = batch_profile(Bt, [i["b"] for i in insts], P0.iters)
+    Bt.close()
+    del insts, dev_ops
+    torch.cuda.empty_cache()
+    out = batch_report(ms, reps, P0.iters, len(probs), make_dynct(seed=3, frames=32, frame_ops=ops), 3, G, dev,
+                       flush)
+    out["groups"] = groups
+    out["kernels"] = prof
+    out["workload"] = ("dynct: 128x128 x F frames, F in {8,16,24,32} x 4 instances, 30 angles/frame x 185 bins, "
+                       "space-time L, 1% noise, sparse-sign s=800 zeta=8, 200 iterations, FP32 + 3 refinement steps")
     return out
 
 

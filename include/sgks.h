@@ -270,6 +270,68 @@ int64_t sgks_kernel_launches(void);
 #define SGKS_PROFILE_CLASSES 8
 int sgks_profile_steps(sgks_handle* h, int32_t iters, double* ms_out, int64_t* count_out, double* dsum_out);
 
+/* ---- batches: many independent problems in one handle ----------------------------------- */
+/* Each instance i is a problem of its own (eq. tik with A_i, L_i, b_i, lambda_i) solved by
+ * Algorithm 2 exactly as a single handle would solve it, with the same seed: the batch changes
+ * the schedule, not the arithmetic of an instance.  Instances whose A and L descriptors are equal
+ * field by field (the same device arrays) form groups that share the prepared operator and run
+ * in one instance-interleaved pass over A per kernel; the group size is a power of two <= 256, a
+ * larger set of equal instances is split (largest power of two first), and instances with
+ * different operators (ragged sizes) form separate groups that run concurrently. */
+typedef struct sgks_batch sgks_batch;
+
+/* Create a batch of `count` instances and run the setup of each (as sgks_create).
+ *  A, L:     host arrays of `count` descriptors (their device arrays as for sgks_create).
+ *  b:        host array of `count` device pointers, b[i] holding m_i values of the solver
+ *            precision.  Copied at create and at sgks_batch_reset.
+ *  lambdas:  host array of `count` parameters, each > 0.
+ *  x_true:   NULL, or a host array of `count` device pointers (n_i values each): RRE records.
+ *  sketch_rows, seed, opt: as for sgks_create, shared by every instance; opt->x_true is ignored.
+ *            Supported: precision SGKS_PREC_FP64 or SGKS_PREC_FP32, the sparse-sign sketch.
+ * Errors as for sgks_create; SGKS_ERR_INVALID names the first bad instance. */
+int sgks_batch_create(sgks_batch** h, int32_t count, const sgks_op* A, const sgks_reg* L,
+                      const void* const* b, const double* lambdas, const void* const* x_true,
+                      int32_t sketch_rows, uint64_t seed, const sgks_options* opt, void* stream);
+
+/* Re-run the setup of every instance with new right-hand sides (host array of `count` device
+ * pointers).  Asynchronous on the handle's stream. */
+int sgks_batch_reset(sgks_batch* h, const void* const* b_new);
+
+/* One iteration of every live instance (as sgks_step).  Asynchronous. */
+int sgks_batch_step(sgks_batch* h);
+
+/* Run `iters` iterations of every instance by replaying one captured graph, an instance leaving
+ * the loop on its own when its RC_k < tol (tol > 0) or on breakdown / non-finite values.
+ *  x_out: NULL, or a host array of `count` device pointers (NULL entries skipped) receiving x_k.
+ *  reps:  NULL, or a host array of `count` reports (rc / rre pointers inside as for sgks_solve).
+ * Synchronises.  Returns the most severe negative instance status, else SGKS_OK. */
+int sgks_batch_solve(sgks_batch* h, int32_t iters, double tol, void* const* x_out, sgks_report* reps);
+
+/* Copy the current iterate x_k of every instance to x_out (host array of `count` device
+ * pointers, NULL entries skipped; n_i values of the solver precision each).  Synchronises. */
+int sgks_batch_get_x(sgks_batch* h, void* const* x_out);
+
+/* Synchronise and write each instance's status code (as sgks_status) to codes[count] (host). */
+int sgks_batch_status(sgks_batch* h, int32_t* codes);
+
+/* Number of groups; optionally the group index and group size of every instance (host arrays of
+ * `count` entries, may be NULL). */
+int sgks_batch_layout(sgks_batch* h, int32_t* group_of, int32_t* group_size);
+
+/* Per-kernel timing of `iters` eager iterations of every group (groups one after another, each
+ * launch timed with a CUDA event pair and synchronised: for measurement only).  Host arrays of
+ * SGKS_BATCH_PROFILE_CLASSES entries receive the total milliseconds and the launch count per
+ * kernel class: the classes of sgks_profile_steps, except that class 1 is the operator apply
+ * alone and class 8 the sketch gather. */
+#define SGKS_BATCH_PROFILE_CLASSES 9
+int sgks_batch_profile_steps(sgks_batch* h, int32_t iters, double* ms_out, int64_t* count_out);
+
+/* Last error of h, or of the last failed sgks_batch_create when h is NULL. */
+const char* sgks_batch_last_error(const sgks_batch* h);
+
+/* Release the batch's device memory, streams and graph.  NULL-safe.  Synchronises. */
+void sgks_batch_destroy(sgks_batch* h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,19 @@ _SIGNATURES = {
                                      C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgks_csr_transpose_noalloc": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sgks_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(sgks_op), C.POINTER(sgks_reg),
+                                    C.POINTER(C.c_void_p), C.POINTER(C.c_double), C.POINTER(C.c_void_p), C.c_int32,
+                                    C.c_uint64, C.POINTER(sgks_options), C.c_void_p]),
+    "sgks_batch_reset": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "sgks_batch_step": (C.c_int, [C.c_void_p]),
+    "sgks_batch_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(C.c_void_p),
+                                   C.POINTER(sgks_report)]),
+    "sgks_batch_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "sgks_batch_get_x": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "sgks_batch_layout": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "sgks_batch_profile_steps": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "sgks_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "sgks_batch_destroy": (None, [C.c_void_p]),
     "sgks_kernel_launches": (C.c_int64, []),
     "sgks_profile_steps": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                      C.POINTER(C.c_double)]),
@@ -91,6 +104,9 @@ SGKS_PROFILE_CLASSES = 8
 PROFILE_CLASS_NAMES = ["gradient_append", "sketch_column", "qr_append", "stacked_solve", "combine_refine",
                        "gradient_refine", "refine_solve", "combine"]
 SGKS_FLAG_GLOBAL_SMALL = 1
+SGKS_BATCH_PROFILE_CLASSES = 9
+BATCH_PROFILE_CLASS_NAMES = ["gradient_append", "apply_column", "qr_append", "stacked_solve", "combine_refine",
+                             "gradient_refine", "refine_solve", "combine", "sketch_gather"]
 
 _lib = None
 
@@ -126,5 +142,13 @@ def check(code, handle=None):
     if code < 0:
         lib = load()
         msg = lib.sgks_last_error(handle)
+        raise SGKSError(code, msg.decode() if msg else "")
+    return code
+
+
+def check_batch(code, handle=None):
+    if code < 0:
+        lib = load()
+        msg = lib.sgks_batch_last_error(handle)
         raise SGKSError(code, msg.decode() if msg else "")
     return code

@@ -1,0 +1,669 @@
+// Batched sGKS: B independent instances (right-hand sides b_i, parameters lambda_i) of one
+// problem shape solved together, each by Algorithm 2.
+//
+// Layout: every n-, m- or p-vector of all instances is instance-interleaved,
+// v[q * B + i] = component q of instance i, and the bases as W[(j * n + q) * B + i].  A thread
+// owns one (row, instance) pair and the B threads of a row are consecutive, so every CSR,
+// convolution or dense row of A (and of A^T) is read once for all instances of a warp -- the
+// operator passes are SpMM with the instance dimension innermost -- and every vector access is
+// coalesced across instances.  B is a power of two (<= 256), so a grid-stride loop whose stride
+// is a multiple of B keeps each thread on one instance.
+//
+// Each instance keeps its own subspace size d_i and stop flag (DevScalars): the kernels here
+// read them on the device, so a stopped or broken-down instance drops out while the others go
+// on, and one captured step graph serves every iteration.  The FP64 small phase (QR append,
+// projected solve, refinement solve) is the single-instance cluster code of k_small2.cu
+// launched with one cluster group per instance.
+#include <math.h>
+
+#include "sgks_internal.cuh"
+
+namespace sgks {
+
+constexpr int kBatchCluster = 8;
+constexpr int kCombRows = 8;       // rows per thread in a kb_combine tile
+constexpr int kYStage = 4096;      // y values staged per chunk in kb_combine (chunk = kYStage / B)
+
+// ------------------------------------------------------------------ batched operator rows
+template <typename T, typename V>
+__device__ __forceinline__ T ba_row(const DevA<T, V>& A, const T* psf_s, int64_t j, const T* __restrict__ x, int B) {
+    T acc = T(0);
+    if (A.kind == SGKS_OP_CSR) {
+        const int e = A.rp[j + 1];
+#pragma unroll 4
+        for (int k = A.rp[j]; k < e; ++k) acc += (T)ldg(A.val + k) * ldg(x + (int64_t)ldg(A.ci + k) * B);
+    } else if (A.kind == SGKS_OP_CONV2D) {
+        const int nx = A.nx, ny = A.ny, kh = A.kh, kw = A.kw;
+        const int iy = (int)(j / nx), ix = (int)(j - (int64_t)iy * nx);
+        for (int a = 0; a < kh; ++a) {
+            const int yy = iy - a + kh / 2;
+            if (yy < 0 || yy >= ny) continue;
+            for (int c = 0; c < kw; ++c) {
+                const int xx = ix - c + kw / 2;
+                if (xx >= 0 && xx < nx) acc += psf_s[a * kw + c] * ldg(x + ((int64_t)yy * nx + xx) * B);
+            }
+        }
+    } else {
+        const T* row = A.dense + j * A.ld;
+        for (int64_t k = 0; k < A.n; ++k) acc += ldg(row + k) * ldg(x + k * B);
+    }
+    return acc;
+}
+
+template <typename T, typename V>
+__device__ __forceinline__ T bat_row(const DevA<T, V>& A, const T* psf_s, int64_t i, const T* __restrict__ e, int B) {
+    T acc = T(0);
+    if (A.kind == SGKS_OP_CSR) {
+        const int en = A.trp[i + 1];
+#pragma unroll 4
+        for (int k = A.trp[i]; k < en; ++k) acc += (T)ldg(A.tval + k) * ldg(e + (int64_t)ldg(A.tci + k) * B);
+    } else if (A.kind == SGKS_OP_CONV2D) {
+        const int nx = A.nx, ny = A.ny, kh = A.kh, kw = A.kw;
+        const int iy = (int)(i / nx), ix = (int)(i - (int64_t)iy * nx);
+        for (int a = 0; a < kh; ++a) {
+            const int yy = iy + a - kh / 2;
+            if (yy < 0 || yy >= ny) continue;
+            for (int c = 0; c < kw; ++c) {
+                const int xx = ix + c - kw / 2;
+                if (xx >= 0 && xx < nx) acc += psf_s[a * kw + c] * ldg(e + ((int64_t)yy * nx + xx) * B);
+            }
+        }
+    } else {
+        for (int64_t k = 0; k < A.m; ++k) acc += ldg(A.dense + k * A.ld + i) * ldg(e + k * B);
+    }
+    return acc;
+}
+
+template <typename T, typename V>
+__device__ __forceinline__ void load_psf(const DevA<T, V>& A, T* psf_s) {
+    if (A.kind == SGKS_OP_CONV2D)
+        for (int i = threadIdx.x; i < A.kh * A.kw; i += blockDim.x) psf_s[i] = A.psf[i];
+    __syncthreads();
+}
+
+// stride of a grid-stride loop over (row, instance) pairs: a multiple of B, since B divides kThreads
+__device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * kThreads; }
+
+// ------------------------------------------------------------------ a1: apply the newest column
+// u_i = A w_i -> column d_i of AW, t_i = L w_i -> tp (w_i = column d_i of W_i).
+template <typename T, typename V>
+__global__ void __launch_bounds__(kThreads) kb_apply_column(BDims D, DevA<T, V> A, DevL L, BBulk<T> X, BSmall S) {
+    __shared__ T psf_s[128];
+    load_psf(A, psf_s);
+    const int B = D.B;
+    const int b = threadIdx.x & (B - 1);
+    const DevScalars& sc = S.sc[b];
+    if (sc.stop) return;
+    const int d = sc.d;
+    if (d >= D.dmax) return;
+    const T* w = X.W + (size_t)d * D.n * B + b;
+    const int64_t tot = (D.m + D.p) * B;
+    for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < tot; t += gstride()) {
+        if (t < D.m * B) {
+            const int64_t j = t / B;
+            X.AW[((size_t)d * D.m + j) * B + b] = ba_row(A, psf_s, j, w, B);
+        } else {
+            const int64_t k = (t - D.m * B) / B;
+            X.tp[k * B + b] = l_row_x<T>(L, k, Strided<T>{w, B});
+        }
+    }
+}
+
+// ---------------------------------------------------------------------- a1: sketch gathers
+// CTA r < s: row r of S_A applied to u_i; CTA s + r: row r of S_L applied to t_i (vec == nullptr).
+// With vec: row r of S_A applied to the interleaved m-vector vec, scaled, into out_vec[i][r].
+// Thread (g, i) takes entries ptr[r] + g, + G, ... for instance i (G = kThreads / B groups),
+// combined by a fixed pairwise tree.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) kb_sketch_gather(BDims D, BBulk<T> X, SketchCSR SK, BSmall S,
+                                                              const T* __restrict__ vec, double* out_vec) {
+    __shared__ double red[kThreads];
+    const int B = D.B, G = kThreads / B;
+    const int b = threadIdx.x & (B - 1), g = threadIdx.x / B;
+    const bool isA = vec != nullptr || (int)blockIdx.x < D.s;
+    const int r = isA ? (int)blockIdx.x : (int)blockIdx.x - D.s;
+    const int32_t* ptr = isA ? SK.ptrA : SK.ptrL;
+    const uint32_t* idx = isA ? SK.idxA : SK.idxL;
+    const DevScalars& sc = S.sc[b];
+    const bool live = vec != nullptr || (!sc.stop && sc.d < D.dmax);
+    const T* v = vec ? vec : (isA ? X.AW + (size_t)(live ? sc.d : 0) * D.m * B : X.tp);
+    T a = T(0);
+    if (live) {
+        const int e = ptr[r + 1];
+#pragma unroll 4
+        for (int k = ptr[r] + g; k < e; k += G) {
+            const uint32_t u = __ldg(idx + k);
+            const T val = ldg(v + (int64_t)(u & 0x7fffffffu) * B + b);
+            a += (u >> 31) ? -val : val;
+        }
+    }
+    red[threadIdx.x] = (double)a;
+    __syncthreads();
+    for (int h = G / 2; h > 0; h >>= 1) {
+        if (g < h) red[threadIdx.x] += red[threadIdx.x + h * B];
+        __syncthreads();
+    }
+    if (g == 0 && live) {
+        if (vec) out_vec[(size_t)b * D.s + r] = D.sketch_scale * red[b];
+        else (isA ? S.partA : S.partL)[(size_t)b * D.s + r] = red[b];
+    }
+}
+
+// ------------------------------------------------------------------- a5 + a6: combine
+// x_i = W_i y_i and e_i = (A W_i) y_i - b_i.  mode 1 (end of an iteration): RC_k and RRE_k per
+// instance (eq. RC); mode 2 (setup): RRE_0; mode 0 (refinement): x and e only.
+// A tile is kCombRows * G consecutive rows (G = kThreads / B) of either x or e; thread (g, i)
+// owns rows g, g + G, ... of the tile for instance i, so the thread's values of one column lie
+// kThreads apart (immediate offsets from one base address) and each W column slice of the tile
+// is one contiguous run.  Two columns are loaded before they are used: 2 * kCombRows loads in
+// flight per thread.  y is staged in shared memory as [j][B] in chunks of kYStage / B entries.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 4) kb_combine(BDims D, BBulk<T> X, BSmall S, int mode) {
+    __shared__ T ys[kYStage];
+    __shared__ int sd[kMaxBatch];
+    __shared__ int s_dlive;
+    __shared__ double red[3][kThreads];
+    __shared__ int am_last;
+    const int B = D.B, G = kThreads / B;
+    const int b = threadIdx.x & (B - 1), g = threadIdx.x / B;
+    const int JC = kYStage / B;
+    if (threadIdx.x == 0) {
+        int mx = 0;
+        for (int i = 0; i < B; ++i) {
+            const int di = S.sc[i].stop ? 0 : S.sc[i].d;
+            sd[i] = di;
+            mx = di > mx ? di : mx;
+        }
+        s_dlive = mx;
+    }
+    __syncthreads();
+    const int db = sd[b], dlive = s_dlive;
+    const bool live = !S.sc[b].stop;
+    const int TR = kCombRows * G;
+    const int64_t ntx = (D.n + TR - 1) / TR, nte = (D.m + TR - 1) / TR;
+    T q0 = T(0), q1 = T(0), q2 = T(0);
+    for (int64_t tile = blockIdx.x; tile < ntx + nte; tile += gridDim.x) {
+        const bool isx = tile < ntx;
+        const int64_t rows = isx ? D.n : D.m;
+        const int64_t row0 = (isx ? tile : tile - ntx) * TR + g;   // this thread's first row
+        const int nv = row0 < rows ? (int)min((int64_t)kCombRows, (rows - row0 + G - 1) / G) : 0;
+        const size_t cstride = (size_t)rows * B;
+        const T* base = (isx ? X.W : X.AW) + (size_t)row0 * B + b;
+        T acc[kCombRows];
+#pragma unroll
+        for (int r = 0; r < kCombRows; ++r) acc[r] = T(0);
+        for (int jc = 0; jc < dlive; jc += JC) {
+            __syncthreads();
+            for (int q = threadIdx.x; q < JC * B; q += kThreads) {
+                const int jj = q / B, i = q & (B - 1), j = jc + jj;
+                ys[q] = j < sd[i] ? (T)S.y[(size_t)i * D.dmax + j] : T(0);
+            }
+            __syncthreads();
+            const int je = min(JC, db - jc);
+            int jj = 0;
+            for (; jj + 2 <= je; jj += 2) {
+                const T* c0 = base + (size_t)(jc + jj) * cstride;
+                const T* c1 = c0 + cstride;
+                T w0[kCombRows], w1[kCombRows];
+#pragma unroll
+                for (int r = 0; r < kCombRows; ++r) {
+                    w0[r] = r < nv ? c0[kThreads * r] : T(0);
+                    w1[r] = r < nv ? c1[kThreads * r] : T(0);
+                }
+                const T y0 = ys[jj * B + b], y1 = ys[(jj + 1) * B + b];
+#pragma unroll
+                for (int r = 0; r < kCombRows; ++r) acc[r] += w0[r] * y0;
+#pragma unroll
+                for (int r = 0; r < kCombRows; ++r) acc[r] += w1[r] * y1;
+            }
+            if (jj < je) {
+                const T* c0 = base + (size_t)(jc + jj) * cstride;
+                const T y0 = ys[jj * B + b];
+#pragma unroll
+                for (int r = 0; r < kCombRows; ++r)
+                    if (r < nv) acc[r] += c0[kThreads * r] * y0;
+            }
+        }
+        if (!live) continue;
+        T* out = (isx ? X.x : X.e) + (size_t)row0 * B + b;
+#pragma unroll
+        for (int r = 0; r < kCombRows; ++r) {
+            if (r >= nv) continue;
+            const size_t o = (size_t)kThreads * r;
+            if (isx) {
+                const T xv = acc[r];
+                out[o] = xv;
+                if (mode >= 1) {
+                    T* xs = X.xs + (size_t)row0 * B + b;
+                    const T old = xs[o];
+                    const T df = xv - old;
+                    q0 += df * df;
+                    q1 += old * old;
+                    if (X.xtrue) {
+                        const T er = xv - X.xtrue[(size_t)row0 * B + b + o];
+                        q2 += er * er;
+                    }
+                    xs[o] = xv;
+                }
+            } else {
+                out[o] = acc[r] - X.b[(size_t)row0 * B + b + o];
+            }
+        }
+    }
+    if (mode == 0) return;
+    red[0][threadIdx.x] = (double)q0;
+    red[1][threadIdx.x] = (double)q1;
+    red[2][threadIdx.x] = (double)q2;
+    __syncthreads();
+    for (int h = G / 2; h > 0; h >>= 1) {
+        if (g < h)
+            for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h * B];
+        __syncthreads();
+    }
+    if (g == 0)
+        for (int q = 0; q < 3; ++q) S.kapart[((size_t)blockIdx.x * B + b) * 3 + q] = red[q][b];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = (atomicAdd(S.ka_done, 1) == (int)gridDim.x - 1);
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    // last CTA: per instance, the CTA partials summed by SUB = kThreads / B threads (thread (u, i)
+    // takes CTAs c = u, u + SUB, ... in order), then the SUB sums by a fixed pairwise tree
+    {
+        const int SUB = kThreads / B, u = threadIdx.x / B, i = threadIdx.x & (B - 1);
+        double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+#pragma unroll 4
+        for (int c = u; c < (int)gridDim.x; c += SUB) {
+            const double* pp = S.kapart + ((size_t)c * B + i) * 3;
+            t0 += __ldcg(pp);
+            t1 += __ldcg(pp + 1);
+            t2 += __ldcg(pp + 2);
+        }
+        __syncthreads();
+        red[0][threadIdx.x] = t0;
+        red[1][threadIdx.x] = t1;
+        red[2][threadIdx.x] = t2;
+        __syncthreads();
+        for (int h = SUB / 2; h > 0; h >>= 1) {
+            if (u < h)
+                for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h * B];
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < B; i += kThreads) {
+        const double t0 = red[0][i], t1 = red[1][i], t2 = red[2][i];
+        DevScalars& s = S.sc[i];
+        if (s.stop) continue;
+        const double rre = X.xtrue ? sqrt(t2 / s.xt2) : (double)NAN;
+        if (mode == 2) {
+            s.rre0 = rre;
+            s.rre_last = rre;
+        } else {
+            const double rc = sqrt(t0 / t1);
+            const int k = s.iter;
+            if (k < D.max_iters) {
+                S.rc_hist[(size_t)i * D.max_iters + k] = rc;
+                S.rre_hist[(size_t)i * D.max_iters + k] = rre;
+            }
+            s.rc_last = rc;
+            s.rre_last = rre;
+            s.iter = k + 1;
+            if (s.tol_on && rc < s.tol) {
+                s.status = ST_STOPPED;
+                s.stop = 1;
+            }
+            if (!(t0 <= 1e300) || !(t1 <= 1e300)) {   // NaN or Inf in the iterate
+                s.status = ST_NONFINITE;
+                s.stop = 1;
+            }
+        }
+    }
+    if (threadIdx.x == 0) *S.ka_done = 0;
+}
+
+// -------------------------------------------------------------------------- a7: gradient
+// r_i = A^T e_i + lambda_i L^T L x_i (eq. gradient).  out == nullptr: appended as column d_i of
+// W_i; otherwise written to out ([n][B], the refinement's residual gradient r(y)).
+template <typename T, typename V>
+__global__ void __launch_bounds__(kThreads) kb_gradient(BDims D, DevA<T, V> A, DevL L, BBulk<T> X, BSmall S,
+                                                        T* out) {
+    __shared__ T psf_s[128];
+    load_psf(A, psf_s);
+    const int B = D.B;
+    const int b = threadIdx.x & (B - 1);
+    DevScalars& sc = S.sc[b];
+    if (sc.stop) return;
+    T* dst = out;
+    if (!dst) {
+        const int d = sc.d;
+        if (d >= D.dmax) {
+            if (blockIdx.x == 0 && threadIdx.x == b) {
+                sc.status = ST_FULL;
+                sc.stop = 1;
+            }
+            return;
+        }
+        dst = X.W + (size_t)d * D.n * B;
+    }
+    const T lam = (T)S.lam[b];
+    for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < D.n * B; t += gstride()) {
+        const int64_t i = t / B;
+        const T adj = bat_row(A, psf_s, i, X.e + b, B);
+        dst[i * B + b] = adj + lam * ltl_row_x<T>(L, i, Strided<T>{X.x + b, B});
+    }
+}
+
+// g_i = W_i^T r_i in FP64 across rows (a4).  Tiles of TR = 1024 / B rows: r of the tile is staged
+// in shared memory; the tile's slice of column j is 1024 contiguous values, of which lane l takes
+// positions l + 32 k (k < 32, all loads independent and in flight together).  NB = B / 32
+// instances per lane for B >= 32 (instance l + 32 (k mod NB)); NB = 0 for B < 32 (one instance
+// per lane, l mod B, combined across the lanes by shuffles).  Warp w owns columns w, w + 8, ...,
+// every (j, i) has one owner, and the 8 CTAs of a cluster are combined by a fixed tree into gpart.
+template <typename T, int NB>
+__global__ void __cluster_dims__(kBatchCluster, 1, 1) __launch_bounds__(kThreads, 2)
+    kb_wtr(BDims D, BBulk<T> X, BSmall S, const T* __restrict__ r) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_dlive;
+    __shared__ int s_stop[kMaxBatch];
+    const int B = D.B;
+    const int TR = 1024 / B;
+    double* gacc = reinterpret_cast<double*>(smem_raw);        // [dmax][B]
+    T* rt = reinterpret_cast<T*>(gacc + (size_t)D.dmax * B);   // [TR][B]
+    cg::cluster_group cl = cg::this_cluster();
+    const int lane = lane_id(), warp = warp_id();
+    if (threadIdx.x == 0) {
+        int mx = 0;
+        for (int i = 0; i < B; ++i) {
+            s_stop[i] = S.sc[i].stop;
+            if (!S.sc[i].stop && S.sc[i].d > mx) mx = S.sc[i].d;
+        }
+        s_dlive = mx;
+    }
+    __syncthreads();
+    const int dlive = s_dlive;
+    for (int q = threadIdx.x; q < dlive * B; q += kThreads) gacc[q] = 0.0;
+    const int64_t ntiles = (D.n + TR - 1) / TR;
+    for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+        const int64_t i0 = tl * TR;
+        const int rows = (int)((D.n - i0) < TR ? (D.n - i0) : TR);
+        const int valid = rows * B;
+        __syncthreads();
+        for (int q = threadIdx.x; q < 1024; q += kThreads)
+            rt[q] = (q < valid && !s_stop[q & (B - 1)]) ? r[(size_t)i0 * B + q] : T(0);
+        __syncthreads();
+        for (int j = warp; j < dlive; j += kWarps) {
+            const T* wc = X.W + ((size_t)j * D.n + i0) * B + lane;
+            const T* rl = rt + lane;
+            if constexpr (NB == 0) {
+                T a = T(0);
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                    if (lane + 32 * k < valid) a += wc[32 * k] * rl[32 * k];
+                for (int off = B; off < 32; off <<= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+                if (lane < B) gacc[(size_t)j * B + lane] += (double)a;
+            } else {
+                T a[NB];
+#pragma unroll
+                for (int q = 0; q < NB; ++q) a[q] = T(0);
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                    if (lane + 32 * k < valid) a[k % NB] += wc[32 * k] * rl[32 * k];
+#pragma unroll
+                for (int q = 0; q < NB; ++q) gacc[(size_t)j * B + lane + 32 * q] += (double)a[q];
+            }
+        }
+    }
+    cl.sync();
+    if (cl.block_rank() == 0) {
+        const int c = blockIdx.x / kBatchCluster, ngp = gridDim.x / kBatchCluster;
+        for (int q = threadIdx.x; q < dlive * B; q += kThreads) {
+            const int j = q / B, bb = q & (B - 1);
+            double v[kBatchCluster];
+#pragma unroll
+            for (int rr = 0; rr < kBatchCluster; ++rr) v[rr] = cl.map_shared_rank(gacc, rr)[q];
+            S.gpart[((size_t)bb * ngp + c) * D.dmax + j] = tree_sumd<kBatchCluster>(v);
+        }
+    }
+    cl.sync();
+}
+
+// --------------------------------------------------------------------------------- setup
+// out = op(in) for op in A, A^T, L, L^T, L^T L, all instances.
+template <typename T, typename V>
+__global__ void __launch_bounds__(kThreads) kb_apply(BDims D, DevA<T, V> A, DevL L, int which, const T* __restrict__ in,
+                                                     T* __restrict__ out, int64_t rows) {
+    __shared__ T psf_s[128];
+    load_psf(A, psf_s);
+    const int B = D.B;
+    const int b = threadIdx.x & (B - 1);
+    for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < rows * B; t += gstride()) {
+        const int64_t q = t / B;
+        T v;
+        switch (which) {
+            case SGKS_APPLY_A: v = ba_row(A, psf_s, q, in + b, B); break;
+            case SGKS_APPLY_AT: v = bat_row(A, psf_s, q, in + b, B); break;
+            case SGKS_APPLY_L: v = l_row_x<T>(L, q, Strided<T>{in + b, B}); break;
+            case SGKS_APPLY_LT: v = lt_row_x<T>(L, q, Strided<T>{in + b, B}); break;
+            default: v = ltl_row_x<T>(L, q, Strided<T>{in + b, B}); break;
+        }
+        out[t] = v;
+    }
+}
+
+// part[(c * k + col) * B + i] = FP64 partial over the rows of CTA c of V_col[., i] . w[., i]
+template <typename T>
+__global__ void __launch_bounds__(kThreads) kb_dots(BDims D, const T* __restrict__ V0, int k, const T* __restrict__ w,
+                                                    double* part) {
+    __shared__ double red[kThreads];
+    const int B = D.B, G = kThreads / B, b = threadIdx.x & (B - 1), g = threadIdx.x / B;
+    for (int col = 0; col < k; ++col) {
+        double a = 0.0;
+        for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < D.n * B; t += gstride())
+            a += (double)V0[(size_t)col * D.n * B + t] * (double)w[t];
+        red[threadIdx.x] = a;
+        __syncthreads();
+        for (int h = G / 2; h > 0; h >>= 1) {
+            if (g < h) red[threadIdx.x] += red[threadIdx.x + h * B];
+            __syncthreads();
+        }
+        if (g == 0) part[((size_t)blockIdx.x * k + col) * B + b] = red[b];
+        __syncthreads();
+    }
+}
+
+// coef[col * B + i] = sum over CTAs c (fixed order) of part[(c * k + col) * B + i]; one CTA per (col, i)
+__global__ void __launch_bounds__(kThreads) kb_reduce_parts(const double* __restrict__ part, int nc, int k, int B,
+                                                            double* coef) {
+    __shared__ double red[kWarps];
+    const int col = blockIdx.x / B, b = blockIdx.x % B;
+    double a = 0.0;
+    for (int c = threadIdx.x; c < nc; c += kThreads) a += part[((size_t)c * k + col) * B + b];
+    a = warp_sum(a);
+    if (lane_id() == 0) red[warp_id()] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) coef[(size_t)col * B + b] = tree_sumd<kWarps>(red);
+}
+
+// mode 0: w[., i] -= sum_col coef[col][i] V_col[., i]   (one Gram-Schmidt projection)
+// mode 1: w[., i] /= sqrt(coef[0][i])                    (normalisation)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) kb_vec_update(BDims D, T* w, const T* __restrict__ V0, int k,
+                                                          const double* __restrict__ coef, int mode) {
+    const int B = D.B;
+    const int b = threadIdx.x & (B - 1);
+    for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < D.n * B; t += gstride()) {
+        if (mode == 0) {
+            double a = (double)w[t];
+            for (int col = 0; col < k; ++col) a -= coef[(size_t)col * B + b] * (double)V0[(size_t)col * D.n * B + t];
+            w[t] = (T)a;
+        } else {
+            w[t] = (T)((double)w[t] / sqrt(coef[b]));
+        }
+    }
+}
+
+// out[q * B + i] = P.p[i][q]
+template <typename T>
+__global__ void kb_gather_in(PtrPack P, T* __restrict__ out, int64_t len, int B) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < len * B; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = t / B;
+        const int i = (int)(t % B);
+        out[t] = static_cast<const T*>(P.p[i])[q];
+    }
+}
+
+// P.p[i][q] = in[q * B + i] (instances with a null pointer are skipped)
+template <typename T>
+__global__ void kb_scatter_out(const T* __restrict__ in, PtrPack P, int64_t len, int B) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < len * B; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = t / B;
+        const int i = (int)(t % B);
+        T* dst = const_cast<T*>(static_cast<const T*>(P.p[i]));
+        if (dst) dst[q] = in[t];
+    }
+}
+
+__global__ void kb_set_xt2(const double* __restrict__ coef, int B, DevScalars* sc) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) sc[b].xt2 = coef[b];
+}
+
+__global__ void kb_set_tol(DevScalars* sc, int B, double tol) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) {
+        sc[b].tol = tol;
+        sc[b].tol_on = tol > 0.0 ? 1 : 0;
+    }
+}
+
+// ------------------------------------------------------------------------------ launchers
+static int bgrid(int64_t work) {
+    int64_t b = (work + kThreads - 1) / kThreads;
+    if (b > 8 * 152) b = 8 * 152;
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <typename T, typename V>
+cudaError_t launchb_apply_column(const BDims& D, const DevA<T, V>& A, const DevL& L, const BBulk<T>& X,
+                                 const BSmall& S, cudaStream_t st) {
+    kb_apply_column<T, V><<<bgrid((D.m + D.p) * D.B), kThreads, 0, st>>>(D, A, L, X, S);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launchb_sketch_gather(const BDims& D, const BBulk<T>& X, const SketchCSR& SK, const BSmall& S,
+                                  const T* vec, double* out_vec, cudaStream_t st) {
+    kb_sketch_gather<T><<<vec ? D.s : 2 * D.s, kThreads, 0, st>>>(D, X, SK, S, vec, out_vec);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launchb_combine(const BDims& D, const BBulk<T>& X, const BSmall& S, int mode, cudaStream_t st) {
+    kb_combine<T><<<D.nb_combine, kThreads, 0, st>>>(D, X, S, mode);
+    return cudaGetLastError();
+}
+
+size_t batch_refine_smem(int dmax, int B, size_t elem) {
+    return (size_t)dmax * B * sizeof(double) + 1024 * elem;
+}
+
+template <typename T, typename V>
+cudaError_t launchb_gradient(const BDims& D, const DevA<T, V>& A, const DevL& L, const BBulk<T>& X, const BSmall& S,
+                             T* out, cudaStream_t st) {
+    kb_gradient<T, V><<<bgrid(D.n * D.B), kThreads, 0, st>>>(D, A, L, X, S, out);
+    return cudaGetLastError();
+}
+
+template <typename T, int NB>
+static cudaError_t wtr_nb(const BDims& D, const BBulk<T>& X, const BSmall& S, const T* r, cudaStream_t st) {
+    const size_t smem = batch_refine_smem(D.dmax, D.B, sizeof(T));
+    auto k = kb_wtr<T, NB>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<D.nb_refine, kThreads, smem, st>>>(D, X, S, r);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launchb_wtr(const BDims& D, const BBulk<T>& X, const BSmall& S, const T* r, cudaStream_t st) {
+    switch (D.B) {
+        case 32: return wtr_nb<T, 1>(D, X, S, r, st);
+        case 64: return wtr_nb<T, 2>(D, X, S, r, st);
+        case 128: return wtr_nb<T, 4>(D, X, S, r, st);
+        case 256: return wtr_nb<T, 8>(D, X, S, r, st);
+        default: return wtr_nb<T, 0>(D, X, S, r, st);
+    }
+}
+
+template <typename T, typename V>
+cudaError_t launchb_apply(const BDims& D, const DevA<T, V>& A, const DevL& L, int which, const T* in, T* out,
+                          cudaStream_t st) {
+    const int64_t rows = which == SGKS_APPLY_A ? D.m : (which == SGKS_APPLY_L ? D.p : D.n);
+    kb_apply<T, V><<<bgrid(rows * D.B), kThreads, 0, st>>>(D, A, L, which, in, out, rows);
+    return cudaGetLastError();
+}
+
+// S.setup_coef[col][i] = V_col[., i] . w[., i] for col < k
+template <typename T>
+cudaError_t launchb_dots(const BDims& D, const T* V0, int k, const T* w, const BSmall& S, cudaStream_t st) {
+    kb_dots<T><<<D.nb_setup, kThreads, 0, st>>>(D, V0, k, w, S.setup_part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    kb_reduce_parts<<<k * D.B, kThreads, 0, st>>>(S.setup_part, D.nb_setup, k, D.B, S.setup_coef);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launchb_vec_update(const BDims& D, T* w, const T* V0, int k, const BSmall& S, int mode, cudaStream_t st) {
+    kb_vec_update<T><<<bgrid(D.n * D.B), kThreads, 0, st>>>(D, w, V0, k, S.setup_coef, mode);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launchb_gather_in(const PtrPack& P, T* out, int64_t len, int B, cudaStream_t st) {
+    kb_gather_in<T><<<bgrid(len * B), kThreads, 0, st>>>(P, out, len, B);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launchb_scatter_out(const T* in, const PtrPack& P, int64_t len, int B, cudaStream_t st) {
+    kb_scatter_out<T><<<bgrid(len * B), kThreads, 0, st>>>(in, P, len, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launchb_set_xt2(const BSmall& S, int B, cudaStream_t st) {
+    kb_set_xt2<<<(B + 255) / 256, 256, 0, st>>>(S.setup_coef, B, S.sc);
+    return cudaGetLastError();
+}
+
+cudaError_t launchb_set_tol(DevScalars* sc, int B, double tol, cudaStream_t st) {
+    kb_set_tol<<<(B + 255) / 256, 256, 0, st>>>(sc, B, tol);
+    return cudaGetLastError();
+}
+
+#define SGKS_INST_B(T, V)                                                                                        \
+    template cudaError_t launchb_apply_column<T, V>(const BDims&, const DevA<T, V>&, const DevL&, const BBulk<T>&, \
+                                                    const BSmall&, cudaStream_t);                                \
+    template cudaError_t launchb_gradient<T, V>(const BDims&, const DevA<T, V>&, const DevL&, const BBulk<T>&,     \
+                                                const BSmall&, T*, cudaStream_t);                                \
+    template cudaError_t launchb_apply<T, V>(const BDims&, const DevA<T, V>&, const DevL&, int, const T*, T*,      \
+                                             cudaStream_t);
+SGKS_INST_B(float, float)
+SGKS_INST_B(double, float)
+SGKS_INST_B(double, double)
+#define SGKS_INST_BT(T)                                                                                          \
+    template cudaError_t launchb_sketch_gather<T>(const BDims&, const BBulk<T>&, const SketchCSR&, const BSmall&, \
+                                                  const T*, double*, cudaStream_t);                              \
+    template cudaError_t launchb_combine<T>(const BDims&, const BBulk<T>&, const BSmall&, int, cudaStream_t);     \
+    template cudaError_t launchb_wtr<T>(const BDims&, const BBulk<T>&, const BSmall&, const T*, cudaStream_t);     \
+    template cudaError_t launchb_dots<T>(const BDims&, const T*, int, const T*, const BSmall&, cudaStream_t);     \
+    template cudaError_t launchb_vec_update<T>(const BDims&, T*, const T*, int, const BSmall&, int, cudaStream_t); \
+    template cudaError_t launchb_gather_in<T>(const PtrPack&, T*, int64_t, int, cudaStream_t);                    \
+    template cudaError_t launchb_scatter_out<T>(const T*, const PtrPack&, int64_t, int, cudaStream_t);
+SGKS_INST_BT(float)
+SGKS_INST_BT(double)
+
+}  // namespace sgks

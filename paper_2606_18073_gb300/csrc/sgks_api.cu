@@ -355,6 +355,187 @@ static cudaError_t dalloc(sgks_handle* h, P** p, size_t count) {
     return cudaSuccess;
 }
 
+namespace sgks {
+
+void add_launches(int64_t k) { g_launches.fetch_add(k); }
+
+DevL make_devl(const sgks_reg* reg) {
+    DevL L{};
+    L.kind = reg->kind;
+    L.nx = reg->nx;
+    L.ny = reg->kind == SGKS_REG_FD1 ? 1 : reg->ny;
+    L.nt = reg->kind == SGKS_REG_SPACETIME ? reg->nt : 1;
+    L.n = (int64_t)L.nx * L.ny * L.nt;
+    const int64_t nx = L.nx, ny = L.ny, nt = L.nt;
+    switch (L.kind) {
+        case SGKS_REG_FD1: L.p = nx - 1; break;
+        case SGKS_REG_GRAD2D: L.p = ny * (nx - 1) + (ny - 1) * nx; break;
+        case SGKS_REG_LAPLACE2D: L.p = nx * ny; break;
+        default: L.p = nt * (ny * (nx - 1) + (ny - 1) * nx) + (nt - 1) * nx * ny; break;
+    }
+    return L;
+}
+
+template <typename P>
+static cudaError_t valloc(std::vector<void*>& allocs, P** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(P) + 16);
+    if (e != cudaSuccess) return e;
+    allocs.push_back(q);
+    *p = (P*)q;
+    return cudaSuccess;
+}
+
+// reads the device error word, then clears it; returns nonzero if it was set
+static cudaError_t take_flag(int* d_err, cudaStream_t st, int* herr) {
+    cudaError_t e = cudaMemcpyAsync(herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    return e;
+}
+
+template <typename T, typename V>
+int prepare_operator(const sgks_op* op, DevA<T, V>& A, std::vector<void*>& allocs, int* d_err, cudaStream_t st,
+                     std::string* why) {
+    cudaError_t e = cudaSuccess;
+#define AL(ptr, cnt)                                                   \
+    do {                                                               \
+        if (e == cudaSuccess) e = valloc(allocs, &(ptr), (size_t)(cnt)); \
+    } while (0)
+    A = DevA<T, V>{};
+    A.kind = op->kind;
+    A.m = op->m;
+    A.n = op->n;
+    const int tdt = sizeof(T) == 4 ? SGKS_F32 : SGKS_F64;
+    const int vdt = sizeof(V) == 4 ? SGKS_F32 : SGKS_F64;
+    if (op->kind == SGKS_OP_CSR) {
+        // malformed CSR (indices out of range) would make the kernels read out of bounds
+        int herr = 0;
+        e = validate_csr_device(op->row_ptr, op->col, op->m, op->n, op->nnz, d_err, st);
+        if (e == cudaSuccess) e = take_flag(d_err, st, &herr);
+        if (e == cudaSuccess && herr) {
+            *why = "CSR arrays are malformed (row_ptr or col)";
+            return SGKS_ERR_INVALID;
+        }
+        if (op->t_row_ptr && op->t_col && e == cudaSuccess) {
+            e = validate_csr_device(op->t_row_ptr, op->t_col, op->n, op->m, op->nnz, d_err, st);
+            if (e == cudaSuccess) e = take_flag(d_err, st, &herr);
+            if (e == cudaSuccess && herr) {
+                *why = "transposed CSR arrays are malformed";
+                return SGKS_ERR_INVALID;
+            }
+        }
+        A.rp = op->row_ptr;
+        A.ci = op->col;
+        if (op->val_dtype == vdt) {
+            A.val = (const V*)op->val;
+        } else {
+            V* v = nullptr;
+            AL(v, op->nnz);
+            if (e == cudaSuccess) e = convert_values(op->val, op->val_dtype, v, vdt, op->nnz, st);
+            A.val = v;
+        }
+        if (op->t_row_ptr && op->t_col && op->t_val) {
+            A.trp = op->t_row_ptr;
+            A.tci = op->t_col;
+            if (op->val_dtype == vdt) {
+                A.tval = (const V*)op->t_val;
+            } else {
+                V* v = nullptr;
+                AL(v, op->nnz);
+                if (e == cudaSuccess) e = convert_values(op->t_val, op->val_dtype, v, vdt, op->nnz, st);
+                A.tval = v;
+            }
+        } else {
+            int32_t *trp = nullptr, *tci = nullptr;
+            V* tv = nullptr;
+            AL(trp, op->n + 1);
+            AL(tci, op->nnz > 0 ? op->nnz : 1);
+            AL(tv, op->nnz > 0 ? op->nnz : 1);
+            if (e == cudaSuccess)
+                e = csr_transpose_device(op->m, op->n, op->nnz, A.rp, A.ci, A.val, vdt, trp, tci, tv, st);
+            A.trp = trp;
+            A.tci = tci;
+            A.tval = tv;
+        }
+    } else if (op->kind == SGKS_OP_DENSE) {
+        T* dd = nullptr;
+        AL(dd, op->m * op->n);
+        if (e == cudaSuccess) {
+            if (op->ld == op->n) {
+                e = convert_values(op->dense, op->val_dtype, dd, tdt, op->m * op->n, st);
+            } else {
+                const size_t es = op->val_dtype == SGKS_F32 ? 4 : 8;
+                for (int64_t r = 0; r < op->m && e == cudaSuccess; ++r)
+                    e = convert_values((const char*)op->dense + (size_t)r * op->ld * es, op->val_dtype,
+                                       dd + (size_t)r * op->n, tdt, op->n, st);
+            }
+        }
+        A.dense = dd;
+        A.ld = op->n;
+    } else {
+        T* pp = nullptr;
+        AL(pp, (size_t)op->kh * op->kw);
+        if (e == cudaSuccess) e = convert_values(op->psf, op->val_dtype, pp, tdt, (int64_t)op->kh * op->kw, st);
+        A.psf = pp;
+        A.nx = op->nx;
+        A.ny = op->ny;
+        A.kh = op->kh;
+        A.kw = op->kw;
+    }
+#undef AL
+    if (e == cudaErrorMemoryAllocation) {
+        *why = std::string("device allocation: ") + cudaGetErrorString(e);
+        return SGKS_ERR_NOMEM;
+    }
+    if (e != cudaSuccess) {
+        *why = std::string("operator preparation: ") + cudaGetErrorString(e);
+        return SGKS_ERR_CUDA;
+    }
+    return SGKS_OK;
+}
+
+int prepare_sparse_sign(uint64_t keyA, uint64_t keyL, int64_t m, int64_t p, int s, int zeta, SketchCSR& SK,
+                        std::vector<void*>& allocs, int* d_err, cudaStream_t st, std::string* why) {
+    cudaError_t e = cudaSuccess;
+    int32_t *pa = nullptr, *pl = nullptr;
+    uint32_t *ia = nullptr, *il = nullptr;
+    e = valloc(allocs, &pa, s + 1);
+    if (e == cudaSuccess) e = valloc(allocs, &pl, s + 1);
+    if (e == cudaSuccess) e = valloc(allocs, &ia, (size_t)m * zeta);
+    if (e == cudaSuccess) e = valloc(allocs, &il, (size_t)p * zeta);
+    if (e != cudaSuccess) {
+        *why = std::string("device allocation: ") + cudaGetErrorString(e);
+        return SGKS_ERR_NOMEM;
+    }
+    e = build_sketch_csr(keyA, m, s, zeta, pa, ia, d_err, st);
+    if (e == cudaSuccess) e = build_sketch_csr(keyL, p, s, zeta, pl, il, d_err, st);
+    int herr = 0;
+    if (e == cudaSuccess) e = take_flag(d_err, st, &herr);
+    if (e != cudaSuccess) {
+        *why = std::string("sketch preparation: ") + cudaGetErrorString(e);
+        return SGKS_ERR_CUDA;
+    }
+    if (herr) {
+        *why = "sparse-sign draw limit exceeded";
+        return SGKS_ERR_SKETCH;
+    }
+    SK.ptrA = pa;
+    SK.idxA = ia;
+    SK.ptrL = pl;
+    SK.idxL = il;
+    return SGKS_OK;
+}
+
+template int prepare_operator<float, float>(const sgks_op*, DevA<float, float>&, std::vector<void*>&, int*,
+                                            cudaStream_t, std::string*);
+template int prepare_operator<double, float>(const sgks_op*, DevA<double, float>&, std::vector<void*>&, int*,
+                                             cudaStream_t, std::string*);
+template int prepare_operator<double, double>(const sgks_op*, DevA<double, double>&, std::vector<void*>&, int*,
+                                              cudaStream_t, std::string*);
+
+}  // namespace sgks
+
 template <typename T, typename V>
 static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, const void* b, double lambda,
                         int s, uint64_t seed, const sgks_options& o, int cluster) {
@@ -399,18 +580,7 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     D.has_xtrue = o.x_true != nullptr;
 
     DevL& L = E->L;
-    L.kind = reg->kind;
-    L.nx = reg->nx;
-    L.ny = reg->kind == SGKS_REG_FD1 ? 1 : reg->ny;
-    L.nt = reg->kind == SGKS_REG_SPACETIME ? reg->nt : 1;
-    L.n = (int64_t)L.nx * L.ny * L.nt;
-    const int64_t nx = L.nx, ny = L.ny, nt = L.nt;
-    switch (L.kind) {
-        case SGKS_REG_FD1: L.p = nx - 1; break;
-        case SGKS_REG_GRAD2D: L.p = ny * (nx - 1) + (ny - 1) * nx; break;
-        case SGKS_REG_LAPLACE2D: L.p = nx * ny; break;
-        default: L.p = nt * (ny * (nx - 1) + (ny - 1) * nx) + (nt - 1) * nx * ny; break;
-    }
+    L = make_devl(reg);
     D.p = L.p;
 
     const int64_t sl_m = (D.m + 31) / 32, sl_p = (D.p + 31) / 32;
@@ -498,114 +668,25 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     if (e == cudaSuccess && xform) e = cudaMemsetAsync(EX->X.xs, 0, 8 * D.n, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(E->d_err, 0, sizeof(int), h->st);
 
-    // operator
-    DevA<T, V>& A = E->A;
-    A.kind = op->kind;
-    A.m = op->m;
-    A.n = op->n;
-    const int tdt = sizeof(T) == 4 ? SGKS_F32 : SGKS_F64;
-    const int vdt = sizeof(V) == 4 ? SGKS_F32 : SGKS_F64;
-    if (op->kind == SGKS_OP_CSR) {
-        // malformed CSR (indices out of range) would make the kernels read out of bounds
-        int herr = 0;
-        if (e == cudaSuccess) e = validate_csr_device(op->row_ptr, op->col, op->m, op->n, op->nnz, E->d_err, h->st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, E->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
-        if (e == cudaSuccess && herr) return fail(h, SGKS_ERR_INVALID, "CSR arrays are malformed (row_ptr or col)");
-        if (e == cudaSuccess) e = cudaMemsetAsync(E->d_err, 0, sizeof(int), h->st);
-        if (op->t_row_ptr && op->t_col && e == cudaSuccess) {
-            e = validate_csr_device(op->t_row_ptr, op->t_col, op->n, op->m, op->nnz, E->d_err, h->st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, E->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
-            if (e == cudaSuccess && herr) return fail(h, SGKS_ERR_INVALID, "transposed CSR arrays are malformed");
-            if (e == cudaSuccess) e = cudaMemsetAsync(E->d_err, 0, sizeof(int), h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "workspace initialisation");
+    {
+        std::string why;
+        const int rc = prepare_operator<T, V>(op, E->A, h->allocs, E->d_err, h->st, &why);
+        if (rc != SGKS_OK) return fail(h, rc, why);
+        if (!gauss) {
+            const int rs = prepare_sparse_sign(D.keyA, D.keyL, D.m, D.p, s, o.zeta, E->SK, h->allocs, E->d_err,
+                                               h->st, &why);
+            if (rs != SGKS_OK) return fail(h, rs, why);
         }
-        A.rp = op->row_ptr;
-        A.ci = op->col;
-        if (op->val_dtype == vdt) {
-            A.val = (const V*)op->val;
-        } else {
-            V* v;
-            AL(v, op->nnz);
-            if (e == cudaSuccess) e = convert_values(op->val, op->val_dtype, v, vdt, op->nnz, h->st);
-            A.val = v;
-        }
-        if (op->t_row_ptr && op->t_col && op->t_val) {
-            A.trp = op->t_row_ptr;
-            A.tci = op->t_col;
-            if (op->val_dtype == vdt) {
-                A.tval = (const V*)op->t_val;
-            } else {
-                V* v;
-                AL(v, op->nnz);
-                if (e == cudaSuccess) e = convert_values(op->t_val, op->val_dtype, v, vdt, op->nnz, h->st);
-                A.tval = v;
-            }
-        } else {
-            int32_t *trp, *tci;
-            V* tv;
-            AL(trp, op->n + 1);
-            AL(tci, op->nnz > 0 ? op->nnz : 1);
-            AL(tv, op->nnz > 0 ? op->nnz : 1);
-            if (e == cudaSuccess)
-                e = csr_transpose_device(op->m, op->n, op->nnz, A.rp, A.ci, A.val, vdt, trp, tci, tv, h->st);
-            A.trp = trp;
-            A.tci = tci;
-            A.tval = tv;
-        }
-    } else if (op->kind == SGKS_OP_DENSE) {
-        T* dd;
-        AL(dd, op->m * op->n);
-        if (e == cudaSuccess) {
-            if (op->ld == op->n) {
-                e = convert_values(op->dense, op->val_dtype, dd, tdt, op->m * op->n, h->st);
-            } else {
-                for (int64_t r = 0; r < op->m && e == cudaSuccess; ++r) {
-                    const size_t es = op->val_dtype == SGKS_F32 ? 4 : 8;
-                    e = convert_values((const char*)op->dense + (size_t)r * op->ld * es, op->val_dtype,
-                                       dd + (size_t)r * op->n, tdt, op->n, h->st);
-                }
-            }
-        }
-        A.dense = dd;
-        A.ld = op->n;
-    } else {
-        T* pp;
-        AL(pp, (size_t)op->kh * op->kw);
-        if (e == cudaSuccess) e = convert_values(op->psf, op->val_dtype, pp, tdt, (int64_t)op->kh * op->kw, h->st);
-        A.psf = pp;
-        A.nx = op->nx;
-        A.ny = op->ny;
-        A.kh = op->kh;
-        A.kw = op->kw;
-    }
-    if (!gauss && e == cudaSuccess) {
-        int32_t *pa, *pl;
-        uint32_t *ia, *il;
-        AL(pa, s + 1);
-        AL(pl, s + 1);
-        AL(ia, (size_t)D.m * o.zeta);
-        AL(il, (size_t)D.p * o.zeta);
-        if (e == cudaSuccess) e = build_sketch_csr(D.keyA, D.m, s, o.zeta, pa, ia, E->d_err, h->st);
-        if (e == cudaSuccess) e = build_sketch_csr(D.keyL, D.p, s, o.zeta, pl, il, E->d_err, h->st);
-        int herr = 0;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, E->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
-        if (e == cudaSuccess && herr) return fail(h, SGKS_ERR_SKETCH, "sparse-sign draw limit exceeded");
-        E->SK.ptrA = pa;
-        E->SK.idxA = ia;
-        E->SK.ptrL = pl;
-        E->SK.idxL = il;
     }
 #undef AL
-    if (e != cudaSuccess) return cuda_fail(h, e, "operator preparation");
     E->gSA = o.gauss_SA;
     E->gSL = o.gauss_SL;
     return SGKS_OK;
 }
 
-static int validate(const sgks_op* A, const sgks_reg* L, const void* b, double lambda, int s, const sgks_options& o,
-                    std::string* why) {
+int sgks::validate_problem(const sgks_op* A, const sgks_reg* L, const void* b, double lambda, int s,
+                           const sgks_options& o, std::string* why) {
     auto bad = [&](const char* m) {
         *why = m;
         return SGKS_ERR_INVALID;
@@ -673,7 +754,7 @@ int sgks_create(sgks_handle** hp, const sgks_op* A, const sgks_reg* L, const voi
     if (o.zeta == 0) o.zeta = 8;
     if (o.cgs_passes == 0) o.cgs_passes = 2;
     std::string why;
-    int rc = validate(A, L, b, lambda, sketch_rows, o, &why);
+    int rc = validate_problem(A, L, b, lambda, sketch_rows, o, &why);
     if (rc != SGKS_OK) return fail(nullptr, rc, why);
 
     sgks_handle* h = new (std::nothrow) sgks_handle();

@@ -1,0 +1,726 @@
+// Batched handle: many sGKS problems (Algorithm 2 each) solved in one handle.
+//
+// Instances whose operator descriptors (A and L) are identical share the prepared operator and
+// run together as one group of B instances in the interleaved layout of k_batch.cu, so each pass
+// over A serves B right-hand sides.  A group size is a power of two (<= 256); a set of identical
+// instances is split into power-of-two groups, largest first.  Instances with different
+// operators -- ragged sizes such as space-time problems with different frame counts -- form
+// separate groups.  Every group runs on its own stream, forked from and joined back to the
+// handle's stream, and one captured CUDA graph holds one iteration of every group.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sgks_internal.cuh"
+
+using namespace sgks;
+
+namespace {
+
+thread_local std::string g_batch_error;
+
+// Per-kernel timing of eager steps (sgks_batch_profile_steps): the classes of sgks_profile_steps.
+enum { BK_GRAD_APPEND = 0, BK_APPLY = 1, BK_QR_APPEND = 2, BK_STACKED_SOLVE = 3, BK_COMBINE_REFINE = 4,
+       BK_GRAD_REFINE = 5, BK_REFINE_SOLVE = 6, BK_COMBINE = 7, BK_GATHER = 8, BK_COUNT = 9, BK_NONE = -1 };
+
+struct BProf {
+    cudaEvent_t ev[2];
+    double ms[BK_COUNT] = {0};
+    int64_t count[BK_COUNT] = {0};
+};
+
+struct GroupBase {
+    BProf* prof = nullptr;
+    BDims D{};
+    Dims Ds{};                  // dimensions read by the FP64 cluster kernels (k_small2.cu)
+    BSmall S{};
+    Small* Sarr = nullptr;      // device [B]: per-instance views for the cluster kernels
+    std::vector<int> members;   // instance index of each slot
+    cudaStream_t st = nullptr;
+    int n_refine = 0;
+    PtrPack bp{}, xtp{};
+    bool has_xt = false;
+    virtual ~GroupBase() {}
+    virtual cudaError_t setup() = 0;
+    virtual cudaError_t step() = 0;
+    virtual cudaError_t copy_x(const PtrPack& out, cudaStream_t s) = 0;
+};
+
+// one launcher call: counted, and timed with an event pair when profiling
+template <typename F>
+cudaError_t run_timed(GroupBase* g, int cls, int nl, F&& f) {
+    add_launches(nl);
+    if (!g->prof || cls == BK_NONE) return f();
+    cudaEventRecord(g->prof->ev[0], g->st);
+    cudaError_t e = f();
+    cudaEventRecord(g->prof->ev[1], g->st);
+    cudaEventSynchronize(g->prof->ev[1]);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, g->prof->ev[0], g->prof->ev[1]);
+    g->prof->ms[cls] += t;
+    g->prof->count[cls] += 1;
+    return e;
+}
+
+#define RUNC(cls, nl, expr)                                          \
+    do {                                                             \
+        if (e == cudaSuccess) e = run_timed(this, cls, nl, [&] { return (expr); }); \
+    } while (0)
+#define RUN(nl, expr) RUNC(BK_NONE, nl, expr)
+
+template <typename T, typename V>
+struct Group : GroupBase {
+    DevA<T, V> A{};
+    DevL L{};
+    BBulk<T> X{};
+    SketchCSR SK{};
+
+    cudaError_t sketch_column() {
+        cudaError_t e = cudaSuccess;
+        RUNC(BK_APPLY, 1, (launchb_apply_column<T, V>(D, A, L, X, S, st)));
+        RUNC(BK_GATHER, 1, launchb_sketch_gather<T>(D, X, SK, S, nullptr, nullptr, st));
+        return e;
+    }
+
+    cudaError_t small_append() {
+        cudaError_t e = cudaSuccess;
+        RUNC(BK_QR_APPEND, 1, launch_qr_append(Ds, Small{}, st, Sarr, D.B));
+        RUNC(BK_STACKED_SOLVE, 1, launch_stacked_solve(Ds, Small{}, st, Sarr, D.B));
+        return e;
+    }
+
+    cudaError_t refine() {
+        cudaError_t e = cudaSuccess;
+        RUNC(BK_COMBINE_REFINE, 1, launchb_combine<T>(D, X, S, 0, st));
+        RUNC(BK_GRAD_REFINE, 1, (launchb_gradient<T, V>(D, A, L, X, S, X.r, st)));
+        RUNC(BK_GRAD_REFINE, 1, launchb_wtr<T>(D, X, S, X.r, st));
+        RUNC(BK_REFINE_SOLVE, 1, launch_refine_solve2(Ds, Small{}, st, Sarr, D.B, D.nb_refine / 8));
+        return e;
+    }
+
+    cudaError_t normalize(T* w) {
+        cudaError_t e = cudaSuccess;
+        RUN(2, launchb_dots<T>(D, w, 1, w, S, st));
+        RUN(1, launchb_vec_update<T>(D, w, w, 0, S, 1, st));
+        return e;
+    }
+
+    // x_0 of every instance: S_A b_i, ||x_true_i||^2, W_0 = orthonormal basis of K_l(A^T A, A^T b_i)
+    // by CGS2 (Sec. 2.1, Sec. 4), the sketched QR of W_0, y_0, refinement, x_0
+    cudaError_t setup() override {
+        const int B = D.B;
+        cudaError_t e = cudaMemsetAsync(S.sc, 0, sizeof(DevScalars) * B, st);
+        RUN(1, launchb_gather_in<T>(bp, X.b, D.m, B, st));
+        RUN(1, launchb_sketch_gather<T>(D, X, SK, S, X.b, S.Sb, st));
+        if (has_xt) {
+            RUN(1, launchb_gather_in<T>(xtp, X.xtrue, D.n, B, st));
+            RUN(2, launchb_dots<T>(D, X.xtrue, 1, X.xtrue, S, st));
+            RUN(1, launchb_set_xt2(S, B, st));
+        }
+        T* W = X.W;
+        const size_t col = (size_t)D.n * B;
+        RUN(1, (launchb_apply<T, V>(D, A, L, SGKS_APPLY_AT, X.b, W, st)));
+        if (e == cudaSuccess) e = normalize(W);
+        for (int j = 1; j < D.ell && e == cudaSuccess; ++j) {
+            T* wj = W + j * col;
+            RUN(1, (launchb_apply<T, V>(D, A, L, SGKS_APPLY_A, W + (j - 1) * col, X.tm, st)));
+            RUN(1, (launchb_apply<T, V>(D, A, L, SGKS_APPLY_AT, X.tm, wj, st)));
+            for (int pass = 0; pass < 2; ++pass) {
+                RUN(2, launchb_dots<T>(D, W, j, wj, S, st));
+                RUN(1, launchb_vec_update<T>(D, wj, W, j, S, 0, st));
+            }
+            if (e == cudaSuccess) e = normalize(wj);
+        }
+        for (int j = 0; j < D.ell && e == cudaSuccess; ++j) {
+            e = sketch_column();
+            if (e == cudaSuccess) e = small_append();
+        }
+        for (int r = 0; r < n_refine && e == cudaSuccess; ++r) e = refine();
+        RUN(1, launchb_combine<T>(D, X, S, 2, st));
+        return e;
+    }
+
+    // one iteration of Algorithm 2 for every live instance of the group
+    cudaError_t step() override {
+        cudaError_t e = cudaSuccess;
+        RUNC(BK_GRAD_APPEND, 1, (launchb_gradient<T, V>(D, A, L, X, S, nullptr, st)));
+        if (e == cudaSuccess) e = sketch_column();
+        if (e == cudaSuccess) e = small_append();
+        for (int r = 0; r < n_refine && e == cudaSuccess; ++r) e = refine();
+        RUNC(BK_COMBINE, 1, launchb_combine<T>(D, X, S, 1, st));
+        return e;
+    }
+
+    cudaError_t copy_x(const PtrPack& out, cudaStream_t s) override {
+        cudaError_t e = cudaSuccess;
+        RUN(1, launchb_scatter_out<T>(X.xs, out, D.n, D.B, s));
+        return e;
+    }
+};
+
+int map_status(int dev) {
+    switch (dev) {
+        case ST_OK: return SGKS_OK;
+        case ST_BREAKDOWN: return SGKS_BREAKDOWN;
+        case ST_STOPPED: return SGKS_STOPPED;
+        case ST_NONFINITE: return SGKS_ERR_NONFINITE;
+        case ST_SKETCH: return SGKS_ERR_SKETCH;
+        default: return SGKS_ERR_STATE;
+    }
+}
+
+}  // namespace
+
+struct sgks_batch {
+    std::vector<GroupBase*> groups;
+    std::vector<cudaStream_t> gst;     // one stream per group when there are several
+    std::vector<cudaEvent_t> ev_join;
+    cudaEvent_t ev_fork = nullptr;
+    cudaStream_t st = nullptr, user = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::vector<void*> allocs;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t graph_launches = 0;
+    std::string err;
+    DevScalars* sc_host = nullptr;     // pinned, one entry per instance slot (groups in order)
+    int count = 0;
+    int max_iters = 0;
+    int steps_since_setup = 0;
+    int* d_err = nullptr;
+};
+
+namespace {
+
+int bfail(sgks_batch* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_batch_error = msg;
+    return code;
+}
+
+int bcuda_fail(sgks_batch* h, cudaError_t e, const char* where) {
+    return bfail(h, SGKS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <typename P>
+cudaError_t balloc(sgks_batch* h, P** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(P) + 16);
+    if (e != cudaSuccess) return e;
+    h->allocs.push_back(q);
+    *p = (P*)q;
+    return cudaSuccess;
+}
+
+void join_in(sgks_batch* h) {
+    cudaEventRecord(h->ev_in, h->user);
+    cudaStreamWaitEvent(h->st, h->ev_in, 0);
+}
+
+void join_out(sgks_batch* h) {
+    cudaEventRecord(h->ev_out, h->st);
+    cudaStreamWaitEvent(h->user, h->ev_out, 0);
+}
+
+// run f(group) for every group, each on its own stream, forked from and joined to h->st
+template <typename F>
+cudaError_t for_groups(sgks_batch* h, F&& f) {
+    if (h->groups.size() == 1) return f(h->groups[0]);
+    cudaError_t e = cudaEventRecord(h->ev_fork, h->st);
+    for (size_t g = 0; g < h->groups.size() && e == cudaSuccess; ++g) {
+        e = cudaStreamWaitEvent(h->gst[g], h->ev_fork, 0);
+        if (e == cudaSuccess) e = f(h->groups[g]);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_join[g], h->gst[g]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->st, h->ev_join[g], 0);
+    }
+    return e;
+}
+
+// largest group size: a power of two <= 256 whose refinement accumulators fit in shared memory
+int max_group_size(int dmax, int n_refine, size_t elem) {
+    int B = kMaxBatch;
+    while (B > 1 && n_refine > 0 && batch_refine_smem(dmax, B, elem) > 200 * 1024) B >>= 1;
+    return B;
+}
+
+template <typename T, typename V>
+int build_groups(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const std::vector<int>& inst,
+                 const void* const* b, const double* lambdas, const void* const* x_true, int s, uint64_t seed,
+                 const sgks_options& o, int cluster2) {
+    // operator, L and the sketches: prepared once, shared by the groups of this operator
+    DevA<T, V> A{};
+    std::string why;
+    int rc = prepare_operator<T, V>(op, A, h->allocs, h->d_err, h->st, &why);
+    if (rc != SGKS_OK) return bfail(h, rc, why);
+    const DevL L = make_devl(reg);
+    SketchCSR SK{};
+    rc = prepare_sparse_sign(sketch_key_host_dev(seed, 0), sketch_key_host_dev(seed, 1), op->m, L.p, s, o.zeta, SK,
+                             h->allocs, h->d_err, h->st, &why);
+    if (rc != SGKS_OK) return bfail(h, rc, why);
+
+    const int dmax = o.ell + o.max_iters;
+    const int bcap = max_group_size(dmax, o.n_refine, sizeof(T));
+    if (o.n_refine > 0 && batch_refine_smem(dmax, 1, sizeof(T)) > 200 * 1024)
+        return bfail(h, SGKS_ERR_INVALID, "ell + max_iters too large for the batched refinement");
+    size_t pos = 0;
+    while (pos < inst.size()) {
+        int B = bcap;
+        while ((size_t)B > inst.size() - pos) B >>= 1;
+        Group<T, V>* G = new (std::nothrow) Group<T, V>();
+        if (!G) return bfail(h, SGKS_ERR_NOMEM, "host allocation failed");
+        h->groups.push_back(G);
+        G->members.assign(inst.begin() + pos, inst.begin() + pos + B);
+        pos += B;
+        G->A = A;
+        G->L = L;
+        G->SK = SK;
+        G->n_refine = o.n_refine;
+        G->has_xt = x_true != nullptr;
+        for (int i = 0; i < B; ++i) {
+            G->bp.p[i] = b[G->members[i]];
+            G->xtp.p[i] = x_true ? x_true[G->members[i]] : nullptr;
+        }
+        BDims& D = G->D;
+        D.n = op->n;
+        D.m = op->m;
+        D.p = L.p;
+        D.B = B;
+        D.s = s;
+        D.dmax = dmax;
+        D.ell = o.ell;
+        D.max_iters = o.max_iters;
+        D.sketch_scale = 1.0 / sqrt((double)o.zeta);
+        const int G8 = kThreads / B;   // rows of a combine tile per row slot
+        const int64_t TR = 8 * (int64_t)G8;
+        const int64_t ctiles = (D.n + TR - 1) / TR + (D.m + TR - 1) / TR;
+        D.nb_combine = (int)std::min<int64_t>(ctiles, 4 * 152);
+        const int64_t rtiles = (D.n + 1024 / B - 1) / (1024 / B);
+        {   // enough CTAs to fill every SM at the residency the refinement's shared memory allows
+            const size_t sm = batch_refine_smem(dmax, B, sizeof(T)) + 2048;
+            int64_t per_sm = (int64_t)((227 * 1024) / sm);
+            per_sm = std::max<int64_t>(1, std::min<int64_t>(per_sm, 8));
+            const int64_t cap = std::max<int64_t>(8, 152 * per_sm / 8 * 8);
+            D.nb_refine = (int)std::min<int64_t>((rtiles + 7) / 8 * 8, cap);
+        }
+        D.nb_setup = (int)std::min<int64_t>((D.n * B + kThreads - 1) / kThreads, 304);
+        Dims& Ds = G->Ds;
+        Ds.n = D.n;
+        Ds.m = D.m;
+        Ds.p = D.p;
+        Ds.s = s;
+        Ds.zeta = o.zeta;
+        Ds.dmax = dmax;
+        Ds.ell = o.ell;
+        Ds.npA = 1;
+        Ds.npL = 1;
+        Ds.cluster2 = cluster2;
+        Ds.fast_small = 1;
+        Ds.sketch_kind = SGKS_SKETCH_SPARSE_SIGN;
+        Ds.sketch_scale = D.sketch_scale;
+        Ds.cgs_passes = o.cgs_passes;
+        Ds.max_iters = o.max_iters;
+
+        cudaError_t e = cudaSuccess;
+#define BA(ptr, cnt)                                              \
+    do {                                                          \
+        if (e == cudaSuccess) e = balloc(h, &(ptr), (size_t)(cnt)); \
+    } while (0)
+        BBulk<T>& X = G->X;
+        const size_t nB = (size_t)D.n * B, mB = (size_t)D.m * B, pB = (size_t)D.p * B;
+        BA(X.W, (size_t)dmax * nB);
+        BA(X.AW, (size_t)dmax * mB);
+        BA(X.x, nB);
+        BA(X.xs, nB);
+        BA(X.e, mB);
+        BA(X.b, mB);
+        if (G->has_xt) BA(X.xtrue, nB);
+        BA(X.tp, pB);
+        BA(X.tm, mB);
+        if (o.n_refine > 0) BA(X.r, nB);
+        BSmall& S = G->S;
+        BA(S.partA, (size_t)B * s);
+        BA(S.partL, (size_t)B * s);
+        BA(S.Sb, (size_t)B * s);
+        BA(S.gpart, (size_t)B * (D.nb_refine / 8) * dmax);
+        BA(S.kapart, (size_t)D.nb_combine * B * 3);
+        BA(S.y, (size_t)B * dmax);
+        BA(S.lam, B);
+        BA(S.rc_hist, (size_t)B * o.max_iters);
+        BA(S.rre_hist, (size_t)B * o.max_iters);
+        BA(S.setup_part, (size_t)D.nb_setup * o.ell * B);
+        BA(S.setup_coef, (size_t)o.ell * B);
+        BA(S.sc, B);
+        BA(S.ka_done, 1);
+        // per-instance FP64 state of the sketched QR factors and the projected solve
+        const size_t dm2 = (size_t)dmax * dmax;
+        double *QA, *QL, *RA, *RL, *QT, *Xr, *z, *qo, *Xm, *Tm, *dA;
+        BA(QA, (size_t)B * s * dmax);
+        BA(QL, (size_t)B * s * dmax);
+        BA(RA, B * dm2);
+        BA(RL, B * dm2);
+        BA(QT, B * 2 * dm2);
+        BA(Xr, B * dm2);
+        BA(z, (size_t)B * dmax);
+        BA(qo, (size_t)B * 8);
+        BA(Xm, B * dm2);
+        BA(Tm, B * dm2);
+        BA(dA, (size_t)B * dmax);
+        BA(G->Sarr, B);
+#undef BA
+        if (e != cudaSuccess) return bfail(h, SGKS_ERR_NOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
+        std::vector<Small> sm((size_t)B);
+        std::vector<double> lam((size_t)B);
+        for (int i = 0; i < B; ++i) {
+            Small& q = sm[i];
+            q = Small{};
+            q.QA = QA + (size_t)i * s * dmax;
+            q.QL = QL + (size_t)i * s * dmax;
+            q.RA = RA + i * dm2;
+            q.RL = RL + i * dm2;
+            q.QT = QT + i * 2 * dm2;
+            q.Xr = Xr + i * dm2;
+            q.z = z + (size_t)i * dmax;
+            q.qr_out = qo + (size_t)i * 8;
+            q.X = Xm + i * dm2;
+            q.Tm = Tm + i * dm2;
+            q.dA = dA + (size_t)i * dmax;
+            q.y = S.y + (size_t)i * dmax;
+            q.Sb = S.Sb + (size_t)i * s;
+            q.partA = S.partA + (size_t)i * s;
+            q.partL = S.partL + (size_t)i * s;
+            q.gpart = S.gpart + (size_t)i * (D.nb_refine / 8) * dmax;
+            q.sc = S.sc + i;
+            q.lam = lambdas[G->members[i]];
+            lam[i] = q.lam;
+        }
+        e = cudaMemcpy(G->Sarr, sm.data(), sizeof(Small) * B, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(S.lam, lam.data(), sizeof(double) * B, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemsetAsync(S.y, 0, sizeof(double) * B * dmax, h->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(X.xs, 0, sizeof(T) * nB, h->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(S.ka_done, 0, sizeof(int), h->st);
+        if (e != cudaSuccess) return bcuda_fail(h, e, "batch workspace initialisation");
+    }
+    return SGKS_OK;
+}
+
+cudaError_t ensure_graph(sgks_batch* h) {
+    if (h->gexec) return cudaSuccess;
+    cudaError_t e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    const int64_t l0 = sgks_kernel_launches();
+    cudaError_t e2 = for_groups(h, [](GroupBase* g) { return g->step(); });
+    h->graph_launches = sgks_kernel_launches() - l0;
+    add_launches(-h->graph_launches);
+    e = cudaStreamEndCapture(h->st, &h->graph);
+    if (e2 != cudaSuccess) return e2;
+    if (e != cudaSuccess) return e;
+    return cudaGraphInstantiate(&h->gexec, h->graph, 0);
+}
+
+cudaError_t read_scalars(sgks_batch* h) {
+    size_t off = 0;
+    cudaError_t e = cudaSuccess;
+    for (GroupBase* g : h->groups) {
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->sc_host + off, g->S.sc, sizeof(DevScalars) * g->D.B, cudaMemcpyDeviceToHost, h->st);
+        off += g->D.B;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sgks_batch_create(sgks_batch** hp, int32_t count, const sgks_op* A, const sgks_reg* L, const void* const* b,
+                      const double* lambdas, const void* const* x_true, int32_t sketch_rows, uint64_t seed,
+                      const sgks_options* opt, void* stream) {
+    if (!hp) return bfail(nullptr, SGKS_ERR_INVALID, "h must be non-NULL");
+    *hp = nullptr;
+    if (count < 1 || !A || !L || !b || !lambdas) return bfail(nullptr, SGKS_ERR_INVALID, "bad batch arguments");
+    sgks_options o{};
+    if (opt) o = *opt;
+    if (o.max_iters == 0) o.max_iters = 100;
+    if (o.ell == 0) o.ell = 3;
+    if (o.zeta == 0) o.zeta = 8;
+    if (o.cgs_passes == 0) o.cgs_passes = 2;
+    if (o.precision != SGKS_PREC_FP64 && o.precision != SGKS_PREC_FP32)
+        return bfail(nullptr, SGKS_ERR_INVALID, "batches support SGKS_PREC_FP64 and SGKS_PREC_FP32");
+    if (o.sketch_kind != SGKS_SKETCH_SPARSE_SIGN)
+        return bfail(nullptr, SGKS_ERR_INVALID, "batches support the sparse-sign sketch only");
+    o.x_true = nullptr;
+    for (int i = 0; i < count; ++i) {
+        std::string why;
+        const int rc = validate_problem(&A[i], &L[i], b[i], lambdas[i], sketch_rows, o, &why);
+        if (rc != SGKS_OK) return bfail(nullptr, rc, "instance " + std::to_string(i) + ": " + why);
+        if (x_true && !x_true[i]) return bfail(nullptr, SGKS_ERR_INVALID, "x_true must be given for every instance");
+    }
+    sgks_batch* h = new (std::nothrow) sgks_batch();
+    if (!h) return bfail(nullptr, SGKS_ERR_NOMEM, "host allocation failed");
+    h->user = (cudaStream_t)stream;
+    h->count = count;
+    h->max_iters = o.max_iters;
+    int cluster2 = 0;
+    cudaError_t e = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->sc_host, sizeof(DevScalars) * count);
+    if (e == cudaSuccess) e = balloc(h, &h->d_err, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->st);
+    if (e == cudaSuccess) {
+        e = configure_small_fast(&cluster2, sketch_rows, o.ell + o.max_iters);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            g_batch_error = "sketch_rows x (ell + max_iters) too large for the on-chip QR kernels of a batch";
+            sgks_batch_destroy(h);
+            return SGKS_ERR_INVALID;
+        }
+    }
+    if (e != cudaSuccess) {
+        const int rc = bcuda_fail(h, e, "sgks_batch_create");
+        g_batch_error = h->err;
+        sgks_batch_destroy(h);
+        return rc;
+    }
+    join_in(h);
+    // group instances by operator descriptor
+    std::vector<int> rep;                 // first instance of each distinct operator
+    std::vector<std::vector<int>> members;
+    for (int i = 0; i < count; ++i) {
+        size_t k = 0;
+        for (; k < rep.size(); ++k)
+            if (memcmp(&A[i], &A[rep[k]], sizeof(sgks_op)) == 0 && memcmp(&L[i], &L[rep[k]], sizeof(sgks_reg)) == 0)
+                break;
+        if (k == rep.size()) {
+            rep.push_back(i);
+            members.emplace_back();
+        }
+        members[k].push_back(i);
+    }
+    int rc = SGKS_OK;
+    for (size_t k = 0; k < rep.size() && rc == SGKS_OK; ++k) {
+        const sgks_op* op = &A[rep[k]];
+        const sgks_reg* reg = &L[rep[k]];
+        if (o.precision == SGKS_PREC_FP32)
+            rc = build_groups<float, float>(h, op, reg, members[k], b, lambdas, x_true, sketch_rows, seed, o, cluster2);
+        else if (op->kind == SGKS_OP_CSR && op->val_dtype == SGKS_F64)
+            rc = build_groups<double, double>(h, op, reg, members[k], b, lambdas, x_true, sketch_rows, seed, o,
+                                              cluster2);
+        else
+            rc = build_groups<double, float>(h, op, reg, members[k], b, lambdas, x_true, sketch_rows, seed, o,
+                                             cluster2);
+    }
+    if (rc == SGKS_OK && h->groups.size() > 1) {
+        for (size_t g = 0; g < h->groups.size() && e == cudaSuccess; ++g) {
+            cudaStream_t s = nullptr;
+            cudaEvent_t ev = nullptr;
+            e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+            if (e == cudaSuccess) h->gst.push_back(s);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) h->ev_join.push_back(ev);
+            if (e == cudaSuccess) h->groups[g]->st = s;
+        }
+        if (e != cudaSuccess) rc = bcuda_fail(h, e, "group streams");
+    } else if (rc == SGKS_OK) {
+        h->groups[0]->st = h->st;
+    }
+    if (rc == SGKS_OK) {
+        e = cudaStreamSynchronize(h->st);   // operator preparation done before the group streams start
+        if (e == cudaSuccess) e = for_groups(h, [](GroupBase* g) { return g->setup(); });
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        if (e != cudaSuccess) rc = bcuda_fail(h, e, "batch setup");
+    }
+    if (rc != SGKS_OK) {
+        g_batch_error = h->err;
+        sgks_batch_destroy(h);
+        return rc;
+    }
+    join_out(h);
+    *hp = h;
+    return SGKS_OK;
+}
+
+int sgks_batch_reset(sgks_batch* h, const void* const* b_new) {
+    if (!h || !b_new) return bfail(h, SGKS_ERR_INVALID, "handle and b_new must be non-NULL");
+    for (int i = 0; i < h->count; ++i)
+        if (!b_new[i]) return bfail(h, SGKS_ERR_INVALID, "b_new must hold a pointer for every instance");
+    for (GroupBase* g : h->groups)
+        for (int i = 0; i < g->D.B; ++i) g->bp.p[i] = b_new[g->members[i]];
+    join_in(h);
+    cudaError_t e = for_groups(h, [](GroupBase* g) { return g->setup(); });
+    join_out(h);
+    if (e != cudaSuccess) return bcuda_fail(h, e, "sgks_batch_reset");
+    h->steps_since_setup = 0;
+    return SGKS_OK;
+}
+
+int sgks_batch_step(sgks_batch* h) {
+    if (!h) return SGKS_ERR_INVALID;
+    if (h->steps_since_setup >= h->max_iters) return bfail(h, SGKS_ERR_STATE, "basis is full (max_iters reached)");
+    join_in(h);
+    cudaError_t e = for_groups(h, [](GroupBase* g) { return g->step(); });
+    join_out(h);
+    if (e != cudaSuccess) return bcuda_fail(h, e, "sgks_batch_step");
+    h->steps_since_setup++;
+    return SGKS_OK;
+}
+
+int sgks_batch_solve(sgks_batch* h, int32_t iters, double tol, void* const* x_out, sgks_report* reps) {
+    if (!h || iters < 0) return bfail(h, SGKS_ERR_INVALID, "bad handle or iters < 0");
+    if (iters > h->max_iters - h->steps_since_setup)
+        return bfail(h, SGKS_ERR_STATE, "iters exceeds the remaining basis capacity");
+    join_in(h);
+    cudaError_t e = ensure_graph(h);
+    if (e != cudaSuccess) {
+        join_out(h);
+        return bcuda_fail(h, e, "graph capture");
+    }
+    for (GroupBase* g : h->groups) {
+        if (e == cudaSuccess) e = launchb_set_tol(g->S.sc, g->D.B, tol, h->st);
+        add_launches(1);
+    }
+    const int it0 = h->steps_since_setup;
+    for (int k = 0; k < iters && e == cudaSuccess; ++k) e = cudaGraphLaunch(h->gexec, h->st);
+    add_launches(h->graph_launches * iters);
+    h->steps_since_setup += iters;
+    if (x_out) {
+        for (GroupBase* g : h->groups) {
+            PtrPack out{};
+            for (int i = 0; i < g->D.B; ++i) out.p[i] = x_out[g->members[i]];
+            if (e == cudaSuccess) e = g->copy_x(out, h->st);
+        }
+    }
+    if (e == cudaSuccess) e = read_scalars(h);
+    join_out(h);
+    if (e != cudaSuccess) return bcuda_fail(h, e, "sgks_batch_solve");
+    int worst = SGKS_OK;
+    size_t off = 0;
+    std::vector<double> tmp;
+    for (GroupBase* g : h->groups) {
+        for (int i = 0; i < g->D.B; ++i) {
+            const DevScalars& sc = h->sc_host[off + i];
+            const int st = map_status(sc.status);
+            if (st < 0) worst = st;
+            if (!reps) continue;
+            sgks_report& r = reps[g->members[i]];
+            const int done = sc.iter - it0;
+            r.iters_done = done;
+            r.status = st;
+            r.subspace_dim = sc.d;
+            r.rc_last = sc.rc_last;
+            r.rre_last = sc.rre_last;
+            r.rre0 = sc.rre0;
+            if (done > 0 && (r.rc || r.rre)) {
+                tmp.resize((size_t)done);
+                const size_t base = (size_t)i * h->max_iters + it0;
+                if (r.rc) {
+                    e = cudaMemcpy(tmp.data(), g->S.rc_hist + base, sizeof(double) * done, cudaMemcpyDeviceToHost);
+                    for (int k = 0; k < done; ++k) r.rc[k] = tmp[k];
+                }
+                if (r.rre && e == cudaSuccess) {
+                    e = cudaMemcpy(tmp.data(), g->S.rre_hist + base, sizeof(double) * done, cudaMemcpyDeviceToHost);
+                    for (int k = 0; k < done; ++k) r.rre[k] = tmp[k];
+                }
+                if (e != cudaSuccess) return bcuda_fail(h, e, "sgks_batch_solve (report)");
+            }
+        }
+        off += g->D.B;
+    }
+    return worst < 0 ? bfail(h, worst, "device status: an instance stopped on an error") : SGKS_OK;
+}
+
+int sgks_batch_get_x(sgks_batch* h, void* const* x_out) {
+    if (!h || !x_out) return bfail(h, SGKS_ERR_INVALID, "handle and x_out must be non-NULL");
+    join_in(h);
+    cudaError_t e = cudaSuccess;
+    for (GroupBase* g : h->groups) {
+        PtrPack out{};
+        for (int i = 0; i < g->D.B; ++i) out.p[i] = x_out[g->members[i]];
+        if (e == cudaSuccess) e = g->copy_x(out, h->st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    join_out(h);
+    if (e != cudaSuccess) return bcuda_fail(h, e, "sgks_batch_get_x");
+    return SGKS_OK;
+}
+
+int sgks_batch_status(sgks_batch* h, int32_t* codes) {
+    if (!h || !codes) return SGKS_ERR_INVALID;
+    cudaError_t e = read_scalars(h);
+    if (e != cudaSuccess) return bcuda_fail(h, e, "sgks_batch_status");
+    size_t off = 0;
+    for (GroupBase* g : h->groups) {
+        for (int i = 0; i < g->D.B; ++i) codes[g->members[i]] = map_status(h->sc_host[off + i].status);
+        off += g->D.B;
+    }
+    return SGKS_OK;
+}
+
+int sgks_batch_layout(sgks_batch* h, int32_t* group_of, int32_t* group_size) {
+    if (!h) return SGKS_ERR_INVALID;
+    for (size_t g = 0; g < h->groups.size(); ++g)
+        for (int i = 0; i < h->groups[g]->D.B; ++i) {
+            if (group_of) group_of[h->groups[g]->members[i]] = (int32_t)g;
+            if (group_size) group_size[h->groups[g]->members[i]] = h->groups[g]->D.B;
+        }
+    return (int)h->groups.size();
+}
+
+int sgks_batch_profile_steps(sgks_batch* h, int32_t iters, double* ms_out, int64_t* count_out) {
+    if (!h || iters < 0 || !ms_out || !count_out) return SGKS_ERR_INVALID;
+    if (iters > h->max_iters - h->steps_since_setup) return bfail(h, SGKS_ERR_STATE, "iters exceeds capacity");
+    BProf p;
+    cudaEventCreate(&p.ev[0]);
+    cudaEventCreate(&p.ev[1]);
+    join_in(h);
+    cudaError_t e = cudaStreamSynchronize(h->st);
+    // groups one after another, each launch timed on its own
+    for (int k = 0; k < iters && e == cudaSuccess; ++k)
+        for (GroupBase* g : h->groups) {
+            g->prof = &p;
+            if (e == cudaSuccess) e = g->step();
+            g->prof = nullptr;
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+        }
+    h->steps_since_setup += iters;
+    join_out(h);
+    cudaEventDestroy(p.ev[0]);
+    cudaEventDestroy(p.ev[1]);
+    if (e != cudaSuccess) return bcuda_fail(h, e, "sgks_batch_profile_steps");
+    for (int c = 0; c < BK_COUNT; ++c) {
+        ms_out[c] = p.ms[c];
+        count_out[c] = p.count[c];
+    }
+    return SGKS_OK;
+}
+
+const char* sgks_batch_last_error(const sgks_batch* h) {
+    if (!h) return g_batch_error.c_str();
+    return h->err.c_str();
+}
+
+void sgks_batch_destroy(sgks_batch* h) {
+    if (!h) return;
+    if (h->st) cudaStreamSynchronize(h->st);
+    for (cudaStream_t s : h->gst) cudaStreamSynchronize(s);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    for (void* p : h->allocs) cudaFree(p);
+    for (GroupBase* g : h->groups) delete g;
+    for (cudaEvent_t ev : h->ev_join) cudaEventDestroy(ev);
+    for (cudaStream_t s : h->gst) cudaStreamDestroy(s);
+    if (h->sc_host) cudaFreeHost(h->sc_host);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->st) cudaStreamDestroy(h->st);
+    delete h;
+}
+
+}  // extern "C"

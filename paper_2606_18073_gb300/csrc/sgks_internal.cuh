@@ -5,6 +5,9 @@
 
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
 #include <stdint.h>
 
 #include "../../include/sgks.h"
@@ -535,6 +538,93 @@ cudaError_t launch_sqnorm(const T* w, int64_t n, double* part, int nb, cudaStrea
 cudaError_t csr_transpose_device(int64_t m, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
                                  const void* val, int vdt, int32_t* trp, int32_t* tci, void* tval,
                                  cudaStream_t st);
+// ------------------------------------------------------------------- batched form
+// B instances of one problem shape (same A and L; their own b_i, lambda_i, x_true_i), all n-,
+// m- and p-vectors instance-interleaved: v[q * B + i].  B is a power of two, 1 <= B <= 256.
+constexpr int kMaxBatch = 256;
+
+struct BDims {
+    int64_t n, m, p;
+    int B;
+    int s, dmax, ell, max_iters;
+    int nb_combine;           // CTAs of kb_combine
+    int nb_refine;            // CTAs of kb_wtr (a multiple of 8: one cluster = 8 CTAs)
+    int nb_setup;             // CTAs of the setup reductions
+    double sketch_scale;      // 1/sqrt(zeta)
+};
+
+template <typename T>
+struct BBulk {
+    T *W, *AW;                // [dmax][n][B], [dmax][m][B]
+    T *x, *xs, *e;            // [n][B] current x, x of the last full iteration, [m][B] A x - b
+    T* b;                     // [m][B]
+    T* xtrue;                 // [n][B] or nullptr
+    T *tp, *tm;               // [p][B] L w of the newest column; [m][B] setup temporary
+    T* r;                     // [n][B] gradient r(y) inside the refinement
+};
+
+struct BSmall {
+    double *partA, *partL;    // [B][s] sketched newest column (one partial)
+    double* Sb;               // [B][s] S_A b_i
+    double* gpart;            // [B][nb_refine / 8][dmax] refinement partials
+    double* kapart;           // [nb_combine][B][3] norm partials
+    double* y;                // [B][dmax]
+    double* lam;              // [B]
+    double *rc_hist, *rre_hist;   // [B][max_iters]
+    double *setup_part, *setup_coef;   // [nb_setup][ell][B], [ell][B]
+    DevScalars* sc;           // [B]
+    int* ka_done;             // block counter of kb_combine
+};
+
+// Input / output pointers of the B instances (kernel parameter, 2 KB).
+struct PtrPack {
+    const void* p[kMaxBatch];
+};
+
+template <typename T, typename V>
+cudaError_t launchb_apply_column(const BDims& D, const DevA<T, V>& A, const DevL& L, const BBulk<T>& X,
+                                 const BSmall& S, cudaStream_t st);
+template <typename T>
+cudaError_t launchb_sketch_gather(const BDims& D, const BBulk<T>& X, const SketchCSR& SK, const BSmall& S,
+                                  const T* vec, double* out_vec, cudaStream_t st);
+template <typename T>
+cudaError_t launchb_combine(const BDims& D, const BBulk<T>& X, const BSmall& S, int mode, cudaStream_t st);
+// out == nullptr: append the gradient as column d_i of W_i; else write it to out ([n][B])
+template <typename T, typename V>
+cudaError_t launchb_gradient(const BDims& D, const DevA<T, V>& A, const DevL& L, const BBulk<T>& X, const BSmall& S,
+                             T* out, cudaStream_t st);
+// refinement partials g_i = W_i^T r_i into S.gpart
+template <typename T>
+cudaError_t launchb_wtr(const BDims& D, const BBulk<T>& X, const BSmall& S, const T* r, cudaStream_t st);
+template <typename T, typename V>
+cudaError_t launchb_apply(const BDims& D, const DevA<T, V>& A, const DevL& L, int which, const T* in, T* out,
+                          cudaStream_t st);
+template <typename T>
+cudaError_t launchb_dots(const BDims& D, const T* V0, int k, const T* w, const BSmall& S, cudaStream_t st);
+template <typename T>
+cudaError_t launchb_vec_update(const BDims& D, T* w, const T* V0, int k, const BSmall& S, int mode, cudaStream_t st);
+template <typename T>
+cudaError_t launchb_gather_in(const PtrPack& P, T* out, int64_t len, int B, cudaStream_t st);
+template <typename T>
+cudaError_t launchb_scatter_out(const T* in, const PtrPack& P, int64_t len, int B, cudaStream_t st);
+cudaError_t launchb_set_xt2(const BSmall& S, int B, cudaStream_t st);
+cudaError_t launchb_set_tol(DevScalars* sc, int B, double tol, cudaStream_t st);
+size_t batch_refine_smem(int dmax, int B, size_t elem);
+
+// Host-side preparation shared by the single and the batched handles (sgks_api.cu): the L
+// descriptor, the operator in the solver precision (CSR validation, value conversion, device
+// transpose) and the sparse-sign sketches by rows.  Device memory goes to `allocs`; the int
+// returned is an SGKS_* status with the reason in *why.
+void add_launches(int64_t k);
+int validate_problem(const sgks_op* A, const sgks_reg* L, const void* b, double lambda, int s, const sgks_options& o,
+                     std::string* why);
+DevL make_devl(const sgks_reg* reg);
+template <typename T, typename V>
+int prepare_operator(const sgks_op* op, DevA<T, V>& A, std::vector<void*>& allocs, int* d_err, cudaStream_t st,
+                     std::string* why);
+int prepare_sparse_sign(uint64_t keyA, uint64_t keyL, int64_t m, int64_t p, int s, int zeta, SketchCSR& SK,
+                        std::vector<void*>& allocs, int* d_err, cudaStream_t st, std::string* why);
+
 // Scratch size of the allocation-free CSR transpose and the bytes a given size needs of it.
 constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;
 size_t transpose_noalloc_need(int64_t n, int64_t nnz, int vdt);

@@ -232,6 +232,130 @@ class Solver:
             pass
 
 
+class Batch:
+    """Many independent sGKS problems in one handle (sgks_batch_*).
+
+    instances: list of dicts with keys A (CSR | Dense | Conv2D), reg (Reg), b (device tensor of
+    the solver precision), lam (> 0) and optionally x_true.  Instances whose A and reg describe
+    the same device arrays and shape share the operator and run as interleaved groups; the
+    others (ragged sizes) form groups of their own.  sketch_rows, seed and the options are shared
+    and have the meaning they have for ``Solver``.  Tensors must outlive the batch.
+    """
+
+    def __init__(self, instances, sketch_rows: int, seed: int = 0, *, max_iters: int = 100, ell: int = 3,
+                 n_refine: int = 0, precision: str = "fp64", zeta: int = 8, cgs_passes: int = 2, stream=None):
+        self._lib = L.load()
+        self.precision = precision
+        self.dtype = torch.float32 if precision in ("fp32", "fp32x") else torch.float64
+        k = len(instances)
+        if k < 1:
+            raise ValueError("a batch needs at least one instance")
+        has_xt = all(inst.get("x_true") is not None for inst in instances)
+        for inst in instances:
+            for nm in ("b", "x_true"):
+                t = inst.get(nm)
+                _need_cuda(t, nm)
+                if t is not None and t.dtype != self.dtype:
+                    raise ValueError(f"{nm} must be {self.dtype} for precision={precision}")
+        self._keep = [[inst["A"], inst["b"], inst.get("x_true")] for inst in instances]
+        self.count = k
+        self.n = [inst["A"].desc().n for inst in instances]
+        self._adesc = (L.sgks_op * k)(*[inst["A"].desc() for inst in instances])
+        self._rdesc = (L.sgks_reg * k)(*[inst["reg"].desc() for inst in instances])
+        self._b = (C.c_void_p * k)(*[inst["b"].data_ptr() for inst in instances])
+        self._lam = (C.c_double * k)(*[float(inst["lam"]) for inst in instances])
+        self._xt = (C.c_void_p * k)(*[inst["x_true"].data_ptr() for inst in instances]) if has_xt else None
+        o = L.sgks_options()
+        o.max_iters, o.ell, o.n_refine, o.zeta, o.cgs_passes = max_iters, ell, n_refine, zeta, cgs_passes
+        o.precision = {"fp64": L.SGKS_PREC_FP64, "fp32": L.SGKS_PREC_FP32, "fp32x": L.SGKS_PREC_FP32X}[precision]
+        o.sketch_kind = L.SGKS_SKETCH_SPARSE_SIGN
+        self.max_iters = max_iters
+        dev = instances[0]["b"].device
+        self.device = dev
+        self._stream = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream
+        h = C.c_void_p()
+        rc = self._lib.sgks_batch_create(C.byref(h), k, self._adesc, self._rdesc, self._b, self._lam, self._xt,
+                                         int(sketch_rows), int(seed), C.byref(o), C.c_void_p(self._stream))
+        L.check_batch(rc, None)
+        self._h = h
+
+    def reset(self, bs):
+        if len(bs) != self.count:
+            raise ValueError("one b per instance")
+        for i, b in enumerate(bs):
+            _need_cuda(b, "b")
+            self._keep[i][1] = b
+        arr = (C.c_void_p * self.count)(*[b.data_ptr() for b in bs])
+        L.check_batch(self._lib.sgks_batch_reset(self._h, arr), self._h)
+
+    def step(self):
+        L.check_batch(self._lib.sgks_batch_step(self._h), self._h)
+
+    def solve(self, iters: int, tol: float = 0.0, x_out=None, history: bool = False):
+        """Run iters iterations; x_out: None or a list of device tensors (None entries skipped).
+        Returns one report dict per instance."""
+        k = self.count
+        reps = (L.sgks_report * k)()
+        hist = []
+        if history:
+            for i in range(k):
+                rc_arr, rre_arr = (C.c_double * max(iters, 1))(), (C.c_double * max(iters, 1))()
+                reps[i].rc = C.cast(rc_arr, C.POINTER(C.c_double))
+                reps[i].rre = C.cast(rre_arr, C.POINTER(C.c_double))
+                hist.append((rc_arr, rre_arr))
+        xo = None
+        if x_out is not None:
+            for t in x_out:
+                _need_cuda(t, "x_out")
+            xo = (C.c_void_p * k)(*[None if t is None else t.data_ptr() for t in x_out])
+        L.check_batch(self._lib.sgks_batch_solve(self._h, int(iters), float(tol), xo, reps), self._h)
+        out = []
+        for i in range(k):
+            r = reps[i]
+            d = dict(iters_done=r.iters_done, status=r.status, d=r.subspace_dim, rc_last=r.rc_last,
+                     rre_last=r.rre_last, rre0=r.rre0)
+            if history:
+                d["rc"] = list(hist[i][0][:r.iters_done])
+                d["rre"] = list(hist[i][1][:r.iters_done])
+            out.append(d)
+        return out
+
+    def x(self):
+        """Current iterates x_k of all instances (list of device tensors)."""
+        xs = [torch.empty(n, dtype=self.dtype, device=self.device) for n in self.n]
+        arr = (C.c_void_p * self.count)(*[t.data_ptr() for t in xs])
+        L.check_batch(self._lib.sgks_batch_get_x(self._h, arr), self._h)
+        return xs
+
+    def status(self):
+        codes = (C.c_int32 * self.count)()
+        L.check_batch(self._lib.sgks_batch_status(self._h, codes), self._h)
+        return list(codes)
+
+    def profile(self, iters: int):
+        """Per-kernel CUDA-event timing of `iters` eager iterations (sgks_batch_profile_steps)."""
+        n = L.SGKS_BATCH_PROFILE_CLASSES
+        ms, cnt = (C.c_double * n)(), (C.c_int64 * n)()
+        L.check_batch(self._lib.sgks_batch_profile_steps(self._h, int(iters), ms, cnt), self._h)
+        return {L.BATCH_PROFILE_CLASS_NAMES[i]: dict(ms=ms[i], launches=cnt[i]) for i in range(n)}
+
+    def layout(self):
+        g, sz = (C.c_int32 * self.count)(), (C.c_int32 * self.count)()
+        ng = L.check_batch(self._lib.sgks_batch_layout(self._h, g, sz), self._h)
+        return ng, list(g), list(sz)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sgks_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def kernel_launches() -> int:
     """Kernel launches enqueued by the library in this process (sgks_kernel_launches)."""
     return int(L.load().sgks_kernel_launches())

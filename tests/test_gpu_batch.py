@@ -1,0 +1,271 @@
+"""Batched handle (sgks_batch_*) against the FP64 oracle, instance by instance.
+
+Each instance of a batch is its own problem solved by Algorithm 2 with the batch's sketch seed,
+so its iterates are compared with the oracle run on that problem alone, under the same
+floor-based tolerance as the single-handle parity tests.  Covered: CSR, convolution and dense
+operators with each regularizer; groups split into powers of two (5 = 4 + 1); ragged instances
+(different frame counts) in concurrent groups; refinement; the FP32 form; graph replay against
+eager steps; per-instance stopping and a non-finite instance that must not disturb the others.
+"""
+import os
+import sys
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from workloads import small_problem
+from workloads.problem import SketchDesc
+
+sys.path.insert(0, os.path.join(os.path.dirname(__file__), "golden"))
+from make_floors import EPS, floor_curve  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32 = 1e-10, 1e-4
+FACTOR64, FACTOR32 = 100.0, 10.0
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2606_18073_gb300 as G
+    G.build()
+    return G
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def share_operators(problems, s, zeta=8, seed=0):
+    """Give problems with equal operators one OperatorDesc (so the batch groups them) and the
+    batch's common sketch (s, zeta, seed)."""
+    firsts = []
+    for P in problems:
+        for Q in firsts:
+            same = (Q.A.kind == P.A.kind and Q.A.m == P.A.m and Q.A.n == P.A.n and Q.L == P.L)
+            if same and P.A.kind == "csr":
+                same = (np.array_equal(Q.A.row_ptr, P.A.row_ptr) and np.array_equal(Q.A.col, P.A.col)
+                        and np.array_equal(Q.A.val, P.A.val))
+            elif same and P.A.kind == "conv2d":
+                same = np.array_equal(Q.A.psf, P.A.psf)
+            elif same:
+                same = np.array_equal(Q.A.dense, P.A.dense)
+            if same:
+                P.A = Q.A
+                break
+        else:
+            firsts.append(P)
+        P.sketch = SketchDesc("sparse_sign", s, zeta, seed)
+    return problems
+
+
+def batch_inputs(G, problems, prec):
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    ops = {}
+    insts = []
+    for P in problems:
+        if id(P.A) not in ops:
+            kw = G.device_inputs(P, prec)
+            ops[id(P.A)] = (kw["A"], kw["reg"])
+        A, reg = ops[id(P.A)]
+        insts.append(dict(A=A, reg=reg, lam=P.lam,
+                          b=torch.from_numpy(np.asarray(P.b)).to("cuda", dt),
+                          x_true=torch.from_numpy(np.asarray(P.x_true)).to("cuda", dt)))
+    return insts
+
+
+def make_batch(G, problems, prec, **over):
+    P0 = problems[0]
+    kw = dict(max_iters=P0.iters, n_refine=P0.n_refine, precision=prec, zeta=P0.sketch.zeta)
+    kw.update(over)
+    return G.Batch(batch_inputs(G, problems, prec), P0.sketch.s, P0.sketch.seed, **kw)
+
+
+def batch_iterates(G, problems, prec, iters, **over):
+    Bt = make_batch(G, problems, prec, **over)
+    xs = [[x.double().cpu().numpy()] for x in Bt.x()]
+    for _ in range(iters):
+        Bt.step()
+        for i, x in enumerate(Bt.x()):
+            xs[i].append(x.double().cpu().numpy())
+    return Bt, xs
+
+
+def check_instance(xs, P, prec):
+    ref = O.sgks(P, iters=len(xs) - 1, record_x=True)
+    eps = EPS["fp64" if prec == "fp64" else "fp32"]
+    fl = floor_curve(P, len(xs) - 1, eps)[0]
+    tol, fac = (TOL64, FACTOR64) if prec == "fp64" else (TOL32, FACTOR32)
+    errs = [rel(a, b) for a, b in zip(xs, ref["xs"])]
+    bad = [(k, e, fl[k]) for k, e in enumerate(errs) if e > max(tol, fac * fl[k])]
+    assert not bad, f"{P.name}: iterates above max(tol, {fac} x floor): {bad[:4]}"
+    return ref
+
+
+def ct_instances(count, iters=15):
+    A0 = small_problem("ct2d").A
+    probs = [small_problem("ct2d", instance=int(i), A=A0, iters=iters)
+             for i in np.linspace(0, 63, count).astype(int)]
+    return share_operators(probs, s=80)
+
+
+# --------------------------------------------------------------------------------- parity
+
+def test_batch_ct_instances_split_into_groups_match_oracle(G):
+    """Five CT instances (own noise and lambda_i = 10^(-4 + 3i/63)) sharing one CSR: groups 4 + 1."""
+    probs = ct_instances(5)
+    Bt, xs = batch_iterates(G, probs, "fp64", probs[0].iters)
+    ng, grp, size = Bt.layout()
+    assert ng == 2 and sorted(size) == [1, 4, 4, 4, 4]
+    for P, x in zip(probs, xs):
+        check_instance(x, P, "fp64")
+    Bt.close()
+
+
+@pytest.mark.parametrize("kind", ["deblur2d", "seismic2d", "deconv1d"])
+def test_batch_operator_families_match_oracle(G, kind):
+    """Convolution + grad2d with refinement, CSR + Laplacian, dense + fd1: four instances each."""
+    if kind == "deblur2d":
+        probs = [small_problem("deblur2d", seed=i, precision="fp64", n_refine=2, iters=12) for i in range(4)]
+        for i, P in enumerate(probs):
+            P.lam = 5e-3 * (1 + i)
+    elif kind == "seismic2d":
+        probs = [small_problem("seismic2d", seed=i, iters=12) for i in range(4)]
+    else:
+        probs = [small_problem("deconv1d", seed=i, iters=10) for i in range(4)]
+    share_operators(probs, s=probs[0].sketch.s)
+    assert all(P.A is probs[0].A for P in probs)
+    Bt, xs = batch_iterates(G, probs, "fp64", probs[0].iters)
+    assert Bt.layout()[0] == 1
+    for P, x in zip(probs, xs):
+        check_instance(x, P, "fp64")
+    Bt.close()
+
+
+def test_batch_ragged_frames_run_as_concurrent_groups(G):
+    """Space-time instances with 2, 3, 4 and 4 frames: three groups on their own streams."""
+    probs = [small_problem("dynct", frames=F, seed=i, iters=12) for i, F in enumerate((2, 3, 4, 4))]
+    share_operators(probs, s=100)
+    Bt, xs = batch_iterates(G, probs, "fp64", probs[0].iters)
+    ng, grp, size = Bt.layout()
+    assert ng == 3 and grp[2] == grp[3] and len({grp[0], grp[1], grp[2]}) == 3
+    for P, x in zip(probs, xs):
+        check_instance(x, P, "fp64")
+    Bt.close()
+
+
+def test_batch_fp32_form(G):
+    """FP32 operators and accumulation: early iterates within 1e-4 of the oracle while the
+    method's FP32 floor is below 1e-6, final RRE within 5 % (as for the single handle)."""
+    probs = [small_problem("deblur2d", seed=i, iters=20) for i in range(4)]
+    share_operators(probs, s=80)
+    Bt, xs = batch_iterates(G, probs, "fp32", probs[0].iters)
+    for P, x in zip(probs, xs):
+        ref = O.sgks(P, record_x=True)
+        fl = floor_curve(P, P.iters, EPS["fp32"])[0]
+        errs = [rel(a, b) for a, b in zip(x, ref["xs"])]
+        early = [k for k in range(len(errs)) if max(fl[:k + 1]) < 1e-6]
+        assert early and max(errs[k] for k in early) < TOL32, errs
+        assert abs(rel(x[-1], P.x_true) - ref["rre"][-1]) < 0.05 * ref["rre"][-1]
+    Bt.close()
+
+
+def test_batch_instance_equals_single_handle(G):
+    """The batch changes the schedule, not the method: instance i tracks a single handle on the
+    same problem to the FP64 parity bar."""
+    probs = ct_instances(4, iters=12)
+    Bt = make_batch(G, probs, "fp64")
+    Bt.solve(12)
+    xb = [x.cpu().numpy() for x in Bt.x()]
+    for P, x in zip(probs, xb):
+        S = G.Solver(**G.device_inputs(P, "fp64"))
+        S.solve(12)
+        assert rel(x, S.x().cpu().numpy()) < 1e-9
+        S.close()
+    Bt.close()
+
+
+# ---------------------------------------------------------------------- graph and control
+
+def test_batch_graph_replay_equals_steps(G):
+    probs = ct_instances(3, iters=10)
+    B1 = make_batch(G, probs, "fp64")
+    for _ in range(10):
+        B1.step()
+    x1 = [x.cpu().numpy() for x in B1.x()]
+    B2 = make_batch(G, probs, "fp64")
+    out = B2.solve(10, history=True)
+    x2 = [x.cpu().numpy() for x in B2.x()]
+    for a, b, o in zip(x1, x2, out):
+        assert np.array_equal(a, b)
+        assert o["iters_done"] == 10 and len(o["rc"]) == 10
+    # reset with the same right-hand sides reproduces the solve bit for bit
+    B2.reset([torch.from_numpy(np.asarray(P.b)).cuda() for P in probs])
+    B2.solve(10)
+    for a, b in zip(x2, B2.x()):
+        assert np.array_equal(a, b.cpu().numpy())
+    B1.close()
+    B2.close()
+
+
+def test_batch_tolerance_stops_each_instance_on_its_own(G):
+    # (seed, lambda) pairs whose oracle runs stop at iterations 15, 6, 31 and 22
+    probs = []
+    for seed, lam in ((0, 5e-3), (1, 1e-2), (0, 1e-3), (1, 2e-3)):
+        P = small_problem("deblur2d", seed=seed, precision="fp64", n_refine=0, iters=40)
+        P.lam = lam
+        probs.append(P)
+    share_operators(probs, s=80)
+    Bt = make_batch(G, probs, "fp64")
+    out = Bt.solve(40, tol=1e-3)
+    xs = Bt.x()
+    done = []
+    for P, o, x in zip(probs, out, xs):
+        ref = O.sgks(P, tol=1e-3)
+        assert o["status"] == G._lib.SGKS_STOPPED
+        assert o["iters_done"] == ref["iters"]
+        fl = floor_curve(P, ref["iters"], EPS["fp64"])[0]
+        assert rel(x.cpu().numpy(), ref["x"]) < max(TOL64, FACTOR64 * fl[-1])
+        done.append(o["iters_done"])
+    assert len(set(done)) > 1, done      # the instances really stopped at different iterations
+    Bt.close()
+
+
+def test_batch_nonfinite_instance_does_not_disturb_the_others(G):
+    probs = ct_instances(4, iters=10)
+    insts = batch_inputs(G, probs, "fp64")
+    insts[1]["b"][3] = float("nan")
+    Bt = G.Batch(insts, 80, 0, max_iters=10, precision="fp64")
+    with pytest.raises(G._lib.SGKSError) as ei:
+        Bt.solve(10)
+    assert ei.value.code == G._lib.SGKS_ERR_NONFINITE
+    st = Bt.status()
+    assert st[1] == G._lib.SGKS_ERR_NONFINITE and st[0] == st[2] == st[3] == G._lib.SGKS_OK
+    xs = Bt.x()
+    for i in (0, 2, 3):
+        ref = O.sgks(probs[i], iters=10)
+        assert rel(xs[i].cpu().numpy(), ref["x"]) < 1e-8
+    Bt.close()
+
+
+def test_batch_invalid_arguments(G):
+    probs = ct_instances(2, iters=5)
+    insts = batch_inputs(G, probs, "fp64")
+    insts32 = batch_inputs(G, probs, "fp32")
+    with pytest.raises(G._lib.SGKSError) as ei:
+        G.Batch(insts32, 80, 0, max_iters=5, precision="fp32x")     # no batched compensated form
+    assert ei.value.code == G._lib.SGKS_ERR_INVALID
+    insts[1]["lam"] = 0.0
+    with pytest.raises(G._lib.SGKSError) as ei:
+        G.Batch(insts, 80, 0, max_iters=5, precision="fp64")
+    assert ei.value.code == G._lib.SGKS_ERR_INVALID and "instance 1" in str(ei.value)
+    insts[1]["lam"] = 1.0
+    with pytest.raises(G._lib.SGKSError) as ei:
+        G.Batch(insts, 7, 0, max_iters=5, precision="fp64")      # s < ell + max_iters
+    assert ei.value.code == G._lib.SGKS_ERR_INVALID
