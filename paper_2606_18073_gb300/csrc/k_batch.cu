@@ -16,6 +16,8 @@
 // launched with one cluster group per instance.
 #include <math.h>
 
+#include <algorithm>
+
 #include "sgks_internal.cuh"
 
 namespace sgks {
@@ -86,8 +88,10 @@ __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * kThre
 
 // ------------------------------------------------------------------ a1: apply the newest column
 // u_i = A w_i -> column d_i of AW, t_i = L w_i -> tp (w_i = column d_i of W_i).
+// t0 = D.m * B skips the A rows (done by kb_csr_apply for a CSR operator).
 template <typename T, typename V>
-__global__ void __launch_bounds__(kThreads) kb_apply_column(BDims D, DevA<T, V> A, DevL L, BBulk<T> X, BSmall S) {
+__global__ void __launch_bounds__(kThreads) kb_apply_column(BDims D, DevA<T, V> A, DevL L, BBulk<T> X, BSmall S,
+                                                            int64_t t0) {
     __shared__ T psf_s[128];
     load_psf(A, psf_s);
     const int B = D.B;
@@ -98,7 +102,7 @@ __global__ void __launch_bounds__(kThreads) kb_apply_column(BDims D, DevA<T, V> 
     if (d >= D.dmax) return;
     const T* w = X.W + (size_t)d * D.n * B + b;
     const int64_t tot = (D.m + D.p) * B;
-    for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < tot; t += gstride()) {
+    for (int64_t t = t0 + (int64_t)blockIdx.x * kThreads + threadIdx.x; t < tot; t += gstride()) {
         if (t < D.m * B) {
             const int64_t j = t / B;
             X.AW[((size_t)d * D.m + j) * B + b] = ba_row(A, psf_s, j, w, B);
@@ -106,6 +110,177 @@ __global__ void __launch_bounds__(kThreads) kb_apply_column(BDims D, DevA<T, V> 
             const int64_t k = (t - D.m * B) / B;
             X.tp[k * B + b] = l_row_x<T>(L, k, Strided<T>{w, B});
         }
+    }
+}
+
+// ------------------------------------------------------------------- CSR rows, one warp per row
+// A CSR matrix (row_ptr, col, val) times the instance-interleaved vectors of a group: a warp
+// takes RPW rows and up to 32 instance groups of VV consecutive instances; lane (r, ig, nl) loads
+// the VV instances of group ig with one 16-byte (or VV-value) load per matrix entry, for the
+// entries nl, nl + NL, ... of row r; the NL (<= 8) partial sums are combined by a fixed xor tree.
+// Per (entry, instance) this is one load and one FMA plus 2 / VV index loads, and the entries of
+// a row are read by consecutive lanes.  VV = min(B, 16 / sizeof(T)).
+template <typename T, int VV>
+__device__ __forceinline__ void ldvec(const T* __restrict__ p, T (&o)[VV]) {
+    if constexpr (VV * sizeof(T) == 16) {
+        if constexpr (sizeof(T) == 4) {
+            const float4 f = __ldg(reinterpret_cast<const float4*>(p));
+            o[0] = f.x; o[1] = f.y; o[2] = f.z; o[3] = f.w;
+        } else {
+            const double2 f = __ldg(reinterpret_cast<const double2*>(p));
+            o[0] = f.x; o[1] = f.y;
+        }
+    } else if constexpr (VV == 2 && sizeof(T) == 4) {
+        const float2 f = __ldg(reinterpret_cast<const float2*>(p));
+        o[0] = f.x; o[1] = f.y;
+    } else {
+#pragma unroll
+        for (int v = 0; v < VV; ++v) o[v] = ldg(p + v);
+    }
+}
+
+struct RowLanes {
+    int64_t row;
+    bool valid;
+    int b0;    // first of this lane's VV instances
+    int nl, NL;
+};
+
+// lanes of a work item: NL = min(32 / igw, 8) lanes per (row, instance group), igw instance
+// groups per pass, RPW = 32 / (igw * NL) rows per warp; lane = (r * igw + ig) * NL + nl
+template <int VV>
+__device__ __forceinline__ int rl_rpw(int B) {
+    const int IG = B / VV, igw = IG < 32 ? IG : 32;
+    const int NL = (32 / igw) < 8 ? 32 / igw : 8;
+    return 32 / (igw * NL);
+}
+
+template <int VV>
+__device__ __forceinline__ RowLanes row_lanes(int64_t item, int64_t rows, int B) {
+    const int IG = B / VV;
+    const int igw = IG < 32 ? IG : 32;   // instance groups per pass
+    const int NP = IG / igw;
+    RowLanes r;
+    r.NL = (32 / igw) < 8 ? 32 / igw : 8;
+    const int RPW = 32 / (igw * r.NL);
+    const int lane = lane_id();
+    const int64_t rg = item / NP;
+    const int pass = (int)(item - rg * NP);
+    r.nl = lane & (r.NL - 1);
+    const int ig = (lane / r.NL) % igw;
+    r.row = rg * RPW + lane / (igw * r.NL);
+    r.valid = r.row < rows;
+    r.b0 = (pass * igw + ig) * VV;
+    return r;
+}
+
+__host__ __device__ inline int64_t rl_items(int64_t rows, int B, int VV) {
+    const int IG = B / VV, igw = IG < 32 ? IG : 32;
+    const int NL = (32 / igw) < 8 ? 32 / igw : 8;
+    const int RPW = 32 / (igw * NL);
+    return (rows + RPW - 1) / RPW * (IG / igw);
+}
+
+// sum over the row's entries of val * x[col * B + v] for v < VV (x already offset to instance b0);
+// per-instance bases xb[v] are used instead when the VV instances read different columns
+template <typename T, typename V, int VV>
+__device__ __forceinline__ void csr_row_vec(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                            const V* __restrict__ val, const RowLanes& rl, int B, const T* x,
+                                            bool same, const T* const (&xb)[VV], T (&acc)[VV]) {
+#pragma unroll
+    for (int v = 0; v < VV; ++v) acc[v] = T(0);
+    const int beg = rl.valid ? rp[rl.row] : 0, end = rl.valid ? rp[rl.row + 1] : 0;
+#pragma unroll 4
+    for (int kk = beg + rl.nl; kk < end; kk += rl.NL) {
+        const int64_t c = (int64_t)__ldg(ci + kk) * B;
+        const T a = (T)ldg(val + kk);
+        T xv[VV];
+        if (same) {
+            ldvec<T, VV>(x + c, xv);
+        } else {
+#pragma unroll
+            for (int v = 0; v < VV; ++v) xv[v] = xb[v] ? ldg(xb[v] + c) : T(0);
+        }
+#pragma unroll
+        for (int v = 0; v < VV; ++v) acc[v] += a * xv[v];
+    }
+    for (int off = 1; off < rl.NL; off <<= 1)
+#pragma unroll
+        for (int v = 0; v < VV; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
+}
+
+// a1 for a CSR operator: u_i = A w_i -> column d_i of AW
+template <typename T, typename V, int VV>
+__global__ void __launch_bounds__(kThreads) kb_csr_apply(BDims D, DevA<T, V> A, BBulk<T> X, BSmall S) {
+    const int B = D.B;
+    const int64_t items = rl_items(D.m, B, VV);
+    for (int64_t wi = (int64_t)blockIdx.x * kWarps + warp_id(); wi < items; wi += (int64_t)gridDim.x * kWarps) {
+        const RowLanes rl = row_lanes<VV>(wi, D.m, B);
+        int dv[VV];
+        bool live[VV], same = true, any = false;
+        const T* xb[VV];
+#pragma unroll
+        for (int v = 0; v < VV; ++v) {
+            const DevScalars& sc = S.sc[rl.b0 + v];
+            dv[v] = sc.d;
+            live[v] = rl.valid && !sc.stop && sc.d < D.dmax;
+            xb[v] = live[v] ? X.W + (size_t)dv[v] * D.n * B + rl.b0 + v : nullptr;
+            same = same && live[v] && dv[v] == dv[0];
+            any = any || live[v];
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        T acc[VV];
+        csr_row_vec<T, V, VV>(A.rp, A.ci, A.val, rl, B, xb[0], same, xb, acc);
+        if (rl.nl == 0)
+#pragma unroll
+            for (int v = 0; v < VV; ++v)
+                if (live[v]) X.AW[((size_t)dv[v] * D.m + rl.row) * B + rl.b0 + v] = acc[v];
+    }
+}
+
+// a7 for a CSR operator: r_i = A^T e_i + lambda_i L^T L x_i (rows of the stored transpose),
+// appended as column d_i of W_i (out == nullptr) or written to out.
+template <typename T, typename V, int VV>
+__global__ void __launch_bounds__(kThreads) kb_csr_gradient(BDims D, DevA<T, V> A, DevL L, BBulk<T> X, BSmall S,
+                                                            T* out) {
+    const int B = D.B;
+    const int64_t items = rl_items(D.n, B, VV);
+    for (int64_t wi = (int64_t)blockIdx.x * kWarps + warp_id(); wi < items; wi += (int64_t)gridDim.x * kWarps) {
+        const RowLanes rl = row_lanes<VV>(wi, D.n, B);
+        bool live[VV], any = false;
+        T* dst[VV];
+#pragma unroll
+        for (int v = 0; v < VV; ++v) {
+            DevScalars& sc = S.sc[rl.b0 + v];
+            live[v] = rl.valid && !sc.stop;
+            dst[v] = out;
+            if (live[v] && !out) {
+                if (sc.d >= D.dmax) {
+                    if (rl.row == 0 && rl.nl == 0) {
+                        sc.status = ST_FULL;
+                        sc.stop = 1;
+                    }
+                    live[v] = false;
+                } else {
+                    dst[v] = X.W + (size_t)sc.d * D.n * B;
+                }
+            }
+            any = any || live[v];
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        const T* xb[VV];
+#pragma unroll
+        for (int v = 0; v < VV; ++v) xb[v] = X.e + rl.b0 + v;
+        T acc[VV];
+        csr_row_vec<T, V, VV>(A.trp, A.tci, A.tval, rl, B, X.e + rl.b0, true, xb, acc);
+        if (rl.nl == 0)
+#pragma unroll
+            for (int v = 0; v < VV; ++v) {
+                if (!live[v]) continue;
+                const int bb = rl.b0 + v;
+                dst[v][rl.row * B + bb] =
+                    acc[v] + (T)S.lam[bb] * ltl_row_x<T>(L, rl.row, Strided<T>{X.x + bb, B});
+            }
     }
 }
 
@@ -147,6 +322,65 @@ __global__ void __launch_bounds__(kThreads) kb_sketch_gather(BDims D, BBulk<T> X
         if (vec) out_vec[(size_t)b * D.s + r] = D.sketch_scale * red[b];
         else (isA ? S.partA : S.partL)[(size_t)b * D.s + r] = red[b];
     }
+}
+
+// Last CTA of a combine: per instance, the CTA partials summed by SUB = kThreads / B threads
+// (thread (u, i) takes CTAs c = u, u + SUB, ... in order), the SUB sums by a fixed pairwise tree,
+// then RC_k / RRE_k (eq. RC) and the stopping tests.
+template <typename T>
+__device__ void combine_finish(const BDims& D, const BBulk<T>& X, const BSmall& S, int mode,
+                               double (*red)[kThreads]) {
+    const int B = D.B;
+    {
+        const int SUB = kThreads / B, u = threadIdx.x / B, i = threadIdx.x & (B - 1);
+        double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+#pragma unroll 4
+        for (int c = u; c < (int)gridDim.x; c += SUB) {
+            const double* pp = S.kapart + ((size_t)c * B + i) * 3;
+            t0 += __ldcg(pp);
+            t1 += __ldcg(pp + 1);
+            t2 += __ldcg(pp + 2);
+        }
+        __syncthreads();
+        red[0][threadIdx.x] = t0;
+        red[1][threadIdx.x] = t1;
+        red[2][threadIdx.x] = t2;
+        __syncthreads();
+        for (int h = SUB / 2; h > 0; h >>= 1) {
+            if (u < h)
+                for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h * B];
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < B; i += kThreads) {
+        const double t0 = red[0][i], t1 = red[1][i], t2 = red[2][i];
+        DevScalars& s = S.sc[i];
+        if (s.stop) continue;
+        const double rre = X.xtrue ? sqrt(t2 / s.xt2) : (double)NAN;
+        if (mode == 2) {
+            s.rre0 = rre;
+            s.rre_last = rre;
+        } else {
+            const double rc = sqrt(t0 / t1);
+            const int k = s.iter;
+            if (k < D.max_iters) {
+                S.rc_hist[(size_t)i * D.max_iters + k] = rc;
+                S.rre_hist[(size_t)i * D.max_iters + k] = rre;
+            }
+            s.rc_last = rc;
+            s.rre_last = rre;
+            s.iter = k + 1;
+            if (s.tol_on && rc < s.tol) {
+                s.status = ST_STOPPED;
+                s.stop = 1;
+            }
+            if (!(t0 <= 1e300) || !(t1 <= 1e300)) {   // NaN or Inf in the iterate
+                s.status = ST_NONFINITE;
+                s.stop = 1;
+            }
+        }
+    }
+    if (threadIdx.x == 0) *S.ka_done = 0;
 }
 
 // ------------------------------------------------------------------- a5 + a6: combine
@@ -268,58 +502,183 @@ __global__ void __launch_bounds__(kThreads, 4) kb_combine(BDims D, BBulk<T> X, B
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    // last CTA: per instance, the CTA partials summed by SUB = kThreads / B threads (thread (u, i)
-    // takes CTAs c = u, u + SUB, ... in order), then the SUB sums by a fixed pairwise tree
-    {
-        const int SUB = kThreads / B, u = threadIdx.x / B, i = threadIdx.x & (B - 1);
-        double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-#pragma unroll 4
-        for (int c = u; c < (int)gridDim.x; c += SUB) {
-            const double* pp = S.kapart + ((size_t)c * B + i) * 3;
-            t0 += __ldcg(pp);
-            t1 += __ldcg(pp + 1);
-            t2 += __ldcg(pp + 2);
+    combine_finish(D, X, S, mode, red);
+}
+
+// Bulk-copy form of the combine (used when every column start is 16-byte aligned): a tile is one
+// slice of kSlice contiguous values per column (TR = kSlice / B rows), and the slices of successive
+// columns stream through an NS-stage ring in shared memory, filled by cp.async.bulk from one
+// thread and tracked by one mbarrier per stage, so NS - 1 slices per CTA are in flight without
+// holding registers.  Thread t owns the slice positions t + kThreads r (instance t mod B), the same
+// (row, instance) pairs as the register form, and sums the columns in the same order.
+// 16 KB column slices in a 4-stage ring: measured on GB300 at 5.6 - 6.7 TB/s for 16 - 64 instances,
+// against 4.4 - 4.9 TB/s for 8 KB slices in 6 stages and 2.5 - 3.5 TB/s for 4 KB slices.
+template <typename T>
+__host__ __device__ constexpr int slice_of() { return 16384 / (int)sizeof(T); }
+
+template <typename T, int NS>
+__global__ void __launch_bounds__(kThreads) kb_combine_tma(BDims D, BBulk<T> X, BSmall S, int mode) {
+    constexpr int kSlice = slice_of<T>();
+    constexpr int RPT = kSlice / kThreads;       // slice positions per thread
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* stg = reinterpret_cast<T*>(smem_raw);     // [NS][kSlice]
+    T* ys = stg + (size_t)NS * kSlice;           // [kYStage]
+    __shared__ __align__(8) uint64_t full[NS];
+    __shared__ int sd[kMaxBatch];
+    __shared__ int s_dlive;
+    __shared__ double red[3][kThreads];
+    __shared__ int am_last;
+    const int B = D.B, G = kThreads / B;
+    const int t = threadIdx.x, b = t & (B - 1), g = t / B;
+    const int JC = kYStage / B;
+    if (t == 0) {
+        int mx = 0;
+        for (int i = 0; i < B; ++i) {
+            const int di = S.sc[i].stop ? 0 : S.sc[i].d;
+            sd[i] = di;
+            mx = di > mx ? di : mx;
         }
-        __syncthreads();
-        red[0][threadIdx.x] = t0;
-        red[1][threadIdx.x] = t1;
-        red[2][threadIdx.x] = t2;
-        __syncthreads();
-        for (int h = SUB / 2; h > 0; h >>= 1) {
-            if (u < h)
-                for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h * B];
+        s_dlive = mx;
+        for (int q = 0; q < NS; ++q) mbar_init(&full[q], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int db = sd[b], dlive = s_dlive;
+    const bool live = !S.sc[b].stop;
+    const int TR = kSlice / B;
+    const int64_t ntx = (D.n + TR - 1) / TR, nte = (D.m + TR - 1) / TR;
+    // this CTA's work as one flat sequence of items (its tiles in order, dlive columns each), so
+    // the ring keeps NS slices in flight across tile boundaries
+    const int64_t ntiles = ntx + nte;
+    const int my_tiles = ntiles > blockIdx.x ? (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x) : 0;
+    const int nitems = my_tiles * dlive;
+    auto item = [&](int k, uint32_t* bytes) -> const T* {
+        const int64_t tile = blockIdx.x + (int64_t)(k / dlive) * gridDim.x;
+        const int j = k % dlive;
+        const bool isx = tile < ntx;
+        const int64_t rows = isx ? D.n : D.m;
+        const int64_t r0 = (isx ? tile : tile - ntx) * TR;
+        const int64_t vrows = min((int64_t)TR, rows - r0);
+        *bytes = (uint32_t)(((size_t)vrows * B * sizeof(T) + 15) & ~(size_t)15);
+        return (isx ? X.W : X.AW) + ((size_t)j * rows + r0) * B;
+    };
+    if (t == 0) {
+        const int pre = min(NS, nitems);
+        for (int q = 0; q < pre; ++q) {
+            uint32_t bytes;
+            const T* src = item(q, &bytes);
+            mbar_expect_tx(&full[q], bytes);
+            bulk_g2s(stg + (size_t)q * kSlice, src, bytes, &full[q]);
+        }
+    }
+    T q0 = T(0), q1 = T(0), q2 = T(0);
+    T acc[RPT], pa[RPT], pb[RPT];   // pa, pb: the tile's x_{k-1} and x_true, or b
+    int err = 0, k = 0;
+    bool isx = true;
+    int64_t rows = 0, row0 = 0;
+    int nv = 0;
+    for (; k < nitems; ++k) {
+        const int j = k % dlive;
+        if (j == 0) {
+            const int64_t tile = blockIdx.x + (int64_t)(k / dlive) * gridDim.x;
+            isx = tile < ntx;
+            rows = isx ? D.n : D.m;
+            row0 = (isx ? tile : tile - ntx) * TR + g;
+            nv = row0 < rows ? (int)min((int64_t)RPT, (rows - row0 + G - 1) / G) : 0;
+            // the operands of the tile's epilogue are loaded now, so that their latency passes
+            // while the columns stream in
+            const size_t o0 = (size_t)row0 * B + b;
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                acc[r] = T(0);
+                const size_t o = o0 + (size_t)kThreads * r;
+                const bool in = live && r < nv;
+                pa[r] = in && isx && mode >= 1 ? X.xs[o] : (in && !isx ? X.b[o] : T(0));
+                pb[r] = in && isx && mode >= 1 && X.xtrue ? X.xtrue[o] : T(0);
+            }
+        }
+        if (j % JC == 0 && (k == 0 || dlive > JC)) {   // y chunk [j, j + JC) as [jj][B]
+            __syncthreads();
+            for (int q = t; q < JC * B; q += kThreads) {
+                const int jj = q / B, i = q & (B - 1), jg = j + jj;
+                ys[q] = jg < sd[i] ? (T)S.y[(size_t)i * D.dmax + jg] : T(0);
+            }
             __syncthreads();
         }
-    }
-    for (int i = threadIdx.x; i < B; i += kThreads) {
-        const double t0 = red[0][i], t1 = red[1][i], t2 = red[2][i];
-        DevScalars& s = S.sc[i];
-        if (s.stop) continue;
-        const double rre = X.xtrue ? sqrt(t2 / s.xt2) : (double)NAN;
-        if (mode == 2) {
-            s.rre0 = rre;
-            s.rre_last = rre;
-        } else {
-            const double rc = sqrt(t0 / t1);
-            const int k = s.iter;
-            if (k < D.max_iters) {
-                S.rc_hist[(size_t)i * D.max_iters + k] = rc;
-                S.rre_hist[(size_t)i * D.max_iters + k] = rre;
-            }
-            s.rc_last = rc;
-            s.rre_last = rre;
-            s.iter = k + 1;
-            if (s.tol_on && rc < s.tol) {
-                s.status = ST_STOPPED;
-                s.stop = 1;
-            }
-            if (!(t0 <= 1e300) || !(t1 <= 1e300)) {   // NaN or Inf in the iterate
-                s.status = ST_NONFINITE;
-                s.stop = 1;
+        const int st = k % NS;
+        const bool ok = mbar_wait(&full[st], (k / NS) & 1);
+        if (ok && j < db) {
+            const T yv = ys[(j % JC) * B + b];
+            const T* sl = stg + (size_t)st * kSlice + t;
+#pragma unroll
+            for (int r = 0; r < RPT; ++r)
+                if (r < nv) acc[r] += sl[kThreads * r] * yv;
+        }
+        err = __syncthreads_or(!ok);   // every reader of stage st is done; err is uniform
+        if (err) break;
+        if (t == 0 && k + NS < nitems) {
+            uint32_t bytes;
+            const T* src = item(k + NS, &bytes);
+            fence_proxy_async();
+            mbar_expect_tx(&full[st], bytes);
+            bulk_g2s(stg + (size_t)st * kSlice, src, bytes, &full[st]);
+        }
+        if (j != dlive - 1 || !live) continue;
+        T* out = (isx ? X.x : X.e) + (size_t)row0 * B + b;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            if (r >= nv) continue;
+            const size_t o = (size_t)kThreads * r;
+            if (isx) {
+                const T xv = acc[r];
+                out[o] = xv;
+                if (mode >= 1) {
+                    const T old = pa[r];
+                    const T df = xv - old;
+                    q0 += df * df;
+                    q1 += old * old;
+                    if (X.xtrue) {
+                        const T er = xv - pb[r];
+                        q2 += er * er;
+                    }
+                    X.xs[(size_t)row0 * B + b + o] = xv;
+                }
+            } else {
+                out[o] = acc[r] - pa[r];
             }
         }
     }
-    if (threadIdx.x == 0) *S.ka_done = 0;
+    if (err) {
+        // drain this CTA's own copies (bounded), then stop every instance with the timeout status
+        if (t == 0) {
+            const int last = min(nitems, k + NS);
+            for (int q = k; q < last; ++q) mbar_wait(&full[q % NS], (q / NS) & 1);
+            for (int i = 0; i < B; ++i) {
+                S.sc[i].status = ST_TIMEOUT;
+                S.sc[i].stop = 1;
+            }
+        }
+        return;
+    }
+    if (mode == 0) return;
+    red[0][t] = (double)q0;
+    red[1][t] = (double)q1;
+    red[2][t] = (double)q2;
+    __syncthreads();
+    for (int h = G / 2; h > 0; h >>= 1) {
+        if (g < h)
+            for (int q = 0; q < 3; ++q) red[q][t] += red[q][t + h * B];
+        __syncthreads();
+    }
+    if (g == 0)
+        for (int q = 0; q < 3; ++q) S.kapart[((size_t)blockIdx.x * B + b) * 3 + q] = red[q][b];
+    __threadfence();
+    __syncthreads();
+    if (t == 0) am_last = (atomicAdd(S.ka_done, 1) == (int)gridDim.x - 1);
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    combine_finish(D, X, S, mode, red);
 }
 
 // -------------------------------------------------------------------------- a7: gradient
@@ -363,7 +722,7 @@ __global__ void __launch_bounds__(kThreads) kb_gradient(BDims D, DevA<T, V> A, D
 template <typename T, int NB>
 __global__ void __cluster_dims__(kBatchCluster, 1, 1) __launch_bounds__(kThreads, 2)
     kb_wtr(BDims D, BBulk<T> X, BSmall S, const T* __restrict__ r) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_dlive;
     __shared__ int s_stop[kMaxBatch];
     const int B = D.B;
@@ -544,10 +903,44 @@ static int bgrid(int64_t work) {
     return (int)(b < 1 ? 1 : b);
 }
 
+static int wgrid(int64_t items) {   // CTAs for one warp per work item
+    int64_t b = (items + kWarps - 1) / kWarps;
+    if (b > 8 * 152) b = 8 * 152;
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+constexpr int vec_width() { return 16 / (int)sizeof(T); }
+
+template <typename T, typename V, int VV>
+static cudaError_t csr_apply_vv(const BDims& D, const DevA<T, V>& A, const BBulk<T>& X, const BSmall& S,
+                                cudaStream_t st) {
+    const int64_t items = rl_items(D.m, D.B, VV);
+    kb_csr_apply<T, V, VV><<<wgrid(items), kThreads, 0, st>>>(D, A, X, S);
+    return cudaGetLastError();
+}
+
+template <typename T, typename V, int VV>
+static cudaError_t csr_gradient_vv(const BDims& D, const DevA<T, V>& A, const DevL& L, const BBulk<T>& X,
+                                   const BSmall& S, T* out, cudaStream_t st) {
+    const int64_t items = rl_items(D.n, D.B, VV);
+    kb_csr_gradient<T, V, VV><<<wgrid(items), kThreads, 0, st>>>(D, A, L, X, S, out);
+    return cudaGetLastError();
+}
+
 template <typename T, typename V>
 cudaError_t launchb_apply_column(const BDims& D, const DevA<T, V>& A, const DevL& L, const BBulk<T>& X,
                                  const BSmall& S, cudaStream_t st) {
-    kb_apply_column<T, V><<<bgrid((D.m + D.p) * D.B), kThreads, 0, st>>>(D, A, L, X, S);
+    if (A.kind == SGKS_OP_CSR) {
+        constexpr int VW = vec_width<T>();
+        cudaError_t e = D.B >= VW ? csr_apply_vv<T, V, VW>(D, A, X, S, st)
+                        : D.B == 2 ? csr_apply_vv<T, V, 2>(D, A, X, S, st)
+                                   : csr_apply_vv<T, V, 1>(D, A, X, S, st);
+        if (e != cudaSuccess) return e;
+        kb_apply_column<T, V><<<bgrid(D.p * D.B), kThreads, 0, st>>>(D, A, L, X, S, D.m * D.B);
+        return cudaGetLastError();
+    }
+    kb_apply_column<T, V><<<bgrid((D.m + D.p) * D.B), kThreads, 0, st>>>(D, A, L, X, S, 0);
     return cudaGetLastError();
 }
 
@@ -558,8 +951,27 @@ cudaError_t launchb_sketch_gather(const BDims& D, const BBulk<T>& X, const Sketc
     return cudaGetLastError();
 }
 
+constexpr int kCombStages = 4;
+
+size_t batch_combine_tma_smem(size_t elem) {
+    return (size_t)kCombStages * 16384 + (size_t)kYStage * elem;
+}
+
+int batch_combine_tiles(int64_t n, int64_t m, int B, bool tma, size_t elem) {
+    const int64_t TR = tma ? (int64_t)(16384 / elem) / B : (int64_t)kCombRows * (kThreads / B);
+    return (int)std::min<int64_t>((n + TR - 1) / TR + (m + TR - 1) / TR, 1 << 30);
+}
+
 template <typename T>
 cudaError_t launchb_combine(const BDims& D, const BBulk<T>& X, const BSmall& S, int mode, cudaStream_t st) {
+    if (D.tma) {
+        const size_t smem = batch_combine_tma_smem(sizeof(T));
+        auto k = kb_combine_tma<T, kCombStages>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<D.nb_combine, kThreads, smem, st>>>(D, X, S, mode);
+        return cudaGetLastError();
+    }
     kb_combine<T><<<D.nb_combine, kThreads, 0, st>>>(D, X, S, mode);
     return cudaGetLastError();
 }
@@ -571,6 +983,12 @@ size_t batch_refine_smem(int dmax, int B, size_t elem) {
 template <typename T, typename V>
 cudaError_t launchb_gradient(const BDims& D, const DevA<T, V>& A, const DevL& L, const BBulk<T>& X, const BSmall& S,
                              T* out, cudaStream_t st) {
+    if (A.kind == SGKS_OP_CSR) {
+        constexpr int VW = vec_width<T>();
+        return D.B >= VW ? csr_gradient_vv<T, V, VW>(D, A, L, X, S, out, st)
+               : D.B == 2 ? csr_gradient_vv<T, V, 2>(D, A, L, X, S, out, st)
+                          : csr_gradient_vv<T, V, 1>(D, A, L, X, S, out, st);
+    }
     kb_gradient<T, V><<<bgrid(D.n * D.B), kThreads, 0, st>>>(D, A, L, X, S, out);
     return cudaGetLastError();
 }

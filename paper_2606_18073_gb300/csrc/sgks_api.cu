@@ -830,6 +830,7 @@ static int map_status(int dev) {
         case ST_STOPPED: return SGKS_STOPPED;
         case ST_NONFINITE: return SGKS_ERR_NONFINITE;
         case ST_SKETCH: return SGKS_ERR_SKETCH;
+        case ST_TIMEOUT: return SGKS_ERR_CUDA;
         case ST_FULL: return SGKS_ERR_STATE;
         default: return SGKS_ERR_STATE;
     }

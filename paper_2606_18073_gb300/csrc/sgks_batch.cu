@@ -81,7 +81,7 @@ struct Group : GroupBase {
 
     cudaError_t sketch_column() {
         cudaError_t e = cudaSuccess;
-        RUNC(BK_APPLY, 1, (launchb_apply_column<T, V>(D, A, L, X, S, st)));
+        RUNC(BK_APPLY, A.kind == SGKS_OP_CSR ? 2 : 1, (launchb_apply_column<T, V>(D, A, L, X, S, st)));
         RUNC(BK_GATHER, 1, launchb_sketch_gather<T>(D, X, SK, S, nullptr, nullptr, st));
         return e;
     }
@@ -114,6 +114,7 @@ struct Group : GroupBase {
     cudaError_t setup() override {
         const int B = D.B;
         cudaError_t e = cudaMemsetAsync(S.sc, 0, sizeof(DevScalars) * B, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(S.ka_done, 0, sizeof(int), st);
         RUN(1, launchb_gather_in<T>(bp, X.b, D.m, B, st));
         RUN(1, launchb_sketch_gather<T>(D, X, SK, S, X.b, S.Sb, st));
         if (has_xt) {
@@ -169,6 +170,7 @@ int map_status(int dev) {
         case ST_STOPPED: return SGKS_STOPPED;
         case ST_NONFINITE: return SGKS_ERR_NONFINITE;
         case ST_SKETCH: return SGKS_ERR_SKETCH;
+        case ST_TIMEOUT: return SGKS_ERR_CUDA;
         default: return SGKS_ERR_STATE;
     }
 }
@@ -294,10 +296,13 @@ int build_groups(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const st
         D.ell = o.ell;
         D.max_iters = o.max_iters;
         D.sketch_scale = 1.0 / sqrt((double)o.zeta);
-        const int G8 = kThreads / B;   // rows of a combine tile per row slot
-        const int64_t TR = 8 * (int64_t)G8;
-        const int64_t ctiles = (D.n + TR - 1) / TR + (D.m + TR - 1) / TR;
-        D.nb_combine = (int)std::min<int64_t>(ctiles, 4 * 152);
+        // the bulk-copy combine needs every column start of W and AW on a 16-byte boundary
+        D.tma = ((size_t)D.n * B * sizeof(T)) % 16 == 0 && ((size_t)D.m * B * sizeof(T)) % 16 == 0;
+        {
+            const int per_sm = D.tma ? (int)std::max<size_t>(1, (227 * 1024) / (batch_combine_tma_smem(sizeof(T)) + 8192))
+                                     : 4;
+            D.nb_combine = std::min(batch_combine_tiles(D.n, D.m, B, D.tma, sizeof(T)), 152 * per_sm);
+        }
         const int64_t rtiles = (D.n + 1024 / B - 1) / (1024 / B);
         {   // enough CTAs to fill every SM at the residency the refinement's shared memory allows
             const size_t sm = batch_refine_smem(dmax, B, sizeof(T)) + 2048;
@@ -401,7 +406,7 @@ int build_groups(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const st
         if (e == cudaSuccess) e = cudaMemcpy(S.lam, lam.data(), sizeof(double) * B, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemsetAsync(S.y, 0, sizeof(double) * B * dmax, h->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(X.xs, 0, sizeof(T) * nB, h->st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(S.ka_done, 0, sizeof(int), h->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(S.ka_done, 0, sizeof(int), h->st);   // also at every setup
         if (e != cudaSuccess) return bcuda_fail(h, e, "batch workspace initialisation");
     }
     return SGKS_OK;

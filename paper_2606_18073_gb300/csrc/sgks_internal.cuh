@@ -25,7 +25,7 @@ constexpr int kMaxDraws = 256;
 
 // ------------------------------------------------------------------------------ status
 enum DevStatus : int { ST_OK = 0, ST_BREAKDOWN = 1, ST_STOPPED = 2, ST_NONFINITE = 3, ST_SKETCH = 4,
-                       ST_FULL = 5 };
+                       ST_FULL = 5, ST_TIMEOUT = 6 };
 
 // Scalars that live on the device and are updated by the kernels, so that one captured
 // graph of a step replays for every iteration.
@@ -67,6 +67,52 @@ struct DevL {
 // --------------------------------------------------------------------------- utilities
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
+
+// ---------------------------------------------------------- bulk copies (TMA) and mbarriers
+// One elected thread moves a contiguous global range into shared memory with cp.async.bulk and
+// an mbarrier counts the bytes; the other threads wait on the barrier's phase.  Every wait is
+// bounded: after kWaitTries unsuccessful try_wait rounds it reports failure, and the caller
+// records ST_TIMEOUT, drains its own copies (again bounded) and returns.
+constexpr int kWaitTries = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// orders this thread's earlier generic-proxy shared-memory accesses before later bulk copies
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// dst and src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (int i = 0; i < kWaitTries; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -547,7 +593,8 @@ struct BDims {
     int64_t n, m, p;
     int B;
     int s, dmax, ell, max_iters;
-    int nb_combine;           // CTAs of kb_combine
+    int nb_combine;           // CTAs of the combine kernel
+    int tma;                  // 1: combine streams W through shared memory by bulk copies
     int nb_refine;            // CTAs of kb_wtr (a multiple of 8: one cluster = 8 CTAs)
     int nb_setup;             // CTAs of the setup reductions
     double sketch_scale;      // 1/sqrt(zeta)
@@ -610,6 +657,8 @@ cudaError_t launchb_scatter_out(const T* in, const PtrPack& P, int64_t len, int 
 cudaError_t launchb_set_xt2(const BSmall& S, int B, cudaStream_t st);
 cudaError_t launchb_set_tol(DevScalars* sc, int B, double tol, cudaStream_t st);
 size_t batch_refine_smem(int dmax, int B, size_t elem);
+size_t batch_combine_tma_smem(size_t elem);
+int batch_combine_tiles(int64_t n, int64_t m, int B, bool tma, size_t elem);
 
 // Host-side preparation shared by the single and the batched handles (sgks_api.cu): the L
 // descriptor, the operator in the solver precision (CSR validation, value conversion, device
