@@ -429,6 +429,7 @@ def extras(args, G, P, kw, S, iters, dev, flush):
     out["fp64_small_phase"] = small
     if not args.no_batch:
         out["batched"] = {"ct2d_64rhs": bench_ct_batch(G, dev, flush), "dynct_ragged16": bench_dynct_batch(G, dev, flush)}
+        out["differentiable"] = bench_differentiable(G, dev, flush)
     # CPU oracle baseline, bounded sample, one thread
     try:
         r = run_cpu_worker(args.config, args.cpu_sample_iters)
@@ -558,6 +559,70 @@ def bench_dynct_batch(G, dev, flush):
     out["kernels"] = prof
     out["workload"] = ("dynct: 128x128 x F frames, F in {8,16,24,32} x 4 instances, 30 angles/frame x 185 bins, "
                        "space-time L, 1% noise, sparse-sign s=800 zeta=8, 200 iterations, FP32 + 3 refinement steps")
+    return out
+
+
+def bench_differentiable(G, dev, flush):
+    """Seismic travel-time tomography, 256 x 256 slowness, 8192 rays, Laplacian L, 80 iterations:
+    forward solve with the y_k record, then the reverse sweep (dl/db, dl/dlambda for
+    l = ||x_80 - x_true||^2), FP64 and FP32, next to the plain FP64 forward."""
+    import numpy as np
+    import torch
+    P = make_workload("seismic2d", seed=0)
+    P.n_refine = 0
+    iters = P.iters
+    stream = torch_stream(dev)
+    out = {"workload": "seismic2d: 256x256, 64 sources x 128 receivers (8192 rays), laplace2d L, 1% noise, "
+                       "sparse-sign s=400 zeta=8, 80 iterations, loss ||x_80 - x_true||^2"}
+
+    def timed(fn, reps=3):
+        best, res = None, None
+        for _ in range(reps):
+            flush.zero_()
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            res = fn()
+            c.record(stream)
+            torch.cuda.synchronize(dev)
+            t = a.elapsed_time(c)
+            best = t if best is None or t < best else best
+        return best, res
+
+    for prec in ("fp64", "fp32"):
+        kw = G.device_inputs(P, prec, device=dev)
+        kw["n_refine"] = 0
+        S = G.Solver(**kw, record=True)
+        b = kw["b"]
+        xt = torch.from_numpy(np.asarray(P.x_true)).to(dev, S.dtype)
+        t_fwd, _ = timed(lambda: (S.reset(b), S.solve(iters)))
+        xbar = (2.0 * (S.x() - xt)).contiguous()
+        t_bwd, (bbar, lbar) = timed(lambda: S.backward(xbar))
+        rec = {"forward_ms": t_fwd, "backward_ms": t_bwd, "dl_dlambda": lbar,
+               "forward_iters_per_s": iters / (t_fwd / 1e3)}
+        if prec == "fp32":
+            rec["note"] = ("the derivative goes through G_j^{-1}, the squared condition of the projected problem; "
+                           "at 80 iterations the FP64 sweep's own rounding floor is ~1e-2, so the FP32 value "
+                           "carries no digits (timing only)")
+        if prec == "fp64":
+            h = 1e-6 * P.lam
+            vals = []
+            for lam in (P.lam + h, P.lam - h):
+                S.set_lambda(lam)
+                S.reset(b)
+                S.solve(iters)
+                vals.append(float(torch.sum((S.x() - xt) ** 2)))
+            S.set_lambda(P.lam)
+            fd = (vals[0] - vals[1]) / (2 * h)
+            rec["dl_dlambda_central_difference"] = fd
+            rec["dl_dlambda_rel_err"] = abs(lbar - fd) / abs(fd)
+        S.close()
+        out[prec] = rec
+    kw = G.device_inputs(P, "fp64", device=dev)
+    kw["n_refine"] = 0
+    S = G.Solver(**kw)
+    t_plain, _ = timed(lambda: (S.reset(kw["b"]), S.solve(iters)))
+    S.close()
+    out["fp64_plain_forward_ms"] = t_plain
     return out
 
 

@@ -49,7 +49,7 @@ enum { SGKS_OP_DENSE = 1, SGKS_OP_CSR = 2, SGKS_OP_CONV2D = 3 };
 enum { SGKS_REG_FD1 = 1, SGKS_REG_GRAD2D = 2, SGKS_REG_LAPLACE2D = 3, SGKS_REG_SPACETIME = 4 };
 enum { SGKS_SKETCH_SPARSE_SIGN = 0, SGKS_SKETCH_GAUSSIAN = 1 };
 enum { SGKS_PREC_FP64 = 0, SGKS_PREC_FP32 = 1, SGKS_PREC_FP32X = 2 };
-enum { SGKS_FLAG_GLOBAL_SMALL = 1 };
+enum { SGKS_FLAG_GLOBAL_SMALL = 1, SGKS_FLAG_RECORD = 2 };
 
 /* Forward operator A (m x n).
  *  SGKS_OP_CSR:    row_ptr[m+1], col[nnz] (int32, 0-based), val[nnz] of val_dtype.  Optional
@@ -109,7 +109,10 @@ typedef struct sgks_options {
     int32_t cgs_passes;   /* 1 = the single projection printed under eq. updqr, 2 = CGS2 [2]       */
     int32_t flags;        /* bit 0 (SGKS_FLAG_GLOBAL_SMALL): run the FP64 QR append and projected
                              solve with the global-memory kernels instead of the on-chip cluster
-                             kernels (chosen automatically when the on-chip slices do not fit) [0] */
+                             kernels (chosen automatically when the on-chip slices do not fit).
+                             bit 1 (SGKS_FLAG_RECORD): keep y_k of every iteration so that
+                             sgks_backward can differentiate the solve; needs n_refine = 0,
+                             precision FP64 or FP32 and the on-chip kernels [0] */
     const double* gauss_SA; /* Gaussian sketch only: S_A, sketch_rows x m, row-major, FP64, device */
     const double* gauss_SL; /* Gaussian sketch only: S_L, sketch_rows x p, row-major, FP64, device */
     const void* x_true;     /* optional, n values of the solver precision: enables RRE records    */
@@ -269,6 +272,26 @@ int64_t sgks_kernel_launches(void);
  *   7 combine at the end of the iteration (x_k, e_k, RC, RRE) */
 #define SGKS_PROFILE_CLASSES 8
 int sgks_profile_steps(sgks_handle* h, int32_t iters, double* ms_out, int64_t* count_out, double* dsum_out);
+
+/* ---- differentiation ------------------------------------------------------------------- */
+/* Reverse-mode derivative of the solve: for the x_K that the iterations since the last setup
+ * (sgks_create / sgks_reset) produced, and xbar = dl/dx_K (device, n values of the solver
+ * precision), write bbar = dl/db (device, m values of the solver precision) and *lambda_bar =
+ * dl/dlambda (host).  This is the exact derivative of the map (b, lambda) -> x_K of Algorithm 2
+ * (without refinement), x_K = W_K y_K with every basis column r_j = A^T (A x_{j-1} - b) +
+ * lambda L^T L x_{j-1} depending on the earlier iterates (eq. gradient) and W_0 spanning
+ * K_l(A^T A, A^T b).  It is computed by a reverse sweep over the iterations that reuses the
+ * stored basis W and the stored inverse of the stacked triangular factor of
+ * eq. (projected_sketched_bis) (the leading block of which serves every earlier step, since the
+ * factors only grow by columns, eq. updqr).  Needs a handle created with SGKS_FLAG_RECORD.  The
+ * forward state is unchanged, so the call may be repeated.  Device scratch is allocated at the
+ * first call.  Synchronises.  Errors: SGKS_ERR_STATE (no SGKS_FLAG_RECORD, or no iteration
+ * recorded), SGKS_ERR_INVALID, SGKS_ERR_CUDA. */
+int sgks_backward(sgks_handle* h, const void* xbar, void* bbar, double* lambda_bar);
+
+/* Change lambda (> 0) of a handle.  The basis is discarded: call sgks_reset before the next
+ * step or solve.  Synchronises. */
+int sgks_set_lambda(sgks_handle* h, double lambda);
 
 /* ---- batches: many independent problems in one handle ----------------------------------- */
 /* Each instance i is a problem of its own (eq. tik with A_i, L_i, b_i, lambda_i) solved by

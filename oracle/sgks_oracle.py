@@ -396,6 +396,7 @@ def sgks(problem, iters=None, n_refine=None, sketched=True, cgs_passes=2, tol=0.
     y = solve()
     x = W @ y
     rc, rre, xs = [], [np.linalg.norm(x - xt) / nxt], [x.copy()] if record_x else None
+    ys = [y.copy()] if record_x else None
     for k in range(1, iters + 1):
         r = gradient(Aop, Lop, b, lam, x)
         W = np.concatenate([W, r[:, None]], axis=1)
@@ -407,12 +408,14 @@ def sgks(problem, iters=None, n_refine=None, sketched=True, cgs_passes=2, tol=0.
         x = x_new
         if record_x:
             xs.append(x.copy())
+            ys.append(y.copy())
         if tol > 0 and rc[-1] < tol:
             break
     out = dict(x=x, y=y, W=W, rc=np.array(rc), rre=np.array(rre), breakdowns=breakdowns,
                iters=k if iters > 0 else 0)
     if record_x:
         out["xs"] = xs
+        out["ys"] = ys
     if record_state:
         out.update(QA=QA, RA=RA, QL=QL, RL=RL, dA=dA, Sb=Sb)
     return out

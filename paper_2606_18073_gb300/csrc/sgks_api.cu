@@ -76,6 +76,18 @@ struct EngineBase {
     Small S{};
     int n_refine = 0;
     int elem = 8;
+    // reverse sweep (sgks_backward): y_k of every iteration, recorded when SGKS_FLAG_RECORD is set
+    double* yhist = nullptr;
+    std::vector<void*>* allocs = nullptr;   // the handle's device allocations
+    virtual cudaError_t backward(const void* xbar, void* bbar, double* lbar_host, int K) {
+        (void)xbar; (void)bbar; (void)lbar_host; (void)K;
+        return cudaErrorNotSupported;
+    }
+    cudaError_t record_y(int offset) {
+        if (!yhist) return cudaSuccess;
+        g_launches.fetch_add(1);
+        return launchd_record_y(S.sc, S.y, yhist, D.dmax, offset, D.max_iters + 1, pst);
+    }
 };
 
 template <typename T, typename V>
@@ -136,6 +148,7 @@ struct Engine : EngineBase {
             e = timed(PK_SKETCH, j, [&] { return sketch(); });
             if (e == cudaSuccess) e = small_append(j);
         }
+        if (e == cudaSuccess) e = record_y(0);
         host_d = D.ell;
         for (int r = 0; r < n_refine && e == cudaSuccess; ++r) e = refine();
         if (e == cudaSuccess) e = timed(PK_COMBINE, host_d, [&] { return launch_combine<T>(D, B, S, 2, st); });
@@ -172,9 +185,177 @@ struct Engine : EngineBase {
         cudaError_t e = timed(PK_GRAD_APPEND, d, [&] { return launch_gradient<T, V>(D, A, L, B, S, false, st); });
         if (e == cudaSuccess) e = timed(PK_SKETCH, d, [&] { return sketch(); });
         if (e == cudaSuccess) e = small_append(d);
+        if (e == cudaSuccess) e = record_y(1);
         host_d = d + 1;
         for (int r = 0; r < n_refine && e == cudaSuccess; ++r) e = refine();
         if (e == cudaSuccess) e = timed(PK_COMBINE, host_d, [&] { return launch_combine<T>(D, B, S, 1, st); });
+        return e;
+    }
+
+    // ------------------------------------------------------------------ reverse sweep
+    struct Bw {
+        T *Wb = nullptr, *xb = nullptr, *xj = nullptr, *wz = nullptr, *t1 = nullptr, *t2 = nullptr;
+        T *P = nullptr, *Q = nullptr, *tm = nullptr, *tp = nullptr, *Kv = nullptr, *Kb = nullptr;
+        double *uy = nullptr, *uz = nullptr, *vy = nullptr, *vz = nullptr, *cb = nullptr, *st = nullptr;
+        double *ybar = nullptr, *z = nullptr, *part = nullptr, *acc = nullptr, *R0 = nullptr, *Ri = nullptr;
+        int* err = nullptr;
+    } bw;
+
+    template <typename P>
+    cudaError_t bw_alloc(P** p, size_t count) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, count * sizeof(P) + 16);
+        if (e != cudaSuccess) return e;
+        allocs->push_back(q);
+        *p = (P*)q;
+        return cudaSuccess;
+    }
+
+    cudaError_t bw_prepare() {
+        if (bw.Wb) return cudaSuccess;
+        const size_t n = D.n, m = D.m, p = D.p, s = D.s, dm = D.dmax, ell = D.ell;
+        cudaError_t e = cudaSuccess;
+        auto A1 = [&](auto** ptr, size_t c) { if (e == cudaSuccess) e = bw_alloc(ptr, c); };
+        A1(&bw.Wb, dm * n); A1(&bw.xb, n); A1(&bw.xj, n); A1(&bw.wz, n); A1(&bw.t1, n); A1(&bw.t2, n);
+        A1(&bw.P, n); A1(&bw.Q, n); A1(&bw.tm, m); A1(&bw.tp, p); A1(&bw.Kv, ell * n); A1(&bw.Kb, ell * n);
+        A1(&bw.uy, s); A1(&bw.uz, s); A1(&bw.vy, s); A1(&bw.vz, s); A1(&bw.cb, s); A1(&bw.st, s);
+        A1(&bw.ybar, dm); A1(&bw.z, dm); A1(&bw.part, (size_t)nbS * dm); A1(&bw.acc, 2);
+        A1(&bw.R0, ell * ell); A1(&bw.Ri, ell * ell); A1(&bw.err, 1);
+        if (e != cudaSuccess) bw.Wb = nullptr;
+        return e;
+    }
+
+    // out[0..k) = V[:, 0..k)^T w  (FP64)
+    cudaError_t bw_dots(const T* V0, int k, const T* w, double* out) {
+        cudaError_t e = launch_dots<T>(V0, D.n, k, w, bw.part, nbS, st);
+        if (e == cudaSuccess) e = launch_reduce_rows(bw.part, nbS, k, 1.0, out, st);
+        g_launches.fetch_add(2);
+        return e;
+    }
+
+    cudaError_t bw_apply(int which, const T* in, T* out) {
+        g_launches.fetch_add(1);
+        return launch_apply<T, V>(D, A, L, which, in, out, st);
+    }
+
+    // S_A v (isA) or S_L v as FP64 s-vectors, as in the forward sketch of the same precision
+    cudaError_t bw_sketch(bool isA, const T* in, double* out) {
+        g_launches.fetch_add(2);
+        return sketch_vector(isA, in, sizeof(T) == 4 ? SGKS_F32 : SGKS_F64, sizeof(T) == 4, out);
+    }
+
+    cudaError_t bw_sketch_adj(bool isA, const double* u, T* out) {
+        g_launches.fetch_add(1);
+        return launchd_sketch_adj<T>(isA ? D.keyA : D.keyL, isA ? gSA : gSL, isA ? D.m : D.p, D.s, D.zeta,
+                                     D.sketch_scale, u, out, bw.err, st);
+    }
+
+    // The reverse sweep of the derivative of x_K (see sgks_backward in the header):
+    //   for j = K .. 0 (d = ell + j):  ybar = W_j^T xbar_j;  z = G_j^{-1} ybar;
+    //     c-bar += U_j z;  lambdabar -= (V_j z).(V_j y_j);
+    //     Wbar[:, :d] += (xbar_j + Q) y_j^T + P z^T with P = A^T S_A^T (c - U_j y_j) - lambda L^T S_L^T V_j y_j,
+    //                                                   Q = -(A^T S_A^T U_j z + lambda L^T S_L^T V_j z);
+    //     column d-1 (r_j): xbar_{j-1} = (A^T A + lambda L^T L) rbar, bbar -= A rbar,
+    //                       lambdabar += rbar . L^T L x_{j-1};
+    //   W_0 = K R_0^{-1} with R_0 = W_0^T K fixed: Kbar = Wbar_0 R_0^{-T}, vbar = sum_i (A^T A)^i Kbar_i,
+    //   bbar += A vbar + S_A^T c-bar.
+    cudaError_t backward(const void* xbar, void* bbar_v, double* lbar_host, int K) override {
+        if (!yhist || !D.fast_small) return cudaErrorNotSupported;
+        cudaError_t e = bw_prepare();
+        if (e != cudaSuccess) return e;
+        const int64_t n = D.n;
+        const int ell = D.ell;
+        const double lam = D.lam;
+        T* bbar = static_cast<T*>(bbar_v);
+        T* W = B.W;
+        e = cudaMemsetAsync(bw.Wb, 0, sizeof(T) * (size_t)(ell + K) * n, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(bw.cb, 0, sizeof(double) * D.s, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(bw.acc, 0, sizeof(double) * 2, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(bw.err, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(bbar, 0, sizeof(T) * D.m, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(bw.xb, xbar, sizeof(T) * n, cudaMemcpyDeviceToDevice, st);
+        auto L1 = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+        for (int j = K; j >= 0 && e == cudaSuccess; --j) {
+            const int d = ell + j;
+            const double* yj = yhist + (size_t)j * D.dmax;
+            L1(bw_dots(W, d, bw.xb, bw.ybar));
+            L1(launchd_solve_G(S.X, S.Xr, D.dmax, d, bw.ybar, bw.z, st));
+            L1(launchd_gemv_n<T>(W, n, d, yj, bw.xj, st));
+            L1(launchd_gemv_n<T>(W, n, d, bw.z, bw.wz, st));
+            g_launches.fetch_add(3);
+            L1(bw_apply(SGKS_APPLY_A, bw.xj, bw.tm));
+            L1(bw_sketch(true, bw.tm, bw.uy));
+            L1(bw_apply(SGKS_APPLY_A, bw.wz, bw.tm));
+            L1(bw_sketch(true, bw.tm, bw.uz));
+            L1(bw_apply(SGKS_APPLY_L, bw.xj, bw.tp));
+            L1(bw_sketch(false, bw.tp, bw.vy));
+            L1(bw_apply(SGKS_APPLY_L, bw.wz, bw.tp));
+            L1(bw_sketch(false, bw.tp, bw.vz));
+            L1(launchd_axpby_d(bw.cb, bw.cb, 1.0, bw.uz, 1.0, D.s, st));
+            L1(launchd_dot_acc(bw.vz, bw.vy, D.s, -1.0, bw.acc, st));
+            L1(launchd_axpby_d(bw.st, S.Sb, 1.0, bw.uy, -1.0, D.s, st));
+            g_launches.fetch_add(3);
+            // P = A^T S_A^T (c - U y) - lambda L^T S_L^T V y
+            L1(bw_sketch_adj(true, bw.st, bw.tm));
+            L1(bw_apply(SGKS_APPLY_AT, bw.tm, bw.P));
+            L1(bw_sketch_adj(false, bw.vy, bw.tp));
+            L1(bw_apply(SGKS_APPLY_LT, bw.tp, bw.t1));
+            L1(launchd_axpby<T>(bw.P, bw.P, 1.0, bw.t1, -lam, n, st));
+            // Q = -(A^T S_A^T U z + lambda L^T S_L^T V z); then xbar_j + Q
+            L1(bw_sketch_adj(true, bw.uz, bw.tm));
+            L1(bw_apply(SGKS_APPLY_AT, bw.tm, bw.Q));
+            L1(bw_sketch_adj(false, bw.vz, bw.tp));
+            L1(bw_apply(SGKS_APPLY_LT, bw.tp, bw.t1));
+            L1(launchd_axpby<T>(bw.Q, bw.Q, -1.0, bw.t1, -lam, n, st));
+            L1(launchd_axpby<T>(bw.t2, bw.xb, 1.0, bw.Q, 1.0, n, st));
+            L1(launchd_rank2<T>(bw.Wb, n, d, bw.t2, yj, bw.P, bw.z, st));
+            g_launches.fetch_add(4);
+            if (j == 0) break;
+            const T* rbar = bw.Wb + (size_t)(d - 1) * n;
+            L1(bw_apply(SGKS_APPLY_A, rbar, bw.tm));
+            L1(launchd_axpby<T>(bbar, bbar, 1.0, bw.tm, -1.0, D.m, st));
+            L1(bw_apply(SGKS_APPLY_AT, bw.tm, bw.xb));
+            L1(bw_apply(SGKS_APPLY_LTL, rbar, bw.t1));
+            L1(launchd_axpby<T>(bw.xb, bw.xb, 1.0, bw.t1, lam, n, st));
+            // lambdabar += rbar . L^T L x_{j-1}
+            L1(launchd_gemv_n<T>(W, n, d - 1, yhist + (size_t)(j - 1) * D.dmax, bw.t2, st));
+            L1(bw_apply(SGKS_APPLY_LTL, bw.t2, bw.t1));
+            L1(launch_dots<T>(rbar, n, 1, bw.t1, bw.part, nbS, st));
+            L1(launchd_acc_parts(bw.part, nbS, 1.0, bw.acc, st));
+            g_launches.fetch_add(5);
+        }
+        // W_0: Krylov vectors K_i = (A^T A)^i A^T b, R_0 = W_0^T K, Kbar = Wbar_0 R_0^{-T}
+        for (int i = 0; i < ell && e == cudaSuccess; ++i) {
+            T* Ki = bw.Kv + (size_t)i * n;
+            if (i == 0) {
+                L1(bw_apply(SGKS_APPLY_AT, b_own, Ki));
+            } else {
+                L1(bw_apply(SGKS_APPLY_A, bw.Kv + (size_t)(i - 1) * n, bw.tm));
+                L1(bw_apply(SGKS_APPLY_AT, bw.tm, Ki));
+            }
+            L1(bw_dots(W, ell, Ki, bw.R0 + (size_t)i * ell));
+        }
+        L1(launchd_small_inverse(bw.R0, ell, bw.Ri, st));
+        L1(launchd_kbar<T>(bw.Wb, n, ell, bw.Ri, bw.Kb, st));
+        g_launches.fetch_add(2);
+        // vbar = sum_i (A^T A)^i Kbar_i by Horner, into t1
+        L1(cudaMemcpyAsync(bw.t1, bw.Kb + (size_t)(ell - 1) * n, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+        for (int i = ell - 2; i >= 0 && e == cudaSuccess; --i) {
+            L1(bw_apply(SGKS_APPLY_A, bw.t1, bw.tm));
+            L1(bw_apply(SGKS_APPLY_AT, bw.tm, bw.t2));
+            L1(launchd_axpby<T>(bw.t1, bw.Kb + (size_t)i * n, 1.0, bw.t2, 1.0, n, st));
+            g_launches.fetch_add(1);
+        }
+        L1(bw_apply(SGKS_APPLY_A, bw.t1, bw.tm));
+        L1(launchd_axpby<T>(bbar, bbar, 1.0, bw.tm, 1.0, D.m, st));
+        L1(bw_sketch_adj(true, bw.cb, bw.tm));
+        L1(launchd_axpby<T>(bbar, bbar, 1.0, bw.tm, 1.0, D.m, st));
+        g_launches.fetch_add(2);
+        int herr = 0;
+        L1(cudaMemcpyAsync(lbar_host, bw.acc, sizeof(double), cudaMemcpyDeviceToHost, st));
+        L1(cudaMemcpyAsync(&herr, bw.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        L1(cudaStreamSynchronize(st));
+        if (e == cudaSuccess && herr) e = cudaErrorInvalidValue;
         return e;
     }
 
@@ -323,6 +504,7 @@ struct sgks_handle {
     int steps_since_setup = 0;
     int prec = 0;
     int64_t graph_launches = 0;   // kernel launches per replay of the step graph
+    bool need_reset = false;      // lambda changed since the last setup
 };
 
 static int fail(sgks_handle* h, int code, const std::string& msg) {
@@ -660,6 +842,8 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     AL(S.rre_hist, (size_t)o.max_iters + 1);
     AL(S.sc, 1);
     AL(E->part_setup, (size_t)E->nbS * 8);
+    if (o.flags & SGKS_FLAG_RECORD) AL(E->yhist, (size_t)(o.max_iters + 1) * dm);
+    E->allocs = &h->allocs;
     S.lam = lambda;
     AL(E->d_err, 1);
     if (e != cudaSuccess) return fail(h, SGKS_ERR_NOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
@@ -738,6 +922,11 @@ int sgks::validate_problem(const sgks_op* A, const sgks_reg* L, const void* b, d
     }
     if (o.cgs_passes != 1 && o.cgs_passes != 2) return bad("cgs_passes must be 1 or 2");
     if (o.n_refine < 0 || o.n_refine > 64) return bad("n_refine out of range");
+    if (o.flags & SGKS_FLAG_RECORD) {
+        if (o.n_refine != 0) return bad("SGKS_FLAG_RECORD needs n_refine = 0");
+        if (o.precision == SGKS_PREC_FP32X) return bad("SGKS_FLAG_RECORD supports the FP64 and FP32 forms");
+        if (o.flags & SGKS_FLAG_GLOBAL_SMALL) return bad("SGKS_FLAG_RECORD needs the on-chip small kernels");
+    }
     return SGKS_OK;
 }
 
@@ -809,11 +998,47 @@ int sgks_reset(sgks_handle* h, const void* b_new) {
     join_out(h);
     if (e != cudaSuccess) return cuda_fail(h, e, "sgks_reset");
     h->steps_since_setup = 0;
+    h->need_reset = false;
+    return SGKS_OK;
+}
+
+int sgks_set_lambda(sgks_handle* h, double lambda) {
+    if (!h) return SGKS_ERR_INVALID;
+    if (!(lambda > 0.0) || !isfinite(lambda)) return fail(h, SGKS_ERR_INVALID, "lambda must be a finite positive number");
+    cudaError_t e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sgks_set_lambda");
+    // kernel parameters hold lambda, so the captured step graph is rebuilt at the next solve
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+    h->eng->D.lam = lambda;
+    h->eng->S.lam = lambda;
+    h->need_reset = true;
+    return SGKS_OK;
+}
+
+int sgks_backward(sgks_handle* h, const void* xbar, void* bbar, double* lambda_bar) {
+    if (!h || !xbar || !bbar || !lambda_bar) return fail(h, SGKS_ERR_INVALID, "bad sgks_backward arguments");
+    EngineBase* E = h->eng;
+    if (!E->yhist) return fail(h, SGKS_ERR_STATE, "the handle was created without SGKS_FLAG_RECORD");
+    if (h->need_reset) return fail(h, SGKS_ERR_STATE, "lambda changed: call sgks_reset first");
+    int64_t info[3];
+    int rc = sgks_get_info(h, info);
+    if (rc != SGKS_OK) return rc;
+    const int K = (int)info[1];
+    if (info[2] < 0 || info[2] == SGKS_BREAKDOWN || info[0] != E->D.ell + K)
+        return fail(h, SGKS_ERR_STATE, "the recorded solve did not complete its iterations cleanly");
+    join_in(h);
+    cudaError_t e = E->backward(xbar, bbar, lambda_bar, K);
+    join_out(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sgks_backward");
     return SGKS_OK;
 }
 
 int sgks_step(sgks_handle* h) {
     if (!h) return SGKS_ERR_INVALID;
+    if (h->need_reset) return fail(h, SGKS_ERR_STATE, "lambda changed: call sgks_reset first");
     if (h->steps_since_setup >= h->max_iters) return fail(h, SGKS_ERR_STATE, "basis is full (max_iters reached)");
     join_in(h);
     cudaError_t e = h->eng->step();
@@ -854,6 +1079,7 @@ static cudaError_t ensure_graph(sgks_handle* h) {
 
 int sgks_solve(sgks_handle* h, int32_t iters, double tol, void* x_out, sgks_report* rep) {
     if (!h || iters < 0) return fail(h, SGKS_ERR_INVALID, "bad handle or iters < 0");
+    if (h->need_reset) return fail(h, SGKS_ERR_STATE, "lambda changed: call sgks_reset first");
     EngineBase* E = h->eng;
     const int avail = h->max_iters - h->steps_since_setup;
     if (iters > avail) return fail(h, SGKS_ERR_STATE, "iters exceeds the remaining basis capacity");

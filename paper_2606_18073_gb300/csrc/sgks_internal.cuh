@@ -660,6 +660,29 @@ size_t batch_refine_smem(int dmax, int B, size_t elem);
 size_t batch_combine_tma_smem(size_t elem);
 int batch_combine_tiles(int64_t n, int64_t m, int B, bool tma, size_t elem);
 
+// ------------------------------------------------------------------- reverse sweep (k_adjoint.cu)
+cudaError_t launchd_record_y(const DevScalars* sc, const double* y, double* yhist, int dmax, int offset, int rows,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t launchd_gemv_n(const T* W, int64_t n, int d, const double* c, T* out, cudaStream_t st);
+template <typename T>
+cudaError_t launchd_rank2(T* Wb, int64_t n, int d, const T* a, const double* p, const T* q, const double* r,
+                          cudaStream_t st);
+template <typename T>
+cudaError_t launchd_axpby(T* out, const T* x, double alpha, const T* y, double beta, int64_t n, cudaStream_t st);
+cudaError_t launchd_axpby_d(double* out, const double* x, double alpha, const double* y, double beta, int n,
+                            cudaStream_t st);
+cudaError_t launchd_dot_acc(const double* a, const double* b, int len, double sign, double* acc, cudaStream_t st);
+cudaError_t launchd_acc_parts(const double* part, int nb, double sign, double* acc, cudaStream_t st);
+template <typename T>
+cudaError_t launchd_sketch_adj(uint64_t key, const double* gauss, int64_t h, int s, int zeta, double scale,
+                               const double* u, T* out, int* err, cudaStream_t st);
+cudaError_t launchd_solve_G(const double* X, const double* Xr, int dm, int d, const double* v, double* z,
+                            cudaStream_t st);
+cudaError_t launchd_small_inverse(const double* R, int ell, double* Rinv, cudaStream_t st);
+template <typename T>
+cudaError_t launchd_kbar(const T* Wb0, int64_t n, int ell, const double* Rinv, T* Kbar, cudaStream_t st);
+
 // Host-side preparation shared by the single and the batched handles (sgks_api.cu): the L
 // descriptor, the operator in the solver precision (CSR validation, value conversion, device
 // transpose) and the sparse-sign sketches by rows.  Device memory goes to `allocs`; the int

@@ -127,7 +127,7 @@ class Solver:
                  max_iters: int = 100, ell: int = 3, n_refine: int = 0, precision: str = "fp64",
                  sketch: str = "sparse_sign", zeta: int = 8, cgs_passes: int = 2,
                  gauss_SA: Optional[torch.Tensor] = None, gauss_SL: Optional[torch.Tensor] = None,
-                 x_true: Optional[torch.Tensor] = None, stream=None, flags: int = 0):
+                 x_true: Optional[torch.Tensor] = None, stream=None, flags: int = 0, record: bool = False):
         self._lib = L.load()
         self.precision = precision
         self.dtype = torch.float32 if precision in ("fp32", "fp32x") else torch.float64
@@ -142,13 +142,15 @@ class Solver:
         self._keep = [A, b, x_true, gauss_SA, gauss_SL]
         self.A, self.reg = A, reg
         self.n = A.desc().n
+        self.m = A.desc().m
+        self.lam = float(lam)
         self.max_iters = max_iters
         o = L.sgks_options()
         o.max_iters, o.ell, o.n_refine, o.zeta, o.cgs_passes = max_iters, ell, n_refine, zeta, cgs_passes
         o.precision = {"fp64": L.SGKS_PREC_FP64, "fp32": L.SGKS_PREC_FP32, "fp32x": L.SGKS_PREC_FP32X}[precision]
         o.sketch_kind = L.SGKS_SKETCH_GAUSSIAN if sketch == "gaussian" else L.SGKS_SKETCH_SPARSE_SIGN
         o.gauss_SA, o.gauss_SL, o.x_true = _ptr(gauss_SA), _ptr(gauss_SL), _ptr(x_true)
-        o.flags = int(flags)
+        o.flags = int(flags) | (L.SGKS_FLAG_RECORD if record else 0)
         self._stream = torch.cuda.current_stream(b.device).cuda_stream if stream is None else stream
         self.device = b.device
         h = C.c_void_p()
@@ -219,6 +221,22 @@ class Solver:
         ms, cnt, ds = (C.c_double * n)(), (C.c_int64 * n)(), (C.c_double * n)()
         L.check(self._lib.sgks_profile_steps(self._h, int(iters), ms, cnt, ds), self._h)
         return {L.PROFILE_CLASS_NAMES[i]: dict(ms=ms[i], launches=cnt[i], dsum=ds[i]) for i in range(n)}
+
+    def set_lambda(self, lam: float):
+        """Change lambda; the basis is discarded, so call reset(b) before the next step/solve."""
+        L.check(self._lib.sgks_set_lambda(self._h, float(lam)), self._h)
+        self.lam = float(lam)
+
+    def backward(self, xbar: torch.Tensor):
+        """(dl/db, dl/dlambda) for xbar = dl/dx_K of the iterations since the last setup
+        (sgks_backward; the solver must have been created with record=True)."""
+        _need_cuda(xbar, "xbar")
+        if xbar.dtype != self.dtype or xbar.numel() != self.n:
+            raise ValueError(f"xbar must hold {self.n} values of {self.dtype}")
+        bbar = torch.empty(self.m, dtype=self.dtype, device=self.device)
+        lb = C.c_double()
+        L.check(self._lib.sgks_backward(self._h, _ptr(xbar), _ptr(bbar), C.byref(lb)), self._h)
+        return bbar, lb.value
 
     def close(self):
         if getattr(self, "_h", None):
@@ -354,6 +372,40 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class SGKSFunction(torch.autograd.Function):
+    """x_K(b, lambda) of a recording Solver as a differentiable torch function.
+
+    forward(b, lam, solver, iters): sets lambda if it changed, resets the solver with b, runs
+    iters iterations and returns a copy of x_K.  backward: the reverse sweep of the library
+    (sgks_backward) gives dl/db and dl/dlambda.  The solver keeps the state of its last forward,
+    so each forward must be followed by its backward before the solver is used again.
+    """
+
+    @staticmethod
+    def forward(ctx, b, lam, solver, iters):
+        lv = float(lam)
+        if lv != solver.lam:
+            solver.set_lambda(lv)
+        solver.reset(b.detach().contiguous())
+        solver.solve(int(iters))
+        ctx.solver = solver
+        ctx.lam_meta = (lam.dtype, lam.device) if torch.is_tensor(lam) else None
+        return solver.x().clone()
+
+    @staticmethod
+    def backward(ctx, gx):
+        gb, gl = ctx.solver.backward(gx.detach().to(ctx.solver.dtype).contiguous())
+        glam = None
+        if ctx.lam_meta is not None:
+            glam = torch.tensor(gl, dtype=ctx.lam_meta[0], device=ctx.lam_meta[1])
+        return gb, glam, None, None
+
+
+def solve_differentiable(solver, b, lam, iters):
+    """x_K = SGKSFunction.apply(b, lam, solver, iters) (lam a 0-dim tensor to get dl/dlambda)."""
+    return SGKSFunction.apply(b, lam, solver, iters)
 
 
 def kernel_launches() -> int:
