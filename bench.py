@@ -430,6 +430,7 @@ def extras(args, G, P, kw, S, iters, dev, flush):
     if not args.no_batch:
         out["batched"] = {"ct2d_64rhs": bench_ct_batch(G, dev, flush), "dynct_ragged16": bench_dynct_batch(G, dev, flush)}
         out["differentiable"] = bench_differentiable(G, dev, flush)
+        out["gks"] = {name: bench_gks(G, name, dev, flush) for name in ("deblur2d", "ct2d")}
     # CPU oracle baseline, bounded sample, one thread
     try:
         r = run_cpu_worker(args.config, args.cpu_sample_iters)
@@ -559,6 +560,34 @@ def bench_dynct_batch(G, dev, flush):
     out["kernels"] = prof
     out["workload"] = ("dynct: 128x128 x F frames, F in {8,16,24,32} x 4 instances, 30 angles/frame x 185 bins, "
                        "space-time L, 1% noise, sparse-sign s=800 zeta=8, 200 iterations, FP32 + 3 refinement steps")
+    return out
+
+
+def bench_gks(G, name, dev, flush):
+    """GKS (Algorithm 1) against sGKS (Algorithm 2) on the GPU, both plain FP64 without
+    refinement, same problem and iteration count; the per-kernel split of a GKS solve."""
+    P = make_workload(name, seed=0)
+    P.n_refine = 0
+    iters = P.iters
+    out = {"iterations": iters}
+    for method in ("sgks", "gks"):
+        kw = G.device_inputs(P, "fp64", device=dev)
+        kw["n_refine"] = 0
+        S = G.Solver(**kw, method=method)
+        t, h = time_solve(G, S, kw["b"], iters, flush, dev)
+        rec = {"ms_per_solve": t, "iters_per_s": iters / (t / 1e3), "final_rre": h["rre_last"]}
+        if method == "gks":
+            S.reset(kw["b"])
+            prof = S.profile(iters)
+            tot = sum(v["ms"] for v in prof.values()) or 1.0
+            names = {"gradient_append": "gradient + orthogonalisation against V",
+                     "sketch_column": "A v, L v", "qr_append": "QR updates of A V and L V (CGS2)",
+                     "stacked_solve": "projected solve", "combine": "x = V y, e, RC"}
+            rec["kernels"] = {names.get(k, k): {"share": v["ms"] / tot, "ms_total": v["ms"]}
+                              for k, v in prof.items() if v["launches"]}
+        S.close()
+        out[method] = rec
+    out["gks_over_sgks_time"] = out["gks"]["ms_per_solve"] / out["sgks"]["ms_per_solve"]
     return out
 
 

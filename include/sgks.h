@@ -49,7 +49,7 @@ enum { SGKS_OP_DENSE = 1, SGKS_OP_CSR = 2, SGKS_OP_CONV2D = 3 };
 enum { SGKS_REG_FD1 = 1, SGKS_REG_GRAD2D = 2, SGKS_REG_LAPLACE2D = 3, SGKS_REG_SPACETIME = 4 };
 enum { SGKS_SKETCH_SPARSE_SIGN = 0, SGKS_SKETCH_GAUSSIAN = 1 };
 enum { SGKS_PREC_FP64 = 0, SGKS_PREC_FP32 = 1, SGKS_PREC_FP32X = 2 };
-enum { SGKS_FLAG_GLOBAL_SMALL = 1, SGKS_FLAG_RECORD = 2 };
+enum { SGKS_FLAG_GLOBAL_SMALL = 1, SGKS_FLAG_RECORD = 2, SGKS_FLAG_GKS = 4 };
 
 /* Forward operator A (m x n).
  *  SGKS_OP_CSR:    row_ptr[m+1], col[nnz] (int32, 0-based), val[nnz] of val_dtype.  Optional
@@ -112,7 +112,14 @@ typedef struct sgks_options {
                              kernels (chosen automatically when the on-chip slices do not fit).
                              bit 1 (SGKS_FLAG_RECORD): keep y_k of every iteration so that
                              sgks_backward can differentiate the solve; needs n_refine = 0,
-                             precision FP64 or FP32 and the on-chip kernels [0] */
+                             precision FP64 or FP32 and the on-chip kernels.
+                             bit 2 (SGKS_FLAG_GKS): run GKS (Algorithm 1) instead: orthonormal
+                             basis V_k (gradient column orthogonalised, a second pass when the
+                             loss ratio of eq. loss_criterion is >= 1e-10, normalised), full-size
+                             thin QR factors of A V_k and L V_k updated by CGS2 (eq. updqr with
+                             S = I), projected problem eq. projected_withQR.  The sketch options
+                             are ignored; needs n_refine = 0, FP64 or FP32, ell + max_iters <=
+                             1024; sgks_solve's tol applies the relative-change test of eq. RC [0] */
     const double* gauss_SA; /* Gaussian sketch only: S_A, sketch_rows x m, row-major, FP64, device */
     const double* gauss_SL; /* Gaussian sketch only: S_L, sketch_rows x p, row-major, FP64, device */
     const void* x_true;     /* optional, n values of the solver precision: enables RRE records    */

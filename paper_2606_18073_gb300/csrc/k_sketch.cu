@@ -316,7 +316,16 @@ cudaError_t build_sketch_csr(uint64_t key, int64_t h, int s, int zeta, int32_t* 
     return e;
 }
 
+// the apply half of launch_sketch_column alone (GKS appends A w and L w without a sketch)
+template <typename T, typename V>
+cudaError_t launch_apply_new_column(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
+                                    const Small& S, cudaStream_t st) {
+    return launch_apply_column<T, V>(D, A, L, B, S, st);
+}
+
 #define SGKS_INST_SK(T, V)                                                                                  \
+    template cudaError_t launch_apply_new_column<T, V>(const Dims&, const DevA<T, V>&, const DevL&,         \
+                                                       const Bulk<T>&, const Small&, cudaStream_t);         \
     template cudaError_t launch_sketch_column<T, V>(const Dims&, const DevA<T, V>&, const DevL&,            \
                                                     const Bulk<T>&, const Small&, const SketchCSR&,         \
                                                     cudaStream_t);                                          \

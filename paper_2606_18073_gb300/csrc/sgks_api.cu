@@ -17,6 +17,7 @@
 #include <atomic>
 #include <type_traits>
 #include <new>
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -106,6 +107,22 @@ struct Engine : EngineBase {
     T* b_own = nullptr;
 
     cudaError_t setup(const void* bptr) override {
+        cudaError_t e = setup_basis(bptr);
+        if (e != cudaSuccess) return e;
+        // sketched QR of W_0, y_0, refinement, x_0
+        for (int j = 0; j < D.ell && e == cudaSuccess; ++j) {
+            e = timed(PK_SKETCH, j, [&] { return sketch(); });
+            if (e == cudaSuccess) e = small_append(j);
+        }
+        if (e == cudaSuccess) e = record_y(0);
+        host_d = D.ell;
+        for (int r = 0; r < n_refine && e == cudaSuccess; ++r) e = refine();
+        if (e == cudaSuccess) e = timed(PK_COMBINE, host_d, [&] { return launch_combine<T>(D, B, S, 2, st); });
+        return e;
+    }
+
+    // b copied into the handle, S_A b, ||x_true||^2 and W_0 (the part of the setup shared with GKS)
+    cudaError_t setup_basis(const void* bptr) {
         // the kernels (and the captured step graph) always read the handle's own copy of b
         cudaError_t e0 = cudaMemcpyAsync(b_own, bptr, sizeof(T) * (size_t)D.m, cudaMemcpyDeviceToDevice, st);
         if (e0 != cudaSuccess) return e0;
@@ -142,16 +159,6 @@ struct Engine : EngineBase {
             if (e == cudaSuccess) e = launch_sqnorm<T>(wj, D.n, part_setup, nbS, st);
             if (e == cudaSuccess) e = launch_normalize<T>(wj, D.n, part_setup, nbS, st);
         }
-        if (e != cudaSuccess) return e;
-        // sketched QR of W_0, y_0, refinement, x_0
-        for (int j = 0; j < D.ell && e == cudaSuccess; ++j) {
-            e = timed(PK_SKETCH, j, [&] { return sketch(); });
-            if (e == cudaSuccess) e = small_append(j);
-        }
-        if (e == cudaSuccess) e = record_y(0);
-        host_d = D.ell;
-        for (int r = 0; r < n_refine && e == cudaSuccess; ++r) e = refine();
-        if (e == cudaSuccess) e = timed(PK_COMBINE, host_d, [&] { return launch_combine<T>(D, B, S, 2, st); });
         return e;
     }
 
@@ -393,6 +400,102 @@ struct Engine : EngineBase {
             case SGKS_BUF_SB: *elem_out = 8; *rows = D.s; *ld = -1; return S.Sb;
             default: return nullptr;
         }
+    }
+};
+
+// GKS (Algorithm 1): orthonormal basis V (kept in W), full-size thin QR factors of A V and L V.
+// One iteration: r = gradient at x (into column d of V); CGS against V, repeated when the loss
+// ratio of eq. loss_criterion is at least tau; normalise; A v -> A V (kept for e = (A V) y - b)
+// and a copy appended to Q_A by CGS2, L v appended to Q_L by CGS2, d_A entry q_A^T b; the stacked
+// solve of eq. projected_withQR (shared with sGKS); x = V y.  Every kernel reads d on the device,
+// so the step graph is replayed as for sGKS.
+template <typename T, typename V>
+struct EngineGKS : Engine<T, V> {
+    using Base = Engine<T, V>;
+    using Base::D; using Base::S; using Base::A; using Base::L; using Base::B; using Base::st;
+    using Base::host_d; using Base::timed; using Base::b_own;
+    T *QA = nullptr, *QL = nullptr;        // [dmax][m], [dmax][p]
+    double *gpart = nullptr, *vpart = nullptr;
+    double *c1 = nullptr, *c2 = nullptr;   // projection coefficients [dmax]
+    double* sc4 = nullptr;                 // n0, n1, scale, spare
+    int* flag = nullptr;
+    double tau = 1e-10;                    // eq. loss_criterion
+
+    cudaError_t qr_col(T* Q, int64_t h, double* Rm, double* out, bool with_b) {
+        const DevScalars* sc = S.sc;
+        const int dm = D.dmax;
+        cudaError_t e = cudaSuccess;
+        auto R = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+        R(launchg_dot<T>(Q, h, nullptr, sc, vpart, sc4 + 0, st));
+        for (int pass = 0; pass < 2; ++pass) {
+            double* c = pass ? c2 : c1;
+            R(launchg_coef<T>(Q, h, Q, sc, dm, gpart, c, st));
+            R(launchg_update<T>(Q, h, sc, c, nullptr, dm, st));
+        }
+        R(launchg_dot<T>(Q, h, nullptr, sc, vpart, sc4 + 1, st));
+        R(launchg_qr_finish(c1, c2, sc, dm, sc4 + 0, sc4 + 1, Rm, out, sc4 + 2, st));
+        R(launchg_scale<T>(Q, h, sc, sc4 + 2, st));
+        if (with_b) R(launchg_dot<T>(Q, h, b_own, sc, vpart, out + 3, st));
+        g_launches.fetch_add(2 + 4 * 2 + 2 + 1 + 1 + (with_b ? 2 : 0));
+        return e;
+    }
+
+    // column d of V (= W) against V[:, :d]: CGS, a second pass when ||V^T v|| >= tau ||v||, normalise
+    cudaError_t orth_new() {
+        const DevScalars* sc = S.sc;
+        const int dm = D.dmax;
+        T* Vm = B.W;
+        cudaError_t e = cudaSuccess;
+        auto R = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+        R(launchg_coef<T>(Vm, D.n, Vm, sc, dm, gpart, c1, st));
+        R(launchg_update<T>(Vm, D.n, sc, c1, nullptr, dm, st));
+        R(launchg_coef<T>(Vm, D.n, Vm, sc, dm, gpart, c2, st));
+        R(launchg_dot<T>(Vm, D.n, nullptr, sc, vpart, sc4 + 1, st));
+        R(launchg_loss(c2, sc, sc4 + 1, tau, flag, st));
+        R(launchg_update<T>(Vm, D.n, sc, c2, flag, dm, st));
+        R(launchg_dot<T>(Vm, D.n, nullptr, sc, vpart, sc4 + 1, st));
+        R(launchg_inv_norm(sc4 + 1, sc4 + 2, S.sc, st));
+        R(launchg_scale<T>(Vm, D.n, sc, sc4 + 2, st));
+        g_launches.fetch_add(2 + 1 + 2 + 2 + 1 + 1 + 2 + 1 + 1);
+        return e;
+    }
+
+    // columns d of A V, Q_A, Q_L from column d of V; R columns and d_A entry; stacked solve
+    cudaError_t append_gks(int d) {
+        cudaError_t e = cudaSuccess;
+        auto R = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+        R(timed(PK_SKETCH, d, [&] { return launch_apply_new_column<T, V>(D, A, L, B, S, st); }));
+        R(launchg_copy_col<T>(B.AW, QA, D.m, S.sc, true, st));      // A v (column d of A V)
+        R(launchg_copy_col<T>(B.tmp_p, QL, D.p, S.sc, false, st));  // L v (a p-vector)
+        g_launches.fetch_add(2);
+        R(timed(PK_QR_APPEND, d, [&] {
+            cudaError_t e2 = qr_col(QA, D.m, S.RA, S.qr_out, true);
+            if (e2 == cudaSuccess) e2 = qr_col(QL, D.p, S.RL, S.qr_out + 4, false);
+            return e2;
+        }));
+        R(timed(PK_STACKED_SOLVE, d, [&] { return launch_stacked_solve(D, S, st); }));
+        return e;
+    }
+
+    cudaError_t setup(const void* bptr) override {
+        cudaError_t e = Base::setup_basis(bptr);
+        for (int j = 0; j < D.ell && e == cudaSuccess; ++j) e = append_gks(j);
+        host_d = D.ell;
+        if (e == cudaSuccess) e = timed(PK_COMBINE, host_d, [&] { return launch_combine<T>(D, B, S, 2, st); });
+        return e;
+    }
+
+    cudaError_t step() override {
+        const int d = host_d;
+        // profile class 0 holds the gradient and its orthogonalisation against V
+        cudaError_t e = timed(PK_GRAD_APPEND, d, [&] {
+            cudaError_t e2 = launch_gradient<T, V>(D, A, L, B, S, false, st);
+            return e2 == cudaSuccess ? orth_new() : e2;
+        });
+        if (e == cudaSuccess) e = append_gks(d);
+        host_d = d + 1;
+        if (e == cudaSuccess) e = timed(PK_COMBINE, host_d, [&] { return launch_combine<T>(D, B, S, 1, st); });
+        return e;
     }
 };
 
@@ -728,6 +831,8 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     if constexpr (kF32) {
         if (xform) E = EX = new (std::nothrow) EngineX();
     }
+    EngineGKS<T, V>* EG = nullptr;
+    if (!E && (o.flags & SGKS_FLAG_GKS)) E = EG = new (std::nothrow) EngineGKS<T, V>();
     if (!E) E = new (std::nothrow) Engine<T, V>();
     if (!E) return fail(h, SGKS_ERR_NOMEM, "host allocation failed");
     h->eng = E;
@@ -843,6 +948,18 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     AL(S.sc, 1);
     AL(E->part_setup, (size_t)E->nbS * 8);
     if (o.flags & SGKS_FLAG_RECORD) AL(E->yhist, (size_t)(o.max_iters + 1) * dm);
+    if (EG) {
+        if (!D.fast_small) return fail(h, SGKS_ERR_INVALID, "GKS needs the on-chip stacked solve (sketch_rows too large)");
+        const int64_t hmax = std::max<int64_t>(std::max<int64_t>(D.n, D.m), D.p);
+        AL(EG->QA, dm * D.m);
+        AL(EG->QL, dm * D.p);
+        AL(EG->gpart, (size_t)gks_blocks(hmax) * dm);
+        AL(EG->vpart, (size_t)gks_vec_blocks(hmax));
+        AL(EG->c1, dm);
+        AL(EG->c2, dm);
+        AL(EG->sc4, 4);
+        AL(EG->flag, 1);
+    }
     E->allocs = &h->allocs;
     S.lam = lambda;
     AL(E->d_err, 1);
@@ -922,6 +1039,13 @@ int sgks::validate_problem(const sgks_op* A, const sgks_reg* L, const void* b, d
     }
     if (o.cgs_passes != 1 && o.cgs_passes != 2) return bad("cgs_passes must be 1 or 2");
     if (o.n_refine < 0 || o.n_refine > 64) return bad("n_refine out of range");
+    if (o.flags & SGKS_FLAG_GKS) {
+        if (o.n_refine != 0) return bad("SGKS_FLAG_GKS (Algorithm 1) has no refinement: n_refine must be 0");
+        if (o.precision == SGKS_PREC_FP32X) return bad("SGKS_FLAG_GKS supports the FP64 and FP32 forms");
+        if (o.flags & (SGKS_FLAG_RECORD | SGKS_FLAG_GLOBAL_SMALL))
+            return bad("SGKS_FLAG_GKS cannot be combined with SGKS_FLAG_RECORD or SGKS_FLAG_GLOBAL_SMALL");
+        if (o.ell + o.max_iters > 1024) return bad("SGKS_FLAG_GKS needs ell + max_iters <= 1024");
+    }
     if (o.flags & SGKS_FLAG_RECORD) {
         if (o.n_refine != 0) return bad("SGKS_FLAG_RECORD needs n_refine = 0");
         if (o.precision == SGKS_PREC_FP32X) return bad("SGKS_FLAG_RECORD supports the FP64 and FP32 forms");

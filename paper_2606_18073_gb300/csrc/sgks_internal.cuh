@@ -683,6 +683,31 @@ cudaError_t launchd_small_inverse(const double* R, int ell, double* Rinv, cudaSt
 template <typename T>
 cudaError_t launchd_kbar(const T* Wb0, int64_t n, int ell, const double* Rinv, T* Kbar, cudaStream_t st);
 
+// ------------------------------------------------------------------------ GKS (k_gks.cu)
+template <typename T, typename V>
+cudaError_t launch_apply_new_column(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
+                                    const Small& S, cudaStream_t st);
+int gks_blocks(int64_t h);
+int gks_vec_blocks(int64_t h);
+template <typename T>
+cudaError_t launchg_coef(const T* Q, int64_t h, const T* U, const DevScalars* sc, int dm, double* part, double* c,
+                         cudaStream_t st);
+template <typename T>
+cudaError_t launchg_update(T* Q, int64_t h, const DevScalars* sc, const double* c, const int* flag, int dm,
+                           cudaStream_t st);
+template <typename T>
+cudaError_t launchg_dot(const T* U, int64_t h, const T* w, const DevScalars* sc, double* part, double* out,
+                        cudaStream_t st);
+template <typename T>
+cudaError_t launchg_copy_col(const T* src, T* dst, int64_t h, const DevScalars* sc, bool src_col, cudaStream_t st);
+template <typename T>
+cudaError_t launchg_scale(T* U, int64_t h, const DevScalars* sc, const double* scale, cudaStream_t st);
+cudaError_t launchg_loss(const double* c2, const DevScalars* sc, const double* nv2, double tau, int* flag,
+                         cudaStream_t st);
+cudaError_t launchg_inv_norm(const double* nv2, double* scale, DevScalars* sc, cudaStream_t st);
+cudaError_t launchg_qr_finish(const double* c1, const double* c2, const DevScalars* sc, int dm, const double* n0,
+                              const double* n1, double* Rm, double* out, double* scale, cudaStream_t st);
+
 // Host-side preparation shared by the single and the batched handles (sgks_api.cu): the L
 // descriptor, the operator in the solver precision (CSR validation, value conversion, device
 // transpose) and the sparse-sign sketches by rows.  Device memory goes to `allocs`; the int

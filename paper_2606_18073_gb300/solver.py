@@ -117,7 +117,7 @@ class Reg:
 
 
 class Solver:
-    """sGKS solver (Algorithm 2) on the current CUDA device and stream.
+    """sGKS solver (Algorithm 2; method="gks": GKS, Algorithm 1) on the current CUDA device and stream.
 
     A: CSR | Dense | Conv2D; L: Reg; b: device tensor (float64 for precision="fp64", float32
     for "fp32"); lam > 0; sketch_rows = s.  Tensors passed here must outlive the solver.
@@ -127,7 +127,8 @@ class Solver:
                  max_iters: int = 100, ell: int = 3, n_refine: int = 0, precision: str = "fp64",
                  sketch: str = "sparse_sign", zeta: int = 8, cgs_passes: int = 2,
                  gauss_SA: Optional[torch.Tensor] = None, gauss_SL: Optional[torch.Tensor] = None,
-                 x_true: Optional[torch.Tensor] = None, stream=None, flags: int = 0, record: bool = False):
+                 x_true: Optional[torch.Tensor] = None, stream=None, flags: int = 0, record: bool = False,
+                 method: str = "sgks"):
         self._lib = L.load()
         self.precision = precision
         self.dtype = torch.float32 if precision in ("fp32", "fp32x") else torch.float64
@@ -150,7 +151,9 @@ class Solver:
         o.precision = {"fp64": L.SGKS_PREC_FP64, "fp32": L.SGKS_PREC_FP32, "fp32x": L.SGKS_PREC_FP32X}[precision]
         o.sketch_kind = L.SGKS_SKETCH_GAUSSIAN if sketch == "gaussian" else L.SGKS_SKETCH_SPARSE_SIGN
         o.gauss_SA, o.gauss_SL, o.x_true = _ptr(gauss_SA), _ptr(gauss_SL), _ptr(x_true)
-        o.flags = int(flags) | (L.SGKS_FLAG_RECORD if record else 0)
+        if method not in ("sgks", "gks"):
+            raise ValueError("method is 'sgks' (Algorithm 2) or 'gks' (Algorithm 1)")
+        o.flags = int(flags) | (L.SGKS_FLAG_RECORD if record else 0) | (L.SGKS_FLAG_GKS if method == "gks" else 0)
         self._stream = torch.cuda.current_stream(b.device).cuda_stream if stream is None else stream
         self.device = b.device
         h = C.c_void_p()
