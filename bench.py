@@ -431,6 +431,7 @@ def extras(args, G, P, kw, S, iters, dev, flush):
         out["batched"] = {"ct2d_64rhs": bench_ct_batch(G, dev, flush), "dynct_ragged16": bench_dynct_batch(G, dev, flush)}
         out["differentiable"] = bench_differentiable(G, dev, flush)
         out["gks"] = {name: bench_gks(G, name, dev, flush) for name in ("deblur2d", "ct2d")}
+        out["srtt_sketch_sweep"] = bench_srtt_sweep(G, dev, flush)
     # CPU oracle baseline, bounded sample, one thread
     try:
         r = run_cpu_worker(args.config, args.cpu_sample_iters)
@@ -588,6 +589,29 @@ def bench_gks(G, name, dev, flush):
         S.close()
         out[method] = rec
     out["gks_over_sgks_time"] = out["gks"]["ms_per_solve"] / out["sgks"]["ms_per_solve"]
+    return out
+
+
+def bench_srtt_sweep(G, dev, flush, sizes=(200, 400, 800)):
+    """The deblurring workload with the paper's SRTT sketch (eq. sketching_trig, dense on the
+    device) at several sketch sizes s, next to the sparse-sign sketch at the workload's s."""
+    from workloads.configs import srtt_sketch
+    out = {}
+    base = make_workload("deblur2d", seed=0)
+    iters = base.iters
+    for s in sizes:
+        P = make_workload("deblur2d", seed=0)
+        P.sketch = srtt_sketch(s, P.m, P.p, seed=0)
+        kw = G.device_inputs(P, P.precision, device=dev)
+        S = G.Solver(**kw)
+        t, h = time_solve(G, S, kw["b"], iters, flush, dev)
+        S.close()
+        out[f"srtt_s{s}"] = {"iters_per_s": iters / (t / 1e3), "final_rre": h["rre_last"]}
+    kw = G.device_inputs(base, base.precision, device=dev)
+    S = G.Solver(**kw)
+    t, h = time_solve(G, S, kw["b"], iters, flush, dev)
+    S.close()
+    out[f"sparse_sign_s{base.sketch.s}"] = {"iters_per_s": iters / (t / 1e3), "final_rre": h["rre_last"]}
     return out
 
 

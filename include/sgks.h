@@ -47,7 +47,7 @@ extern "C" {
 enum { SGKS_F32 = 0, SGKS_F64 = 1 };
 enum { SGKS_OP_DENSE = 1, SGKS_OP_CSR = 2, SGKS_OP_CONV2D = 3 };
 enum { SGKS_REG_FD1 = 1, SGKS_REG_GRAD2D = 2, SGKS_REG_LAPLACE2D = 3, SGKS_REG_SPACETIME = 4 };
-enum { SGKS_SKETCH_SPARSE_SIGN = 0, SGKS_SKETCH_GAUSSIAN = 1 };
+enum { SGKS_SKETCH_SPARSE_SIGN = 0, SGKS_SKETCH_GAUSSIAN = 1, SGKS_SKETCH_SRTT = 2 };
 enum { SGKS_PREC_FP64 = 0, SGKS_PREC_FP32 = 1, SGKS_PREC_FP32X = 2 };
 enum { SGKS_FLAG_GLOBAL_SMALL = 1, SGKS_FLAG_RECORD = 2, SGKS_FLAG_GKS = 4 };
 
@@ -104,7 +104,9 @@ typedef struct sgks_options {
                              b, x_true and x_out are FP64 for FP64 and FP32 otherwise; for FP32X
                              sgks_get_buffer(SGKS_BUF_X / SGKS_BUF_AW) returns (hi, lo) float
                              pairs [FP64]                                                        */
-    int32_t sketch_kind;  /* SGKS_SKETCH_SPARSE_SIGN or SGKS_SKETCH_GAUSSIAN [sparse-sign]          */
+    int32_t sketch_kind;  /* SGKS_SKETCH_SPARSE_SIGN, SGKS_SKETCH_GAUSSIAN or SGKS_SKETCH_SRTT
+                             (eq. sketching_trig: S = sqrt(h/s) D F E, F the orthonormal DCT-II;
+                             built as a dense FP64 matrix on the device at create) [sparse-sign] */
     int32_t zeta;         /* nonzeros per sketch column, 1..16, <= sketch_rows [8]                  */
     int32_t cgs_passes;   /* 1 = the single projection printed under eq. updqr, 2 = CGS2 [2]       */
     int32_t flags;        /* bit 0 (SGKS_FLAG_GLOBAL_SMALL): run the FP64 QR append and projected
@@ -123,6 +125,10 @@ typedef struct sgks_options {
     const double* gauss_SA; /* Gaussian sketch only: S_A, sketch_rows x m, row-major, FP64, device */
     const double* gauss_SL; /* Gaussian sketch only: S_L, sketch_rows x p, row-major, FP64, device */
     const void* x_true;     /* optional, n values of the solver precision: enables RRE records    */
+    const int8_t* srtt_signs_A;  /* SRTT only (device): the Rademacher diagonal E of S_A, m entries +-1 */
+    const int32_t* srtt_rows_A;  /* SRTT only (device): the s sampled rows D of S_A, in [0, m)         */
+    const int8_t* srtt_signs_L;  /* SRTT only: E of S_L, p entries                                      */
+    const int32_t* srtt_rows_L;  /* SRTT only: the s rows of S_L, in [0, p)                            */
 } sgks_options;
 
 /* Per-solve report (host memory).  rc / rre may be NULL; otherwise they receive one value per

@@ -42,7 +42,7 @@ def sgks_vjp(problem, iters, xbar, fwd=None):
     bbar (m), lambdabar, and the forward's x_K.
     """
     P = problem
-    if P.sketch.kind != "sparse_sign" and P.sketch.kind != "gaussian":
+    if P.sketch.kind not in ("sparse_sign", "gaussian", "srtt"):
         raise ValueError(P.sketch.kind)
     if fwd is None:
         fwd = sgks(P, iters=iters, n_refine=0, record_x=True)

@@ -34,6 +34,7 @@ What each function follows, and what pins it (tests/test_oracle_*.py):
 from __future__ import annotations
 
 import numpy as np
+import scipy.fft
 import scipy.linalg
 import scipy.sparse as sp
 
@@ -105,10 +106,50 @@ def sketch_operator(desc, stream: int, h: int):
         M = desc.SA if stream == 0 else desc.SL
         assert M.shape == (desc.s, h)
         return np.asarray(M, dtype=np.float64)
+    if desc.kind == "srtt":
+        signs = desc.signs_A if stream == 0 else desc.signs_L
+        rows = desc.rows_A if stream == 0 else desc.rows_L
+        assert len(signs) == h and len(rows) == desc.s
+        return SRTT(np.asarray(signs, dtype=np.float64), np.asarray(rows, dtype=np.int64))
     rows, signs = sparse_sign_rows(desc.seed, stream, h, desc.s, desc.zeta)
     colptr = np.arange(0, h * desc.zeta + 1, desc.zeta)
     return sp.csc_matrix((signs.ravel() / np.sqrt(desc.zeta), rows.ravel(), colptr),
                          shape=(desc.s, h))
+
+
+class SRTT:
+    """S = sqrt(h/s) D F E of eq. (sketching_trig): E = diag(signs), F = orthonormal DCT-II of
+    length h (scipy.fft.dct, norm="ortho"), D = the rows ``rows`` of the identity.  Applied as
+    S v = sqrt(h/s) (F (E v))[rows]; the transpose S^T u = sqrt(h/s) E F^T (D^T u)."""
+
+    def __init__(self, signs, rows):
+        self.signs, self.rows = signs, rows
+        self.h, self.s = len(signs), len(rows)
+        self.shape = (self.s, self.h)
+        self.scale = np.sqrt(self.h / self.s)
+
+    def __matmul__(self, v):
+        v = np.asarray(v, dtype=np.float64)
+        if v.ndim == 2:
+            return np.stack([self @ v[:, j] for j in range(v.shape[1])], axis=1)
+        return self.scale * scipy.fft.dct(self.signs * v, type=2, norm="ortho")[self.rows]
+
+    @property
+    def T(self):
+        outer = self
+
+        class _T:
+            shape = (outer.h, outer.s)
+
+            def __matmul__(self, u):
+                full = np.zeros(outer.h)
+                full[outer.rows] = u
+                return outer.scale * outer.signs * scipy.fft.idct(full, type=2, norm="ortho")
+
+        return _T()
+
+    def toarray(self):
+        return np.stack([self @ e for e in np.eye(self.h)], axis=1)
 
 
 # -------------------------------------------------------------------------- operators

@@ -18,7 +18,7 @@ SGKS_ERR_STATE, SGKS_ERR_NOMEM, SGKS_ERR_SKETCH = -4, -5, -6
 SGKS_F32, SGKS_F64 = 0, 1
 SGKS_OP_DENSE, SGKS_OP_CSR, SGKS_OP_CONV2D = 1, 2, 3
 SGKS_REG_FD1, SGKS_REG_GRAD2D, SGKS_REG_LAPLACE2D, SGKS_REG_SPACETIME = 1, 2, 3, 4
-SGKS_SKETCH_SPARSE_SIGN, SGKS_SKETCH_GAUSSIAN = 0, 1
+SGKS_SKETCH_SPARSE_SIGN, SGKS_SKETCH_GAUSSIAN, SGKS_SKETCH_SRTT = 0, 1, 2
 SGKS_PREC_FP64, SGKS_PREC_FP32, SGKS_PREC_FP32X = 0, 1, 2
 (SGKS_BUF_X, SGKS_BUF_Y, SGKS_BUF_W, SGKS_BUF_QA, SGKS_BUF_RA, SGKS_BUF_QL, SGKS_BUF_RL,
  SGKS_BUF_DA, SGKS_BUF_SB, SGKS_BUF_T, SGKS_BUF_AW) = range(1, 12)
@@ -54,6 +54,8 @@ class sgks_options(C.Structure):
         ("precision", C.c_int32), ("sketch_kind", C.c_int32), ("zeta", C.c_int32),
         ("cgs_passes", C.c_int32), ("flags", C.c_int32),
         ("gauss_SA", C.c_void_p), ("gauss_SL", C.c_void_p), ("x_true", C.c_void_p),
+        ("srtt_signs_A", C.c_void_p), ("srtt_rows_A", C.c_void_p), ("srtt_signs_L", C.c_void_p),
+        ("srtt_rows_L", C.c_void_p),
     ]
 
 

@@ -368,6 +368,33 @@ cudaError_t csr_transpose_noalloc_device(int64_t m, int64_t n, int64_t nnz, cons
     return transpose_noalloc_impl<double>(m, n, nnz, rp, ci, (const double*)val, trp, tci, (double*)tval, st);
 }
 
+// ------------------------------------------------------------------------- SRTT sketch
+// out[r * h + i] = sqrt(h/s) c_k cos(pi k (2i+1) / (2h)) signs[i] with k = rows[r]: row r of
+// S = sqrt(h/s) D F E (eq. sketching_trig) for F the orthonormal DCT-II (c_0 = sqrt(1/h),
+// c_k = sqrt(2/h)).  The argument k (2i+1) is reduced modulo 4h in integers first, so cospi sees
+// a value in [0, 2).
+__global__ void k_srtt_fill(const int8_t* __restrict__ signs, const int32_t* __restrict__ rows, int64_t h, int s,
+                            double* out) {
+    const double base = sqrt((double)h / (double)s);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)s * h;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(t / h);
+        const int64_t i = t - (int64_t)r * h;
+        const int64_t k = rows[r];
+        int64_t a = (k * (2 * i + 1)) % (4 * h);
+        if (a < 0) a += 4 * h;
+        const double ck = (k == 0 ? sqrt(1.0 / (double)h) : sqrt(2.0 / (double)h)) * base;
+        out[t] = ck * cospi((double)a / (2.0 * (double)h)) * (double)signs[i];
+    }
+}
+
+cudaError_t launch_srtt_fill(const int8_t* signs, const int32_t* rows, int64_t h, int s, double* out, cudaStream_t st) {
+    int64_t blocks = ((int64_t)s * h + 255) / 256;
+    if (blocks > 8 * 152) blocks = 8 * 152;
+    k_srtt_fill<<<(int)blocks, 256, 0, st>>>(signs, rows, h, s, out);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------- conversion
 template <typename A, typename B>
 __global__ void k_convert(const A* __restrict__ in, B* out, int64_t count) {

@@ -838,7 +838,7 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     h->eng = E;
     E->st = h->st;
     E->pst = h->st;
-    E->gauss = o.sketch_kind == SGKS_SKETCH_GAUSSIAN;
+    E->gauss = o.sketch_kind != SGKS_SKETCH_SPARSE_SIGN;   // Gaussian and SRTT: dense FP64 sketches
     E->elem = sizeof(T);
     E->n_refine = o.n_refine;
     Dims& D = E->D;
@@ -851,8 +851,8 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     D.max_iters = o.max_iters;
     D.lam = lambda;
     D.cgs_passes = o.cgs_passes;
-    D.sketch_kind = o.sketch_kind;
-    D.sketch_scale = o.sketch_kind == SGKS_SKETCH_GAUSSIAN ? 1.0 : 1.0 / sqrt((double)o.zeta);
+    D.sketch_kind = o.sketch_kind == SGKS_SKETCH_SPARSE_SIGN ? SGKS_SKETCH_SPARSE_SIGN : SGKS_SKETCH_GAUSSIAN;
+    D.sketch_scale = o.sketch_kind == SGKS_SKETCH_SPARSE_SIGN ? 1.0 / sqrt((double)o.zeta) : 1.0;
     D.keyA = sketch_key_host_dev(seed, 0);
     D.keyL = sketch_key_host_dev(seed, 1);
     D.cluster = cluster;
@@ -879,7 +879,7 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     };
     D.nbA = nb8(sl_m);
     D.nbL = nb8(sl_p);
-    const bool gauss = o.sketch_kind == SGKS_SKETCH_GAUSSIAN;
+    const bool gauss = o.sketch_kind != SGKS_SKETCH_SPARSE_SIGN;
     D.npA = 1;
     D.npL = 1;
     const int64_t tiles = (D.n + kThreads - 1) / kThreads;
@@ -980,9 +980,20 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
             if (rs != SGKS_OK) return fail(h, rs, why);
         }
     }
-#undef AL
     E->gSA = o.gauss_SA;
     E->gSL = o.gauss_SL;
+    if (o.sketch_kind == SGKS_SKETCH_SRTT) {   // S = sqrt(h/s) D F E as dense FP64 rows
+        double *SA = nullptr, *SL = nullptr;
+        AL(SA, (size_t)s * D.m);
+        AL(SL, (size_t)s * D.p);
+        if (e != cudaSuccess) return fail(h, SGKS_ERR_NOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
+        e = launch_srtt_fill(o.srtt_signs_A, o.srtt_rows_A, D.m, s, SA, h->st);
+        if (e == cudaSuccess) e = launch_srtt_fill(o.srtt_signs_L, o.srtt_rows_L, D.p, s, SL, h->st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "SRTT sketch");
+        E->gSA = SA;
+        E->gSL = SL;
+    }
+#undef AL
     return SGKS_OK;
 }
 
@@ -1034,6 +1045,10 @@ int sgks::validate_problem(const sgks_op* A, const sgks_reg* L, const void* b, d
         if (o.zeta < 1 || o.zeta > kMaxZeta || o.zeta > s) return bad("zeta must satisfy 1 <= zeta <= min(16, s)");
     } else if (o.sketch_kind == SGKS_SKETCH_GAUSSIAN) {
         if (!o.gauss_SA || !o.gauss_SL) return bad("Gaussian sketch needs gauss_SA and gauss_SL");
+    } else if (o.sketch_kind == SGKS_SKETCH_SRTT) {
+        if (!o.srtt_signs_A || !o.srtt_rows_A || !o.srtt_signs_L || !o.srtt_rows_L)
+            return bad("SRTT sketch needs srtt_signs_A, srtt_rows_A, srtt_signs_L and srtt_rows_L");
+        if (s > A->m) return bad("SRTT sketch needs sketch_rows <= m");
     } else {
         return bad("unknown sketch kind");
     }

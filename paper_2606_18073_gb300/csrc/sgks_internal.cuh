@@ -731,6 +731,7 @@ cudaError_t csr_transpose_noalloc_device(int64_t m, int64_t n, int64_t nnz, cons
 cudaError_t sparse_sign_rows_device(uint64_t key, int64_t h, int s, int zeta, int32_t* rows, uint8_t* neg,
                                     int* err, cudaStream_t st);
 cudaError_t convert_values(const void* in, int in_dt, void* out, int out_dt, int64_t count, cudaStream_t st);
+cudaError_t launch_srtt_fill(const int8_t* signs, const int32_t* rows, int64_t h, int s, double* out, cudaStream_t st);
 cudaError_t launch_set_tol(DevScalars* sc, double tol, cudaStream_t st);
 cudaError_t validate_csr_device(const int32_t* rp, const int32_t* ci, int64_t m, int64_t n, int64_t nnz, int* err,
                                 cudaStream_t st);

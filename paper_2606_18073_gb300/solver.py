@@ -128,7 +128,7 @@ class Solver:
                  sketch: str = "sparse_sign", zeta: int = 8, cgs_passes: int = 2,
                  gauss_SA: Optional[torch.Tensor] = None, gauss_SL: Optional[torch.Tensor] = None,
                  x_true: Optional[torch.Tensor] = None, stream=None, flags: int = 0, record: bool = False,
-                 method: str = "sgks"):
+                 method: str = "sgks", srtt=None):
         self._lib = L.load()
         self.precision = precision
         self.dtype = torch.float32 if precision in ("fp32", "fp32x") else torch.float64
@@ -149,8 +149,16 @@ class Solver:
         o = L.sgks_options()
         o.max_iters, o.ell, o.n_refine, o.zeta, o.cgs_passes = max_iters, ell, n_refine, zeta, cgs_passes
         o.precision = {"fp64": L.SGKS_PREC_FP64, "fp32": L.SGKS_PREC_FP32, "fp32x": L.SGKS_PREC_FP32X}[precision]
-        o.sketch_kind = L.SGKS_SKETCH_GAUSSIAN if sketch == "gaussian" else L.SGKS_SKETCH_SPARSE_SIGN
+        o.sketch_kind = {"gaussian": L.SGKS_SKETCH_GAUSSIAN, "srtt": L.SGKS_SKETCH_SRTT}.get(
+            sketch, L.SGKS_SKETCH_SPARSE_SIGN)
         o.gauss_SA, o.gauss_SL, o.x_true = _ptr(gauss_SA), _ptr(gauss_SL), _ptr(x_true)
+        if sketch == "srtt":
+            if srtt is None or len(srtt) != 4:
+                raise ValueError("sketch='srtt' needs srtt=(signs_A int8, rows_A int32, signs_L int8, rows_L int32)")
+            for t, nm in zip(srtt, ("signs_A", "rows_A", "signs_L", "rows_L")):
+                _need_cuda(t, nm)
+            self._keep.append(srtt)
+            o.srtt_signs_A, o.srtt_rows_A, o.srtt_signs_L, o.srtt_rows_L = [_ptr(t) for t in srtt]
         if method not in ("sgks", "gks"):
             raise ValueError("method is 'sgks' (Algorithm 2) or 'gks' (Algorithm 1)")
         o.flags = int(flags) | (L.SGKS_FLAG_RECORD if record else 0) | (L.SGKS_FLAG_GKS if method == "gks" else 0)
@@ -461,4 +469,8 @@ def device_inputs(problem, precision: Optional[str] = None, device="cuda", trans
     if sk.kind == "gaussian":
         kw["gauss_SA"] = torch.from_numpy(np.ascontiguousarray(sk.SA, dtype=np.float64)).to(device)
         kw["gauss_SL"] = torch.from_numpy(np.ascontiguousarray(sk.SL, dtype=np.float64)).to(device)
+    if sk.kind == "srtt":
+        kw["srtt"] = tuple(torch.from_numpy(np.ascontiguousarray(a)).to(device)
+                           for a in (sk.signs_A.astype(np.int8), sk.rows_A.astype(np.int32),
+                                     sk.signs_L.astype(np.int8), sk.rows_L.astype(np.int32)))
     return kw

@@ -84,7 +84,19 @@ def _sketch(kind, s, m, p, zeta=8, seed=0):
         SA = _rng(seed, 101).standard_normal((s, m)) / np.sqrt(s)
         SL = _rng(seed, 102).standard_normal((s, p)) / np.sqrt(s)
         return SketchDesc("gaussian", s, zeta, seed, SA=SA, SL=SL)
+    if kind == "srtt":
+        return srtt_sketch(s, m, p, seed)
     return SketchDesc("sparse_sign", s, zeta, seed)
+
+
+def srtt_sketch(s, m, p, seed=0):
+    """Rademacher signs and s distinct sampled rows for S_A (length m) and S_L (length p)."""
+    ra, rl = _rng(seed, 103), _rng(seed, 104)
+    return SketchDesc("srtt", s, 0, seed,
+                      signs_A=ra.choice(np.array([-1, 1], dtype=np.int8), size=m),
+                      rows_A=np.sort(ra.choice(m, size=s, replace=False)).astype(np.int32),
+                      signs_L=rl.choice(np.array([-1, 1], dtype=np.int8), size=p),
+                      rows_L=np.sort(rl.choice(p, size=s, replace=False)).astype(np.int32))
 
 
 # ----------------------------------------------------------------------------- operators

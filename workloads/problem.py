@@ -94,6 +94,11 @@ class SketchDesc:
                           stream 1 is S_L.  Nothing is stored: both sides regenerate it.
     kind = "gaussian":    dense N(0, 1/s) matrices ``SA`` (s x m) and ``SL`` (s x p), drawn here
                           and passed to both sides as inputs.
+    kind = "srtt":        the subsampled randomized trigonometric transform of eq.
+                          (sketching_trig), S = sqrt(h/s) D F E: E = diag(``signs``) (Rademacher),
+                          F the orthonormal DCT-II of length h, D the rows ``rows`` of the identity
+                          (s distinct indices).  Signs and rows are drawn here and passed to
+                          both sides (``signs_A`` / ``rows_A`` for S_A, ``signs_L`` / ``rows_L``).
     """
     kind: str
     s: int
@@ -101,6 +106,10 @@ class SketchDesc:
     seed: int = 0
     SA: Optional[np.ndarray] = None
     SL: Optional[np.ndarray] = None
+    signs_A: Optional[np.ndarray] = None
+    rows_A: Optional[np.ndarray] = None
+    signs_L: Optional[np.ndarray] = None
+    rows_L: Optional[np.ndarray] = None
 
 
 @dataclass
