@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched CT and dynamic-CT measurements")
     ap.add_argument("--cpu-sample-iters", type=int, default=25)
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--profile-batch", default=None, choices=["ct2d", "dynct"],
+                    help="run one batched solve of a reduced CT / dynamic-CT batch (for profiler captures) and exit")
+    ap.add_argument("--batch-size", type=int, default=16)
+    ap.add_argument("--batch-iters", type=int, default=40)
     return ap.parse_args()
 
 
@@ -239,6 +243,9 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile_batch:
+        profile_batch(args)
         return
     import numpy as np
     import torch
@@ -590,6 +597,40 @@ def bench_gks(G, name, dev, flush):
         out[method] = rec
     out["gks_over_sgks_time"] = out["gks"]["ms_per_solve"] / out["sgks"]["ms_per_solve"]
     return out
+
+
+def profile_batch(args):
+    """One reset + solve of a reduced batch, for profiler captures: the 512^2 CT operator with
+    --batch-size right-hand sides (FP32, sparse-sign s = 600), or --batch-size space-time
+    instances of 8 frames (FP32, 3 refinement steps, s = 800), --batch-iters iterations."""
+    import numpy as np
+    import torch
+    import paper_2606_18073_gb300 as G
+    G.build()
+    dev = torch.device("cuda", 0)
+    B, iters = args.batch_size, args.batch_iters
+    if args.profile_batch == "ct2d":
+        from workloads.configs import ct_op, make_ct2d
+        A0 = ct_op(512, np.arange(180) * 1.0, 725)
+        probs = [make_ct2d(instance=i, A=A0, precision="fp32", iters=iters) for i in range(B)]
+    else:
+        from workloads.configs import dynct_frame_ops, make_dynct
+        ops = dynct_frame_ops(128, 8)
+        probs = [make_dynct(seed=i, frames=8, frame_ops=ops, iters=iters) for i in range(B)]
+        for P in probs[1:]:
+            P.A = probs[0].A
+    kw = G.device_inputs(probs[0], "fp32", device=dev)
+    insts = [dict(A=kw["A"], reg=kw["reg"], lam=P.lam, b=torch.from_numpy(np.asarray(P.b)).to(dev, torch.float32),
+                  x_true=torch.from_numpy(np.asarray(P.x_true)).to(dev, torch.float32)) for P in probs]
+    P0 = probs[0]
+    Bt = G.Batch(insts, P0.sketch.s, P0.sketch.seed, max_iters=iters, n_refine=P0.n_refine, precision="fp32",
+                 zeta=P0.sketch.zeta)
+    Bt.reset([i["b"] for i in insts])
+    out = Bt.solve(iters)
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"profile_batch": args.profile_batch, "instances": B, "iterations": iters,
+                      "median_final_rre": float(np.median([o["rre_last"] for o in out]))}))
+    Bt.close()
 
 
 def bench_srtt_sweep(G, dev, flush, sizes=(200, 400, 800)):

@@ -124,14 +124,14 @@ template <typename T, int VV>
 __device__ __forceinline__ void ldvec(const T* __restrict__ p, T (&o)[VV]) {
     if constexpr (VV * sizeof(T) == 16) {
         if constexpr (sizeof(T) == 4) {
-            const float4 f = __ldg(reinterpret_cast<const float4*>(p));
+            const float4 f = __ldcg(reinterpret_cast<const float4*>(p));
             o[0] = f.x; o[1] = f.y; o[2] = f.z; o[3] = f.w;
         } else {
-            const double2 f = __ldg(reinterpret_cast<const double2*>(p));
+            const double2 f = __ldcg(reinterpret_cast<const double2*>(p));
             o[0] = f.x; o[1] = f.y;
         }
     } else if constexpr (VV == 2 && sizeof(T) == 4) {
-        const float2 f = __ldg(reinterpret_cast<const float2*>(p));
+        const float2 f = __ldcg(reinterpret_cast<const float2*>(p));
         o[0] = f.x; o[1] = f.y;
     } else {
 #pragma unroll

@@ -89,7 +89,28 @@ __global__ void __cluster_dims__(kGradCluster, 1, 1) __launch_bounds__(kThreads)
         rt[warp * 32 + lane] = grad_value<T, V, WARPA>(A, L, psf_s, B.e, B.x, D.lam, base, D.n);
         __syncthreads();
         const int64_t rows = (D.n - t0) < kThreads ? (D.n - t0) : kThreads;
-        for (int j = warp; j < d; j += kWarps) {      // column j is owned by warp j % 8
+        // column j is owned by warp j % 8; two columns per step, 16 loads in flight per lane
+        int j = warp;
+        for (; j + kWarps < d; j += 2 * kWarps) {
+            const T* wc = B.W + (size_t)j * D.n + t0;
+            const T* wc2 = wc + (size_t)kWarps * D.n;
+            T a = T(0), a2 = T(0);
+#pragma unroll
+            for (int k = 0; k < kThreads / 32; ++k) {
+                const int rr = lane + 32 * k;
+                if (rr < rows) {
+                    a += wc[rr] * rt[rr];
+                    a2 += wc2[rr] * rt[rr];
+                }
+            }
+            const double s = warp_sum_acc(a);
+            const double s2 = warp_sum_acc(a2);
+            if (lane == 0) {
+                gacc[j] += s;
+                gacc[j + kWarps] += s2;
+            }
+        }
+        if (j < d) {
             const T* wc = B.W + (size_t)j * D.n + t0;
             T a = T(0);
 #pragma unroll
@@ -167,15 +188,27 @@ __global__ void __launch_bounds__(kThreads) k_combine(Dims D, Bulk<T> B, Small S
         const int64_t i = (int64_t)blockIdx.x * kThreads + tid;
         if (i < D.n) {
             const T* w = B.W + i;
-            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+            // eight columns per step: eight independent loads in flight per thread
+            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0), a4 = T(0), a5 = T(0), a6 = T(0), a7 = T(0);
             int j = 0;
-            for (; j + 3 < d; j += 4) {
-                a0 += w[(size_t)j * D.n] * ys[j];
-                a1 += w[(size_t)(j + 1) * D.n] * ys[j + 1];
-                a2 += w[(size_t)(j + 2) * D.n] * ys[j + 2];
-                a3 += w[(size_t)(j + 3) * D.n] * ys[j + 3];
+            for (; j + 7 < d; j += 8) {
+                const T w0 = w[(size_t)j * D.n], w1 = w[(size_t)(j + 1) * D.n], w2 = w[(size_t)(j + 2) * D.n],
+                        w3 = w[(size_t)(j + 3) * D.n], w4 = w[(size_t)(j + 4) * D.n], w5 = w[(size_t)(j + 5) * D.n],
+                        w6 = w[(size_t)(j + 6) * D.n], w7 = w[(size_t)(j + 7) * D.n];
+                a0 += w0 * ys[j];
+                a1 += w1 * ys[j + 1];
+                a2 += w2 * ys[j + 2];
+                a3 += w3 * ys[j + 3];
+                a4 += w4 * ys[j + 4];
+                a5 += w5 * ys[j + 5];
+                a6 += w6 * ys[j + 6];
+                a7 += w7 * ys[j + 7];
             }
             for (; j < d; ++j) a0 += w[(size_t)j * D.n] * ys[j];
+            a0 += a4;
+            a1 += a5;
+            a2 += a6;
+            a3 += a7;
             const T xv = (a0 + a1) + (a2 + a3);
             B.x[i] = xv;
             if (mode >= 1) {
@@ -194,15 +227,27 @@ __global__ void __launch_bounds__(kThreads) k_combine(Dims D, Bulk<T> B, Small S
         const int64_t i = (int64_t)(blockIdx.x - D.nbX) * kThreads + tid;
         if (i < D.m) {
             const T* w = B.AW + i;
-            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+            // eight columns per step: eight independent loads in flight per thread
+            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0), a4 = T(0), a5 = T(0), a6 = T(0), a7 = T(0);
             int j = 0;
-            for (; j + 3 < d; j += 4) {
-                a0 += w[(size_t)j * D.m] * ys[j];
-                a1 += w[(size_t)(j + 1) * D.m] * ys[j + 1];
-                a2 += w[(size_t)(j + 2) * D.m] * ys[j + 2];
-                a3 += w[(size_t)(j + 3) * D.m] * ys[j + 3];
+            for (; j + 7 < d; j += 8) {
+                const T w0 = w[(size_t)j * D.m], w1 = w[(size_t)(j + 1) * D.m], w2 = w[(size_t)(j + 2) * D.m],
+                        w3 = w[(size_t)(j + 3) * D.m], w4 = w[(size_t)(j + 4) * D.m], w5 = w[(size_t)(j + 5) * D.m],
+                        w6 = w[(size_t)(j + 6) * D.m], w7 = w[(size_t)(j + 7) * D.m];
+                a0 += w0 * ys[j];
+                a1 += w1 * ys[j + 1];
+                a2 += w2 * ys[j + 2];
+                a3 += w3 * ys[j + 3];
+                a4 += w4 * ys[j + 4];
+                a5 += w5 * ys[j + 5];
+                a6 += w6 * ys[j + 6];
+                a7 += w7 * ys[j + 7];
             }
             for (; j < d; ++j) a0 += w[(size_t)j * D.m] * ys[j];
+            a0 += a4;
+            a1 += a5;
+            a2 += a6;
+            a3 += a7;
             B.e[i] = ((a0 + a1) + (a2 + a3)) - B.b[i];
         }
     }
