@@ -519,7 +519,8 @@ def bench_ct_batch(G, dev, flush, count=64):
                   x_true=_dev_tensor(P.x_true, torch.float32, dev)) for P in probs]
     P0 = probs[0]
     Bt = G.Batch(insts, P0.sketch.s, P0.sketch.seed, max_iters=P0.iters, n_refine=0, precision="fp32",
-                 zeta=P0.sketch.zeta)
+                 zeta=P0.sketch.zeta, autotune=True)
+    tuned = Bt.config(0)
     ms, reps = time_batch(Bt, [i["b"] for i in insts], P0.iters, flush, dev)
     prof = batch_profile(Bt, [i["b"] for i in insts], P0.iters)
     Bt.close()
@@ -527,6 +528,7 @@ def bench_ct_batch(G, dev, flush, count=64):
     torch.cuda.empty_cache()
     out = batch_report(ms, reps, P0.iters, count, make_ct2d(instance=42, A=A0), 42, G, dev, flush)
     out["kernels"] = prof
+    out["autotuned"] = tuned
     out["workload"] = ("ct2d: 512x512, 180 angles x 725 bins, CSR FP32 (nnz %d), grad2d L, 2%% noise, "
                        "lambda_i = 10^(-4+3i/63), sparse-sign s=600 zeta=8, 150 iterations, FP32, 64 RHS" % len(A0.col))
     return out
@@ -555,8 +557,9 @@ def bench_dynct_batch(G, dev, flush):
                           x_true=_dev_tensor(P.x_true, torch.float32, dev)))
     P0 = probs[0]
     Bt = G.Batch(insts, P0.sketch.s, P0.sketch.seed, max_iters=P0.iters, n_refine=P0.n_refine, precision="fp32",
-                 zeta=P0.sketch.zeta)
+                 zeta=P0.sketch.zeta, autotune=True)
     groups = Bt.layout()[0]
+    tuned = [Bt.config(g) for g in range(groups)]
     ms, reps = time_batch(Bt, [i["b"] for i in insts], P0.iters, flush, dev)
     prof = batch_profile(Bt, [i["b"] for i in insts], P0.iters)
     Bt.close()
@@ -566,6 +569,7 @@ def bench_dynct_batch(G, dev, flush):
                        flush)
     out["groups"] = groups
     out["kernels"] = prof
+    out["autotuned"] = tuned
     out["workload"] = ("dynct: 128x128 x F frames, F in {8,16,24,32} x 4 instances, 30 angles/frame x 185 bins, "
                        "space-time L, 1% noise, sparse-sign s=800 zeta=8, 200 iterations, FP32 + 3 refinement steps")
     return out

@@ -49,7 +49,7 @@ enum { SGKS_OP_DENSE = 1, SGKS_OP_CSR = 2, SGKS_OP_CONV2D = 3 };
 enum { SGKS_REG_FD1 = 1, SGKS_REG_GRAD2D = 2, SGKS_REG_LAPLACE2D = 3, SGKS_REG_SPACETIME = 4 };
 enum { SGKS_SKETCH_SPARSE_SIGN = 0, SGKS_SKETCH_GAUSSIAN = 1, SGKS_SKETCH_SRTT = 2 };
 enum { SGKS_PREC_FP64 = 0, SGKS_PREC_FP32 = 1, SGKS_PREC_FP32X = 2 };
-enum { SGKS_FLAG_GLOBAL_SMALL = 1, SGKS_FLAG_RECORD = 2, SGKS_FLAG_GKS = 4 };
+enum { SGKS_FLAG_GLOBAL_SMALL = 1, SGKS_FLAG_RECORD = 2, SGKS_FLAG_GKS = 4, SGKS_FLAG_AUTOTUNE = 8 };
 
 /* Forward operator A (m x n).
  *  SGKS_OP_CSR:    row_ptr[m+1], col[nnz] (int32, 0-based), val[nnz] of val_dtype.  Optional
@@ -121,7 +121,12 @@ typedef struct sgks_options {
                              thin QR factors of A V_k and L V_k updated by CGS2 (eq. updqr with
                              S = I), projected problem eq. projected_withQR.  The sketch options
                              are ignored; needs n_refine = 0, FP64 or FP32, ell + max_iters <=
-                             1024; sgks_solve's tol applies the relative-change test of eq. RC [0] */
+                             1024; sgks_solve's tol applies the relative-change test of eq. RC.
+                             bit 3 (SGKS_FLAG_AUTOTUNE, batches only): after the setup, time the
+                             candidate tile choices of each group on its own data and keep the
+                             fastest (bulk-copy slice 8 or 16 KB; lanes per CSR row of A and A^T);
+                             results are cached per shape for the process.  Without it the
+                             defaults are used (16 KB, 8, 8) and results are reproducible [0] */
     const double* gauss_SA; /* Gaussian sketch only: S_A, sketch_rows x m, row-major, FP64, device */
     const double* gauss_SL; /* Gaussian sketch only: S_L, sketch_rows x p, row-major, FP64, device */
     const void* x_true;     /* optional, n values of the solver precision: enables RRE records    */
@@ -361,6 +366,10 @@ int sgks_batch_layout(sgks_batch* h, int32_t* group_of, int32_t* group_size);
  * alone and class 8 the sketch gather. */
 #define SGKS_BATCH_PROFILE_CLASSES 9
 int sgks_batch_profile_steps(sgks_batch* h, int32_t iters, double* ms_out, int64_t* count_out);
+
+/* Description of the tile configuration of group `group` chosen by SGKS_FLAG_AUTOTUNE ("" when
+ * the group was not tuned).  Owned by the handle. */
+const char* sgks_batch_config(const sgks_batch* h, int32_t group);
 
 /* Last error of h, or of the last failed sgks_batch_create when h is NULL. */
 const char* sgks_batch_last_error(const sgks_batch* h);

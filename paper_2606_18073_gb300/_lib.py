@@ -97,6 +97,7 @@ _SIGNATURES = {
     "sgks_batch_layout": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "sgks_batch_profile_steps": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "sgks_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "sgks_batch_config": (C.c_char_p, [C.c_void_p, C.c_int32]),
     "sgks_batch_destroy": (None, [C.c_void_p]),
     "sgks_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "sgks_set_lambda": (C.c_int, [C.c_void_p, C.c_double]),
@@ -110,6 +111,7 @@ PROFILE_CLASS_NAMES = ["gradient_append", "sketch_column", "qr_append", "stacked
 SGKS_FLAG_GLOBAL_SMALL = 1
 SGKS_FLAG_RECORD = 2
 SGKS_FLAG_GKS = 4
+SGKS_FLAG_AUTOTUNE = 8
 SGKS_BATCH_PROFILE_CLASSES = 9
 BATCH_PROFILE_CLASS_NAMES = ["gradient_append", "apply_column", "qr_append", "stacked_solve", "combine_refine",
                              "gradient_refine", "refine_solve", "combine", "sketch_gather"]

@@ -146,22 +146,22 @@ struct RowLanes {
     int nl, NL;
 };
 
-// lanes of a work item: NL = min(32 / igw, 8) lanes per (row, instance group), igw instance
-// groups per pass, RPW = 32 / (igw * NL) rows per warp; lane = (r * igw + ig) * NL + nl
-template <int VV>
-__device__ __forceinline__ int rl_rpw(int B) {
+// lanes of a work item: NL = min(32 / igw, nlmax) lanes per (row, instance group), igw instance
+// groups per pass, RPW = 32 / (igw * NL) rows per warp; lane = (r * igw + ig) * NL + nl.  nlmax (a
+// power of two) is a tuning parameter: more lanes per row for long rows, more rows per warp for
+// short ones.
+__host__ __device__ inline int rl_nl(int B, int VV, int nlmax) {
     const int IG = B / VV, igw = IG < 32 ? IG : 32;
-    const int NL = (32 / igw) < 8 ? 32 / igw : 8;
-    return 32 / (igw * NL);
+    return (32 / igw) < nlmax ? 32 / igw : nlmax;
 }
 
 template <int VV>
-__device__ __forceinline__ RowLanes row_lanes(int64_t item, int64_t rows, int B) {
+__device__ __forceinline__ RowLanes row_lanes(int64_t item, int64_t rows, int B, int nlmax) {
     const int IG = B / VV;
     const int igw = IG < 32 ? IG : 32;   // instance groups per pass
     const int NP = IG / igw;
     RowLanes r;
-    r.NL = (32 / igw) < 8 ? 32 / igw : 8;
+    r.NL = rl_nl(B, VV, nlmax);
     const int RPW = 32 / (igw * r.NL);
     const int lane = lane_id();
     const int64_t rg = item / NP;
@@ -174,10 +174,9 @@ __device__ __forceinline__ RowLanes row_lanes(int64_t item, int64_t rows, int B)
     return r;
 }
 
-__host__ __device__ inline int64_t rl_items(int64_t rows, int B, int VV) {
+__host__ __device__ inline int64_t rl_items(int64_t rows, int B, int VV, int nlmax) {
     const int IG = B / VV, igw = IG < 32 ? IG : 32;
-    const int NL = (32 / igw) < 8 ? 32 / igw : 8;
-    const int RPW = 32 / (igw * NL);
+    const int RPW = 32 / (igw * rl_nl(B, VV, nlmax));
     return (rows + RPW - 1) / RPW * (IG / igw);
 }
 
@@ -213,9 +212,9 @@ __device__ __forceinline__ void csr_row_vec(const int32_t* __restrict__ rp, cons
 template <typename T, typename V, int VV>
 __global__ void __launch_bounds__(kThreads) kb_csr_apply(BDims D, DevA<T, V> A, BBulk<T> X, BSmall S) {
     const int B = D.B;
-    const int64_t items = rl_items(D.m, B, VV);
+    const int64_t items = rl_items(D.m, B, VV, D.nl_a);
     for (int64_t wi = (int64_t)blockIdx.x * kWarps + warp_id(); wi < items; wi += (int64_t)gridDim.x * kWarps) {
-        const RowLanes rl = row_lanes<VV>(wi, D.m, B);
+        const RowLanes rl = row_lanes<VV>(wi, D.m, B, D.nl_a);
         int dv[VV];
         bool live[VV], same = true, any = false;
         const T* xb[VV];
@@ -244,9 +243,9 @@ template <typename T, typename V, int VV>
 __global__ void __launch_bounds__(kThreads) kb_csr_gradient(BDims D, DevA<T, V> A, DevL L, BBulk<T> X, BSmall S,
                                                             T* out) {
     const int B = D.B;
-    const int64_t items = rl_items(D.n, B, VV);
+    const int64_t items = rl_items(D.n, B, VV, D.nl_t);
     for (int64_t wi = (int64_t)blockIdx.x * kWarps + warp_id(); wi < items; wi += (int64_t)gridDim.x * kWarps) {
-        const RowLanes rl = row_lanes<VV>(wi, D.n, B);
+        const RowLanes rl = row_lanes<VV>(wi, D.n, B, D.nl_t);
         bool live[VV], any = false;
         T* dst[VV];
 #pragma unroll
@@ -513,12 +512,10 @@ __global__ void __launch_bounds__(kThreads, 4) kb_combine(BDims D, BBulk<T> X, B
 // (row, instance) pairs as the register form, and sums the columns in the same order.
 // 16 KB column slices in a 4-stage ring: measured on GB300 at 5.6 - 6.7 TB/s for 16 - 64 instances,
 // against 4.4 - 4.9 TB/s for 8 KB slices in 6 stages and 2.5 - 3.5 TB/s for 4 KB slices.
-template <typename T>
-__host__ __device__ constexpr int slice_of() { return 16384 / (int)sizeof(T); }
 
-template <typename T, int NS>
+template <typename T, int NS, int SB>
 __global__ void __launch_bounds__(kThreads) kb_combine_tma(BDims D, BBulk<T> X, BSmall S, int mode) {
-    constexpr int kSlice = slice_of<T>();
+    constexpr int kSlice = SB / (int)sizeof(T);   // values per column slice
     constexpr int RPT = kSlice / kThreads;       // slice positions per thread
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* stg = reinterpret_cast<T*>(smem_raw);     // [NS][kSlice]
@@ -915,7 +912,7 @@ constexpr int vec_width() { return 16 / (int)sizeof(T); }
 template <typename T, typename V, int VV>
 static cudaError_t csr_apply_vv(const BDims& D, const DevA<T, V>& A, const BBulk<T>& X, const BSmall& S,
                                 cudaStream_t st) {
-    const int64_t items = rl_items(D.m, D.B, VV);
+    const int64_t items = rl_items(D.m, D.B, VV, D.nl_a);
     kb_csr_apply<T, V, VV><<<wgrid(items), kThreads, 0, st>>>(D, A, X, S);
     return cudaGetLastError();
 }
@@ -923,7 +920,7 @@ static cudaError_t csr_apply_vv(const BDims& D, const DevA<T, V>& A, const BBulk
 template <typename T, typename V, int VV>
 static cudaError_t csr_gradient_vv(const BDims& D, const DevA<T, V>& A, const DevL& L, const BBulk<T>& X,
                                    const BSmall& S, T* out, cudaStream_t st) {
-    const int64_t items = rl_items(D.n, D.B, VV);
+    const int64_t items = rl_items(D.n, D.B, VV, D.nl_t);
     kb_csr_gradient<T, V, VV><<<wgrid(items), kThreads, 0, st>>>(D, A, L, X, S, out);
     return cudaGetLastError();
 }
@@ -951,22 +948,29 @@ cudaError_t launchb_sketch_gather(const BDims& D, const BBulk<T>& X, const Sketc
     return cudaGetLastError();
 }
 
-constexpr int kCombStages = 4;
+// ring configurations of the bulk-copy combine: 16 KB slices in 4 stages or 8 KB slices in 6
+static int comb_stages(int slice_kb) { return slice_kb == 8 ? 6 : 4; }
 
-size_t batch_combine_tma_smem(size_t elem) {
-    return (size_t)kCombStages * 16384 + (size_t)kYStage * elem;
+size_t batch_combine_tma_smem(size_t elem, int slice_kb) {
+    return (size_t)comb_stages(slice_kb) * slice_kb * 1024 + (size_t)kYStage * elem;
 }
 
-int batch_combine_tiles(int64_t n, int64_t m, int B, bool tma, size_t elem) {
-    const int64_t TR = tma ? (int64_t)(16384 / elem) / B : (int64_t)kCombRows * (kThreads / B);
+int batch_combine_tiles(int64_t n, int64_t m, int B, bool tma, size_t elem, int slice_kb) {
+    const int64_t TR = tma ? (int64_t)(slice_kb * 1024 / elem) / B : (int64_t)kCombRows * (kThreads / B);
     return (int)std::min<int64_t>((n + TR - 1) / TR + (m + TR - 1) / TR, 1 << 30);
+}
+
+int batch_combine_grid(const BDims& D, size_t elem) {
+    const int per_sm = D.tma ? (int)std::max<size_t>(1, (227 * 1024) / (batch_combine_tma_smem(elem, D.slice_kb) + 8192))
+                             : 4;
+    return std::min(batch_combine_tiles(D.n, D.m, D.B, D.tma, elem, D.slice_kb), 152 * per_sm);
 }
 
 template <typename T>
 cudaError_t launchb_combine(const BDims& D, const BBulk<T>& X, const BSmall& S, int mode, cudaStream_t st) {
     if (D.tma) {
-        const size_t smem = batch_combine_tma_smem(sizeof(T));
-        auto k = kb_combine_tma<T, kCombStages>;
+        const size_t smem = batch_combine_tma_smem(sizeof(T), D.slice_kb);
+        auto k = D.slice_kb == 8 ? kb_combine_tma<T, 6, 8192> : kb_combine_tma<T, 4, 16384>;
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k<<<D.nb_combine, kThreads, smem, st>>>(D, X, S, mode);

@@ -11,6 +11,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -44,11 +46,34 @@ struct GroupBase {
     int n_refine = 0;
     PtrPack bp{}, xtp{};
     bool has_xt = false;
+    int64_t nnz = 0;            // nonzeros of a CSR operator (tuner key)
     virtual ~GroupBase() {}
     virtual cudaError_t setup() = 0;
     virtual cudaError_t step() = 0;
     virtual cudaError_t copy_x(const PtrPack& out, cudaStream_t s) = 0;
+    virtual cudaError_t tune() = 0;
+    std::string tuned;   // the configuration the tuner chose (for sgks_batch_tuning)
 };
+
+// Autotuner cache: one entry per (operator shape, nonzeros, group size, precision).
+struct TuneKey {
+    int64_t m, n, p, nnz;
+    int B, elem, kind;
+    bool operator<(const TuneKey& o) const {
+        if (m != o.m) return m < o.m;
+        if (n != o.n) return n < o.n;
+        if (p != o.p) return p < o.p;
+        if (nnz != o.nnz) return nnz < o.nnz;
+        if (B != o.B) return B < o.B;
+        if (elem != o.elem) return elem < o.elem;
+        return kind < o.kind;
+    }
+};
+struct TuneVal {
+    int slice_kb, nl_a, nl_t;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
 
 // one launcher call: counted, and timed with an event pair when profiling
 template <typename F>
@@ -154,6 +179,82 @@ struct Group : GroupBase {
         for (int r = 0; r < n_refine && e == cudaSuccess; ++r) e = refine();
         RUNC(BK_COMBINE, 1, launchb_combine<T>(D, X, S, 1, st));
         return e;
+    }
+
+    // Times each candidate on the group's own data (after its setup) with CUDA events, 3 runs
+    // after a warm-up, and keeps the fastest: the bulk-copy combine's slice (8 or 16 KB) and the
+    // lanes per CSR row for A and A^T (1 .. 32).  The kernels only rewrite state that the next
+    // iteration recomputes from the same inputs.  Results are cached per shape and group size.
+    cudaError_t tune() override {
+        const TuneKey key{D.m, D.n, D.p, A.kind == SGKS_OP_CSR ? nnz : 0, D.B, (int)sizeof(T), A.kind};
+        {
+            std::lock_guard<std::mutex> g(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                D.slice_kb = it->second.slice_kb;
+                D.nl_a = it->second.nl_a;
+                D.nl_t = it->second.nl_t;
+                D.nb_combine = batch_combine_grid(D, sizeof(T));
+                tuned = "cached";
+                return cudaSuccess;
+            }
+        }
+        cudaEvent_t e0, e1;
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        if (e != cudaSuccess) return e;
+        auto time_it = [&](auto&& launch) -> float {
+            float best = 1e30f;
+            for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
+                cudaEventRecord(e0, st);
+                e = launch();
+                cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (r > 0 && ms < best) best = ms;
+            }
+            return best;
+        };
+        std::string log;
+        if (D.tma) {
+            float best = 1e30f;
+            int pick = D.slice_kb;
+            for (int kb : {16, 8}) {
+                D.slice_kb = kb;
+                D.nb_combine = batch_combine_grid(D, sizeof(T));
+                const float t = time_it([&] { return launchb_combine<T>(D, X, S, 0, st); });
+                log += " combine/" + std::to_string(kb) + "KB=" + std::to_string(t);
+                if (t < best) { best = t; pick = kb; }
+            }
+            D.slice_kb = pick;
+            D.nb_combine = batch_combine_grid(D, sizeof(T));
+        }
+        if (A.kind == SGKS_OP_CSR) {
+            for (int which = 0; which < 2; ++which) {
+                int* field = which == 0 ? &D.nl_a : &D.nl_t;
+                float best = 1e30f;
+                int pick = *field;
+                for (int nl : {1, 2, 4, 8, 16, 32}) {
+                    *field = nl;
+                    const float t = time_it([&] {
+                        return which == 0 ? launchb_apply_column<T, V>(D, A, L, X, S, st)
+                                          : launchb_gradient<T, V>(D, A, L, X, S, nullptr, st);
+                    });
+                    log += std::string(which == 0 ? " A/" : " At/") + std::to_string(nl) + "=" + std::to_string(t);
+                    if (t < best) { best = t; pick = nl; }
+                }
+                *field = pick;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (e != cudaSuccess) return e;
+        tuned = "slice " + std::to_string(D.slice_kb) + " KB, lanes/row A " + std::to_string(D.nl_a) + ", A^T " +
+                std::to_string(D.nl_t) + " (ms:" + log + ")";
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune_cache[key] = TuneVal{D.slice_kb, D.nl_a, D.nl_t};
+        return cudaSuccess;
     }
 
     cudaError_t copy_x(const PtrPack& out, cudaStream_t s) override {
@@ -280,6 +381,7 @@ int build_groups(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const st
         G->A = A;
         G->L = L;
         G->SK = SK;
+        G->nnz = op->kind == SGKS_OP_CSR ? op->nnz : 0;
         G->n_refine = o.n_refine;
         G->has_xt = x_true != nullptr;
         for (int i = 0; i < B; ++i) {
@@ -298,10 +400,15 @@ int build_groups(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const st
         D.sketch_scale = 1.0 / sqrt((double)o.zeta);
         // the bulk-copy combine needs every column start of W and AW on a 16-byte boundary
         D.tma = ((size_t)D.n * B * sizeof(T)) % 16 == 0 && ((size_t)D.m * B * sizeof(T)) % 16 == 0;
-        {
-            const int per_sm = D.tma ? (int)std::max<size_t>(1, (227 * 1024) / (batch_combine_tma_smem(sizeof(T)) + 8192))
-                                     : 4;
-            D.nb_combine = std::min(batch_combine_tiles(D.n, D.m, B, D.tma, sizeof(T)), 152 * per_sm);
+        D.slice_kb = 16;
+        D.nl_a = 8;
+        D.nl_t = 8;
+        D.nb_combine = batch_combine_grid(D, sizeof(T));
+        int nb_comb_max = D.nb_combine;
+        if (D.tma) {   // the tuner may pick 8 KB slices: size the partials for the larger grid
+            BDims D8 = D;
+            D8.slice_kb = 8;
+            nb_comb_max = std::max(nb_comb_max, batch_combine_grid(D8, sizeof(T)));
         }
         const int64_t rtiles = (D.n + 1024 / B - 1) / (1024 / B);
         {   // enough CTAs to fill every SM at the residency the refinement's shared memory allows
@@ -351,7 +458,7 @@ int build_groups(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const st
         BA(S.partL, (size_t)B * s);
         BA(S.Sb, (size_t)B * s);
         BA(S.gpart, (size_t)B * (D.nb_refine / 8) * dmax);
-        BA(S.kapart, (size_t)D.nb_combine * B * 3);
+        BA(S.kapart, (size_t)nb_comb_max * B * 3);
         BA(S.y, (size_t)B * dmax);
         BA(S.lam, B);
         BA(S.rc_hist, (size_t)B * o.max_iters);
@@ -458,6 +565,8 @@ int sgks_batch_create(sgks_batch** hp, int32_t count, const sgks_op* A, const sg
         return bfail(nullptr, SGKS_ERR_INVALID, "batches support SGKS_PREC_FP64 and SGKS_PREC_FP32");
     if (o.sketch_kind != SGKS_SKETCH_SPARSE_SIGN)
         return bfail(nullptr, SGKS_ERR_INVALID, "batches support the sparse-sign sketch only");
+    if (o.flags & (SGKS_FLAG_GKS | SGKS_FLAG_RECORD | SGKS_FLAG_GLOBAL_SMALL))
+        return bfail(nullptr, SGKS_ERR_INVALID, "batches take SGKS_FLAG_AUTOTUNE only");
     o.x_true = nullptr;
     for (int i = 0; i < count; ++i) {
         std::string why;
@@ -539,6 +648,11 @@ int sgks_batch_create(sgks_batch** hp, int32_t count, const sgks_op* A, const sg
         e = cudaStreamSynchronize(h->st);   // operator preparation done before the group streams start
         if (e == cudaSuccess) e = for_groups(h, [](GroupBase* g) { return g->setup(); });
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        // tuning one group at a time, so that the timings do not overlap
+        for (size_t g = 0; g < h->groups.size() && e == cudaSuccess && (o.flags & SGKS_FLAG_AUTOTUNE); ++g) {
+            e = h->groups[g]->tune();
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->groups[g]->st);
+        }
         if (e != cudaSuccess) rc = bcuda_fail(h, e, "batch setup");
     }
     if (rc != SGKS_OK) {
@@ -703,6 +817,11 @@ int sgks_batch_profile_steps(sgks_batch* h, int32_t iters, double* ms_out, int64
         count_out[c] = p.count[c];
     }
     return SGKS_OK;
+}
+
+const char* sgks_batch_config(const sgks_batch* h, int32_t group) {
+    if (!h || group < 0 || group >= (int32_t)h->groups.size()) return "";
+    return h->groups[group]->tuned.c_str();
 }
 
 const char* sgks_batch_last_error(const sgks_batch* h) {

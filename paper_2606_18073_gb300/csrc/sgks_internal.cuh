@@ -595,6 +595,8 @@ struct BDims {
     int s, dmax, ell, max_iters;
     int nb_combine;           // CTAs of the combine kernel
     int tma;                  // 1: combine streams W through shared memory by bulk copies
+    int slice_kb;             // bulk-copy combine: column slice of 8 or 16 KB (tuned)
+    int nl_a, nl_t;           // CSR rows: lanes per row of A and of A^T (powers of two <= 32, tuned)
     int nb_refine;            // CTAs of kb_wtr (a multiple of 8: one cluster = 8 CTAs)
     int nb_setup;             // CTAs of the setup reductions
     double sketch_scale;      // 1/sqrt(zeta)
@@ -657,8 +659,10 @@ cudaError_t launchb_scatter_out(const T* in, const PtrPack& P, int64_t len, int 
 cudaError_t launchb_set_xt2(const BSmall& S, int B, cudaStream_t st);
 cudaError_t launchb_set_tol(DevScalars* sc, int B, double tol, cudaStream_t st);
 size_t batch_refine_smem(int dmax, int B, size_t elem);
-size_t batch_combine_tma_smem(size_t elem);
-int batch_combine_tiles(int64_t n, int64_t m, int B, bool tma, size_t elem);
+size_t batch_combine_tma_smem(size_t elem, int slice_kb);
+int batch_combine_tiles(int64_t n, int64_t m, int B, bool tma, size_t elem, int slice_kb);
+// CTAs of the combine for a configuration (residency from its shared memory)
+int batch_combine_grid(const BDims& D, size_t elem);
 
 // ------------------------------------------------------------------- reverse sweep (k_adjoint.cu)
 cudaError_t launchd_record_y(const DevScalars* sc, const double* y, double* yhist, int dmax, int offset, int rows,

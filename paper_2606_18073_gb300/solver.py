@@ -272,7 +272,8 @@ class Batch:
     """
 
     def __init__(self, instances, sketch_rows: int, seed: int = 0, *, max_iters: int = 100, ell: int = 3,
-                 n_refine: int = 0, precision: str = "fp64", zeta: int = 8, cgs_passes: int = 2, stream=None):
+                 n_refine: int = 0, precision: str = "fp64", zeta: int = 8, cgs_passes: int = 2, stream=None,
+                 autotune: bool = False):
         self._lib = L.load()
         self.precision = precision
         self.dtype = torch.float32 if precision in ("fp32", "fp32x") else torch.float64
@@ -298,6 +299,7 @@ class Batch:
         o.max_iters, o.ell, o.n_refine, o.zeta, o.cgs_passes = max_iters, ell, n_refine, zeta, cgs_passes
         o.precision = {"fp64": L.SGKS_PREC_FP64, "fp32": L.SGKS_PREC_FP32, "fp32x": L.SGKS_PREC_FP32X}[precision]
         o.sketch_kind = L.SGKS_SKETCH_SPARSE_SIGN
+        o.flags = L.SGKS_FLAG_AUTOTUNE if autotune else 0
         self.max_iters = max_iters
         dev = instances[0]["b"].device
         self.device = dev
@@ -367,6 +369,11 @@ class Batch:
         ms, cnt = (C.c_double * n)(), (C.c_int64 * n)()
         L.check_batch(self._lib.sgks_batch_profile_steps(self._h, int(iters), ms, cnt), self._h)
         return {L.BATCH_PROFILE_CLASS_NAMES[i]: dict(ms=ms[i], launches=cnt[i]) for i in range(n)}
+
+    def config(self, group: int = 0) -> str:
+        """The tile configuration the autotuner chose for a group ("" when not tuned)."""
+        c = self._lib.sgks_batch_config(self._h, int(group))
+        return c.decode() if c else ""
 
     def layout(self):
         g, sz = (C.c_int32 * self.count)(), (C.c_int32 * self.count)()

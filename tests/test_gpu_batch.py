@@ -269,3 +269,18 @@ def test_batch_invalid_arguments(G):
     with pytest.raises(G._lib.SGKSError) as ei:
         G.Batch(insts, 7, 0, max_iters=5, precision="fp64")      # s < ell + max_iters
     assert ei.value.code == G._lib.SGKS_ERR_INVALID
+
+
+def test_batch_autotune_keeps_parity_and_caches(G):
+    """SGKS_FLAG_AUTOTUNE times the tile candidates after the setup and keeps the fastest; the
+    iterates still match the oracle, and a second batch of the same shape reuses the choice."""
+    probs = ct_instances(4, iters=12)
+    Bt, xs = batch_iterates(G, probs, "fp64", 12, autotune=True)
+    cfg = Bt.config(0)
+    assert cfg.startswith("slice") or cfg == "cached", cfg
+    for P, x in zip(probs, xs):
+        check_instance(x, P, "fp64")
+    Bt.close()
+    B2 = make_batch(G, probs, "fp64", autotune=True)
+    assert B2.config(0) == "cached"
+    B2.close()
