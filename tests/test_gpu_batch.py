@@ -284,3 +284,20 @@ def test_batch_autotune_keeps_parity_and_caches(G):
     B2 = make_batch(G, probs, "fp64", autotune=True)
     assert B2.config(0) == "cached"
     B2.close()
+
+
+@pytest.mark.parametrize("count,prec,tol", [(33, "fp64", 1e-10), (128, "fp64", 1e-10), (64, "fp32", 1e-4)])
+def test_batch_large_groups(G, count, prec, tol):
+    """Wide groups: 32 + 1 and 128 instances in FP64 (two instance passes per warp at 128) and 64
+    in FP32; final iterate of every instance after 8 iterations against the oracle (at 8
+    iterations the method's floor is far below the bar)."""
+    A0 = small_problem("ct2d").A
+    rng = np.random.default_rng(11)
+    probs = [small_problem("ct2d", instance=int(i), A=A0, iters=8) for i in rng.integers(0, 64, size=count)]
+    share_operators(probs, s=80)
+    Bt = make_batch(G, probs, prec)
+    Bt.solve(8)
+    xs = Bt.x()
+    worst = max(rel(x.double().cpu().numpy(), O.sgks(P, iters=8)["x"]) for x, P in zip(xs, probs))
+    assert worst < tol, worst
+    Bt.close()
