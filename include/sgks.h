@@ -291,6 +291,25 @@ int64_t sgks_kernel_launches(void);
 #define SGKS_PROFILE_CLASSES 8
 int sgks_profile_steps(sgks_handle* h, int32_t iters, double* ms_out, int64_t* count_out, double* dsum_out);
 
+/* The same per-class totals measured inside a CUDA graph: `iters` iterations are captured into
+ * one graph with an event pair recorded as graph nodes around every kernel launch, the graph
+ * is launched once, and each launch's time is the elapsed time of its pair.  Launches then
+ * follow each other as in sgks_solve (no host round trip between kernels).  The iterations
+ * count against the basis capacity like sgks_step.  Returns SGKS_ERR_STATE after
+ * sgks_set_lambda without sgks_reset, SGKS_ERR_CUDA on a CUDA error. */
+int sgks_profile_graph(sgks_handle* h, int32_t iters, double* ms_out, int64_t* count_out, double* dsum_out);
+
+/* Average device time of one launch of a streaming kernel class in the handle's current state,
+ * without per-launch events: `reps` launches are captured back to back into one CUDA graph,
+ * which is launched once to warm up and once between two CUDA events on the handle's stream;
+ * *us_out = elapsed microseconds / reps.  Classes (as sgks_profile_steps): 0 gradient -> next
+ * basis column, 1 operator apply + sketch of the next column, 4 combine inside refinement,
+ * 5 refinement gradient + W^T r.  These kernels write only the not-yet-appended column d,
+ * scratch and the refinement's x, e and partials, which the next step recomputes, so the
+ * iteration state is unchanged.  SGKS_ERR_INVALID for another class, for reps < 1 and for the
+ * fp32x and GKS forms; SGKS_ERR_STATE after sgks_set_lambda without sgks_reset. */
+int sgks_time_class(sgks_handle* h, int32_t cls, int32_t reps, double* us_out);
+
 /* ---- differentiation ------------------------------------------------------------------- */
 /* Reverse-mode derivative of the solve: for the x_K that the iterations since the last setup
  * (sgks_create / sgks_reset) produced, and xbar = dl/dx_K (device, n values of the solver

@@ -104,6 +104,9 @@ _SIGNATURES = {
     "sgks_kernel_launches": (C.c_int64, []),
     "sgks_profile_steps": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                      C.POINTER(C.c_double)]),
+    "sgks_profile_graph": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_double)]),
+    "sgks_time_class": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
 }
 SGKS_PROFILE_CLASSES = 8
 PROFILE_CLASS_NAMES = ["gradient_append", "sketch_column", "qr_append", "stacked_solve", "combine_refine",

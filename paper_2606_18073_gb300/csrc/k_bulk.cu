@@ -8,6 +8,8 @@
 //   CTAs through distributed shared memory.
 //   Tiles of 256 rows: warp w computes rows [32w, 32w+32) of the tile (one row per lane for
 //   the stencil / convolution, one warp per row for CSR with the 32 rows done in turn).
+//   These are the generic forms; k_conv.cu holds the register-blocked convolution rows and the
+//   prefetching W^T r that replace them whenever the columns of W are 16-byte aligned.
 // k_combine (K4 + K5): x = W y (n rows) and e = (A W) y - b (m rows) in one launch; the stored
 //   A W columns replace a second pass over A (A (W y) = (A W) y).  In the final call of an
 //   iteration the kernel also forms ||x_k - x_{k-1}||^2, ||x_{k-1}||^2 (eq. RC) and
@@ -21,25 +23,6 @@ namespace sgks {
 
 constexpr int kGradCluster = 8;
 
-template <typename T, typename V, bool WARPA>
-__device__ __forceinline__ T grad_value(const DevA<T, V>& A, const DevL& L, const T* psf_s, const T* e, const T* x,
-                                        double lam, int64_t base, int64_t n) {
-    const int lane = lane_id();
-    const int64_t i = base + lane;
-    T adj = T(0);
-    if (WARPA) {
-        for (int r = 0; r < 32; ++r) {
-            const int64_t ii = base + r;
-            if (ii >= n) break;
-            const T v = at_row_warp(A, ii, e);
-            if (lane == r) adj = v;
-        }
-    } else if (i < n) {
-        adj = at_row_conv(A, psf_s, i, e);
-    }
-    if (i >= n) return T(0);
-    return adj + (T)lam * ltl_row<T>(L, i, x);
-}
 
 // Append variant: W[:, d] = r.
 template <typename T, typename V, bool WARPA>
@@ -140,6 +123,10 @@ template <typename T, typename V>
 cudaError_t launch_gradient(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B, const Small& S,
                             bool refine, cudaStream_t st) {
     const bool warpa = A.kind != SGKS_OP_CONV2D;
+    bool done = false;
+    cudaError_t e = refine ? launch_gradient_refine2<T, V>(D, A, L, B, S, st, &done)
+                           : launch_gradient_append_conv<T, V>(D, A, L, B, S, st, &done);
+    if (done || e != cudaSuccess) return e;
     if (!refine) {
         const int64_t tiles = (D.n + kThreads - 1) / kThreads;
         const int blocks = (int)(tiles < 8 * 152 ? tiles : 8 * 152);
@@ -171,84 +158,106 @@ cudaError_t launch_gradient(const Dims& D, const DevA<T, V>& A, const DevL& L, c
 // ------------------------------------------------------------------------------ combine
 // mode 0: refinement (x, e only); 1: end of an iteration (x, e, RC / RRE record);
 // 2: end of the setup (x, e, RRE_0).
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_combine(Dims D, Bulk<T> B, Small S, int mode) {
+// A thread owns VW consecutive rows (16-byte or 8-byte loads when the row counts are even) and
+// walks the columns kCombCols at a time: the loads of the next kCombCols columns are issued
+// before the current ones are multiplied, and columns past d read nothing (y is zero-padded).
+constexpr int kCombCols = 16;
+
+template <typename T, int VW>
+__device__ __forceinline__ void ld_rows(const T* p, T (&v)[VW]) {
+    if constexpr (VW == 1) {
+        v[0] = __ldcg(p);
+    } else if constexpr (sizeof(T) == 4) {
+        const float2 q = __ldcg(reinterpret_cast<const float2*>(p));
+        v[0] = q.x;
+        v[1] = q.y;
+    } else {
+        const double2 q = __ldcg(reinterpret_cast<const double2*>(p));
+        v[0] = q.x;
+        v[1] = q.y;
+    }
+}
+
+template <typename T, int VW>
+__global__ void __launch_bounds__(kThreads) k_combine(Dims D, Bulk<T> B, Small S, int mode, int nbx) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* ys = reinterpret_cast<T*>(smem_raw);                       // [dmax]
+    T* ys = reinterpret_cast<T*>(smem_raw);                       // [dmax + kCombCols], zero from d on
     __shared__ double red[3][kWarps];
     __shared__ int am_last;
     DevScalars* sc = S.sc;
     if (sc->stop) return;
     const int d = sc->d;
-    for (int j = threadIdx.x; j < d; j += kThreads) ys[j] = (T)S.y[j];
-    __syncthreads();
-    T q0 = T(0), q1 = T(0), q2 = T(0);   // per-element statistics in the solver precision
+    for (int j = threadIdx.x; j < D.dmax + kCombCols; j += kThreads) ys[j] = j < d ? (T)S.y[j] : T(0);
     const int tid = threadIdx.x;
-    if ((int)blockIdx.x < D.nbX) {
-        const int64_t i = (int64_t)blockIdx.x * kThreads + tid;
-        if (i < D.n) {
-            const T* w = B.W + i;
-            // eight columns per step: eight independent loads in flight per thread
-            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0), a4 = T(0), a5 = T(0), a6 = T(0), a7 = T(0);
-            int j = 0;
-            for (; j + 7 < d; j += 8) {
-                const T w0 = w[(size_t)j * D.n], w1 = w[(size_t)(j + 1) * D.n], w2 = w[(size_t)(j + 2) * D.n],
-                        w3 = w[(size_t)(j + 3) * D.n], w4 = w[(size_t)(j + 4) * D.n], w5 = w[(size_t)(j + 5) * D.n],
-                        w6 = w[(size_t)(j + 6) * D.n], w7 = w[(size_t)(j + 7) * D.n];
-                a0 += w0 * ys[j];
-                a1 += w1 * ys[j + 1];
-                a2 += w2 * ys[j + 2];
-                a3 += w3 * ys[j + 3];
-                a4 += w4 * ys[j + 4];
-                a5 += w5 * ys[j + 5];
-                a6 += w6 * ys[j + 6];
-                a7 += w7 * ys[j + 7];
-            }
-            for (; j < d; ++j) a0 += w[(size_t)j * D.n] * ys[j];
-            a0 += a4;
-            a1 += a5;
-            a2 += a6;
-            a3 += a7;
-            const T xv = (a0 + a1) + (a2 + a3);
-            B.x[i] = xv;
-            if (mode >= 1) {
-                const T old = B.xs[i];
-                const T df = xv - old;
-                q0 = df * df;
-                q1 = old * old;
-                if (B.xtrue) {
-                    const T er = xv - B.xtrue[i];
-                    q2 = er * er;
-                }
-                B.xs[i] = xv;
+    const bool isx = (int)blockIdx.x < nbx;
+    const int64_t rows = isx ? D.n : D.m;
+    const int64_t i0 = ((int64_t)(isx ? (int)blockIdx.x : (int)blockIdx.x - nbx) * kThreads + tid) * VW;
+    const bool act = i0 < rows;
+    const T* w = (isx ? B.W : B.AW) + (act ? i0 : 0);
+    T t[kCombCols][VW];
+    auto load = [&](int j) {
+#pragma unroll
+        for (int c = 0; c < kCombCols; ++c) {
+            if (act && j + c < d) {
+                ld_rows<T, VW>(w + (size_t)(j + c) * rows, t[c]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < VW; ++v) t[c][v] = T(0);
             }
         }
-    } else {
-        const int64_t i = (int64_t)(blockIdx.x - D.nbX) * kThreads + tid;
-        if (i < D.m) {
-            const T* w = B.AW + i;
-            // eight columns per step: eight independent loads in flight per thread
-            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0), a4 = T(0), a5 = T(0), a6 = T(0), a7 = T(0);
-            int j = 0;
-            for (; j + 7 < d; j += 8) {
-                const T w0 = w[(size_t)j * D.m], w1 = w[(size_t)(j + 1) * D.m], w2 = w[(size_t)(j + 2) * D.m],
-                        w3 = w[(size_t)(j + 3) * D.m], w4 = w[(size_t)(j + 4) * D.m], w5 = w[(size_t)(j + 5) * D.m],
-                        w6 = w[(size_t)(j + 6) * D.m], w7 = w[(size_t)(j + 7) * D.m];
-                a0 += w0 * ys[j];
-                a1 += w1 * ys[j + 1];
-                a2 += w2 * ys[j + 2];
-                a3 += w3 * ys[j + 3];
-                a4 += w4 * ys[j + 4];
-                a5 += w5 * ys[j + 5];
-                a6 += w6 * ys[j + 6];
-                a7 += w7 * ys[j + 7];
+    };
+    load(0);
+    __syncthreads();
+    // eight partial sums per row (column j into sum j mod 8), combined pairwise at the end: the
+    // unnormalised columns of W make x = W y a sum with cancellation, and short FP32 chains keep
+    // its rounding error at the level of the eight-way split
+    T part[8][VW];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int v = 0; v < VW; ++v) part[k][v] = T(0);
+    for (int j = 0; j < d; j += kCombCols) {
+        T cur[kCombCols][VW];
+#pragma unroll
+        for (int c = 0; c < kCombCols; ++c)
+#pragma unroll
+            for (int v = 0; v < VW; ++v) cur[c][v] = t[c][v];
+        if (j + kCombCols < d) load(j + kCombCols);
+#pragma unroll
+        for (int c = 0; c < kCombCols; ++c) {
+            const T yv = ys[j + c];
+#pragma unroll
+            for (int v = 0; v < VW; ++v) part[c % 8][v] += cur[c][v] * yv;
+        }
+    }
+    T acc[VW];
+#pragma unroll
+    for (int v = 0; v < VW; ++v)
+        acc[v] = ((part[0][v] + part[4][v]) + (part[1][v] + part[5][v])) +
+                 ((part[2][v] + part[6][v]) + (part[3][v] + part[7][v]));
+    T q0 = T(0), q1 = T(0), q2 = T(0);   // per-element statistics in the solver precision
+    if (act) {
+        if (isx) {
+#pragma unroll
+            for (int v = 0; v < VW; ++v) {
+                const int64_t i = i0 + v;
+                const T xv = acc[v];
+                B.x[i] = xv;
+                if (mode >= 1) {
+                    const T old = B.xs[i];
+                    const T df = xv - old;
+                    q0 += df * df;
+                    q1 += old * old;
+                    if (B.xtrue) {
+                        const T er = xv - B.xtrue[i];
+                        q2 += er * er;
+                    }
+                    B.xs[i] = xv;
+                }
             }
-            for (; j < d; ++j) a0 += w[(size_t)j * D.m] * ys[j];
-            a0 += a4;
-            a1 += a5;
-            a2 += a6;
-            a3 += a7;
-            B.e[i] = ((a0 + a1) + (a2 + a3)) - B.b[i];
+        } else {
+#pragma unroll
+            for (int v = 0; v < VW; ++v) B.e[i0 + v] = acc[v] - B.b[i0 + v];
         }
     }
     if (mode == 0) return;
@@ -302,14 +311,26 @@ __global__ void __launch_bounds__(kThreads) k_combine(Dims D, Bulk<T> B, Small S
     }
 }
 
+template <typename T, int VW>
+static cudaError_t combine_vw(const Dims& D, const Bulk<T>& B, const Small& S, int mode, cudaStream_t st) {
+    const size_t smem = (size_t)(D.dmax + kCombCols) * sizeof(T);
+    auto k = k_combine<T, VW>;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    carveout_once((const void*)k);
+    const int64_t per = (int64_t)kThreads * VW;
+    const int nbx = (int)((D.n + per - 1) / per), nbe = (int)((D.m + per - 1) / per);
+    k<<<nbx + nbe, kThreads, smem, st>>>(D, B, S, mode, nbx);
+    return cudaGetLastError();
+}
+
+// Two rows per thread when both row counts are even (aligned 2-wide loads of every column).
 template <typename T>
 cudaError_t launch_combine(const Dims& D, const Bulk<T>& B, const Small& S, int mode, cudaStream_t st) {
-    const size_t smem = (size_t)D.dmax * sizeof(T);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_combine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    carveout_once((const void*)k_combine<T>);
-    k_combine<T><<<D.nbX + D.nbE, kThreads, smem, st>>>(D, B, S, mode);
-    return cudaGetLastError();
+    if (D.n % 2 == 0 && D.m % 2 == 0) return combine_vw<T, 2>(D, B, S, mode, st);
+    return combine_vw<T, 1>(D, B, S, mode, st);
 }
 
 #define SGKS_INST_BULK(T, V)                                                                          \

@@ -146,6 +146,9 @@ static int apply_blocks(const Dims& D) {
 template <typename T, typename V>
 static cudaError_t launch_apply_column(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
                                        const Small& S, cudaStream_t st) {
+    bool done = false;
+    const cudaError_t e = launch_apply_column_conv<T, V>(D, A, L, B, S, st, &done);
+    if (done || e != cudaSuccess) return e;
     if (A.kind == SGKS_OP_CONV2D) {
         carveout_once((const void*)k_apply_column<T, V, false>);
         k_apply_column<T, V, false><<<apply_blocks(D), kThreads, 0, st>>>(D, A, L, B, S);

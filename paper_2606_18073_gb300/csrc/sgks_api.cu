@@ -39,6 +39,10 @@ struct Profiler {
     double ms[PK_COUNT] = {0};
     int64_t count[PK_COUNT] = {0};
     double bytes_d[PK_COUNT] = {0};   // sum over launches of the subspace size d (for byte models)
+    // graph mode: an event pair around every launch, recorded as nodes of one captured graph
+    bool graph = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<int> cls_of;          // kernel class of event pair k
 };
 
 struct EngineBase {
@@ -49,6 +53,17 @@ struct EngineBase {
     cudaError_t timed(int cls, int dcount, F&& f) {
         g_launches.fetch_add(cls == PK_SKETCH ? 2 : 1);
         if (!prof) return f();
+        if (prof->graph) {
+            const size_t k = prof->cls_of.size();
+            if (2 * k + 2 > prof->pool.size()) return cudaErrorInvalidValue;
+            cudaError_t e = cudaEventRecordWithFlags(prof->pool[2 * k], pst, cudaEventRecordExternal);
+            if (e == cudaSuccess) e = f();
+            if (e == cudaSuccess) e = cudaEventRecordWithFlags(prof->pool[2 * k + 1], pst, cudaEventRecordExternal);
+            prof->cls_of.push_back(cls);
+            prof->count[cls] += 1;
+            prof->bytes_d[cls] += dcount;
+            return e;
+        }
         cudaEventRecord(prof->ev[0], pst);
         cudaError_t e = f();
         cudaEventRecord(prof->ev[1], pst);
@@ -64,6 +79,8 @@ struct EngineBase {
     virtual ~EngineBase() {}
     virtual cudaError_t setup(const void* b) = 0;
     virtual cudaError_t step() = 0;
+    // one launch of a streaming kernel class in the current state (sgks_time_class)
+    virtual cudaError_t launch_class(int) { return cudaErrorNotSupported; }
     virtual cudaError_t apply(int which, const void* in, void* out) = 0;
     virtual void* buffer(int which, size_t* elem, int64_t* rows, int64_t* cols_ld) = 0;
     // copy x_k in the public precision (FP64 for the FP64 form, FP32 otherwise)
@@ -185,6 +202,16 @@ struct Engine : EngineBase {
                 return D.fast_small ? launch_refine_solve2(D, S, st) : launch_refine_solve(D, S, st);
             });
         return e;
+    }
+
+    cudaError_t launch_class(int cls) override {
+        switch (cls) {
+            case PK_GRAD_APPEND: return launch_gradient<T, V>(D, A, L, B, S, false, st);
+            case PK_SKETCH: return sketch();
+            case PK_COMBINE_REFINE: return launch_combine<T>(D, B, S, 0, st);
+            case PK_GRAD_REFINE: return launch_gradient<T, V>(D, A, L, B, S, true, st);
+            default: return cudaErrorNotSupported;
+        }
     }
 
     cudaError_t step() override {
@@ -411,6 +438,7 @@ struct Engine : EngineBase {
 // so the step graph is replayed as for sGKS.
 template <typename T, typename V>
 struct EngineGKS : Engine<T, V> {
+    cudaError_t launch_class(int) override { return cudaErrorNotSupported; }
     using Base = Engine<T, V>;
     using Base::D; using Base::S; using Base::A; using Base::L; using Base::B; using Base::st;
     using Base::host_d; using Base::timed; using Base::b_own;
@@ -501,6 +529,7 @@ struct EngineGKS : Engine<T, V> {
 
 // fp32x: FP32 storage of W, compensated arithmetic for A W, x, e and the gradient (k_fp32x.cu).
 struct EngineX : Engine<float, float> {
+    cudaError_t launch_class(int) override { return cudaErrorNotSupported; }
     BulkX X{};
 
     cudaError_t sketchx() {
@@ -767,6 +796,12 @@ int prepare_operator(const sgks_op* op, DevA<T, V>& A, std::vector<void*>& alloc
         A.ny = op->ny;
         A.kh = op->kh;
         A.kw = op->kw;
+        A.kfast = 0;
+        if (e == cudaSuccess && op->kh == op->kw && op->kh <= kFastK && op->nx % 4 == 0) {
+            e = cudaMemcpyAsync(A.tk, pp, sizeof(T) * op->kh * op->kw, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess) A.kfast = op->kh;
+        }
     }
 #undef AL
     if (e == cudaErrorMemoryAllocation) {
@@ -1330,6 +1365,94 @@ int sgks_profile_steps(sgks_handle* h, int32_t iters, double* ms_out, int64_t* c
         count_out[c] = p.count[c];
         dsum_out[c] = p.bytes_d[c];
     }
+    return SGKS_OK;
+}
+
+int sgks_profile_graph(sgks_handle* h, int32_t iters, double* ms_out, int64_t* count_out, double* dsum_out) {
+    if (!h || iters < 0 || !ms_out || !count_out || !dsum_out) return SGKS_ERR_INVALID;
+    if (h->need_reset) return fail(h, SGKS_ERR_STATE, "lambda changed: call sgks_reset first");
+    if (iters > h->max_iters - h->steps_since_setup) return fail(h, SGKS_ERR_STATE, "iters exceeds capacity");
+    Profiler p;
+    p.graph = true;
+    p.pool.resize((size_t)2 * 32 * (iters + 1));
+    cudaError_t e = cudaSuccess;
+    size_t made = 0;
+    for (; made < p.pool.size() && e == cudaSuccess; ++made) e = cudaEventCreate(&p.pool[made]);
+    if (e != cudaSuccess) --made;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    join_in(h);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        h->eng->prof = &p;
+        cudaError_t e2 = cudaSuccess;
+        for (int k = 0; k < iters && e2 == cudaSuccess; ++k) e2 = h->eng->step();
+        h->eng->prof = nullptr;
+        e = cudaStreamEndCapture(h->st, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e == cudaSuccess) {
+        h->steps_since_setup += iters;
+        for (size_t k = 0; k < p.cls_of.size(); ++k) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, p.pool[2 * k], p.pool[2 * k + 1]);
+            p.ms[p.cls_of[k]] += t;
+        }
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    for (size_t k = 0; k < made; ++k) cudaEventDestroy(p.pool[k]);
+    join_out(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sgks_profile_graph");
+    for (int c = 0; c < PK_COUNT; ++c) {
+        ms_out[c] = p.ms[c];
+        count_out[c] = p.count[c];
+        dsum_out[c] = p.bytes_d[c];
+    }
+    return SGKS_OK;
+}
+
+int sgks_time_class(sgks_handle* h, int32_t cls, int32_t reps, double* us_out) {
+    if (!h || reps < 1 || !us_out) return SGKS_ERR_INVALID;
+    if (cls != PK_GRAD_APPEND && cls != PK_SKETCH && cls != PK_COMBINE_REFINE && cls != PK_GRAD_REFINE)
+        return fail(h, SGKS_ERR_INVALID, "kernel class cannot be timed in place");
+    if (h->need_reset) return fail(h, SGKS_ERR_STATE, "lambda changed: call sgks_reset first");
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    join_in(h);
+    const int64_t l0 = g_launches.load();
+    cudaError_t e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        cudaError_t e2 = cudaSuccess;
+        for (int r = 0; r < reps && e2 == cudaSuccess; ++r) e2 = h->eng->launch_class(cls);
+        e = cudaStreamEndCapture(h->st, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    g_launches.store(l0);
+    const bool unsupported = e == cudaErrorNotSupported;
+    if (unsupported) cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, h->st);   // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, h->st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    join_out(h);
+    if (unsupported) return fail(h, SGKS_ERR_INVALID, "kernel class not timed for this form");
+    if (e != cudaSuccess) return cuda_fail(h, e, "sgks_time_class");
+    *us_out = 1e3 * (double)ms / reps;
     return SGKS_OK;
 }
 

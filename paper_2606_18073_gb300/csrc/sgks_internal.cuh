@@ -22,6 +22,7 @@ constexpr int kMaxS = 2048;             // largest sketch size supported
 constexpr int kMaxZeta = 16;
 constexpr int kClusterMax = 16;         // CTAs of the small FP64 cluster kernels
 constexpr int kMaxDraws = 256;
+constexpr int kFastK = 9;               // largest psf side of the register-blocked conv kernels
 
 // ------------------------------------------------------------------------------ status
 enum DevStatus : int { ST_OK = 0, ST_BREAKDOWN = 1, ST_STOPPED = 2, ST_NONFINITE = 3, ST_SKETCH = 4,
@@ -56,6 +57,11 @@ struct DevA {
     int64_t ld;
     int nx, ny, kh, kw;  // conv2d
     const T* psf;
+    // conv2d with a square K x K psf, K <= kFastK, and nx % 4 == 0: the tap values as launch
+    // parameters (read from the constant bank by the register-blocked kernels of k_conv.cu);
+    // kfast = K, or 0 when those kernels do not apply.
+    int kfast;
+    T tk[kFastK * kFastK];
 };
 
 struct DevL {
@@ -394,6 +400,7 @@ __device__ __forceinline__ T ltl_row_x(const DevL& L, int64_t i, const X& x) {
     }
 }
 
+
 // (L^T v)_i for v of length p (used by sgks_apply only).
 template <typename T, typename X>
 __device__ __forceinline__ T lt_row_x(const DevL& L, int64_t i, const X& v) {
@@ -453,6 +460,29 @@ __device__ __forceinline__ T ltl_row(const DevL& L, int64_t i, const T* __restri
 template <typename T>
 __device__ __forceinline__ T lt_row(const DevL& L, int64_t i, const T* __restrict__ v) {
     return lt_row_x<T>(L, i, Unit<T>{v});
+}
+
+// Rows [base, base + 32) of the gradient r = A^T e + lam L^T L x (eq. gradient), lane l holding
+// row base + l (0 beyond n): warp-cooperative A^T rows (CSR, dense) or one convolution row per
+// lane (psf_s: the taps in shared memory).
+template <typename T, typename V, bool WARPA>
+__device__ __forceinline__ T grad_value(const DevA<T, V>& A, const DevL& L, const T* psf_s, const T* e, const T* x,
+                                        double lam, int64_t base, int64_t n) {
+    const int lane = lane_id();
+    const int64_t i = base + lane;
+    T adj = T(0);
+    if (WARPA) {
+        for (int r = 0; r < 32; ++r) {
+            const int64_t ii = base + r;
+            if (ii >= n) break;
+            const T v = at_row_warp(A, ii, e);
+            if (lane == r) adj = v;
+        }
+    } else if (i < n) {
+        adj = at_row_conv(A, psf_s, i, e);
+    }
+    if (i >= n) return T(0);
+    return adj + (T)lam * ltl_row<T>(L, i, x);
 }
 
 // ------------------------------------------------------------------------- workspace
@@ -541,6 +571,17 @@ cudaError_t launchx_sketch_gather_col(const Dims& D, const float2* AW, const dou
 template <typename T, typename V>
 cudaError_t launch_gradient(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
                             const Small& S, bool refine, cudaStream_t st);
+// Register-blocked convolution and fused refinement kernels (k_conv.cu); *done = false when the
+// operator or the sizes are outside their scope (the caller then launches the generic kernel).
+template <typename T, typename V>
+cudaError_t launch_gradient_append_conv(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
+                                        const Small& S, cudaStream_t st, bool* done);
+template <typename T, typename V>
+cudaError_t launch_apply_column_conv(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
+                                     const Small& S, cudaStream_t st, bool* done);
+template <typename T, typename V>
+cudaError_t launch_gradient_refine2(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
+                                    const Small& S, cudaStream_t st, bool* done);
 template <typename T>
 cudaError_t launch_combine(const Dims& D, const Bulk<T>& B, const Small& S, int mode, cudaStream_t st);
 cudaError_t launch_append_solve(const Dims& D, const Small& S, cudaStream_t st);

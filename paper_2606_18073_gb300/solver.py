@@ -226,12 +226,24 @@ class Solver:
         L.check(self._lib.sgks_apply(self._h, which, _ptr(x), _ptr(out)), self._h)
         return out
 
-    def profile(self, iters: int):
-        """Per-kernel CUDA-event timing of `iters` eager iterations (sgks_profile_steps)."""
+    def profile(self, iters: int, graph: bool = False):
+        """Per-kernel CUDA-event timing of `iters` iterations: eager launches with a synchronised
+        event pair around each (sgks_profile_steps), or, with graph=True, event pairs recorded as
+        nodes of one captured graph (sgks_profile_graph), kernels back to back as in solve()."""
         n = L.SGKS_PROFILE_CLASSES
         ms, cnt, ds = (C.c_double * n)(), (C.c_int64 * n)(), (C.c_double * n)()
-        L.check(self._lib.sgks_profile_steps(self._h, int(iters), ms, cnt, ds), self._h)
+        fn = self._lib.sgks_profile_graph if graph else self._lib.sgks_profile_steps
+        L.check(fn(self._h, int(iters), ms, cnt, ds), self._h)
         return {L.PROFILE_CLASS_NAMES[i]: dict(ms=ms[i], launches=cnt[i], dsum=ds[i]) for i in range(n)}
+
+    def time_class(self, name: str, reps: int = 100) -> float:
+        """Microseconds per launch of one streaming kernel class ("gradient_append",
+        "sketch_column", "combine_refine", "gradient_refine") in the current state, from `reps`
+        back-to-back launches in one CUDA graph (sgks_time_class); the iteration state is unchanged."""
+        us = C.c_double()
+        cls = L.PROFILE_CLASS_NAMES.index(name)
+        L.check(self._lib.sgks_time_class(self._h, cls, int(reps), C.byref(us)), self._h)
+        return us.value
 
     def set_lambda(self, lam: float):
         """Change lambda; the basis is discarded, so call reset(b) before the next step/solve."""

@@ -210,6 +210,63 @@ def test_fp32x_iterates_match_oracle(G, kind):
     S.close()
 
 
+def asymmetric_psf(k, seed):
+    """A k x k psf with no symmetry, so that a transposed or unrotated kernel shows in the iterates."""
+    rng = np.random.default_rng(seed)
+    h = rng.random((k, k)) + np.linspace(0.0, 1.0, k * k).reshape(k, k)
+    return (h / h.sum()).astype(np.float32)
+
+
+@pytest.mark.parametrize("k,nx,ny", [(3, 24, 20), (5, 100, 12), (9, 36, 24), (11, 24, 20), (9, 30, 18)])
+def test_conv_rows_asymmetric_psf(G, k, nx, ny):
+    """Iterates of the deblurring problem with an asymmetric psf, FP64 with one refinement step
+    (gradient append, apply and fused refinement gradient all run), through the generic
+    convolution rows (any psf side, any image width)."""
+    P = small_problem("deblur2d", nx=nx, ny=ny, psf=asymmetric_psf(k, k), iters=12, precision="fp64",
+                      n_refine=1)
+    ref = O.sgks(P, record_x=True)
+    S, xs = gpu_iterates(G, P, P.iters, "fp64")
+    check_iterates(xs, ref["xs"], floor_curve(P, P.iters, EPS["fp64"])[0], TOL64, FACTOR64)
+    S.close()
+
+
+def check_fp32_early(P, xs, ref):
+    """FP32 iterates within TOL32 of the FP64 oracle while the method's FP32 floor is below 1e-6."""
+    fl = floor_curve(P, P.iters, EPS["fp32"])[0]
+    errs = [rel(a, b) for a, b in zip(xs, ref["xs"])]
+    early = [i for i in range(len(errs)) if max(fl[:i + 1]) < 1e-6]
+    assert early and max(errs[i] for i in early) < TOL32, errs
+
+
+@pytest.mark.parametrize("k,nx,ny", [(3, 24, 20), (5, 100, 12), (7, 28, 16), (9, 40, 28), (11, 24, 20),
+                                     (9, 30, 18)])
+def test_conv_rows_asymmetric_psf_fp32(G, k, nx, ny):
+    """The FP32 form with an asymmetric psf and two refinement steps: square sides 3 to 9 on images
+    of width % 4 == 0 take the register-blocked rows (A^T as correlation, A with the rotated
+    taps); side 11 and width 30 the generic rows."""
+    P = small_problem("deblur2d", nx=nx, ny=ny, psf=asymmetric_psf(k, k + 1), iters=10, precision="fp32",
+                      n_refine=2)
+    ref = O.sgks(P, record_x=True)
+    S, xs = gpu_iterates(G, P, P.iters, "fp32")
+    check_fp32_early(P, xs, ref)
+    S.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_conv_rows_many_tiles(G, precision):
+    """A 256 x 400 image (102,400 rows): the refinement gradient's CTAs take several 256-row tiles
+    and the append / apply kernels many 512-row tiles; asymmetric 9 x 9 psf."""
+    P = small_problem("deblur2d", nx=256, ny=400, psf=asymmetric_psf(9, 3), iters=6, s=120, precision=precision,
+                      n_refine=1)
+    ref = O.sgks(P, record_x=True)
+    S, xs = gpu_iterates(G, P, P.iters, precision)
+    if precision == "fp64":
+        check_iterates(xs, ref["xs"], floor_curve(P, P.iters, EPS["fp64"])[0], TOL64, FACTOR64)
+    else:
+        check_fp32_early(P, xs, ref)
+    S.close()
+
+
 def test_ragged_sizes_and_extreme_sketch(G):
     """n not a multiple of the 32-row slab or 256-row tile; zeta = 1 and zeta = s."""
     for nx, ny, s, zeta in ((37, 23, 64, 1), (19, 41, 40, 16), (33, 7, 30, 8)):
@@ -250,6 +307,55 @@ def test_solve_graph_replay_equals_steps_and_is_deterministic(G):
     assert np.array_equal(S3.x().cpu().numpy(), S4.x().cpu().numpy())
     for s in (S1, S2, S3, S4):
         s.close()
+
+
+def test_profile_graph_matches_steps(G):
+    """sgks_profile_graph runs the same kernels as sgks_step (the iterate is bit-identical) and
+    counts the same launches per class as the eager profile."""
+    P = small_problem("deblur2d")
+    kw = G.device_inputs(P, "fp32")
+    S1 = G.Solver(**kw)
+    pe = S1.profile(6)
+    S2 = G.Solver(**kw)
+    pg = S2.profile(6, graph=True)
+    S3 = G.Solver(**kw)
+    for _ in range(6):
+        S3.step()
+    assert np.array_equal(S2.x().cpu().numpy(), S3.x().cpu().numpy())
+    assert np.array_equal(S1.x().cpu().numpy(), S3.x().cpu().numpy())
+    for k in pe:
+        assert pe[k]["launches"] == pg[k]["launches"] and pe[k]["dsum"] == pg[k]["dsum"], k
+        assert (pg[k]["ms"] > 0) == (pg[k]["launches"] > 0), k
+    with pytest.raises(G._lib.SGKSError):
+        S2.profile(10 ** 6, graph=True)
+    for S in (S1, S2, S3):
+        S.close()
+
+
+def test_time_class_leaves_state(G):
+    """sgks_time_class relaunches streaming kernels in place: the iteration that follows is the
+    same, bit for bit, as without the timing; other classes and the fp32x form are rejected."""
+    P = small_problem("deblur2d")
+    kw = G.device_inputs(P, "fp32")
+    S1, S2 = G.Solver(**kw), G.Solver(**kw)
+    for _ in range(4):
+        S1.step()
+        S2.step()
+    for k in ("gradient_append", "sketch_column", "combine_refine", "gradient_refine"):
+        assert S1.time_class(k, 5) > 0.0
+    for _ in range(3):
+        S1.step()
+        S2.step()
+    assert np.array_equal(S1.x().cpu().numpy(), S2.x().cpu().numpy())
+    with pytest.raises(G._lib.SGKSError) as ei:
+        S1.time_class("qr_append", 5)
+    assert ei.value.code == G._lib.SGKS_ERR_INVALID
+    S3 = G.Solver(**G.device_inputs(P, "fp32x"))
+    with pytest.raises(G._lib.SGKSError) as ei:
+        S3.time_class("gradient_refine", 5)
+    assert ei.value.code == G._lib.SGKS_ERR_INVALID
+    for S in (S1, S2, S3):
+        S.close()
 
 
 def test_rc_tolerance_stops(G):
@@ -311,7 +417,7 @@ def test_nonfinite_rhs_is_reported(G):
 
 
 # ----------------------------------------------------------------------- full-size configs
-# BASELINE sizes and iteration counts, launched as bench.py launches them (sgks_solve replays of
+# Full workload sizes and iteration counts of the five test problems, launched as bench.py launches them (sgks_solve replays of
 # the captured step graph after sgks_reset); iterates are read after every replay.
 
 def gpu_graph_iterates(G, P, precision, **over):

@@ -310,7 +310,8 @@ def make_problem(name: str, **kw) -> Problem:
 def small_problem(kind: str, seed: int = 0, **kw) -> Problem:
     """Reduced sizes of each operator family, for tests that the oracle finishes in seconds.
 
-    kinds: deconv1d (n = 48), deblur2d (24 x 20 image, 5x5 PSF), ct2d (32 x 32, 24 angles),
+    kinds: deconv1d (n = 48), deblur2d (24 x 20 image, 5x5 PSF; nx, ny, psf may be given),
+    ct2d (32 x 32, 24 angles),
     seismic2d (32 x 32), dynct (16 x 16 x 4 frames), laplace (conv A with Laplacian L).
     """
     if kind == "deconv1d":
@@ -320,7 +321,8 @@ def small_problem(kind: str, seed: int = 0, **kw) -> Problem:
     if kind == "deblur2d":
         rng = _rng(seed, 0)
         nx, ny = kw.pop("nx", 24), kw.pop("ny", 20)
-        A = conv2d_op(nx, ny, gaussian_psf(5, 1.2))
+        psf = kw.pop("psf", None)
+        A = conv2d_op(nx, ny, gaussian_psf(5, 1.2) if psf is None else psf)
         L = RegDesc("grad2d", nx=nx, ny=ny)
         x = phantom_rectangles(nx, ny, 5, rng)
         b = _noisy(A, x, 0.01, _rng(seed, 1))
