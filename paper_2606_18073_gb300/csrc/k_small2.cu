@@ -55,6 +55,41 @@ __device__ __forceinline__ double block_sum2(double v, double* scratch) {
     return scratch[kThreads];
 }
 
+// Copies `total` values with the CTA's threads: each thread issues up to eight loads (ld(idx))
+// before it stores them (st(idx, value)).
+template <typename Ld, typename St>
+__device__ __forceinline__ void stage_batched(int total, Ld ld, St st) {
+    constexpr int U = 8;
+    for (int base = threadIdx.x; base < total; base += U * kThreads) {
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * kThreads;
+            v[u] = idx < total ? ld(idx) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * kThreads;
+            if (idx < total) st(idx, v[u]);
+        }
+    }
+}
+
+// sum over k = k0, k0 + step, ... < k1 of a[k sa] b[k sb] with four interleaved accumulators,
+// so that the dependent FP64 FMA chain is a quarter as long
+__device__ __forceinline__ double dot4s(const double* a, int sa, const double* b, int sb, int k0, int k1, int step) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int k = k0;
+    for (; k + 3 * step < k1; k += 4 * step) {
+        s0 += a[k * sa] * b[k * sb];
+        s1 += a[(k + step) * sa] * b[(k + step) * sb];
+        s2 += a[(k + 2 * step) * sa] * b[(k + 2 * step) * sb];
+        s3 += a[(k + 3 * step) * sa] * b[(k + 3 * step) * sb];
+    }
+    for (; k < k1; k += step) s0 += a[k * sa] * b[k * sb];
+    return (s0 + s1) + (s2 + s3);
+}
+
 constexpr int kGrp = 4;   // lanes that share one dot product or one row update
 
 // Sum over the 4 lanes of an aligned lane group (fixed xor tree, result in every lane).
@@ -117,20 +152,35 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads)
     const double* part = fac ? S.partL : S.partA;
     const int np = fac ? D.npL : D.npA;
 
-    // stage the Q slice (coalesced along rows of each column)
-    for (int idx = tid; idx < dq * nr; idx += kThreads) {
+    // own row of the new sketched column (one sketch partial) and of S_A b: loaded before the
+    // staging below so that both wait on one round trip (nr <= kMaxS / 8 = kThreads)
+    const bool own = tid < nr;
+    double vpre = 0.0, sbpre = 0.0;
+    if (own) {
+        if (np == 1) vpre = __ldcg(part + i0 + tid);
+        if (fac == 0) sbpre = __ldcg(S.Sb + i0 + tid);
+    }
+    // stage the Q slice (coalesced along rows of each column), eight loads per thread in flight
+    // before their stores: the global source could alias the shared destination as far as the
+    // compiler knows, so a plain copy loop would wait for each load in turn
+    stage_batched(dq * nr, [&](int idx) {
         const int j = idx / nr, li = idx - j * nr;
-        Qs[(size_t)j * RP + li] = Q[(size_t)j * s + i0 + li];
+        return __ldcg(Q + (size_t)j * s + i0 + li);
+    }, [&](int idx, double val) {
+        const int j = idx / nr, li = idx - j * nr;
+        Qs[(size_t)j * RP + li] = val;
+    });
+    if (np == 1) {
+        if (own) v[tid] = vpre * D.sketch_scale;
+    } else {   // several sketch partials: warp per row, lanes over the partials
+        for (int li = warp; li < nr; li += kWarps) {
+            double a = 0.0;
+            for (int b = lane; b < np; b += 32) a += part[(size_t)b * s + i0 + li];
+            a = warp_sum(a);
+            if (lane == 0) v[li] = a * D.sketch_scale;
+        }
     }
-    // sketch partials -> own rows of the new sketched column; warp per row, lanes over partials
-    for (int li = warp; li < nr; li += kWarps) {
-        double a = 0.0;
-        for (int b = lane; b < np; b += 32) a += part[(size_t)b * s + i0 + li];
-        a = warp_sum(a);
-        if (lane == 0) v[li] = a * D.sketch_scale;
-    }
-    if (fac == 0)
-        for (int li = tid; li < nr; li += kThreads) sb[li] = S.Sb[i0 + li];
+    if (fac == 0 && own) sb[tid] = sbpre;
     for (int j = tid; j < dq; j += kThreads) p[j] = 0.0;
     __syncthreads();
     if (warp == 0) {
@@ -149,8 +199,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads)
             const bool act = t < dq * kGrp;
             double a = 0.0;
             if (act) {
-                const double* q = Qs + (size_t)j * RP;
-                for (int li = gl; li < nr; li += kGrp) a += q[li] * v[li];
+                a = dot4s(Qs + (size_t)j * RP, 1, v, 1, gl, nr, kGrp);
             }
             a = group_sum(a);
             if (act && gl == 0) push<CS>(cl, cbuf + (size_t)rank * dm, j, a);
@@ -168,8 +217,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads)
             const int t = base + tid, li = t / kGrp;
             const bool act = t < nr * kGrp;
             double a = 0.0;
-            if (act)
-                for (int j = gl; j < dq; j += kGrp) a += Qs[(size_t)j * RP + li] * c[j];
+            if (act) a = dot4s(Qs + li, RP, c, 1, gl, dq, kGrp);
             a = group_sum(a);
             if (act && gl == 0) {
                 const double nv = v[li] - a;
@@ -267,19 +315,24 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads)
     double* scal = red + 4 * CS;                    // [8]
     double* scratch = scal + 8;                     // [kThreads + 1]
 
-    // stage the Q_T slice; column j is zero below row 2j+2
-    for (int idx = tid; idx < dq * nr; idx += kThreads) {
-        const int j = idx / nr, lr = idx - j * nr, row = r0 + lr;
-        Qs[(size_t)j * RP2 + lr] = row < 2 * j + 2 ? S.QT[(size_t)j * ldT + row] : 0.0;
-    }
-    // own rows of the new stacked column [p_A; sqrt(lam) p_L] in creation order
-    for (int lr = tid; lr < nr; lr += kThreads) {
+    // own rows of the new stacked column [p_A; sqrt(lam) p_L] in creation order, loaded before
+    // the staging of the Q_T slice (column j is zero below row 2j+2; loads batched as in
+    // k_qr_append) so that both wait on one round trip
+    auto new_row = [&](int lr) {
         const int row = r0 + lr, j = row >> 1;
-        double val;
-        if (j < dq) val = (row & 1) ? sl * S.RL[(size_t)dq * dm + j] : S.RA[(size_t)dq * dm + j];
-        else val = (row & 1) ? sl * rhoL : rhoA;
-        v[lr] = val;
-    }
+        if (j < dq) return (row & 1) ? sl * __ldcg(S.RL + (size_t)dq * dm + j) : __ldcg(S.RA + (size_t)dq * dm + j);
+        return (row & 1) ? sl * rhoL : rhoA;
+    };
+    const double vpre = tid < nr ? new_row(tid) : 0.0;
+    stage_batched(dq * nr, [&](int idx) {
+        const int j = idx / nr, lr = idx - j * nr, row = r0 + lr;
+        return row < 2 * j + 2 ? __ldcg(S.QT + (size_t)j * ldT + row) : 0.0;
+    }, [&](int idx, double val) {
+        const int j = idx / nr, lr = idx - j * nr;
+        Qs[(size_t)j * RP2 + lr] = val;
+    });
+    if (tid < nr) v[tid] = vpre;
+    for (int lr = tid + kThreads; lr < nr; lr += kThreads) v[lr] = new_row(lr);
     for (int j = tid; j < dq; j += kThreads) tau[j] = 0.0;
     __syncthreads();
     double rr = 0.0;
@@ -290,8 +343,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads)
             const bool act = t < dq * kGrp;
             double a = 0.0;
             if (act) {
-                const double* q = Qs + (size_t)j * RP2;
-                for (int lr = gl; lr < nr; lr += kGrp) a += q[lr] * v[lr];
+                a = dot4s(Qs + (size_t)j * RP2, 1, v, 1, gl, nr, kGrp);
             }
             a = group_sum(a);
             if (act && gl == 0) push<CS>(cl, cbuf + (size_t)rank * dm, j, a);
@@ -308,8 +360,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads)
             const int t = base + tid, lr = t / kGrp;
             const bool act = t < nr * kGrp;
             double a = 0.0;
-            if (act)
-                for (int j = gl; j < dq; j += kGrp) a += Qs[(size_t)j * RP2 + lr] * c[j];
+            if (act) a = dot4s(Qs + lr, RP2, c, 1, gl, dq, kGrp);
             a = group_sum(a);
             if (act && gl == 0) {
                 const double nv = v[lr] - a;
@@ -386,40 +437,10 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads)
     k_refine_solve2(Dims D, Small S0, const Small* __restrict__ Sarr, int npart) {
     cg::cluster_group cl = cg::this_cluster();
     const Small S = Sarr ? Sarr[blockIdx.x / CS] : S0;
-    const int rank = (int)cl.block_rank();
-    const int tid = threadIdx.x, lane = lane_id(), warp = warp_id();
-    const int gw = rank * kWarps + warp, GW = CS * kWarps;
-    const int dm = D.dmax;
     extern __shared__ __align__(16) double sm[];
-    double* g = sm;        // [dm]
-    double* h = g + dm;    // [dm]
     const DevScalars* sc = S.sc;
     if (sc->stop) return;
-    const int d = sc->d;
-    // g_j: warp per j over the cluster, lanes over the partials; pushed to every CTA
-    for (int j = gw; j < d; j += GW) {
-        double a = 0.0;
-        for (int b = lane; b < npart; b += 32) a += S.gpart[(size_t)b * dm + j];
-        a = warp_sum(a);
-        if (lane < CS) cl.map_shared_rank(g, lane)[j] = a;
-    }
-    cl.sync();
-    for (int i = gw; i < d; i += GW) {     // h = X^T g: column i of X (contiguous) with g[0..i]
-        const double* xc = S.X + (size_t)i * dm;
-        double a = 0.0;
-        for (int j = lane; j <= i; j += 32) a += xc[j] * g[j];
-        a = warp_sum(a);
-        if (lane < CS) cl.map_shared_rank(h, lane)[i] = a;
-    }
-    cl.sync();
-    for (int i = gw; i < d; i += GW) {     // y_i -= (X h)_i: row i of X (row-major copy)
-        const double* xr = S.Xr + (size_t)i * dm;
-        double a = 0.0;
-        for (int j = i + lane; j < d; j += 32) a += xr[j] * h[j];
-        a = warp_sum(a);
-        if (lane == 0) S.y[i] -= a;
-    }
-    (void)tid;
+    refine_solve_cluster<CS>(cl, D, S, sc->d, npart, sm, sm + D.dmax);
 }
 
 // ----------------------------------------------------------------------------- launchers

@@ -554,6 +554,42 @@ struct Dims {
     int max_iters;
 };
 
+// Refinement solve of the fast small path on one thread-block cluster of CS CTAs:
+// y -= X X^T g, X = T^{-1} of the stacked factor (G^{-1} = X X^T), g_j the fixed-order sum of the
+// npart refinement partials S.gpart[b][j].  g and h: dmax doubles of shared memory at the same
+// offset in every CTA of the cluster (the partial results are pushed through distributed
+// shared memory).  Warp per output, lanes over the sum, FP64 throughout.
+template <int CS>
+__device__ __forceinline__ void refine_solve_cluster(cg::cluster_group& cl, const Dims& D, const Small& S, int d,
+                                                     int npart, double* g, double* h) {
+    const int rank = (int)cl.block_rank();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gw = rank * (blockDim.x >> 5) + warp, GW = CS * (blockDim.x >> 5);
+    const int dm = D.dmax;
+    for (int j = gw; j < d; j += GW) {   // g_j: lanes over the partials, pushed to every CTA
+        double a = 0.0;
+        for (int b = lane; b < npart; b += 32) a += __ldcg(S.gpart + (size_t)b * dm + j);
+        a = warp_sum(a);
+        if (lane < CS) cl.map_shared_rank(g, lane)[j] = a;
+    }
+    cl.sync();
+    for (int i = gw; i < d; i += GW) {   // h = X^T g: column i of X (contiguous) with g[0..i]
+        const double* xc = S.X + (size_t)i * dm;
+        double a = 0.0;
+        for (int j = lane; j <= i; j += 32) a += xc[j] * g[j];
+        a = warp_sum(a);
+        if (lane < CS) cl.map_shared_rank(h, lane)[i] = a;
+    }
+    cl.sync();
+    for (int i = gw; i < d; i += GW) {   // y_i -= (X h)_i: row i of X (row-major copy)
+        const double* xr = S.Xr + (size_t)i * dm;
+        double a = 0.0;
+        for (int j = i + lane; j < d; j += 32) a += xr[j] * h[j];
+        a = warp_sum(a);
+        if (lane == 0) S.y[i] -= a;
+    }
+}
+
 template <typename T, typename V>
 cudaError_t launch_sketch_column(const Dims& D, const DevA<T, V>& A, const DevL& L, const Bulk<T>& B,
                                  const Small& S, const SketchCSR& SK, cudaStream_t st);
