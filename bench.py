@@ -504,6 +504,43 @@ def batch_profile(Bt, bs, iters):
                 "us_per_launch": 1e3 * v["ms"] / v["launches"]} for k, v in prof.items() if v["launches"]}
 
 
+def batch_roofline(prof, sizes, nnz, ell, iters, hbm):
+    """Achieved bandwidth of the batched streaming kernels at the solve's average subspace size.
+    sizes: (n_i, m_i) per instance; nnz: nonzeros of the CSR matrices the instances share
+    (counted once per pass).  combine: W and AW columns plus the vectors of every instance,
+    against HBM.  CSR passes: the matrix once plus the vectors written, against HBM; the
+    instance-vector gathers (nnz x B values per pass, served from L2) as a separate rate."""
+    d = ell + (iters - 1) / 2.0
+    B = len(sizes)
+    out = {"d_avg": d}
+    vec_n = sum(n for n, _ in sizes) * 4
+    vec_m = sum(m for _, m in sizes) * 4
+    defs = {
+        "combine": (d * (vec_n + vec_m) + 3 * vec_n + 2 * vec_m, 0),
+        "apply_column": (nnz * 8 + vec_n + vec_m, nnz * B * 4),
+        "gradient_append": (nnz * 8 + vec_m + 3 * vec_n, nnz * B * 4),
+    }
+    for k, (hb, gb) in defs.items():
+        v = prof.get(k)
+        if not v:
+            continue
+        t = v["us_per_launch"] * 1e-6
+        rec = {"alg_bytes_per_launch": hb, "gbps": hb / t / 1e9, "frac_of_hbm": hb / t / 1e9 / hbm}
+        if gb:
+            rec["gathered_bytes_per_launch"] = gb
+            rec["gather_gbps"] = gb / t / 1e9
+        out[k] = rec
+    return out
+
+
+def measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f).get("hbm_gbs", 6800.0))
+    except OSError:
+        return 6800.0
+
+
 def batch_report(ms, reps, iters, count, P64, ref_idx, G, dev, flush):
     """Instance-iterations/s of the batch next to plain FP64 GPU sGKS on instance ref_idx."""
     import numpy as np
@@ -546,7 +583,17 @@ def bench_ct_batch(G, dev, flush, count=64):
     torch.cuda.empty_cache()
     out = batch_report(ms, reps, P0.iters, count, make_ct2d(instance=42, A=A0), 42, G, dev, flush)
     out["kernels"] = prof
+    out["roofline"] = batch_roofline(prof, [(P.n, P.m) for P in probs], len(A0.col), 3, P0.iters, measured_hbm())
     out["autotuned"] = tuned
+    # the same instance alone in the FP32 form (no refinement), for the batch's gain
+    P1 = make_ct2d(instance=42, A=A0, precision="fp32")
+    P1.n_refine = 0
+    kw1 = G.device_inputs(P1, "fp32", device=dev)
+    S1 = G.Solver(**kw1)
+    t1, h1 = time_solve(G, S1, kw1["b"], P1.iters, flush, dev)
+    S1.close()
+    out["fp32_single"] = {"instance": 42, "iters_per_s": P1.iters / (t1 / 1e3), "ms_per_solve": t1,
+                          "final_rre": h1["rre_last"]}
     out["workload"] = ("ct2d: 512x512, 180 angles x 725 bins, CSR FP32 (nnz %d), grad2d L, 2%% noise, "
                        "lambda_i = 10^(-4+3i/63), sparse-sign s=600 zeta=8, 150 iterations, FP32, 64 RHS" % len(A0.col))
     return out
@@ -587,6 +634,9 @@ def bench_dynct_batch(G, dev, flush):
                        flush)
     out["groups"] = groups
     out["kernels"] = prof
+    # each group streams its own frame CSR (shared by its instances): matrix bytes once per F
+    nnz_groups = sum(len(A.col) for A in shared.values())
+    out["roofline"] = batch_roofline(prof, [(P.n, P.m) for P in probs], nnz_groups, 3, P0.iters, measured_hbm())
     out["autotuned"] = tuned
     out["workload"] = ("dynct: 128x128 x F frames, F in {8,16,24,32} x 4 instances, 30 angles/frame x 185 bins, "
                        "space-time L, 1% noise, sparse-sign s=800 zeta=8, 200 iterations, FP32 + 3 refinement steps")
