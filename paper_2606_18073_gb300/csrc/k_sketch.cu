@@ -63,11 +63,23 @@ __device__ __forceinline__ double as_double<float2>(float2 v) { return (double)v
 template <typename Acc, typename TV>
 __device__ __forceinline__ double gather_row(const uint32_t* __restrict__ idx, int b, int e, const TV* __restrict__ v,
                                              double* red) {
+    // eight entries per thread per round: their indices first, then the eight gathers, then the
+    // sum in entry order (an S_L row of the 256^2 problem has ~2,600 entries, ten per thread)
     Acc a = Acc(0);
-    for (int k = b + (int)threadIdx.x; k < e; k += kThreads) {
-        const uint32_t u = __ldg(idx + k);
-        const Acc val = (Acc)as_double(v[u & 0x7fffffffu]);
-        a += (u >> 31) ? -val : val;
+    for (int k0 = b + (int)threadIdx.x; k0 < e; k0 += 8 * kThreads) {
+        uint32_t u[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = k0 + q * kThreads;
+            u[q] = k < e ? __ldg(idx + k) : 0u;
+        }
+        Acc val[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            val[q] = k0 + q * kThreads < e ? (Acc)as_double(v[u[q] & 0x7fffffffu]) : Acc(0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (k0 + q * kThreads < e) a += (u[q] >> 31) ? -val[q] : val[q];
     }
     const double t = warp_sum_acc(a);
     if (lane_id() == 0) red[warp_id()] = t;
