@@ -39,6 +39,27 @@ __global__ void __launch_bounds__(kThreads) k_gradient_append(Dims D, DevA<T, V>
         for (int i = threadIdx.x; i < A.kh * A.kw; i += kThreads) psf_s[i] = A.psf[i];
     __syncthreads();
     T* out = B.W + (size_t)d * D.n;
+    if (WARPA) {
+        // rows of A^T one per warp, dealt round-robin over every warp of the grid (a row is a
+        // chain of dependent loads, so the rows are spread as widely as the grid allows); a warp
+        // collects 32 of its rows, lane t holding row i0 + t GW, and the lanes then add the
+        // L^T L term of their own rows together (one warp instruction for 32 rows: in FP64 an
+        // instruction costs the FP64 pipe the same whether one lane or 32 are active)
+        const int64_t GW = (int64_t)gridDim.x * kWarps;
+        const int lane = lane_id();
+        for (int64_t i0 = (int64_t)blockIdx.x * kWarps + warp_id(); i0 < D.n; i0 += 32 * GW) {
+            T adj = T(0);
+            for (int t = 0; t < 32; ++t) {
+                const int64_t i = i0 + t * GW;
+                if (i >= D.n) break;
+                const T v = at_row_warp(A, i, B.e);
+                if (lane == t) adj = v;
+            }
+            const int64_t my = i0 + lane * GW;
+            if (my < D.n) out[my] = adj + (T)D.lam * ltl_row<T>(L, my, B.x);
+        }
+        return;
+    }
     const int64_t ntiles = (D.n + kThreads - 1) / kThreads;
     for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
         const int64_t base = tl * kThreads + warp_id() * 32;
@@ -128,7 +149,7 @@ cudaError_t launch_gradient(const Dims& D, const DevA<T, V>& A, const DevL& L, c
                            : launch_gradient_append_conv<T, V>(D, A, L, B, S, st, &done);
     if (done || e != cudaSuccess) return e;
     if (!refine) {
-        const int64_t tiles = (D.n + kThreads - 1) / kThreads;
+        const int64_t tiles = warpa ? (D.n + kWarps - 1) / kWarps : (D.n + kThreads - 1) / kThreads;
         const int blocks = (int)(tiles < 8 * 152 ? tiles : 8 * 152);
         if (warpa) {
             carveout_once((const void*)k_gradient_append<T, V, true>);

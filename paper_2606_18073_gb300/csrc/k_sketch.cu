@@ -32,6 +32,18 @@ __global__ void __launch_bounds__(kThreads) k_apply_column(Dims D, DevA<T, V> A,
     const T* w = B.W + (size_t)d * D.n;
     T* u = B.AW + (size_t)d * D.m;
     const int lane = lane_id();
+    if (WARPA) {
+        // rows of A one per warp, dealt round-robin over every warp of the grid (a row is a chain
+        // of dependent loads); then the rows of L one per thread
+        const int64_t GW = (int64_t)gridDim.x * kWarps;
+        for (int64_t j = (int64_t)blockIdx.x * kWarps + warp_id(); j < D.m; j += GW) {
+            const T v = a_row_warp(A, j, w);
+            if (lane == 0) u[j] = v;
+        }
+        const int64_t GT = (int64_t)gridDim.x * kThreads;
+        for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < D.p; j += GT) B.tmp_p[j] = l_row<T>(L, j, w);
+        return;
+    }
     const int64_t slA = (D.m + 31) / 32, slL = (D.p + 31) / 32;
     for (int64_t sl = (int64_t)blockIdx.x * kWarps + warp_id(); sl < slA + slL; sl += (int64_t)gridDim.x * kWarps) {
         if (sl < slA) {
@@ -148,9 +160,13 @@ __global__ void __launch_bounds__(kThreads) k_dense_sketch(const double* __restr
 }
 
 // --------------------------------------------------------------------------- launchers
-static int apply_blocks(const Dims& D) {
+static int apply_blocks(const Dims& D, bool warpa = false) {
     const int64_t slabs = (D.m + 31) / 32 + (D.p + 31) / 32;
     int64_t blocks = (slabs + kWarps - 1) / kWarps;
+    if (warpa) {   // a warp per row of A, a thread per row of L
+        const int64_t ba = (D.m + kWarps - 1) / kWarps, bl = (D.p + kThreads - 1) / kThreads;
+        blocks = ba > bl ? ba : bl;
+    }
     if (blocks > 8 * 152) blocks = 8 * 152;
     return (int)(blocks < 1 ? 1 : blocks);
 }
@@ -167,7 +183,7 @@ static cudaError_t launch_apply_column(const Dims& D, const DevA<T, V>& A, const
     }
     else {
         carveout_once((const void*)k_apply_column<T, V, true>);
-        k_apply_column<T, V, true><<<apply_blocks(D), kThreads, 0, st>>>(D, A, L, B, S);
+        k_apply_column<T, V, true><<<apply_blocks(D, true), kThreads, 0, st>>>(D, A, L, B, S);
     }
     return cudaGetLastError();
 }
