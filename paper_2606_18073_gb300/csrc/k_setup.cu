@@ -39,6 +39,23 @@ __global__ void __launch_bounds__(kThreads) k_apply(DevA<T, V> A, DevL L, int wh
         for (int i = threadIdx.x; i < A.kh * A.kw; i += kThreads) psf_s[i] = A.psf[i];
     __syncthreads();
     const int lane = lane_id();
+    if (WARPA && (which == SGKS_APPLY_A || which == SGKS_APPLY_AT)) {
+        // rows one per warp, dealt round-robin over the grid; lane t keeps row i0 + t GW
+        const bool adj = which == SGKS_APPLY_AT;
+        const int64_t GW = (int64_t)gridDim.x * kWarps;
+        for (int64_t i0 = (int64_t)blockIdx.x * kWarps + warp_id(); i0 < rows; i0 += 32 * GW) {
+            T v = T(0);
+            for (int t = 0; t < 32; ++t) {
+                const int64_t ii = i0 + t * GW;
+                if (ii >= rows) break;
+                const T r = adj ? at_row_warp(A, ii, in) : a_row_warp(A, ii, in);
+                if (lane == t) v = r;
+            }
+            const int64_t my = i0 + lane * GW;
+            if (my < rows) out[my] = v;
+        }
+        return;
+    }
     const int64_t nslab = (rows + 31) / 32;
     for (int64_t sl = (int64_t)blockIdx.x * kWarps + warp_id(); sl < nslab; sl += (int64_t)gridDim.x * kWarps) {
         const int64_t base = sl * 32, i = base + lane;
@@ -73,8 +90,9 @@ cudaError_t launch_apply(const Dims& D, const DevA<T, V>& A, const DevL& L, int 
         case SGKS_APPLY_L: rows = D.p; break;
         default: rows = D.n; break;
     }
+    const bool warp_rows = A.kind != SGKS_OP_CONV2D && (which == SGKS_APPLY_A || which == SGKS_APPLY_AT);
     const int64_t slabs = (rows + 31) / 32;
-    int64_t blocks = (slabs + kWarps - 1) / kWarps;
+    int64_t blocks = warp_rows ? (rows + kWarps - 1) / kWarps : (slabs + kWarps - 1) / kWarps;
     if (blocks > 8 * 152) blocks = 8 * 152;
     if (blocks < 1) blocks = 1;
     if (A.kind == SGKS_OP_CONV2D) {
