@@ -504,12 +504,14 @@ def batch_profile(Bt, bs, iters):
                 "us_per_launch": 1e3 * v["ms"] / v["launches"]} for k, v in prof.items() if v["launches"]}
 
 
-def batch_roofline(prof, sizes, nnz, ell, iters, hbm):
+def batch_roofline(prof, sizes, nnz, ell, iters, hbm, groups=1):
     """Achieved bandwidth of the batched streaming kernels at the solve's average subspace size.
     sizes: (n_i, m_i) per instance; nnz: nonzeros of the CSR matrices the instances share
     (counted once per pass).  combine: W and AW columns plus the vectors of every instance,
     against HBM.  CSR passes: the matrix once plus the vectors written, against HBM; the
-    instance-vector gathers (nnz x B values per pass, served from L2) as a separate rate."""
+    instance-vector gathers (nnz x B values per pass, served from L2) as a separate rate.
+    groups: launches of a class per step (ragged batches run one launch per group), whose
+    times add up to the step's time for that class."""
     d = ell + (iters - 1) / 2.0
     B = len(sizes)
     out = {"d_avg": d}
@@ -524,10 +526,10 @@ def batch_roofline(prof, sizes, nnz, ell, iters, hbm):
         v = prof.get(k)
         if not v:
             continue
-        t = v["us_per_launch"] * 1e-6
-        rec = {"alg_bytes_per_launch": hb, "gbps": hb / t / 1e9, "frac_of_hbm": hb / t / 1e9 / hbm}
+        t = v["us_per_launch"] * groups * 1e-6
+        rec = {"alg_bytes_per_step": hb, "gbps": hb / t / 1e9, "frac_of_hbm": hb / t / 1e9 / hbm}
         if gb:
-            rec["gathered_bytes_per_launch"] = gb
+            rec["gathered_bytes_per_step"] = gb
             rec["gather_gbps"] = gb / t / 1e9
         out[k] = rec
     return out
@@ -636,7 +638,8 @@ def bench_dynct_batch(G, dev, flush):
     out["kernels"] = prof
     # each group streams its own frame CSR (shared by its instances): matrix bytes once per F
     nnz_groups = sum(len(A.col) for A in shared.values())
-    out["roofline"] = batch_roofline(prof, [(P.n, P.m) for P in probs], nnz_groups, 3, P0.iters, measured_hbm())
+    out["roofline"] = batch_roofline(prof, [(P.n, P.m) for P in probs], nnz_groups, 3, P0.iters, measured_hbm(),
+                                     groups=groups)
     out["autotuned"] = tuned
     out["workload"] = ("dynct: 128x128 x F frames, F in {8,16,24,32} x 4 instances, 30 angles/frame x 185 bins, "
                        "space-time L, 1% noise, sparse-sign s=800 zeta=8, 200 iterations, FP32 + 3 refinement steps")
