@@ -36,7 +36,7 @@ __device__ __forceinline__ T ba_row(const DevA<T, V>& A, const T* psf_s, int64_t
         for (int k = A.rp[j]; k < e; ++k) acc += (T)ldg(A.val + k) * ldg(x + (int64_t)ldg(A.ci + k) * B);
     } else if (A.kind == SGKS_OP_CONV2D) {
         const int nx = A.nx, ny = A.ny, kh = A.kh, kw = A.kw;
-        const int iy = (int)(j / nx), ix = (int)(j - (int64_t)iy * nx);
+        const int iy = (int)qdiv(j, nx), ix = (int)(j - (int64_t)iy * nx);
         for (int a = 0; a < kh; ++a) {
             const int yy = iy - a + kh / 2;
             if (yy < 0 || yy >= ny) continue;
@@ -61,7 +61,7 @@ __device__ __forceinline__ T bat_row(const DevA<T, V>& A, const T* psf_s, int64_
         for (int k = A.trp[i]; k < en; ++k) acc += (T)ldg(A.tval + k) * ldg(e + (int64_t)ldg(A.tci + k) * B);
     } else if (A.kind == SGKS_OP_CONV2D) {
         const int nx = A.nx, ny = A.ny, kh = A.kh, kw = A.kw;
-        const int iy = (int)(i / nx), ix = (int)(i - (int64_t)iy * nx);
+        const int iy = (int)qdiv(i, nx), ix = (int)(i - (int64_t)iy * nx);
         for (int a = 0; a < kh; ++a) {
             const int yy = iy + a - kh / 2;
             if (yy < 0 || yy >= ny) continue;
@@ -104,10 +104,10 @@ __global__ void __launch_bounds__(kThreads) kb_apply_column(BDims D, DevA<T, V> 
     const int64_t tot = (D.m + D.p) * B;
     for (int64_t t = t0 + (int64_t)blockIdx.x * kThreads + threadIdx.x; t < tot; t += gstride()) {
         if (t < D.m * B) {
-            const int64_t j = t / B;
+            const int64_t j = qdiv(t, B);
             X.AW[((size_t)d * D.m + j) * B + b] = ba_row(A, psf_s, j, w, B);
         } else {
-            const int64_t k = (t - D.m * B) / B;
+            const int64_t k = qdiv(t - D.m * B, B);
             X.tp[k * B + b] = l_row_x<T>(L, k, Strided<T>{w, B});
         }
     }
@@ -272,14 +272,16 @@ __global__ void __launch_bounds__(kThreads) kb_csr_gradient(BDims D, DevA<T, V> 
         for (int v = 0; v < VV; ++v) xb[v] = X.e + rl.b0 + v;
         T acc[VV];
         csr_row_vec<T, V, VV>(A.trp, A.tci, A.tval, rl, B, X.e + rl.b0, true, xb, acc);
-        if (rl.nl == 0)
+        if (rl.nl == 0 && any) {   // any live instance implies a valid row
+            // L^T L x for the lane's VV instances with one index decomposition of the row
+            const VecN<T, VV> lt = ltl_row_x<VecN<T, VV>>(L, rl.row, StridedVec<T, VV>{X.x + rl.b0, B});
 #pragma unroll
             for (int v = 0; v < VV; ++v) {
                 if (!live[v]) continue;
                 const int bb = rl.b0 + v;
-                dst[v][rl.row * B + bb] =
-                    acc[v] + (T)S.lam[bb] * ltl_row_x<T>(L, rl.row, Strided<T>{X.x + bb, B});
+                dst[v][rl.row * B + bb] = acc[v] + (T)S.lam[bb] * lt.v[v];
             }
+        }
     }
 }
 
@@ -716,7 +718,7 @@ __global__ void __launch_bounds__(kThreads) kb_gradient(BDims D, DevA<T, V> A, D
     }
     const T lam = (T)S.lam[b];
     for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < D.n * B; t += gstride()) {
-        const int64_t i = t / B;
+        const int64_t i = qdiv(t, B);
         const T adj = bat_row(A, psf_s, i, X.e + b, B);
         dst[i * B + b] = adj + lam * ltl_row_x<T>(L, i, Strided<T>{X.x + b, B});
     }

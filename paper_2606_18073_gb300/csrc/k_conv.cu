@@ -105,7 +105,7 @@ __device__ __forceinline__ void conv_stage(T* es, const T* __restrict__ v, int y
 // convolution (FLIP true) of the rows staged from image row y0 - K/2 on, with the taps of A.
 template <typename T, typename V, int K, bool FLIP>
 __device__ __forceinline__ void conv4(const T* es, const DevA<T, V>& A, int64_t i, int y0, int nx, T (&out)[4]) {
-    const int iy = (int)(i / nx), ix = (int)(i - (int64_t)iy * nx);
+    const int iy = (int)qdiv(i, nx), ix = (int)(i - (int64_t)iy * nx);
     const int SW = nx + 2 * kPad;
     const T* base = es + (iy - y0) * SW + ix;
     T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
@@ -143,7 +143,7 @@ __device__ __forceinline__ void gradient_tile(T* dst, T* es, const DevA<T, V>& A
     T lt[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) lt[u] = q < vr ? ltl_row<T>(L, r0 + q + u, x) : T(0);
-    const int y0 = (int)(r0 / nx), y1 = (int)((r0 + vr - 1) / nx);
+    const int y0 = (int)qdiv(r0, nx), y1 = (int)qdiv(r0 + vr - 1, nx);
     conv_stage<T, K>(es, e, y0, y1, nx, ny);
     __syncthreads();
     if (q < vr) {
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_column_conv(Dims D, DevA<T, 
         for (int64_t tl = blockIdx.x; tl < ntiles; tl += nbc) {
             const int64_t r0 = tl * kConvTile;
             const int vr = (int)min((int64_t)kConvTile, D.m - r0);
-            const int y0 = (int)(r0 / nx), y1 = (int)((r0 + vr - 1) / nx);
+            const int y0 = (int)qdiv(r0, nx), y1 = (int)qdiv(r0 + vr - 1, nx);
             conv_stage<T, K>(es, w, y0, y1, nx, ny);
             __syncthreads();
             const int q = 4 * threadIdx.x;

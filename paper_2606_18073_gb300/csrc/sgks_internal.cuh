@@ -120,6 +120,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
+// Quotient of a non-negative index by a positive divisor, as a 32-bit division when both fit in
+// 32 bits (a 64-bit division is a long instruction sequence; the stencil and convolution rows
+// decompose an index for every row they compute).
+__device__ __forceinline__ int64_t qdiv(int64_t a, int64_t b) {
+    return (((uint64_t)a | (uint64_t)b) >> 32) == 0 ? (int64_t)((uint32_t)a / (uint32_t)b) : a / b;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -227,7 +234,7 @@ template <typename T, typename V>
 __device__ __forceinline__ T a_row_conv(const DevA<T, V>& A, const T* __restrict__ psf_s, int64_t j,
                                         const T* __restrict__ x) {
     const int nx = A.nx, ny = A.ny, kh = A.kh, kw = A.kw;
-    const int iy = (int)(j / nx), ix = (int)(j - (int64_t)iy * nx);
+    const int iy = (int)qdiv(j, nx), ix = (int)(j - (int64_t)iy * nx);
     T acc = T(0);
     for (int a = 0; a < kh; ++a) {
         const int yy = iy - a + kh / 2;
@@ -271,7 +278,7 @@ template <typename T, typename V>
 __device__ __forceinline__ T at_row_conv(const DevA<T, V>& A, const T* __restrict__ psf_s, int64_t i,
                                          const T* __restrict__ e) {
     const int nx = A.nx, ny = A.ny, kh = A.kh, kw = A.kw;
-    const int iy = (int)(i / nx), ix = (int)(i - (int64_t)iy * nx);
+    const int iy = (int)qdiv(i, nx), ix = (int)(i - (int64_t)iy * nx);
     T acc = T(0);
     for (int a = 0; a < kh; ++a) {
         const int yy = iy + a - kh / 2;
@@ -302,6 +309,52 @@ struct Strided {
     __device__ __forceinline__ T operator()(int64_t q) const { return ldg(p + q * st); }
 };
 
+// VV values of consecutive instances handled as one number by the stencil rows (elementwise
+// arithmetic, the same operations per instance as with T), so that one index decomposition of
+// a row serves all VV instances.
+template <typename T, int VV>
+struct VecN {
+    T v[VV];
+    __device__ __forceinline__ VecN() {}
+    __device__ __forceinline__ VecN(T s) {
+#pragma unroll
+        for (int k = 0; k < VV; ++k) v[k] = s;
+    }
+    __device__ __forceinline__ VecN& operator+=(const VecN& o) {
+#pragma unroll
+        for (int k = 0; k < VV; ++k) v[k] += o.v[k];
+        return *this;
+    }
+    __device__ __forceinline__ VecN& operator-=(const VecN& o) {
+#pragma unroll
+        for (int k = 0; k < VV; ++k) v[k] -= o.v[k];
+        return *this;
+    }
+};
+template <typename T, int VV>
+__device__ __forceinline__ VecN<T, VV> operator+(VecN<T, VV> a, const VecN<T, VV>& b) { return a += b; }
+template <typename T, int VV>
+__device__ __forceinline__ VecN<T, VV> operator-(VecN<T, VV> a, const VecN<T, VV>& b) { return a -= b; }
+template <typename T, int VV>
+__device__ __forceinline__ VecN<T, VV> operator*(const VecN<T, VV>& a, const VecN<T, VV>& b) {
+    VecN<T, VV> r;
+#pragma unroll
+    for (int k = 0; k < VV; ++k) r.v[k] = a.v[k] * b.v[k];
+    return r;
+}
+// element q of VV interleaved instance vectors: p[q st + k], k < VV
+template <typename T, int VV>
+struct StridedVec {
+    const T* __restrict__ p;
+    int64_t st;
+    __device__ __forceinline__ VecN<T, VV> operator()(int64_t q) const {
+        VecN<T, VV> r;
+#pragma unroll
+        for (int k = 0; k < VV; ++k) r.v[k] = ldg(p + q * st + k);
+        return r;
+    }
+};
+
 template <typename T, typename X>
 __device__ __forceinline__ T l_row_x(const DevL& L, int64_t k, const X& x) {
     const int nx = L.nx, ny = L.ny;
@@ -311,7 +364,7 @@ __device__ __forceinline__ T l_row_x(const DevL& L, int64_t k, const X& x) {
         case SGKS_REG_GRAD2D: {
             const int64_t nh = (int64_t)ny * (nx - 1);
             if (k < nh) {
-                const int64_t iy = k / (nx - 1), ix = k - iy * (nx - 1);
+                const int64_t iy = qdiv(k, nx - 1), ix = k - iy * (nx - 1);
                 const int64_t q = iy * nx + ix;
                 return x(q + 1) - x(q);
             }
@@ -319,7 +372,7 @@ __device__ __forceinline__ T l_row_x(const DevL& L, int64_t k, const X& x) {
             return x(q + nx) - x(q);
         }
         case SGKS_REG_LAPLACE2D: {
-            const int iy = (int)(k / nx), ix = (int)(k - (int64_t)iy * nx);
+            const int iy = (int)qdiv(k, nx), ix = (int)(k - (int64_t)iy * nx);
             T v = T(4) * x(k);
             if (ix > 0) v -= x(k - 1);
             if (ix < nx - 1) v -= x(k + 1);
@@ -332,14 +385,14 @@ __device__ __forceinline__ T l_row_x(const DevL& L, int64_t k, const X& x) {
             const int64_t n1 = per * L.nt, n2 = per2 * L.nt;
             const int64_t fr = (int64_t)nx * ny;
             if (k < n1) {
-                const int64_t t = k / per, r = k - t * per;
-                const int64_t iy = r / (nx - 1), ix = r - iy * (nx - 1);
+                const int64_t t = qdiv(k, per), r = k - t * per;
+                const int64_t iy = qdiv(r, nx - 1), ix = r - iy * (nx - 1);
                 const int64_t q = t * fr + iy * nx + ix;
                 return x(q + 1) - x(q);
             }
             if (k < n1 + n2) {
                 const int64_t kk = k - n1;
-                const int64_t t = kk / per2, r = kk - t * per2;
+                const int64_t t = qdiv(kk, per2), r = kk - t * per2;
                 const int64_t q = t * fr + r;
                 return x(q + nx) - x(q);
             }
@@ -378,11 +431,11 @@ __device__ __forceinline__ T ltl_row_x(const DevL& L, int64_t i, const X& x) {
         case SGKS_REG_FD1:
             return fd_pair_x<T>(x, i, 1, (int)i, nx);
         case SGKS_REG_GRAD2D: {
-            const int iy = (int)(i / nx), ix = (int)(i - (int64_t)iy * nx);
+            const int iy = (int)qdiv(i, nx), ix = (int)(i - (int64_t)iy * nx);
             return fd_pair_x<T>(x, i, 1, ix, nx) + fd_pair_x<T>(x, i, nx, iy, ny);
         }
         case SGKS_REG_LAPLACE2D: {  // L symmetric: L^T L = L^2, 13-point stencil
-            const int iy = (int)(i / nx), ix = (int)(i - (int64_t)iy * nx);
+            const int iy = (int)qdiv(i, nx), ix = (int)(i - (int64_t)iy * nx);
             T v = T(4) * lap5_x<T>(x, iy, ix, nx, ny);
             if (ix > 0) v -= lap5_x<T>(x, iy, ix - 1, nx, ny);
             if (ix < nx - 1) v -= lap5_x<T>(x, iy, ix + 1, nx, ny);
@@ -392,9 +445,9 @@ __device__ __forceinline__ T ltl_row_x(const DevL& L, int64_t i, const X& x) {
         }
         default: {  // SPACETIME
             const int64_t fr = (int64_t)nx * ny;
-            const int t = (int)(i / fr);
+            const int t = (int)qdiv(i, fr);
             const int64_t r = i - (int64_t)t * fr;
-            const int iy = (int)(r / nx), ix = (int)(r - (int64_t)iy * nx);
+            const int iy = (int)qdiv(r, nx), ix = (int)(r - (int64_t)iy * nx);
             return fd_pair_x<T>(x, i, 1, ix, nx) + fd_pair_x<T>(x, i, nx, iy, ny) + fd_pair_x<T>(x, i, fr, t, L.nt);
         }
     }
@@ -413,7 +466,7 @@ __device__ __forceinline__ T lt_row_x(const DevL& L, int64_t i, const X& v) {
             return a;
         }
         case SGKS_REG_GRAD2D: {
-            const int iy = (int)(i / nx), ix = (int)(i - (int64_t)iy * nx);
+            const int iy = (int)qdiv(i, nx), ix = (int)(i - (int64_t)iy * nx);
             const int64_t nh = (int64_t)ny * (nx - 1);
             T a = T(0);
             const int64_t h = (int64_t)iy * (nx - 1) + ix;
@@ -424,14 +477,14 @@ __device__ __forceinline__ T lt_row_x(const DevL& L, int64_t i, const X& v) {
             return a;
         }
         case SGKS_REG_LAPLACE2D: {
-            const int iy = (int)(i / nx), ix = (int)(i - (int64_t)iy * nx);
+            const int iy = (int)qdiv(i, nx), ix = (int)(i - (int64_t)iy * nx);
             return lap5_x<T>(v, iy, ix, nx, ny);
         }
         default: {
             const int64_t fr = (int64_t)nx * ny;
-            const int t = (int)(i / fr);
+            const int t = (int)qdiv(i, fr);
             const int64_t r = i - (int64_t)t * fr;
-            const int iy = (int)(r / nx), ix = (int)(r - (int64_t)iy * nx);
+            const int iy = (int)qdiv(r, nx), ix = (int)(r - (int64_t)iy * nx);
             const int64_t per = (int64_t)ny * (nx - 1), per2 = (int64_t)(ny - 1) * nx;
             const int64_t n1 = per * L.nt, n2 = per2 * L.nt;
             T a = T(0);
