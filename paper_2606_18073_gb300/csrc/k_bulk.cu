@@ -27,6 +27,7 @@ constexpr int kGradCluster = 8;
 // Append variant: W[:, d] = r.
 template <typename T, typename V, bool WARPA>
 __global__ void __launch_bounds__(kThreads) k_gradient_append(Dims D, DevA<T, V> A, DevL L, Bulk<T> B, Small S) {
+    pdl_wait();   // all global reads below depend on the previous kernel
     __shared__ T psf_s[128];
     DevScalars* sc = S.sc;
     if (sc->stop) return;
@@ -73,6 +74,7 @@ __global__ void __launch_bounds__(kThreads) k_gradient_append(Dims D, DevA<T, V>
 template <typename T, typename V, bool WARPA>
 __global__ void __cluster_dims__(kGradCluster, 1, 1) __launch_bounds__(kThreads)
     k_gradient_refine(Dims D, DevA<T, V> A, DevL L, Bulk<T> B, Small S) {
+    pdl_wait();   // all global reads below depend on the previous kernel
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* gacc = reinterpret_cast<double*>(smem_raw);       // [dmax]
     T* rt = reinterpret_cast<T*>(gacc + D.dmax);             // [kThreads]
@@ -153,11 +155,11 @@ cudaError_t launch_gradient(const Dims& D, const DevA<T, V>& A, const DevL& L, c
         const int blocks = (int)(tiles < 8 * 152 ? tiles : 8 * 152);
         if (warpa) {
             carveout_once((const void*)k_gradient_append<T, V, true>);
-            k_gradient_append<T, V, true><<<blocks, kThreads, 0, st>>>(D, A, L, B, S);
+            return launch_pdl(k_gradient_append<T, V, true>, blocks, kThreads, 0, st, D, A, L, B, S);
         }
         else {
             carveout_once((const void*)k_gradient_append<T, V, false>);
-            k_gradient_append<T, V, false><<<blocks, kThreads, 0, st>>>(D, A, L, B, S);
+            return launch_pdl(k_gradient_append<T, V, false>, blocks, kThreads, 0, st, D, A, L, B, S);
         }
         return cudaGetLastError();
     }
@@ -166,12 +168,12 @@ cudaError_t launch_gradient(const Dims& D, const DevA<T, V>& A, const DevL& L, c
         auto k = k_gradient_refine<T, V, true>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         carveout_once((const void*)k);
-        k<<<D.nbG, kThreads, smem, st>>>(D, A, L, B, S);
+        return launch_pdl(k, D.nbG, kThreads, smem, st, D, A, L, B, S);
     } else {
         auto k = k_gradient_refine<T, V, false>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         carveout_once((const void*)k);
-        k<<<D.nbG, kThreads, smem, st>>>(D, A, L, B, S);
+        return launch_pdl(k, D.nbG, kThreads, smem, st, D, A, L, B, S);
     }
     return cudaGetLastError();
 }
@@ -201,6 +203,7 @@ __device__ __forceinline__ void ld_rows(const T* p, T (&v)[VW]) {
 
 template <typename T, int VW>
 __global__ void __launch_bounds__(kThreads) k_combine(Dims D, Bulk<T> B, Small S, int mode, int nbx) {
+    pdl_wait();   // all global reads below depend on the previous kernel
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* ys = reinterpret_cast<T*>(smem_raw);                       // [dmax + kCombCols], zero from d on
     __shared__ double red[3][kWarps];
@@ -343,8 +346,7 @@ static cudaError_t combine_vw(const Dims& D, const Bulk<T>& B, const Small& S, i
     carveout_once((const void*)k);
     const int64_t per = (int64_t)kThreads * VW;
     const int nbx = (int)((D.n + per - 1) / per), nbe = (int)((D.m + per - 1) / per);
-    k<<<nbx + nbe, kThreads, smem, st>>>(D, B, S, mode, nbx);
-    return cudaGetLastError();
+    return launch_pdl(k, nbx + nbe, kThreads, smem, st, D, B, S, mode, nbx);
 }
 
 // Two rows per thread when both row counts are even (aligned 2-wide loads of every column).

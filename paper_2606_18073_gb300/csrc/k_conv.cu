@@ -159,6 +159,7 @@ __device__ __forceinline__ void gradient_tile(T* dst, T* es, const DevA<T, V>& A
 // ------------------------------------------------------------------ append / apply
 template <typename T, typename V, int K>
 __global__ void __launch_bounds__(kThreads) k_gradient_append_conv(Dims D, DevA<T, V> A, DevL L, Bulk<T> B, Small S) {
+    pdl_wait();   // all global reads below depend on the previous kernel
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* es = reinterpret_cast<T*>(smem_raw);
     DevScalars* sc = S.sc;
@@ -185,6 +186,7 @@ __global__ void __launch_bounds__(kThreads) k_gradient_append_conv(Dims D, DevA<
 template <typename T, typename V, int K>
 __global__ void __launch_bounds__(kThreads) k_apply_column_conv(Dims D, DevA<T, V> A, DevL L, Bulk<T> B, Small S,
                                                                int nbc) {
+    pdl_wait();   // all global reads below depend on the previous kernel
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* es = reinterpret_cast<T*>(smem_raw);
     const DevScalars* sc = S.sc;
@@ -223,6 +225,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_column_conv(Dims D, DevA<T, 
 template <typename T, typename V, int MODE, int K, int CB>
 __global__ void __cluster_dims__(kRefCluster, 1, 1) __launch_bounds__(kThreads)
     k_gradient_refine2(Dims D, DevA<T, V> A, DevL L, Bulk<T> B, Small S) {
+    pdl_wait();   // all global reads below depend on the previous kernel
     using VT = typename Vec16<T>::type;
     constexpr int NPV = 16 / (int)sizeof(T);              // values per 16-byte vector
     constexpr int NV = kThreads / NPV / 32;                 // vectors per lane per column of a tile
@@ -325,8 +328,7 @@ static cudaError_t append_k(const Dims& D, const DevA<T, V>& A, const DevL& L, c
     const size_t smem = conv_stage_bytes<T>(kConvTile, A.nx, K);
     cudaError_t e = smem_attr(k, smem);
     if (e != cudaSuccess) return e;
-    k<<<conv_blocks(D.n), kThreads, smem, st>>>(D, A, L, B, S);
-    return cudaGetLastError();
+    return launch_pdl(k, conv_blocks(D.n), kThreads, smem, st, D, A, L, B, S);
 }
 
 template <typename T, typename V, int K>
@@ -340,8 +342,7 @@ static cudaError_t apply_k(const Dims& D, const DevA<T, V>& A, const DevL& L, co
     int64_t nbl = (D.p + kThreads - 1) / kThreads;
     if (nbl > 4 * 152) nbl = 4 * 152;
     if (nbl < 1) nbl = 1;
-    k<<<nbc + (int)nbl, kThreads, smem, st>>>(D, A, L, B, S, nbc);
-    return cudaGetLastError();
+    return launch_pdl(k, nbc + (int)nbl, kThreads, smem, st, D, A, L, B, S, nbc);
 }
 
 template <typename T, typename V, int MODE, int K>
@@ -354,8 +355,7 @@ static cudaError_t refine_k(const Dims& D, const DevA<T, V>& A, const DevL& L, c
     cudaError_t e = smem_attr(k, smem);
     if (e != cudaSuccess) return e;
     carveout_once((const void*)k);
-    k<<<D.nbG, kThreads, smem, st>>>(D, A, L, B, S);
-    return cudaGetLastError();
+    return launch_pdl(k, D.nbG, kThreads, smem, st, D, A, L, B, S);
 }
 
 // Whether the register-blocked rows serve the operator: FP32, 16-byte aligned columns of W, a

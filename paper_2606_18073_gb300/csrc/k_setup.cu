@@ -17,6 +17,14 @@
 
 namespace sgks {
 
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = getenv("SGKS_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 void carveout_once(const void* kernel) {
     static std::mutex mu;
     static std::set<const void*> done;

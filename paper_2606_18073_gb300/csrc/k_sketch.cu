@@ -21,6 +21,7 @@ namespace sgks {
 
 template <typename T, typename V, bool WARPA>
 __global__ void __launch_bounds__(kThreads) k_apply_column(Dims D, DevA<T, V> A, DevL L, Bulk<T> B, Small S) {
+    pdl_wait();   // all global reads below depend on the previous kernel
     __shared__ T psf_s[128];
     const DevScalars* sc = S.sc;
     if (sc->stop) return;
@@ -104,6 +105,7 @@ __device__ __forceinline__ double gather_row(const uint32_t* __restrict__ idx, i
 template <typename TA, typename TL, typename Acc>
 __global__ void __launch_bounds__(kThreads) k_sketch_gather_col(Dims D, const TA* __restrict__ AW, const TL* __restrict__ lw,
                                                                 SketchCSR SK, Small S) {
+    pdl_wait();   // all global reads below depend on the previous kernel
     __shared__ double red[kWarps];
     const DevScalars* sc = S.sc;
     if (sc->stop) return;
@@ -179,11 +181,11 @@ static cudaError_t launch_apply_column(const Dims& D, const DevA<T, V>& A, const
     if (done || e != cudaSuccess) return e;
     if (A.kind == SGKS_OP_CONV2D) {
         carveout_once((const void*)k_apply_column<T, V, false>);
-        k_apply_column<T, V, false><<<apply_blocks(D), kThreads, 0, st>>>(D, A, L, B, S);
+        return launch_pdl(k_apply_column<T, V, false>, apply_blocks(D), kThreads, 0, st, D, A, L, B, S);
     }
     else {
         carveout_once((const void*)k_apply_column<T, V, true>);
-        k_apply_column<T, V, true><<<apply_blocks(D, true), kThreads, 0, st>>>(D, A, L, B, S);
+        return launch_pdl(k_apply_column<T, V, true>, apply_blocks(D, true), kThreads, 0, st, D, A, L, B, S);
     }
     return cudaGetLastError();
 }
@@ -196,8 +198,7 @@ cudaError_t launch_sketch_column(const Dims& D, const DevA<T, V>& A, const DevL&
     cudaError_t e = launch_apply_column<T, V>(D, A, L, B, S, st);
     if (e != cudaSuccess) return e;
     carveout_once((const void*)k_sketch_gather_col<T, T, T>);
-    k_sketch_gather_col<T, T, T><<<2 * D.s, kThreads, 0, st>>>(D, B.AW, B.tmp_p, SK, S);
-    return cudaGetLastError();
+    return launch_pdl(k_sketch_gather_col<T, T, T>, 2 * D.s, kThreads, 0, st, D, (const T*)B.AW, (const T*)B.tmp_p, SK, S);
 }
 
 cudaError_t launchx_sketch_gather_col(const Dims& D, const float2* AW, const double* lw, const SketchCSR& SK,

@@ -122,6 +122,7 @@ __host__ __device__ inline size_t stacked_smem(int dm, int cs) {
 template <int CS>
 __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads)
     k_qr_append(Dims D, Small S0, const Small* __restrict__ Sarr) {
+    pdl_wait();   // all global reads below depend on the previous kernel
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int fac = (blockIdx.x / CS) & 1;  // 0: S_A A W, 1: S_L L W
@@ -277,6 +278,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads)
 template <int CS>
 __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads)
     k_stacked_solve(Dims D, Small S0, const Small* __restrict__ Sarr) {
+    pdl_wait();   // all global reads below depend on the previous kernel
     cg::cluster_group cl = cg::this_cluster();
     const Small S = Sarr ? Sarr[blockIdx.x / CS] : S0;
     const int rank = (int)cl.block_rank();
@@ -435,6 +437,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads)
 template <int CS>
 __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kThreads)
     k_refine_solve2(Dims D, Small S0, const Small* __restrict__ Sarr, int npart) {
+    pdl_wait();   // all global reads below depend on the previous kernel
     cg::cluster_group cl = cg::this_cluster();
     const Small S = Sarr ? Sarr[blockIdx.x / CS] : S0;
     extern __shared__ __align__(16) double sm[];
@@ -500,10 +503,10 @@ cudaError_t configure_small_fast(int* cluster_out, int s, int dm) {
 cudaError_t launch_qr_append(const Dims& D, const Small& S, cudaStream_t st, const Small* Sarr, int ninst) {
     if (D.cluster2 == 16) {
         carveout_once((const void*)k_qr_append<16>);
-        k_qr_append<16><<<32 * ninst, kThreads, qr_append_smem(D.s, D.dmax, 16), st>>>(D, S, Sarr);
+        return launch_pdl(k_qr_append<16>, 32 * ninst, kThreads, qr_append_smem(D.s, D.dmax, 16), st, D, S, Sarr);
     } else {
         carveout_once((const void*)k_qr_append<8>);
-        k_qr_append<8><<<16 * ninst, kThreads, qr_append_smem(D.s, D.dmax, 8), st>>>(D, S, Sarr);
+        return launch_pdl(k_qr_append<8>, 16 * ninst, kThreads, qr_append_smem(D.s, D.dmax, 8), st, D, S, Sarr);
     }
     return cudaGetLastError();
 }
@@ -511,10 +514,10 @@ cudaError_t launch_qr_append(const Dims& D, const Small& S, cudaStream_t st, con
 cudaError_t launch_stacked_solve(const Dims& D, const Small& S, cudaStream_t st, const Small* Sarr, int ninst) {
     if (D.cluster2 == 16) {
         carveout_once((const void*)k_stacked_solve<16>);
-        k_stacked_solve<16><<<16 * ninst, kThreads, stacked_smem(D.dmax, 16), st>>>(D, S, Sarr);
+        return launch_pdl(k_stacked_solve<16>, 16 * ninst, kThreads, stacked_smem(D.dmax, 16), st, D, S, Sarr);
     } else {
         carveout_once((const void*)k_stacked_solve<8>);
-        k_stacked_solve<8><<<8 * ninst, kThreads, stacked_smem(D.dmax, 8), st>>>(D, S, Sarr);
+        return launch_pdl(k_stacked_solve<8>, 8 * ninst, kThreads, stacked_smem(D.dmax, 8), st, D, S, Sarr);
     }
     return cudaGetLastError();
 }
@@ -525,10 +528,10 @@ cudaError_t launch_refine_solve2(const Dims& D, const Small& S, cudaStream_t st,
     const size_t smem = 2 * sizeof(double) * (size_t)D.dmax;
     if (D.cluster2 == 16) {
         carveout_once((const void*)k_refine_solve2<16>);
-        k_refine_solve2<16><<<16 * ninst, kThreads, smem, st>>>(D, S, Sarr, np);
+        return launch_pdl(k_refine_solve2<16>, 16 * ninst, kThreads, smem, st, D, S, Sarr, np);
     } else {
         carveout_once((const void*)k_refine_solve2<8>);
-        k_refine_solve2<8><<<8 * ninst, kThreads, smem, st>>>(D, S, Sarr, np);
+        return launch_pdl(k_refine_solve2<8>, 8 * ninst, kThreads, smem, st, D, S, Sarr, np);
     }
     return cudaGetLastError();
 }

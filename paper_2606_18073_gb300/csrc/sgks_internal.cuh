@@ -120,6 +120,37 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
+// ----------------------------------------------------- programmatic dependent launch (PDL)
+// The kernels of one iteration follow each other on one stream.  Launched with the
+// programmatic-serialization attribute (launch_pdl), a kernel is launched as soon as every CTA of
+// the kernel before it has exited, without waiting for that grid's completion to be processed;
+// its CTAs then wait in pdl_wait until the predecessor's writes are visible.  This overlaps each
+// kernel's launch and CTA start-up with the end of its predecessor.  (Signalling earlier from
+// inside the predecessor, with griddepcontrol.launch_dependents at its start, was measured
+// slower: the waiting CTAs then hold SM resources through the whole predecessor.)  Every kernel
+// launched with launch_pdl calls pdl_wait before it touches global memory; for a kernel launched
+// without the attribute the call does nothing.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// SGKS_PDL=0 in the environment launches plainly (for comparison); default on.
+bool pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Quotient of a non-negative index by a positive divisor, as a 32-bit division when both fit in
 // 32 bits (a 64-bit division is a long instruction sequence; the stencil and convolution rows
 // decompose an index for every row they compute).
