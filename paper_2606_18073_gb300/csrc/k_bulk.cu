@@ -25,7 +25,7 @@ constexpr int kGradCluster = 8;
 
 
 // Append variant: W[:, d] = r.
-template <typename T, typename V, bool WARPA>
+template <typename T, typename V, bool WARPA, int LPR = 32>
 __global__ void __launch_bounds__(kThreads) k_gradient_append(Dims D, DevA<T, V> A, DevL L, Bulk<T> B, Small S) {
     pdl_wait();   // all global reads below depend on the previous kernel
     __shared__ T psf_s[128];
@@ -50,11 +50,15 @@ __global__ void __launch_bounds__(kThreads) k_gradient_append(Dims D, DevA<T, V>
         const int lane = lane_id();
         for (int64_t i0 = (int64_t)blockIdx.x * kWarps + warp_id(); i0 < D.n; i0 += 32 * GW) {
             T adj = T(0);
-            for (int t = 0; t < 32; ++t) {
-                const int64_t i = i0 + t * GW;
-                if (i >= D.n) break;
-                const T v = at_row_warp(A, i, B.e);
-                if (lane == t) adj = v;
+            if (A.kind == SGKS_OP_CSR) {   // LPR lanes per row of the stored transpose
+                adj = csr_rows_rr<T, V, LPR>(A.trp, A.tci, A.tval, B.e, i0, GW, D.n);
+            } else {
+                for (int t = 0; t < 32; ++t) {
+                    const int64_t i = i0 + t * GW;
+                    if (i >= D.n) break;
+                    const T v = at_row_warp(A, i, B.e);
+                    if (lane == t) adj = v;
+                }
             }
             const int64_t my = i0 + lane * GW;
             if (my < D.n) out[my] = adj + (T)D.lam * ltl_row<T>(L, my, B.x);
@@ -154,8 +158,12 @@ cudaError_t launch_gradient(const Dims& D, const DevA<T, V>& A, const DevL& L, c
         const int64_t tiles = warpa ? (D.n + kWarps - 1) / kWarps : (D.n + kThreads - 1) / kThreads;
         const int blocks = (int)(tiles < 8 * 152 ? tiles : 8 * 152);
         if (warpa) {
-            carveout_once((const void*)k_gradient_append<T, V, true>);
-            return launch_pdl(k_gradient_append<T, V, true>, blocks, kThreads, 0, st, D, A, L, B, S);
+            switch (A.kind == SGKS_OP_CSR ? csr_lanes_per_row(A.nnz, D.n) : 32) {
+                case 4: return launch_pdl(k_gradient_append<T, V, true, 4>, blocks, kThreads, 0, st, D, A, L, B, S);
+                case 8: return launch_pdl(k_gradient_append<T, V, true, 8>, blocks, kThreads, 0, st, D, A, L, B, S);
+                case 16: return launch_pdl(k_gradient_append<T, V, true, 16>, blocks, kThreads, 0, st, D, A, L, B, S);
+                default: return launch_pdl(k_gradient_append<T, V, true, 32>, blocks, kThreads, 0, st, D, A, L, B, S);
+            }
         }
         else {
             carveout_once((const void*)k_gradient_append<T, V, false>);

@@ -39,7 +39,7 @@ void carveout_once(const void* kernel) {
 }
 
 // ---------------------------------------------------------------------------- applies
-template <typename T, typename V, bool WARPA>
+template <typename T, typename V, bool WARPA, int LPR = 32>
 __global__ void __launch_bounds__(kThreads) k_apply(DevA<T, V> A, DevL L, int which, const T* __restrict__ in,
                                                      T* __restrict__ out, int64_t rows) {
     __shared__ T psf_s[128];
@@ -53,11 +53,16 @@ __global__ void __launch_bounds__(kThreads) k_apply(DevA<T, V> A, DevL L, int wh
         const int64_t GW = (int64_t)gridDim.x * kWarps;
         for (int64_t i0 = (int64_t)blockIdx.x * kWarps + warp_id(); i0 < rows; i0 += 32 * GW) {
             T v = T(0);
-            for (int t = 0; t < 32; ++t) {
-                const int64_t ii = i0 + t * GW;
-                if (ii >= rows) break;
-                const T r = adj ? at_row_warp(A, ii, in) : a_row_warp(A, ii, in);
-                if (lane == t) v = r;
+            if (A.kind == SGKS_OP_CSR) {
+                v = adj ? csr_rows_rr<T, V, LPR>(A.trp, A.tci, A.tval, in, i0, GW, rows)
+                        : csr_rows_rr<T, V, LPR>(A.rp, A.ci, A.val, in, i0, GW, rows);
+            } else {
+                for (int t = 0; t < 32; ++t) {
+                    const int64_t ii = i0 + t * GW;
+                    if (ii >= rows) break;
+                    const T r = adj ? at_row_warp(A, ii, in) : a_row_warp(A, ii, in);
+                    if (lane == t) v = r;
+                }
             }
             const int64_t my = i0 + lane * GW;
             if (my < rows) out[my] = v;
@@ -108,8 +113,11 @@ cudaError_t launch_apply(const Dims& D, const DevA<T, V>& A, const DevL& L, int 
         k_apply<T, V, false><<<(int)blocks, kThreads, 0, st>>>(A, L, which, in, out, rows);
     }
     else {
-        carveout_once((const void*)k_apply<T, V, true>);
-        k_apply<T, V, true><<<(int)blocks, kThreads, 0, st>>>(A, L, which, in, out, rows);
+        const int lpr = warp_rows && A.kind == SGKS_OP_CSR ? csr_lanes_per_row(A.nnz, rows) : 32;
+        if (lpr == 4) k_apply<T, V, true, 4><<<(int)blocks, kThreads, 0, st>>>(A, L, which, in, out, rows);
+        else if (lpr == 8) k_apply<T, V, true, 8><<<(int)blocks, kThreads, 0, st>>>(A, L, which, in, out, rows);
+        else if (lpr == 16) k_apply<T, V, true, 16><<<(int)blocks, kThreads, 0, st>>>(A, L, which, in, out, rows);
+        else k_apply<T, V, true, 32><<<(int)blocks, kThreads, 0, st>>>(A, L, which, in, out, rows);
     }
     return cudaGetLastError();
 }

@@ -19,7 +19,7 @@
 
 namespace sgks {
 
-template <typename T, typename V, bool WARPA>
+template <typename T, typename V, bool WARPA, int LPR = 32>
 __global__ void __launch_bounds__(kThreads) k_apply_column(Dims D, DevA<T, V> A, DevL L, Bulk<T> B, Small S) {
     pdl_wait();   // all global reads below depend on the previous kernel
     __shared__ T psf_s[128];
@@ -37,9 +37,17 @@ __global__ void __launch_bounds__(kThreads) k_apply_column(Dims D, DevA<T, V> A,
         // rows of A one per warp, dealt round-robin over every warp of the grid (a row is a chain
         // of dependent loads); then the rows of L one per thread
         const int64_t GW = (int64_t)gridDim.x * kWarps;
-        for (int64_t j = (int64_t)blockIdx.x * kWarps + warp_id(); j < D.m; j += GW) {
-            const T v = a_row_warp(A, j, w);
-            if (lane == 0) u[j] = v;
+        if (A.kind == SGKS_OP_CSR) {   // LPR lanes per row; lane t ends with row j0 + t GW
+            for (int64_t j0 = (int64_t)blockIdx.x * kWarps + warp_id(); j0 < D.m; j0 += 32 * GW) {
+                const T v = csr_rows_rr<T, V, LPR>(A.rp, A.ci, A.val, w, j0, GW, D.m);
+                const int64_t my = j0 + lane * GW;
+                if (my < D.m) u[my] = v;
+            }
+        } else {
+            for (int64_t j = (int64_t)blockIdx.x * kWarps + warp_id(); j < D.m; j += GW) {
+                const T v = a_row_warp(A, j, w);
+                if (lane == 0) u[j] = v;
+            }
         }
         const int64_t GT = (int64_t)gridDim.x * kThreads;
         for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < D.p; j += GT) B.tmp_p[j] = l_row<T>(L, j, w);
@@ -185,7 +193,12 @@ static cudaError_t launch_apply_column(const Dims& D, const DevA<T, V>& A, const
     }
     else {
         carveout_once((const void*)k_apply_column<T, V, true>);
-        return launch_pdl(k_apply_column<T, V, true>, apply_blocks(D, true), kThreads, 0, st, D, A, L, B, S);
+        switch (A.kind == SGKS_OP_CSR ? csr_lanes_per_row(A.nnz, D.m) : 32) {
+            case 4: return launch_pdl(k_apply_column<T, V, true, 4>, apply_blocks(D, true), kThreads, 0, st, D, A, L, B, S);
+            case 8: return launch_pdl(k_apply_column<T, V, true, 8>, apply_blocks(D, true), kThreads, 0, st, D, A, L, B, S);
+            case 16: return launch_pdl(k_apply_column<T, V, true, 16>, apply_blocks(D, true), kThreads, 0, st, D, A, L, B, S);
+            default: return launch_pdl(k_apply_column<T, V, true, 32>, apply_blocks(D, true), kThreads, 0, st, D, A, L, B, S);
+        }
     }
     return cudaGetLastError();
 }

@@ -740,6 +740,7 @@ int prepare_operator(const sgks_op* op, DevA<T, V>& A, std::vector<void*>& alloc
             }
         }
         A.rp = op->row_ptr;
+        A.nnz = op->nnz;
         A.ci = op->col;
         if (op->val_dtype == vdt) {
             A.val = (const V*)op->val;

@@ -47,6 +47,7 @@ template <typename T, typename V>
 struct DevA {
     int kind;            // SGKS_OP_*
     int64_t m, n;
+    int64_t nnz;         // CSR: stored entries (0 for the other kinds)
     const int32_t* rp;   // CSR
     const int32_t* ci;
     const V* val;
@@ -258,6 +259,43 @@ __device__ __forceinline__ T a_row_warp(const DevA<T, V>& A, int64_t j, const T*
         for (int64_t k = lane; k < A.n; k += 32) acc += ldg(row + k) * ldg(x + k);
     }
     return warp_sum(acc);
+}
+
+// Rows i0 + t GW (t < 32) of a CSR matrix times x, LPR lanes per row (32 / LPR rows at a time):
+// lane l of a row's group sums the entries b + l, b + l + LPR, ... and the group combines them by
+// a fixed xor tree; the result of row i0 + t GW ends in lane t (0 past nrows).  Short rows take
+// fewer lanes, so that a row does not pay a 32-lane reduction for a few dozen entries (in FP64
+// each reduction step is a warp instruction on GB300's narrow FP64 pipe).
+template <typename T, typename V, int LPR>
+__device__ __forceinline__ T csr_rows_rr(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                         const V* __restrict__ val, const T* __restrict__ x, int64_t i0, int64_t GW,
+                                         int64_t nrows) {
+    constexpr int RPW = 32 / LPR;
+    const int lane = lane_id(), sub = lane / LPR, sl = lane % LPR;
+    T mine = T(0);
+#pragma unroll 1
+    for (int p = 0; p < LPR; ++p) {
+        if (i0 + (int64_t)(p * RPW) * GW >= nrows) break;   // warp-uniform: rows grow with t
+        const int64_t row = i0 + (int64_t)(p * RPW + sub) * GW;
+        T acc = T(0);
+        if (row < nrows) {
+            const int b = rp[row], e = rp[row + 1];
+#pragma unroll 4
+            for (int k = b + sl; k < e; k += LPR) acc += (T)ldg(val + k) * ldg(x + ldg(ci + k));
+        }
+#pragma unroll
+        for (int off = LPR / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        const int s = lane - p * RPW;   // this lane's row within the pass, if any
+        const T v = __shfl_sync(0xffffffffu, acc, (s >= 0 && s < RPW ? s : 0) * LPR);
+        if (s >= 0 && s < RPW) mine = v;
+    }
+    return mine;
+}
+
+// lanes per CSR row for rows of `avg` entries on average
+inline int csr_lanes_per_row(int64_t nnz, int64_t rows) {
+    const int64_t avg = rows > 0 ? nnz / rows : 0;
+    return avg >= 96 ? 32 : (avg >= 48 ? 16 : (avg >= 16 ? 8 : 4));
 }
 
 // Thread-level rows (2D convolution).
