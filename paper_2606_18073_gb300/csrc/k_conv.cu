@@ -16,8 +16,8 @@
 // k_gradient_append_conv (K6 without refinement): r = A^T e + lam L^T L x -> W[:, d].
 // k_apply_column_conv (the apply half of K2): u = A w -> (A W)[:, d] and t = L w -> scratch.
 // k_gradient_refine2 (K7 with refinement): r(y) for a tile of 256 rows on chip, then
-//   g = W^T r over the tile, g accumulated in FP64 per column across the CTA's tiles and
-//   reduced over a cluster of 8 CTAs through distributed shared memory.  The loads of the
+//   g = W^T r over the tile, g accumulated in FP64 per column across the CTA's tiles; every CTA
+//   writes its partial, and the refinement solve sums them in a fixed order.  The loads of the
 //   first columns of the tile are issued before r is computed, so their latency overlaps the
 //   operator rows; each warp then streams CB columns at a time (16-byte loads, the next CB
 //   columns requested before the current ones are reduced).
@@ -27,7 +27,6 @@ namespace sgks {
 
 constexpr int kPad = 4;          // zero columns on each side of a staged row (>= K/2, K <= 9)
 constexpr int kConvTile = 512;   // output rows per tile of the append / apply kernels (<= 4 kThreads)
-constexpr int kRefCluster = 8;
 
 // ------------------------------------------------------------------ 4-wide vector access
 template <typename T>
@@ -223,8 +222,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_column_conv(Dims D, DevA<T, 
 // MODE 0: A^T rows warp-cooperative (CSR, dense); 1: generic convolution rows, one per lane;
 // 2: register-blocked convolution with K x K taps.
 template <typename T, typename V, int MODE, int K, int CB>
-__global__ void __cluster_dims__(kRefCluster, 1, 1) __launch_bounds__(kThreads)
-    k_gradient_refine2(Dims D, DevA<T, V> A, DevL L, Bulk<T> B, Small S) {
+__global__ void __launch_bounds__(kThreads) k_gradient_refine2(Dims D, DevA<T, V> A, DevL L, Bulk<T> B, Small S) {
     pdl_wait();   // all global reads below depend on the previous kernel
     using VT = typename Vec16<T>::type;
     constexpr int NPV = 16 / (int)sizeof(T);              // values per 16-byte vector
@@ -234,7 +232,6 @@ __global__ void __cluster_dims__(kRefCluster, 1, 1) __launch_bounds__(kThreads)
     T* rts = reinterpret_cast<T*>(gacc + ((D.dmax + 1) & ~1));   // [kThreads], 16-byte aligned
     T* es = rts + kThreads;                                 // staged rows (MODE 2)
     __shared__ T psf_s[128];
-    cg::cluster_group cl = cg::this_cluster();
     const DevScalars* sc = S.sc;
     if (sc->stop) return;
     const int d = sc->d;
@@ -291,17 +288,9 @@ __global__ void __cluster_dims__(kRefCluster, 1, 1) __launch_bounds__(kThreads)
         }
         __syncthreads();
     }
-    cl.sync();
-    if (cl.block_rank() == 0) {
-        double* out = S.gpart + (size_t)(blockIdx.x / kRefCluster) * D.dmax;
-        for (int j = threadIdx.x; j < d; j += kThreads) {
-            double v[kRefCluster];
-#pragma unroll
-            for (int r = 0; r < kRefCluster; ++r) v[r] = cl.map_shared_rank(gacc, r)[j];
-            out[j] = tree_sumd<kRefCluster>(v);
-        }
-    }
-    cl.sync();
+    __syncthreads();
+    double* out = S.gpart + (size_t)blockIdx.x * D.dmax;   // this CTA's partial, summed by the solve
+    for (int j = threadIdx.x; j < d; j += kThreads) out[j] = gacc[j];
 }
 
 // ------------------------------------------------------------------ launchers

@@ -357,7 +357,7 @@ cudaError_t launch_append_solve(const Dims& D, const Small& S, cudaStream_t st) 
 }
 
 cudaError_t launch_refine_solve(const Dims& D, const Small& S, cudaStream_t st) {
-    const int np = D.nbG / 8;
+    const int np = D.refine_np;
     if (D.cluster == 16) {
         carveout_once((const void*)k_refine_solve<16>);
         k_refine_solve<16><<<16, kThreads, refine_smem(D.dmax), st>>>(D, S, np);

@@ -524,7 +524,7 @@ cudaError_t launch_stacked_solve(const Dims& D, const Small& S, cudaStream_t st,
 
 cudaError_t launch_refine_solve2(const Dims& D, const Small& S, cudaStream_t st, const Small* Sarr, int ninst,
                                  int npart) {
-    const int np = npart >= 0 ? npart : D.nbG / 8;
+    const int np = npart >= 0 ? npart : D.refine_np;
     const size_t smem = 2 * sizeof(double) * (size_t)D.dmax;
     if (D.cluster2 == 16) {
         carveout_once((const void*)k_refine_solve2<16>);

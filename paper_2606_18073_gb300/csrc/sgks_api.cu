@@ -922,6 +922,10 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     int64_t nbG = (tiles + 7) / 8 * 8;
     if (nbG > 304) nbG = 304;
     D.nbG = (int)nbG;
+    // k_gradient_refine2 (16-byte aligned columns of W, plain engine) leaves one partial per CTA,
+    // the cluster kernels of the other cases one per cluster of 8
+    D.refine_np = (!(o.precision == SGKS_PREC_FP32X && std::is_same<T, float>::value) &&
+                   (D.n * (int64_t)sizeof(T)) % 16 == 0) ? D.nbG : D.nbG / 8;
     D.nbX = (int)tiles;
     D.nbE = (int)((D.m + kThreads - 1) / kThreads);
     E->nbS = (int)(tiles < 304 ? tiles : 304);
@@ -977,7 +981,7 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     AL(S.Sb, s);
     AL(S.partA, (size_t)(D.nbA / 8 + 1) * s);
     AL(S.partL, (size_t)(D.nbL / 8 + 1) * s);
-    AL(S.gpart, (size_t)(D.nbG / 8) * dm);
+    AL(S.gpart, (size_t)D.refine_np * dm);
     AL(S.kapart, (size_t)(D.nbX + D.nbE) * 3);
     AL(S.rc_hist, (size_t)o.max_iters + 1);
     AL(S.rre_hist, (size_t)o.max_iters + 1);

@@ -663,6 +663,7 @@ struct Dims {
     int nbA, nbL;             // blocks of the sketch kernel for the A rows and the L rows (multiples of 8)
     int npA, npL;             // sketch partials (one per cluster of 8 blocks; 1 for the dense sketch)
     int nbG;                  // blocks of the gradient kernels (n / kThreads tiles)
+    int refine_np;            // refinement partials S.gpart holds (nbG, or nbG / 8 from 8-CTA clusters)
     int nbX, nbE;             // blocks of the combine kernel (x rows, e rows)
     int cluster;              // CTAs of the small kernels (global-memory fallback path)
     int cluster2;             // CTAs per cluster of the fast small path
