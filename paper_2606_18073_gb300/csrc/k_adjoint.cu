@@ -241,6 +241,53 @@ cudaError_t launchd_solve_G(const double* X, const double* Xr, int dm, int d, co
     return cudaGetLastError();
 }
 
+// U_j y, U_j z, V_j y, V_j z of a reverse step from the stored sketched QR factors: U_j = S_A A W_j
+// = Q_A R_A and V_j = S_L L W_j = Q_L R_L over the leading d columns (appending columns leaves
+// the leading blocks of Q and R unchanged), so no operator apply or sketch is needed.  Product
+// p = blockIdx.x / kQrSplit (0: Q_A R_A y, 1: Q_A R_A z, 2: Q_L R_L y, 3: Q_L R_L z); CTA
+// blockIdx.x % kQrSplit takes rows [c R, (c + 1) R) of the s outputs.  FP64, fixed order: t = R v
+// with a warp per entry, then u_i = sum_k Q(i, k) t_k with four interleaved partial sums.
+constexpr int kQrSplit = 8;
+
+__global__ void __launch_bounds__(kThreads) kd_qr_products(Small S, int s, int dm, int d, const double* __restrict__ y,
+                                                           const double* __restrict__ z, double* uy, double* uz,
+                                                           double* vy, double* vz) {
+    extern __shared__ double t[];   // [d]
+    const int p = blockIdx.x / kQrSplit, c = blockIdx.x % kQrSplit;
+    const double* Q = p < 2 ? S.QA : S.QL;
+    const double* R = p < 2 ? S.RA : S.RL;
+    const double* v = (p & 1) ? z : y;
+    double* out = p == 0 ? uy : (p == 1 ? uz : (p == 2 ? vy : vz));
+    const int lane = lane_id(), warp = warp_id();
+    for (int k = warp; k < d; k += kWarps) {   // t_k = sum_{l >= k} R(k, l) v_l
+        double a = 0.0;
+        for (int l = k + lane; l < d; l += 32) a += R[(size_t)l * dm + k] * v[l];
+        a = warp_sum(a);
+        if (lane == 0) t[k] = a;
+    }
+    __syncthreads();
+    const int rows = (s + kQrSplit - 1) / kQrSplit, i1 = min(s, (c + 1) * rows);
+    for (int i = c * rows + (int)threadIdx.x; i < i1; i += kThreads) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int k = 0;
+        for (; k + 3 < d; k += 4) {
+            a0 += Q[(size_t)k * s + i] * t[k];
+            a1 += Q[(size_t)(k + 1) * s + i] * t[k + 1];
+            a2 += Q[(size_t)(k + 2) * s + i] * t[k + 2];
+            a3 += Q[(size_t)(k + 3) * s + i] * t[k + 3];
+        }
+        for (; k < d; ++k) a0 += Q[(size_t)k * s + i] * t[k];
+        out[i] = (a0 + a1) + (a2 + a3);
+    }
+}
+
+cudaError_t launchd_qr_products(const Small& S, int s, int dm, int d, const double* y, const double* z, double* uy,
+                                double* uz, double* vy, double* vz, cudaStream_t st) {
+    kd_qr_products<<<4 * kQrSplit, kThreads, sizeof(double) * (size_t)(d > 0 ? d : 1), st>>>(S, s, dm, d, y, z, uy,
+                                                                                              uz, vy, vz);
+    return cudaGetLastError();
+}
+
 cudaError_t launchd_small_inverse(const double* R, int ell, double* Rinv, cudaStream_t st) {
     if (ell > 8) return cudaErrorInvalidValue;
     kd_small_inverse<<<1, 32, 0, st>>>(R, ell, Rinv);

@@ -228,7 +228,7 @@ struct Engine : EngineBase {
 
     // ------------------------------------------------------------------ reverse sweep
     struct Bw {
-        T *Wb = nullptr, *xb = nullptr, *xj = nullptr, *wz = nullptr, *t1 = nullptr, *t2 = nullptr;
+        T *Wb = nullptr, *xb = nullptr, *t1 = nullptr, *t2 = nullptr;
         T *P = nullptr, *Q = nullptr, *tm = nullptr, *tp = nullptr, *Kv = nullptr, *Kb = nullptr;
         double *uy = nullptr, *uz = nullptr, *vy = nullptr, *vz = nullptr, *cb = nullptr, *st = nullptr;
         double *ybar = nullptr, *z = nullptr, *part = nullptr, *acc = nullptr, *R0 = nullptr, *Ri = nullptr;
@@ -250,7 +250,7 @@ struct Engine : EngineBase {
         const size_t n = D.n, m = D.m, p = D.p, s = D.s, dm = D.dmax, ell = D.ell;
         cudaError_t e = cudaSuccess;
         auto A1 = [&](auto** ptr, size_t c) { if (e == cudaSuccess) e = bw_alloc(ptr, c); };
-        A1(&bw.Wb, dm * n); A1(&bw.xb, n); A1(&bw.xj, n); A1(&bw.wz, n); A1(&bw.t1, n); A1(&bw.t2, n);
+        A1(&bw.Wb, dm * n); A1(&bw.xb, n); A1(&bw.t1, n); A1(&bw.t2, n);
         A1(&bw.P, n); A1(&bw.Q, n); A1(&bw.tm, m); A1(&bw.tp, p); A1(&bw.Kv, ell * n); A1(&bw.Kb, ell * n);
         A1(&bw.uy, s); A1(&bw.uz, s); A1(&bw.vy, s); A1(&bw.vz, s); A1(&bw.cb, s); A1(&bw.st, s);
         A1(&bw.ybar, dm); A1(&bw.z, dm); A1(&bw.part, (size_t)nbS * dm); A1(&bw.acc, 2);
@@ -270,12 +270,6 @@ struct Engine : EngineBase {
     cudaError_t bw_apply(int which, const T* in, T* out) {
         g_launches.fetch_add(1);
         return launch_apply<T, V>(D, A, L, which, in, out, st);
-    }
-
-    // S_A v (isA) or S_L v as FP64 s-vectors, as in the forward sketch of the same precision
-    cudaError_t bw_sketch(bool isA, const T* in, double* out) {
-        g_launches.fetch_add(2);
-        return sketch_vector(isA, in, sizeof(T) == 4 ? SGKS_F32 : SGKS_F64, sizeof(T) == 4, out);
     }
 
     cudaError_t bw_sketch_adj(bool isA, const double* u, T* out) {
@@ -314,17 +308,9 @@ struct Engine : EngineBase {
             const double* yj = yhist + (size_t)j * D.dmax;
             L1(bw_dots(W, d, bw.xb, bw.ybar));
             L1(launchd_solve_G(S.X, S.Xr, D.dmax, d, bw.ybar, bw.z, st));
-            L1(launchd_gemv_n<T>(W, n, d, yj, bw.xj, st));
-            L1(launchd_gemv_n<T>(W, n, d, bw.z, bw.wz, st));
-            g_launches.fetch_add(3);
-            L1(bw_apply(SGKS_APPLY_A, bw.xj, bw.tm));
-            L1(bw_sketch(true, bw.tm, bw.uy));
-            L1(bw_apply(SGKS_APPLY_A, bw.wz, bw.tm));
-            L1(bw_sketch(true, bw.tm, bw.uz));
-            L1(bw_apply(SGKS_APPLY_L, bw.xj, bw.tp));
-            L1(bw_sketch(false, bw.tp, bw.vy));
-            L1(bw_apply(SGKS_APPLY_L, bw.wz, bw.tp));
-            L1(bw_sketch(false, bw.tp, bw.vz));
+            // U_j y, U_j z, V_j y, V_j z from the sketched QR factors (U_j = Q_A R_A, V_j = Q_L R_L)
+            L1(launchd_qr_products(S, D.s, D.dmax, d, yj, bw.z, bw.uy, bw.uz, bw.vy, bw.vz, st));
+            g_launches.fetch_add(2);
             L1(launchd_axpby_d(bw.cb, bw.cb, 1.0, bw.uz, 1.0, D.s, st));
             L1(launchd_dot_acc(bw.vz, bw.vy, D.s, -1.0, bw.acc, st));
             L1(launchd_axpby_d(bw.st, S.Sb, 1.0, bw.uy, -1.0, D.s, st));

@@ -883,6 +883,8 @@ cudaError_t launchd_sketch_adj(uint64_t key, const double* gauss, int64_t h, int
                                const double* u, T* out, int* err, cudaStream_t st);
 cudaError_t launchd_solve_G(const double* X, const double* Xr, int dm, int d, const double* v, double* z,
                             cudaStream_t st);
+cudaError_t launchd_qr_products(const Small& S, int s, int dm, int d, const double* y, const double* z, double* uy,
+                                double* uz, double* vy, double* vz, cudaStream_t st);
 cudaError_t launchd_small_inverse(const double* R, int ell, double* Rinv, cudaStream_t st);
 template <typename T>
 cudaError_t launchd_kbar(const T* Wb0, int64_t n, int ell, const double* Rinv, T* Kbar, cudaStream_t st);
