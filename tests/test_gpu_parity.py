@@ -267,6 +267,63 @@ def test_conv_rows_many_tiles(G, precision):
     S.close()
 
 
+def random_csr_problem(avg_row, seed=0, n_side=24, m=700):
+    """The small CT problem with A replaced by a random sparse m x n matrix of about `avg_row`
+    entries per row (non-negative, like path lengths), b = A x_true + 1% noise."""
+    from workloads.configs import _noisy
+    from workloads.problem import OperatorDesc
+    P = small_problem("ct2d", N=n_side, iters=12, precision="fp64", n_refine=0)
+    rng = np.random.default_rng(seed)
+    n = P.n
+    rows, cols = [], []
+    for i in range(m):
+        k = max(1, int(rng.poisson(avg_row)))
+        cols.append(np.sort(rng.choice(n, size=min(k, n), replace=False)))
+        rows.append(len(cols[-1]))
+    rp = np.concatenate([[0], np.cumsum(rows)]).astype(np.int32)
+    col = np.concatenate(cols).astype(np.int32)
+    val = rng.uniform(0.1, 1.0, size=len(col)).astype(np.float32)
+    P.A = OperatorDesc("csr", m, n, row_ptr=rp, col=col, val=val, nx=n_side, ny=n_side)
+    P.b = _noisy(P.A, P.x_true, 0.01, np.random.default_rng(seed + 1))
+    return P
+
+
+@pytest.mark.parametrize("avg_row", [5, 24, 60, 160])
+def test_csr_lanes_per_row(G, avg_row):
+    """CSR rows of about 5, 24, 60 and 160 entries (4, 8, 16 and 32 lanes per row for A; the
+    transposed rows are shorter), FP64 iterates against the oracle."""
+    P = random_csr_problem(avg_row, seed=avg_row)
+    ref = O.sgks(P, record_x=True)
+    S, xs = gpu_iterates(G, P, P.iters, "fp64")
+    check_iterates(xs, ref["xs"], floor_curve(P, P.iters, EPS["fp64"])[0], TOL64, FACTOR64)
+    S.close()
+
+
+def test_programmatic_launch_changes_nothing(G, tmp_path):
+    """The iteration's kernels launch with programmatic dependent launch; SGKS_PDL=0 launches them
+    plainly.  Only the scheduling differs, so the solve is bit-identical (checked in a child
+    process, since the switch is read once per process)."""
+    import subprocess
+    code = (
+        "import sys, numpy as np; sys.path.insert(0, %r)\n"
+        "import paper_2606_18073_gb300 as G\n"
+        "from workloads import small_problem\n"
+        "G.build()\n"
+        "P = small_problem('deblur2d')\n"
+        "S = G.Solver(**G.device_inputs(P, 'fp32'))\n"
+        "S.solve(P.iters)\n"
+        "np.save(%r, S.x().cpu().numpy())\n"
+    ) % (os.path.dirname(os.path.dirname(os.path.abspath(__file__))), str(tmp_path / "x.npy"))
+    env = dict(os.environ, SGKS_PDL="0")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    P = small_problem("deblur2d")
+    S = G.Solver(**G.device_inputs(P, "fp32"))
+    S.solve(P.iters)
+    assert np.array_equal(S.x().cpu().numpy(), np.load(tmp_path / "x.npy"))
+    S.close()
+
+
 def test_ragged_sizes_and_extreme_sketch(G):
     """n not a multiple of the 32-row slab or 256-row tile; zeta = 1 and zeta = s."""
     for nx, ny, s, zeta in ((37, 23, 64, 1), (19, 41, 40, 16), (33, 7, 30, 8)):
