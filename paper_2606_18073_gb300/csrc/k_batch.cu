@@ -729,10 +729,10 @@ __global__ void __launch_bounds__(kThreads) kb_gradient(BDims D, DevA<T, V> A, D
 // positions l + 32 k (k < 32, all loads independent and in flight together).  NB = B / 32
 // instances per lane for B >= 32 (instance l + 32 (k mod NB)); NB = 0 for B < 32 (one instance
 // per lane, l mod B, combined across the lanes by shuffles).  Warp w owns columns w, w + 8, ...,
-// every (j, i) has one owner, and the 8 CTAs of a cluster are combined by a fixed tree into gpart.
+// every (j, i) has one owner, and each CTA writes its partials to gpart for the refinement solve,
+// which sums them in CTA order.
 template <typename T, int NB>
-__global__ void __cluster_dims__(kBatchCluster, 1, 1) __launch_bounds__(kThreads, 2)
-    kb_wtr(BDims D, BBulk<T> X, BSmall S, const T* __restrict__ r) {
+__global__ void __launch_bounds__(kThreads, 2) kb_wtr(BDims D, BBulk<T> X, BSmall S, const T* __restrict__ r) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_dlive;
     __shared__ int s_stop[kMaxBatch];
@@ -740,7 +740,6 @@ __global__ void __cluster_dims__(kBatchCluster, 1, 1) __launch_bounds__(kThreads
     const int TR = 1024 / B;
     double* gacc = reinterpret_cast<double*>(smem_raw);        // [dmax][B]
     T* rt = reinterpret_cast<T*>(gacc + (size_t)D.dmax * B);   // [TR][B]
-    cg::cluster_group cl = cg::this_cluster();
     const int lane = lane_id(), warp = warp_id();
     if (threadIdx.x == 0) {
         int mx = 0;
@@ -784,18 +783,12 @@ __global__ void __cluster_dims__(kBatchCluster, 1, 1) __launch_bounds__(kThreads
             }
         }
     }
-    cl.sync();
-    if (cl.block_rank() == 0) {
-        const int c = blockIdx.x / kBatchCluster, ngp = gridDim.x / kBatchCluster;
-        for (int q = threadIdx.x; q < dlive * B; q += kThreads) {
-            const int j = q / B, bb = q & (B - 1);
-            double v[kBatchCluster];
-#pragma unroll
-            for (int rr = 0; rr < kBatchCluster; ++rr) v[rr] = cl.map_shared_rank(gacc, rr)[q];
-            S.gpart[((size_t)bb * ngp + c) * D.dmax + j] = tree_sumd<kBatchCluster>(v);
-        }
+    __syncthreads();
+    // this CTA's partials, summed by the refinement solve in CTA order
+    for (int q = threadIdx.x; q < dlive * B; q += kThreads) {
+        const int j = q / B, bb = q & (B - 1);
+        S.gpart[((size_t)bb * gridDim.x + blockIdx.x) * D.dmax + j] = gacc[q];
     }
-    cl.sync();
 }
 
 // --------------------------------------------------------------------------------- setup

@@ -123,7 +123,7 @@ struct Group : GroupBase {
         RUNC(BK_COMBINE_REFINE, 1, launchb_combine<T>(D, X, S, 0, st));
         RUNC(BK_GRAD_REFINE, 1, (launchb_gradient<T, V>(D, A, L, X, S, X.r, st)));
         RUNC(BK_GRAD_REFINE, 1, launchb_wtr<T>(D, X, S, X.r, st));
-        RUNC(BK_REFINE_SOLVE, 1, launch_refine_solve2(Ds, Small{}, st, Sarr, D.B, D.nb_refine / 8));
+        RUNC(BK_REFINE_SOLVE, 1, launch_refine_solve2(Ds, Small{}, st, Sarr, D.B, D.nb_refine));
         return e;
     }
 
@@ -414,7 +414,8 @@ int build_groups(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const st
         {   // enough CTAs to fill every SM at the residency the refinement's shared memory allows
             const size_t sm = batch_refine_smem(dmax, B, sizeof(T)) + 2048;
             int64_t per_sm = (int64_t)((227 * 1024) / sm);
-            per_sm = std::max<int64_t>(1, std::min<int64_t>(per_sm, 8));
+            // at most two per SM: each CTA leaves one partial per instance for the solve to sum
+            per_sm = std::max<int64_t>(1, std::min<int64_t>(per_sm, 2));
             const int64_t cap = std::max<int64_t>(8, 152 * per_sm / 8 * 8);
             D.nb_refine = (int)std::min<int64_t>((rtiles + 7) / 8 * 8, cap);
         }
@@ -457,7 +458,7 @@ int build_groups(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const st
         BA(S.partA, (size_t)B * s);
         BA(S.partL, (size_t)B * s);
         BA(S.Sb, (size_t)B * s);
-        BA(S.gpart, (size_t)B * (D.nb_refine / 8) * dmax);
+        BA(S.gpart, (size_t)B * D.nb_refine * dmax);
         BA(S.kapart, (size_t)nb_comb_max * B * 3);
         BA(S.y, (size_t)B * dmax);
         BA(S.lam, B);
@@ -504,7 +505,7 @@ int build_groups(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const st
             q.Sb = S.Sb + (size_t)i * s;
             q.partA = S.partA + (size_t)i * s;
             q.partL = S.partL + (size_t)i * s;
-            q.gpart = S.gpart + (size_t)i * (D.nb_refine / 8) * dmax;
+            q.gpart = S.gpart + (size_t)i * D.nb_refine * dmax;
             q.sc = S.sc + i;
             q.lam = lambdas[G->members[i]];
             lam[i] = q.lam;

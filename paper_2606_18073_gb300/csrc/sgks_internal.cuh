@@ -797,7 +797,7 @@ struct BDims {
     int tma;                  // 1: combine streams W through shared memory by bulk copies
     int slice_kb;             // bulk-copy combine: column slice of 8 or 16 KB (tuned)
     int nl_a, nl_t;           // CSR rows: lanes per row of A and of A^T (powers of two <= 32, tuned)
-    int nb_refine;            // CTAs of kb_wtr (a multiple of 8: one cluster = 8 CTAs)
+    int nb_refine;            // CTAs of kb_wtr (each leaves one partial per instance)
     int nb_setup;             // CTAs of the setup reductions
     double sketch_scale;      // 1/sqrt(zeta)
 };
@@ -815,7 +815,7 @@ struct BBulk {
 struct BSmall {
     double *partA, *partL;    // [B][s] sketched newest column (one partial)
     double* Sb;               // [B][s] S_A b_i
-    double* gpart;            // [B][nb_refine / 8][dmax] refinement partials
+    double* gpart;            // [B][nb_refine][dmax] refinement partials
     double* kapart;           // [nb_combine][B][3] norm partials
     double* y;                // [B][dmax]
     double* lam;              // [B]
