@@ -2,8 +2,9 @@
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline / reference leg
 may import this module.  It differentiates the map (b, lambda) -> x_K of Algorithm 2 run for K
-iterations without refinement, for a loss l(x_K) whose gradient xbar = dl/dx_K is given, by a
-reverse sweep over the iterations written from the algorithm's own equations:
+iterations, with or without the q = 0 refinement steps of the projected problem (Sec. 3.1),
+for a loss l(x_K) whose gradient xbar = dl/dx_K is given, by a reverse sweep over the
+iterations written from the algorithm's own equations:
 
   * x_j = W_j y_j, with y_j the minimiser of eq. (projected_sketched_bis).  In exact arithmetic
     y_j = G_j^{-1} h_j with G_j = U_j^T U_j + lambda V_j^T V_j, h_j = U_j^T c, U_j = S_A A W_j,
@@ -13,6 +14,17 @@ reverse sweep over the iterations written from the algorithm's own equations:
         Wbar_j += P z^T + Q y^T,  P = A^T S_A^T (c - U_j y_j) - lambda L^T S_L^T V_j y_j,
                                   Q = -(A^T S_A^T U_j z + lambda L^T S_L^T V_j z).
   * x_j = W_j y_j itself gives ybar = W_j^T xbar_j and Wbar_j += xbar_j y_j^T.
+  * With refinement, y_j = y^R is reached from y^0 (the projected solve above) by steps
+    y^r = y^{r-1} - G_j^{-1} W_j^T rho(W_j y^{r-1}), rho(x) = H x - A^T b, H = A^T A + lambda L^T L
+    (the gradient of eq. gradient).  The adjoint of one step, for ybar = ybar^r, with
+    w = G_j^{-1} ybar and delta = y^{r-1} - y^r:
+        ybar^{r-1} = ybar - W_j^T H W_j w,    bbar += A W_j w,
+        lambdabar += (V_j w).(V_j delta) - (W_j w).(L^T L W_j y^{r-1}),
+        Wbar_j += -rho(W_j y^{r-1}) w^T - (H W_j w) (y^{r-1})^T
+                  + (A^T S_A^T U_j delta + lambda L^T S_L^T V_j delta) w^T
+                  + (A^T S_A^T U_j w + lambda L^T S_L^T V_j w) delta^T,
+    the last line from G_j = U_j^T U_j + lambda V_j^T V_j depending on W_j and lambda.  The
+    projected solve's adjoint then runs with ybar^0 and y^0.
   * The new column r_j = A^T (A x_{j-1} - b) + lambda L^T L x_{j-1} (eq. gradient) gives, once
     its adjoint rbar = Wbar[:, d_j - 1] is complete (no later step touches it),
     xbar_{j-1} += (A^T A + lambda L^T L) rbar, bbar -= A rbar, lambdabar += rbar . L^T L x_{j-1}.
@@ -35,17 +47,18 @@ import numpy as np
 from .sgks_oracle import dense_matrix, make_operators, sgks, sketch_operator
 
 
-def sgks_vjp(problem, iters, xbar, fwd=None):
-    """Reverse sweep: (bbar, lambdabar) = xbar^T d x_K / d(b, lambda) for K = iters, no refinement.
+def sgks_vjp(problem, iters, xbar, fwd=None, n_refine=0):
+    """Reverse sweep: (bbar, lambdabar) = xbar^T d x_K / d(b, lambda) for K = iters.
 
-    fwd: the oracle forward run with record_x=True (recomputed if None).  Returns a dict with
-    bbar (m), lambdabar, and the forward's x_K.
+    fwd: the oracle forward run with record_x=True (recomputed with n_refine refinement steps
+    if None; otherwise its own refinement count is used).  Returns a dict with bbar (m),
+    lambdabar, and the forward's x_K.
     """
     P = problem
     if P.sketch.kind not in ("sparse_sign", "gaussian", "srtt"):
         raise ValueError(P.sketch.kind)
     if fwd is None:
-        fwd = sgks(P, iters=iters, n_refine=0, record_x=True)
+        fwd = sgks(P, iters=iters, n_refine=n_refine, record_x=True)
     Aop, Lop = make_operators(P)
     lam = float(P.lam)
     b = np.asarray(P.b, dtype=np.float64)
@@ -53,7 +66,7 @@ def sgks_vjp(problem, iters, xbar, fwd=None):
     SL = sketch_operator(P.sketch, 1, P.p)
     c = SA @ b
     W = fwd["W"]
-    ys, xs = fwd["ys"], fwd["xs"]
+    ys, xs, yrs = fwd["ys"], fwd["xs"], fwd["yrs"]
     K = len(ys) - 1
     ell = W.shape[1] - K
     # U = S_A A W, V = S_L L W, column by column (the sketched columns of eq. updqr)
@@ -69,6 +82,9 @@ def sgks_vjp(problem, iters, xbar, fwd=None):
     def H(v):   # A^T A + lambda L^T L
         return Aop.adjoint(Aop.apply(v)) + lam * Lop.adjoint(Lop.apply(v))
 
+    def LtL(v):
+        return Lop.adjoint(Lop.apply(v))
+
     Wbar = np.zeros_like(W)
     bbar = np.zeros(P.m)
     cbar = np.zeros(len(c))
@@ -76,10 +92,26 @@ def sgks_vjp(problem, iters, xbar, fwd=None):
     xbar_j = np.array(xbar, dtype=np.float64)
     for j in range(K, -1, -1):
         d = ell + j
-        Wj, Uj, Vj, y = W[:, :d], U[:, :d], V[:, :d], ys[j]
+        Wj, Uj, Vj = W[:, :d], U[:, :d], V[:, :d]
+        chain = yrs[j]
         ybar = Wj.T @ xbar_j
-        Wbar[:, :d] += np.outer(xbar_j, y)
+        Wbar[:, :d] += np.outer(xbar_j, chain[-1])
         G = Uj.T @ Uj + lam * (Vj.T @ Vj)
+        for r in range(len(chain) - 1, 0, -1):   # refinement steps, last first
+            yprev = chain[r - 1]
+            delta = yprev - chain[r]
+            w = np.linalg.solve(G, ybar)
+            Ww = Wj @ w
+            AWw = Aop.apply(Ww)
+            HWw = Aop.adjoint(AWw) + lam * LtL(Ww)
+            xprev = Wj @ yprev
+            rho = Aop.adjoint(Aop.apply(xprev) - b) + lam * LtL(xprev)
+            bbar += AWw
+            lg, Wg = _preconditioner_terms(Uj, Vj, lam, w, delta, AtSAt, LtSLt)
+            lbar += lg - float(Ww @ LtL(xprev))
+            Wbar[:, :d] += Wg - np.outer(rho, w) - np.outer(HWw, yprev)
+            ybar = ybar - Wj.T @ HWw
+        y = chain[0]
         z = np.linalg.solve(G, ybar)
         Uy, Uz, Vy, Vz = Uj @ y, Uj @ z, Vj @ y, Vj @ z
         cbar += Uz
@@ -111,11 +143,21 @@ def sgks_vjp(problem, iters, xbar, fwd=None):
     return dict(bbar=bbar, lambdabar=lbar, x=xs[-1], fwd=fwd)
 
 
-def loss_and_grad(problem, iters, target=None):
-    """l = ||x_K - target||^2 (target = x_true by default) and its gradient w.r.t. (b, lambda)."""
+def _preconditioner_terms(Uj, Vj, lam, w, delta, AtSAt, LtSLt):
+    """The contribution of G_j = U_j^T U_j + lambda V_j^T V_j (through W_j and lambda) to the
+    adjoint of one refinement step: lambdabar += (V w).(V delta), and Wbar gains
+    (A^T S_A^T U delta + lambda L^T S_L^T V delta) w^T + (A^T S_A^T U w + lambda L^T S_L^T V w) delta^T."""
+    a1 = AtSAt(Uj @ delta) + lam * LtSLt(Vj @ delta)
+    a2 = AtSAt(Uj @ w) + lam * LtSLt(Vj @ w)
+    return float((Vj @ w) @ (Vj @ delta)), np.outer(a1, w) + np.outer(a2, delta)
+
+
+def loss_and_grad(problem, iters, target=None, n_refine=0):
+    """l = ||x_K - target||^2 (target = x_true by default) and its gradient w.r.t. (b, lambda),
+    for the solve with n_refine refinement steps per iteration."""
     P = problem
     t = np.asarray(P.x_true if target is None else target, dtype=np.float64)
-    fwd = sgks(P, iters=iters, n_refine=0, record_x=True)
+    fwd = sgks(P, iters=iters, n_refine=n_refine, record_x=True)
     x = fwd["xs"][-1]
     g = sgks_vjp(P, iters, 2.0 * (x - t), fwd=fwd)
     return float(np.sum((x - t) ** 2)), g["bbar"], g["lambdabar"]

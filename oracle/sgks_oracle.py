@@ -427,22 +427,26 @@ def sgks(problem, iters=None, n_refine=None, sketched=True, cgs_passes=2, tol=0.
         append(W[:, j])
 
     def solve():
+        # the projected solve and its refinement steps; returns y_k and the chain y^0 .. y^R
         y, T = projected_solve(RA, RL, dA, lam)
+        chain = [y]
         for _ in range(n_refine):
             y = refine_step(Aop, Lop, b, lam, W, y, T)
-        return y
+            chain.append(y)
+        return y, chain
 
     xt = np.asarray(P.x_true, dtype=np.float64)
     nxt = np.linalg.norm(xt)
-    y = solve()
+    y, chain = solve()
     x = W @ y
     rc, rre, xs = [], [np.linalg.norm(x - xt) / nxt], [x.copy()] if record_x else None
     ys = [y.copy()] if record_x else None
+    yrs = [[c.copy() for c in chain]] if record_x else None
     for k in range(1, iters + 1):
         r = gradient(Aop, Lop, b, lam, x)
         W = np.concatenate([W, r[:, None]], axis=1)
         append(r)
-        y = solve()
+        y, chain = solve()
         x_new = W @ y
         rc.append(np.linalg.norm(x_new - x) / np.linalg.norm(x))
         rre.append(np.linalg.norm(x_new - xt) / nxt)
@@ -450,6 +454,7 @@ def sgks(problem, iters=None, n_refine=None, sketched=True, cgs_passes=2, tol=0.
         if record_x:
             xs.append(x.copy())
             ys.append(y.copy())
+            yrs.append([c.copy() for c in chain])
         if tol > 0 and rc[-1] < tol:
             break
     out = dict(x=x, y=y, W=W, rc=np.array(rc), rre=np.array(rre), breakdowns=breakdowns,
@@ -457,6 +462,7 @@ def sgks(problem, iters=None, n_refine=None, sketched=True, cgs_passes=2, tol=0.
     if record_x:
         out["xs"] = xs
         out["ys"] = ys
+        out["yrs"] = yrs   # per iteration: y before refinement, then after each refinement step
     if record_state:
         out.update(QA=QA, RA=RA, QL=QL, RL=RL, dA=dA, Sb=Sb)
     return out

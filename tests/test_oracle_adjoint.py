@@ -14,13 +14,13 @@ from workloads import small_problem
 from workloads.problem import SketchDesc
 
 
-def _fd(P, it, h=1e-6, seed=3, ndir=2):
-    L0, bb, lb = loss_and_grad(P, it)
+def _fd(P, it, h=1e-6, seed=3, ndir=2, n_refine=0):
+    L0, bb, lb = loss_and_grad(P, it, n_refine=n_refine)
     lam0 = P.lam
     P.lam = lam0 + h
-    lp = loss_and_grad(P, it)[0]
+    lp = loss_and_grad(P, it, n_refine=n_refine)[0]
     P.lam = lam0 - h
-    lm = loss_and_grad(P, it)[0]
+    lm = loss_and_grad(P, it, n_refine=n_refine)[0]
     P.lam = lam0
     out = [(lb, (lp - lm) / (2 * h))]
     rng = np.random.default_rng(seed)
@@ -28,9 +28,9 @@ def _fd(P, it, h=1e-6, seed=3, ndir=2):
     for _ in range(ndir):
         dv = rng.standard_normal(P.m)
         P.b = b0 + h * dv
-        lp = loss_and_grad(P, it)[0]
+        lp = loss_and_grad(P, it, n_refine=n_refine)[0]
         P.b = b0 - h * dv
-        lm = loss_and_grad(P, it)[0]
+        lm = loss_and_grad(P, it, n_refine=n_refine)[0]
         P.b = b0
         out.append((float(bb @ dv), (lp - lm) / (2 * h)))
     return out
@@ -42,6 +42,31 @@ def test_adjoint_matches_central_differences(kind, iters):
     P.n_refine = 0
     for an, fd in _fd(P, iters):
         assert abs(an - fd) <= 1e-6 * abs(fd) + 1e-9, (kind, an, fd)
+
+
+@pytest.mark.parametrize("kind,iters,n_refine", [("seismic2d", 10, 1), ("deblur2d", 8, 2), ("ct2d", 8, 2),
+                                                  ("deconv1d", 8, 3)])
+def test_adjoint_with_refinement_matches_central_differences(kind, iters, n_refine):
+    """The sweep through the q = 0 refinement steps (their dependence on y, W, b and lambda,
+    including lambda and W inside the sketched preconditioner G) against central differences
+    of the refined forward map."""
+    P = small_problem(kind, iters=iters)
+    for an, fd in _fd(P, iters, n_refine=n_refine):
+        assert abs(an - fd) <= 1e-6 * abs(fd) + 1e-9, (kind, n_refine, an, fd)
+
+
+def test_refinement_adjoint_terms_are_all_needed(monkeypatch):
+    """A planted mistake: dropping the preconditioner's dependence on W and lambda (the G_j terms
+    of the refinement adjoint) must fail the finite-difference pin, so the pin is not blind to
+    those terms."""
+    import oracle.sgks_adjoint as OA
+    P = small_problem("seismic2d", iters=6)
+    def no_g_terms(Uj, Vj, lam, w, delta, AtSAt, LtSLt):
+        return 0.0, np.zeros((AtSAt(Uj @ w).shape[0], len(w)))
+
+    monkeypatch.setattr(OA, "_preconditioner_terms", no_g_terms)
+    errs = [abs(an - fd) / abs(fd) for an, fd in _fd(P, 6, n_refine=2)]
+    assert max(errs) > 1e-4, errs
 
 
 def test_adjoint_equals_closed_form_once_basis_spans_space():
