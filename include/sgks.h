@@ -112,9 +112,10 @@ typedef struct sgks_options {
     int32_t flags;        /* bit 0 (SGKS_FLAG_GLOBAL_SMALL): run the FP64 QR append and projected
                              solve with the global-memory kernels instead of the on-chip cluster
                              kernels (chosen automatically when the on-chip slices do not fit).
-                             bit 1 (SGKS_FLAG_RECORD): keep y_k of every iteration so that
-                             sgks_backward can differentiate the solve; needs n_refine = 0,
-                             precision FP64 or FP32 and the on-chip kernels.
+                             bit 1 (SGKS_FLAG_RECORD): keep y_k of every iteration (and the
+                             y after each refinement step) so that sgks_backward can
+                             differentiate the solve; needs precision FP64 or FP32 and the
+                             on-chip kernels.
                              bit 2 (SGKS_FLAG_GKS): run GKS (Algorithm 1) instead: orthonormal
                              basis V_k (gradient column orthogonalised, a second pass when the
                              loss ratio of eq. loss_criterion is >= 1e-10, normalised), full-size
@@ -315,7 +316,9 @@ int sgks_time_class(sgks_handle* h, int32_t cls, int32_t reps, double* us_out);
  * (sgks_create / sgks_reset) produced, and xbar = dl/dx_K (device, n values of the solver
  * precision), write bbar = dl/db (device, m values of the solver precision) and *lambda_bar =
  * dl/dlambda (host).  This is the exact derivative of the map (b, lambda) -> x_K of Algorithm 2
- * (without refinement), x_K = W_K y_K with every basis column r_j = A^T (A x_{j-1} - b) +
+ * with the handle's n_refine q = 0 refinement steps per iteration (Sec. 3.1: y^r = y^{r-1} -
+ * G_k^{-1} W_k^T rho(W_k y^{r-1}), G_k = U_k^T U_k + lambda V_k^T V_k, rho the residual of the
+ * normal equations), x_K = W_K y_K with every basis column r_j = A^T (A x_{j-1} - b) +
  * lambda L^T L x_{j-1} depending on the earlier iterates (eq. gradient) and W_0 spanning
  * K_l(A^T A, A^T b).  It is computed by a reverse sweep over the iterations that reuses the
  * stored basis W and the stored inverse of the stacked triangular factor of

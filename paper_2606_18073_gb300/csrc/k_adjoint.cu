@@ -16,13 +16,15 @@
 
 namespace sgks {
 
-// y_hist[(iter + offset) * dmax + j] = y[j], j < d (iter, d from the device scalars)
+// y_hist[((iter + offset) * nsub + sub) * dmax + j] = y[j], j < d (iter, d from the device scalars):
+// sub = 0 the projected solve's y, sub = r the y after refinement step r
 __global__ void kd_record_y(const DevScalars* sc, const double* __restrict__ y, double* yhist, int dmax, int offset,
-                            int max_rows) {
+                            int max_rows, int sub, int nsub) {
     if (sc->stop) return;
     const int row = sc->iter + offset;
     if (row >= max_rows) return;
-    for (int j = threadIdx.x; j < sc->d; j += blockDim.x) yhist[(size_t)row * dmax + j] = y[j];
+    double* out = yhist + ((size_t)row * nsub + sub) * dmax;
+    for (int j = threadIdx.x; j < sc->d; j += blockDim.x) out[j] = y[j];
 }
 
 // out[i] = sum_{j < d} W[j * n + i] c[j]  (FP64 accumulation, fixed column order)
@@ -39,7 +41,7 @@ __global__ void __launch_bounds__(kThreads) kd_gemv_n(const T* __restrict__ W, i
     }
 }
 
-// Wb[j * n + i] += a[i] p[j] + q[i] r[j], j < d
+// Wb[j * n + i] += a[i] p[j] + q[i] r[j], j < d (q = nullptr: the first term only)
 template <typename T>
 __global__ void __launch_bounds__(kThreads) kd_rank2(T* Wb, int64_t n, int d, const T* __restrict__ a,
                                                      const double* __restrict__ p, const T* __restrict__ q,
@@ -48,7 +50,7 @@ __global__ void __launch_bounds__(kThreads) kd_rank2(T* Wb, int64_t n, int d, co
          t += (int64_t)gridDim.x * kThreads) {
         const int j = (int)(t / n);
         const int64_t i = t - (int64_t)j * n;
-        Wb[t] = (T)((double)Wb[t] + (double)a[i] * p[j] + (double)q[i] * r[j]);
+        Wb[t] = (T)((double)Wb[t] + (double)a[i] * p[j] + (q ? (double)q[i] * r[j] : 0.0));
     }
 }
 
@@ -186,8 +188,8 @@ static int agrid(int64_t work) {
 }
 
 cudaError_t launchd_record_y(const DevScalars* sc, const double* y, double* yhist, int dmax, int offset, int rows,
-                             cudaStream_t st) {
-    kd_record_y<<<1, 256, 0, st>>>(sc, y, yhist, dmax, offset, rows);
+                             int sub, int nsub, cudaStream_t st) {
+    kd_record_y<<<1, 256, 0, st>>>(sc, y, yhist, dmax, offset, rows, sub, nsub);
     return cudaGetLastError();
 }
 

@@ -101,10 +101,11 @@ struct EngineBase {
         (void)xbar; (void)bbar; (void)lbar_host; (void)K;
         return cudaErrorNotSupported;
     }
-    cudaError_t record_y(int offset) {
+    // y of the current iteration after `sub` refinement steps (sub = 0: the projected solve's y)
+    cudaError_t record_y(int offset, int sub) {
         if (!yhist) return cudaSuccess;
         g_launches.fetch_add(1);
-        return launchd_record_y(S.sc, S.y, yhist, D.dmax, offset, D.max_iters + 1, pst);
+        return launchd_record_y(S.sc, S.y, yhist, D.dmax, offset, D.max_iters + 1, sub, n_refine + 1, pst);
     }
 };
 
@@ -131,9 +132,12 @@ struct Engine : EngineBase {
             e = timed(PK_SKETCH, j, [&] { return sketch(); });
             if (e == cudaSuccess) e = small_append(j);
         }
-        if (e == cudaSuccess) e = record_y(0);
+        if (e == cudaSuccess) e = record_y(0, 0);
         host_d = D.ell;
-        for (int r = 0; r < n_refine && e == cudaSuccess; ++r) e = refine();
+        for (int r = 0; r < n_refine && e == cudaSuccess; ++r) {
+            e = refine();
+            if (e == cudaSuccess) e = record_y(0, r + 1);
+        }
         if (e == cudaSuccess) e = timed(PK_COMBINE, host_d, [&] { return launch_combine<T>(D, B, S, 2, st); });
         return e;
     }
@@ -219,9 +223,12 @@ struct Engine : EngineBase {
         cudaError_t e = timed(PK_GRAD_APPEND, d, [&] { return launch_gradient<T, V>(D, A, L, B, S, false, st); });
         if (e == cudaSuccess) e = timed(PK_SKETCH, d, [&] { return sketch(); });
         if (e == cudaSuccess) e = small_append(d);
-        if (e == cudaSuccess) e = record_y(1);
+        if (e == cudaSuccess) e = record_y(1, 0);
         host_d = d + 1;
-        for (int r = 0; r < n_refine && e == cudaSuccess; ++r) e = refine();
+        for (int r = 0; r < n_refine && e == cudaSuccess; ++r) {
+            e = refine();
+            if (e == cudaSuccess) e = record_y(1, r + 1);
+        }
         if (e == cudaSuccess) e = timed(PK_COMBINE, host_d, [&] { return launch_combine<T>(D, B, S, 1, st); });
         return e;
     }
@@ -232,6 +239,10 @@ struct Engine : EngineBase {
         T *P = nullptr, *Q = nullptr, *tm = nullptr, *tp = nullptr, *Kv = nullptr, *Kb = nullptr;
         double *uy = nullptr, *uz = nullptr, *vy = nullptr, *vz = nullptr, *cb = nullptr, *st = nullptr;
         double *ybar = nullptr, *z = nullptr, *part = nullptr, *acc = nullptr, *R0 = nullptr, *Ri = nullptr;
+        // refinement steps: w = G^{-1} ybar, delta = y^{r-1} - y^r, W^T v scratch; W w, H W w,
+        // W y^{r-1}, rho(W y^{r-1}) and the two rank-2 left vectors
+        double *w = nullptr, *dl = nullptr, *td = nullptr;
+        T *Ww = nullptr, *HWw = nullptr, *xp = nullptr, *rho = nullptr, *a1 = nullptr, *a2 = nullptr;
         int* err = nullptr;
     } bw;
 
@@ -255,6 +266,10 @@ struct Engine : EngineBase {
         A1(&bw.uy, s); A1(&bw.uz, s); A1(&bw.vy, s); A1(&bw.vz, s); A1(&bw.cb, s); A1(&bw.st, s);
         A1(&bw.ybar, dm); A1(&bw.z, dm); A1(&bw.part, (size_t)nbS * dm); A1(&bw.acc, 2);
         A1(&bw.R0, ell * ell); A1(&bw.Ri, ell * ell); A1(&bw.err, 1);
+        if (n_refine > 0) {
+            A1(&bw.w, dm); A1(&bw.dl, dm); A1(&bw.td, dm);
+            A1(&bw.Ww, n); A1(&bw.HWw, n); A1(&bw.xp, n); A1(&bw.rho, n); A1(&bw.a1, n); A1(&bw.a2, n);
+        }
         if (e != cudaSuccess) bw.Wb = nullptr;
         return e;
     }
@@ -278,10 +293,64 @@ struct Engine : EngineBase {
                                      D.sketch_scale, u, out, bw.err, st);
     }
 
+    // Adjoint of one refinement step y^r = y^{r-1} - G^{-1} W^T rho(W y^{r-1}), rho(x) = H x - A^T b,
+    // H = A^T A + lambda L^T L, for ybar = bw.ybar (updated in place to ybar^{r-1}); with
+    // w = G^{-1} ybar, delta = y^{r-1} - y^r:
+    //   ybar -= W^T H W w;  bbar += A W w;
+    //   lambdabar += (V w).(V delta) - (W w).(L^T L W y^{r-1});
+    //   Wbar += (A^T S_A^T U delta + lambda L^T S_L^T V delta - rho) w^T
+    //           + (A^T S_A^T U w + lambda L^T S_L^T V w) delta^T - (H W w) (y^{r-1})^T.
+    cudaError_t bw_refine_step(int d, const double* yprev, const double* ycur, T* bbar) {
+        const int64_t n = D.n;
+        const double lam = D.lam;
+        cudaError_t e = cudaSuccess;
+        auto L1 = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+        L1(launchd_axpby_d(bw.dl, yprev, 1.0, ycur, -1.0, d, st));
+        L1(launchd_solve_G(S.X, S.Xr, D.dmax, d, bw.ybar, bw.w, st));
+        L1(launchd_gemv_n<T>(B.W, n, d, bw.w, bw.Ww, st));
+        L1(bw_apply(SGKS_APPLY_A, bw.Ww, bw.tm));
+        L1(launchd_axpby<T>(bbar, bbar, 1.0, bw.tm, 1.0, D.m, st));
+        L1(bw_apply(SGKS_APPLY_AT, bw.tm, bw.HWw));
+        L1(bw_apply(SGKS_APPLY_LTL, bw.Ww, bw.t1));
+        L1(launchd_axpby<T>(bw.HWw, bw.HWw, 1.0, bw.t1, lam, n, st));
+        L1(bw_dots(B.W, d, bw.HWw, bw.td));
+        L1(launchd_axpby_d(bw.ybar, bw.ybar, 1.0, bw.td, -1.0, d, st));
+        // rho(W y^{r-1}) and lambdabar -= (W w).(L^T L W y^{r-1})
+        L1(launchd_gemv_n<T>(B.W, n, d, yprev, bw.xp, st));
+        L1(bw_apply(SGKS_APPLY_A, bw.xp, bw.tm));
+        L1(launchd_axpby<T>(bw.tm, bw.tm, 1.0, b_own, -1.0, D.m, st));
+        L1(bw_apply(SGKS_APPLY_AT, bw.tm, bw.rho));
+        L1(bw_apply(SGKS_APPLY_LTL, bw.xp, bw.t1));
+        L1(launchd_axpby<T>(bw.rho, bw.rho, 1.0, bw.t1, lam, n, st));
+        L1(launch_dots<T>(bw.Ww, n, 1, bw.t1, bw.part, nbS, st));
+        L1(launchd_acc_parts(bw.part, nbS, -1.0, bw.acc, st));
+        // the preconditioner's dependence on W and lambda: U w, U delta, V w, V delta
+        L1(launchd_qr_products(S, D.s, D.dmax, d, bw.w, bw.dl, bw.uy, bw.uz, bw.vy, bw.vz, st));
+        L1(launchd_dot_acc(bw.vy, bw.vz, D.s, 1.0, bw.acc, st));
+        L1(bw_sketch_adj(true, bw.uz, bw.tm));      // a1 = A^T S_A^T U delta + lambda L^T S_L^T V delta
+        L1(bw_apply(SGKS_APPLY_AT, bw.tm, bw.a1));
+        L1(bw_sketch_adj(false, bw.vz, bw.tp));
+        L1(bw_apply(SGKS_APPLY_LT, bw.tp, bw.t1));
+        L1(launchd_axpby<T>(bw.a1, bw.a1, 1.0, bw.t1, lam, n, st));
+        L1(launchd_axpby<T>(bw.a1, bw.a1, 1.0, bw.rho, -1.0, n, st));
+        L1(bw_sketch_adj(true, bw.uy, bw.tm));      // a2 = A^T S_A^T U w + lambda L^T S_L^T V w
+        L1(bw_apply(SGKS_APPLY_AT, bw.tm, bw.a2));
+        L1(bw_sketch_adj(false, bw.vy, bw.tp));
+        L1(bw_apply(SGKS_APPLY_LT, bw.tp, bw.t1));
+        L1(launchd_axpby<T>(bw.a2, bw.a2, 1.0, bw.t1, lam, n, st));
+        L1(launchd_rank2<T>(bw.Wb, n, d, bw.a1, bw.w, bw.a2, bw.dl, st));
+        L1(launchd_axpby<T>(bw.t1, bw.HWw, -1.0, nullptr, 0.0, n, st));
+        L1(launchd_rank2<T>(bw.Wb, n, d, bw.t1, yprev, nullptr, nullptr, st));
+        g_launches.fetch_add(19);
+        return e;
+    }
+
     // The reverse sweep of the derivative of x_K (see sgks_backward in the header):
-    //   for j = K .. 0 (d = ell + j):  ybar = W_j^T xbar_j;  z = G_j^{-1} ybar;
+    //   for j = K .. 0 (d = ell + j):  ybar = W_j^T xbar_j;  with refinement, Wbar += xbar_j (y^R)^T and
+    //     ybar passes back through the refinement steps (bw_refine_step) to the projected solve's y_j = y^0;
+    //     then z = G_j^{-1} ybar;
     //     c-bar += U_j z;  lambdabar -= (V_j z).(V_j y_j);
-    //     Wbar[:, :d] += (xbar_j + Q) y_j^T + P z^T with P = A^T S_A^T (c - U_j y_j) - lambda L^T S_L^T V_j y_j,
+    //     Wbar[:, :d] += (xbar_j [R = 0 only] + Q) y_j^T + P z^T with P = A^T S_A^T (c - U_j y_j) - lambda L^T S_L^T V_j y_j,
     //                                                   Q = -(A^T S_A^T U_j z + lambda L^T S_L^T V_j z);
     //     column d-1 (r_j): xbar_{j-1} = (A^T A + lambda L^T L) rbar, bbar -= A rbar,
     //                       lambdabar += rbar . L^T L x_{j-1};
@@ -303,10 +372,18 @@ struct Engine : EngineBase {
         if (e == cudaSuccess) e = cudaMemsetAsync(bbar, 0, sizeof(T) * D.m, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(bw.xb, xbar, sizeof(T) * n, cudaMemcpyDeviceToDevice, st);
         auto L1 = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+        const int NS = n_refine + 1;
+        auto yrow = [&](int j, int r) { return yhist + ((size_t)j * NS + r) * D.dmax; };
         for (int j = K; j >= 0 && e == cudaSuccess; --j) {
             const int d = ell + j;
-            const double* yj = yhist + (size_t)j * D.dmax;
+            const double* yj = yrow(j, 0);   // the projected solve's y^0
             L1(bw_dots(W, d, bw.xb, bw.ybar));
+            if (n_refine > 0) {
+                // x_j = W_j y^R: Wbar += xbar_j (y^R)^T; then the refinement steps, last first
+                L1(launchd_rank2<T>(bw.Wb, n, d, bw.xb, yrow(j, n_refine), nullptr, nullptr, st));
+                g_launches.fetch_add(1);
+                for (int r = n_refine; r >= 1 && e == cudaSuccess; --r) L1(bw_refine_step(d, yrow(j, r - 1), yrow(j, r), bbar));
+            }
             L1(launchd_solve_G(S.X, S.Xr, D.dmax, d, bw.ybar, bw.z, st));
             // U_j y, U_j z, V_j y, V_j z from the sketched QR factors (U_j = Q_A R_A, V_j = Q_L R_L)
             L1(launchd_qr_products(S, D.s, D.dmax, d, yj, bw.z, bw.uy, bw.uz, bw.vy, bw.vz, st));
@@ -327,8 +404,12 @@ struct Engine : EngineBase {
             L1(bw_sketch_adj(false, bw.vz, bw.tp));
             L1(bw_apply(SGKS_APPLY_LT, bw.tp, bw.t1));
             L1(launchd_axpby<T>(bw.Q, bw.Q, -1.0, bw.t1, -lam, n, st));
-            L1(launchd_axpby<T>(bw.t2, bw.xb, 1.0, bw.Q, 1.0, n, st));
-            L1(launchd_rank2<T>(bw.Wb, n, d, bw.t2, yj, bw.P, bw.z, st));
+            if (n_refine == 0) {   // y^0 = y_j: the xbar_j y_j^T term joins Q y_j^T
+                L1(launchd_axpby<T>(bw.t2, bw.xb, 1.0, bw.Q, 1.0, n, st));
+                L1(launchd_rank2<T>(bw.Wb, n, d, bw.t2, yj, bw.P, bw.z, st));
+            } else {
+                L1(launchd_rank2<T>(bw.Wb, n, d, bw.Q, yj, bw.P, bw.z, st));
+            }
             g_launches.fetch_add(4);
             if (j == 0) break;
             const T* rbar = bw.Wb + (size_t)(d - 1) * n;
@@ -338,7 +419,7 @@ struct Engine : EngineBase {
             L1(bw_apply(SGKS_APPLY_LTL, rbar, bw.t1));
             L1(launchd_axpby<T>(bw.xb, bw.xb, 1.0, bw.t1, lam, n, st));
             // lambdabar += rbar . L^T L x_{j-1}
-            L1(launchd_gemv_n<T>(W, n, d - 1, yhist + (size_t)(j - 1) * D.dmax, bw.t2, st));
+            L1(launchd_gemv_n<T>(W, n, d - 1, yrow(j - 1, n_refine), bw.t2, st));   // x_{j-1}
             L1(bw_apply(SGKS_APPLY_LTL, bw.t2, bw.t1));
             L1(launch_dots<T>(rbar, n, 1, bw.t1, bw.part, nbS, st));
             L1(launchd_acc_parts(bw.part, nbS, 1.0, bw.acc, st));
@@ -973,7 +1054,7 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     AL(S.rre_hist, (size_t)o.max_iters + 1);
     AL(S.sc, 1);
     AL(E->part_setup, (size_t)E->nbS * 8);
-    if (o.flags & SGKS_FLAG_RECORD) AL(E->yhist, (size_t)(o.max_iters + 1) * dm);
+    if (o.flags & SGKS_FLAG_RECORD) AL(E->yhist, (size_t)(o.max_iters + 1) * (o.n_refine + 1) * dm);
     if (EG) {
         if (!D.fast_small) return fail(h, SGKS_ERR_INVALID, "GKS needs the on-chip stacked solve (sketch_rows too large)");
         const int64_t hmax = std::max<int64_t>(std::max<int64_t>(D.n, D.m), D.p);
@@ -1088,7 +1169,6 @@ int sgks::validate_problem(const sgks_op* A, const sgks_reg* L, const void* b, d
         if (o.ell + o.max_iters > 1024) return bad("SGKS_FLAG_GKS needs ell + max_iters <= 1024");
     }
     if (o.flags & SGKS_FLAG_RECORD) {
-        if (o.n_refine != 0) return bad("SGKS_FLAG_RECORD needs n_refine = 0");
         if (o.precision == SGKS_PREC_FP32X) return bad("SGKS_FLAG_RECORD supports the FP64 and FP32 forms");
         if (o.flags & SGKS_FLAG_GLOBAL_SMALL) return bad("SGKS_FLAG_RECORD needs the on-chip small kernels");
     }

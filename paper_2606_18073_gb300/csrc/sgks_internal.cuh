@@ -866,7 +866,7 @@ int batch_combine_grid(const BDims& D, size_t elem);
 
 // ------------------------------------------------------------------- reverse sweep (k_adjoint.cu)
 cudaError_t launchd_record_y(const DevScalars* sc, const double* y, double* yhist, int dmax, int offset, int rows,
-                             cudaStream_t st);
+                             int sub, int nsub, cudaStream_t st);
 template <typename T>
 cudaError_t launchd_gemv_n(const T* W, int64_t n, int d, const double* c, T* out, cudaStream_t st);
 template <typename T>

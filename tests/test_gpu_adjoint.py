@@ -1,9 +1,10 @@
 """Differentiable form: sgks_backward against the FP64 oracle's reverse sweep and against
 central finite differences of the GPU forward map; the torch autograd Function on top.
 
-Loss l = ||x_K - x_true||^2 after K iterations without refinement.  In FP64 the GPU derivative
-tracks the oracle's to 1e-7 (both are exact derivatives of forward maps that agree to the
-method's rounding floor); the FP32 form is compared loosely.
+Loss l = ||x_K - x_true||^2 after K iterations, without refinement or with n_refine q = 0
+refinement steps per iteration (Sec. 3.1).  In FP64 the GPU derivative tracks the oracle's to
+1e-7 (both are exact derivatives of forward maps that agree to the method's rounding floor);
+the FP32 form is compared loosely.
 """
 import numpy as np
 import pytest
@@ -40,9 +41,9 @@ def gpu_loss_grad(G, S, P, b, iters):
     return loss, bbar.double().cpu().numpy(), lbar
 
 
-def recording_solver(G, P, prec):
+def recording_solver(G, P, prec, n_refine=0):
     kw = G.device_inputs(P, prec)
-    kw["n_refine"] = 0
+    kw["n_refine"] = n_refine
     return G.Solver(**kw, record=True), kw["b"]
 
 
@@ -83,6 +84,52 @@ def test_backward_matches_gpu_finite_differences(G):
     assert abs(lbar - fd) <= 1e-6 * abs(fd)
     rng = np.random.default_rng(5)
     for _ in range(3):
+        dv = torch.from_numpy(rng.standard_normal(P.m)).cuda()
+        fd = (loss_at(b + h * dv, lam0) - loss_at(b - h * dv, lam0)) / (2 * h)
+        an = float(bbar @ dv.cpu().numpy())
+        assert abs(an - fd) <= 1e-6 * abs(fd) + 1e-10
+    S.close()
+
+
+@pytest.mark.parametrize("kind,iters,n_refine", [("seismic2d", 12, 1), ("deblur2d", 10, 2), ("ct2d", 8, 1),
+                                                  ("deconv1d", 8, 3), ("dynct", 8, 2)])
+def test_backward_with_refinement_matches_oracle(G, kind, iters, n_refine):
+    """Held to 1e-7, or to 10 x the oracle's own rounding floor where that is larger: the terms
+    of a refinement step carry y^{r-1} - y^r, a difference at the rounding level once the steps
+    have converged (on the 1-D deconvolution with 3 steps the oracle against itself, with
+    rounding-level perturbations of its gradient columns, differs by ~1e-7 in dl/dlambda)."""
+    P = small_problem(kind, iters=iters)
+    S, b = recording_solver(G, P, "fp64", n_refine)
+    loss, bbar, lbar = gpu_loss_grad(G, S, P, b, iters)
+    L0, bb, lb = loss_and_grad(P, iters, n_refine=n_refine)
+    _, _, fb, fl = adjoint_floor(P, iters, n_refine=n_refine)
+    assert abs(loss - L0) <= 1e-9 * L0
+    assert rel(bbar, bb) < max(1e-7, 10.0 * fb)
+    assert abs(lbar - lb) <= max(1e-7, 10.0 * fl) * abs(lb)
+    # the refinement steps change the derivative: the one without them is measurably different
+    _, bb0, _ = loss_and_grad(P, iters, n_refine=0)
+    assert rel(bb0, bb) > 1e3 * rel(bbar, bb)
+    S.close()
+
+
+def test_backward_with_refinement_matches_gpu_finite_differences(G):
+    P = small_problem("deblur2d", iters=10)
+    S, b = recording_solver(G, P, "fp64", 2)
+    _, bbar, lbar = gpu_loss_grad(G, S, P, b, 10)
+    h = 1e-6
+    lam0 = P.lam
+
+    def loss_at(bv, lam):
+        S.set_lambda(lam)
+        S.reset(bv)
+        S.solve(10)
+        x = S.x().cpu().numpy()
+        return float(np.sum((x - np.asarray(P.x_true)) ** 2))
+
+    fd = (loss_at(b, lam0 * (1 + h)) - loss_at(b, lam0 * (1 - h))) / (2 * h * lam0)
+    assert abs(lbar - fd) <= 1e-6 * abs(fd)
+    rng = np.random.default_rng(6)
+    for _ in range(2):
         dv = torch.from_numpy(rng.standard_normal(P.m)).cuda()
         fd = (loss_at(b + h * dv, lam0) - loss_at(b - h * dv, lam0)) / (2 * h)
         an = float(bbar @ dv.cpu().numpy())
@@ -133,11 +180,10 @@ def test_backward_errors(G):
         S.backward(torch.zeros(P.n, dtype=torch.float64, device="cuda"))
     assert ei.value.code == G._lib.SGKS_ERR_STATE
     S.close()
-    kw["n_refine"] = 1
+    kx = G.device_inputs(P, "fp32x")        # the recorded forward keeps W in the solve precision
     with pytest.raises(G._lib.SGKSError) as ei:
-        G.Solver(**kw, record=True)
+        G.Solver(**kx, record=True)
     assert ei.value.code == G._lib.SGKS_ERR_INVALID
-    kw["n_refine"] = 0
     S = G.Solver(**kw, record=True)
     S.solve(4)
     S.set_lambda(2.0 * P.lam)
@@ -149,16 +195,16 @@ def test_backward_errors(G):
     S.close()
 
 
-def adjoint_floor(P, iters, seed=0):
+def adjoint_floor(P, iters, seed=0, n_refine=0):
     """Rounding floor of the reverse sweep itself: the oracle's gradient against the oracle's
     gradient with every forward gradient column perturbed by (1 + 2^-53 N(0, 1))."""
     from oracle import sgks_oracle as OS
-    _, b0, l0 = loss_and_grad(P, iters)
+    _, b0, l0 = loss_and_grad(P, iters, n_refine=n_refine)
     rng = np.random.default_rng(seed)
     orig = OS.gradient
     OS.gradient = lambda A, L, b, lam, x: orig(A, L, b, lam, x) * (1.0 + 2.0 ** -53 * rng.standard_normal(P.n))
     try:
-        _, b1, l1 = loss_and_grad(P, iters)
+        _, b1, l1 = loss_and_grad(P, iters, n_refine=n_refine)
     finally:
         OS.gradient = orig
     return b0, l0, rel(b1, b0), abs(l1 - l0) / abs(l0)
