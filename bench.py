@@ -39,7 +39,8 @@ WORKLOAD = ("deblur2d: 256x256 image, 9x9 Gaussian PSF sigma=2 zero boundary, gr
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 100: about 1 s of GPU work; 20 for --impl reference)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="deblur2d")
@@ -51,7 +52,10 @@ def parse():
                     help="run one batched solve of a reduced CT / dynamic-CT batch (for profiler captures) and exit")
     ap.add_argument("--batch-size", type=int, default=16)
     ap.add_argument("--batch-iters", type=int, default=40)
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 20 if args.impl == "reference" else 100
+    return args
 
 
 def dist_env():
@@ -110,6 +114,10 @@ def run_cpu_worker(name, iters):
 
 # ------------------------------------------------------------------------------ clocks
 class ClockSampler:
+    """nvidia-smi samples every 100 ms, read by a thread with host timestamps.  start() waits for
+    the first sample, so the sampler is running before the timed region opens; stop() keeps only
+    the samples taken between begin() and end() (the region's host-side bounds, each taken right
+    after a device synchronize)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -117,27 +125,51 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.monotonic(), line))
 
     def start(self):
+        import threading
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        deadline = time.monotonic() + 10.0
+        while not self.lines and time.monotonic() < deadline and self.proc.poll() is None:
+            time.sleep(0.01)
+
+    def begin(self):
+        self.t0 = time.monotonic()
+
+    def end(self):
+        self.t1 = time.monotonic()
 
     def stop(self):
         if not self.proc:
             return None
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
+            self.proc.wait()
+        self.thread.join(timeout=5)
+        t0 = self.t0 if self.t0 is not None else float("-inf")
+        t1 = self.t1 if self.t1 is not None else float("inf")
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.splitlines():
+        for t, line in self.lines:
+            if not (t0 <= t <= t1):
+                continue
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -152,7 +184,8 @@ class ClockSampler:
         if not sm:
             return None
         sm.sort()
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm),
+                "window_s": round(t1 - t0, 3), "interval_ms": 100}
 
 
 # -------------------------------------------------------------------------- byte models
@@ -285,6 +318,7 @@ def main():
     launches0 = G.kernel_launches()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize(dev)
+    clk.begin()
     rep = None
     for k in range(args.steps):
         flush.zero_()
@@ -292,6 +326,7 @@ def main():
         rep = one_step(S, kw["b"])
         evs[k][1].record(stream)
     torch.cuda.synchronize(dev)
+    clk.end()
     launches = G.kernel_launches() - launches0
     ms = sum(a.elapsed_time(b) for a, b in evs)
     if ws > 1:
