@@ -769,15 +769,12 @@ def bench_srtt_sweep(G, dev, flush, sizes=(200, 400, 800)):
 def bench_differentiable(G, dev, flush):
     """Seismic travel-time tomography, 256 x 256 slowness, 8192 rays, Laplacian L, 80 iterations:
     forward solve with the y_k record, then the reverse sweep (dl/db, dl/dlambda for
-    l = ||x_80 - x_true||^2), FP64 and FP32, next to the plain FP64 forward."""
+    l = ||x_80 - x_true||^2), FP64 and FP32, next to the plain FP64 forward.  Also the 256 x 256
+    deblurring problem with its 2 refinement steps per iteration (40 iterations), whose sweep
+    runs back through every refinement step."""
     import numpy as np
     import torch
-    P = make_workload("seismic2d", seed=0)
-    P.n_refine = 0
-    iters = P.iters
     stream = torch_stream(dev)
-    out = {"workload": "seismic2d: 256x256, 64 sources x 128 receivers (8192 rays), laplace2d L, 1% noise, "
-                       "sparse-sign s=400 zeta=8, 80 iterations, loss ||x_80 - x_true||^2"}
 
     def timed(fn, reps=3):
         best, res = None, None
@@ -792,41 +789,59 @@ def bench_differentiable(G, dev, flush):
             best = t if best is None or t < best else best
         return best, res
 
-    for prec in ("fp64", "fp32"):
-        kw = G.device_inputs(P, prec, device=dev)
-        kw["n_refine"] = 0
-        S = G.Solver(**kw, record=True)
-        b = kw["b"]
-        xt = torch.from_numpy(np.asarray(P.x_true)).to(dev, S.dtype)
-        t_fwd, _ = timed(lambda: (S.reset(b), S.solve(iters)))
-        xbar = (2.0 * (S.x() - xt)).contiguous()
-        t_bwd, (bbar, lbar) = timed(lambda: S.backward(xbar))
-        rec = {"forward_ms": t_fwd, "backward_ms": t_bwd, "dl_dlambda": lbar,
-               "forward_iters_per_s": iters / (t_fwd / 1e3)}
-        if prec == "fp32":
-            rec["note"] = ("the derivative goes through G_j^{-1}, the squared condition of the projected problem; "
-                           "at 80 iterations the FP64 sweep's own rounding floor is ~1e-2, so the FP32 value "
-                           "carries no digits (timing only)")
-        if prec == "fp64":
-            h = 1e-6 * P.lam
-            vals = []
-            for lam in (P.lam + h, P.lam - h):
-                S.set_lambda(lam)
-                S.reset(b)
-                S.solve(iters)
-                vals.append(float(torch.sum((S.x() - xt) ** 2)))
-            S.set_lambda(P.lam)
-            fd = (vals[0] - vals[1]) / (2 * h)
-            rec["dl_dlambda_central_difference"] = fd
-            rec["dl_dlambda_rel_err"] = abs(lbar - fd) / abs(fd)
-        S.close()
-        out[prec] = rec
+    def case(P, n_refine, fp32_note):
+        iters = P.iters
+        res = {}
+        for prec in ("fp64", "fp32"):
+            kw = G.device_inputs(P, prec, device=dev)
+            kw["n_refine"] = n_refine
+            S = G.Solver(**kw, record=True)
+            b = kw["b"]
+            xt = torch.from_numpy(np.asarray(P.x_true)).to(dev, S.dtype)
+            t_fwd, _ = timed(lambda: (S.reset(b), S.solve(iters)))
+            xbar = (2.0 * (S.x() - xt)).contiguous()
+            t_bwd, (bbar, lbar) = timed(lambda: S.backward(xbar))
+            rec = {"forward_ms": t_fwd, "backward_ms": t_bwd, "dl_dlambda": lbar,
+                   "forward_iters_per_s": iters / (t_fwd / 1e3)}
+            if prec == "fp32":
+                rec["note"] = fp32_note
+            if prec == "fp64":
+                h = 1e-6 * P.lam
+                vals = []
+                for lam in (P.lam + h, P.lam - h):
+                    S.set_lambda(lam)
+                    S.reset(b)
+                    S.solve(iters)
+                    vals.append(float(torch.sum((S.x() - xt) ** 2)))
+                S.set_lambda(P.lam)
+                fd = (vals[0] - vals[1]) / (2 * h)
+                rec["dl_dlambda_central_difference"] = fd
+                rec["dl_dlambda_rel_err"] = abs(lbar - fd) / abs(fd)
+            S.close()
+            res[prec] = rec
+        return res
+
+    P = make_workload("seismic2d", seed=0)
+    out = {"workload": "seismic2d: 256x256, 64 sources x 128 receivers (8192 rays), laplace2d L, 1% noise, "
+                       "sparse-sign s=400 zeta=8, 80 iterations, loss ||x_80 - x_true||^2"}
+    out.update(case(P, 0, "the derivative goes through G_j^{-1}, the squared condition of the projected problem; "
+                          "at 80 iterations the FP64 sweep's own rounding floor is ~1e-2, so the FP32 value "
+                          "carries no digits (timing only)"))
     kw = G.device_inputs(P, "fp64", device=dev)
     kw["n_refine"] = 0
     S = G.Solver(**kw)
-    t_plain, _ = timed(lambda: (S.reset(kw["b"]), S.solve(iters)))
+    t_plain, _ = timed(lambda: (S.reset(kw["b"]), S.solve(P.iters)))
     S.close()
     out["fp64_plain_forward_ms"] = t_plain
+    # The unrolled derivative's conditioning grows with K (it goes through G_j^{-1}): on this problem
+    # the FP64 oracle against itself under rounding-level perturbations differs by 2e-7 in dl/db at
+    # K = 40, 1e-4 at K = 60 and O(1) at K = 100, so the derivative is taken at K = 40.
+    Pd = make_workload("deblur2d", seed=0)
+    Pd.iters = 40
+    ref = {"workload": f"deblur2d: 256x256, 9x9 Gaussian psf, grad2d L, {Pd.n_refine} refinement steps per "
+                       f"iteration, {Pd.iters} iterations, loss ||x_K - x_true||^2"}
+    ref.update(case(Pd, Pd.n_refine, "FP32 form of the same solve: timing only"))
+    out["refined"] = ref
     return out
 
 

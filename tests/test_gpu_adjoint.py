@@ -171,6 +171,20 @@ def test_backward_fp32_form(G):
     S.close()
 
 
+def test_backward_fp32_form_with_refinement(G):
+    """The FP32 form's derivative with 2 refinement steps, against the FP64 oracle's: FP32
+    operators and W, FP64 sketched QR, solves and refinement reductions, compared as loosely as
+    the form without refinement."""
+    P = small_problem("deblur2d", iters=10)
+    S, b = recording_solver(G, P, "fp32", 2)
+    _, bbar, lbar = gpu_loss_grad(G, S, P, b, 10)
+    _, bb, lb = loss_and_grad(P, 10, n_refine=2)
+    print(f"fp32 refined: rel(bbar) = {rel(bbar, bb):.2e}, rel(lambdabar) = {abs(lbar - lb) / abs(lb):.2e}")
+    assert rel(bbar, bb) < 2e-2
+    assert abs(lbar - lb) <= 2e-2 * abs(lb)
+    S.close()
+
+
 def test_backward_errors(G):
     P = small_problem("seismic2d", iters=4)
     kw = G.device_inputs(P, "fp64")
@@ -237,4 +251,22 @@ def test_full_size_seismic_gradient(G, iters):
     fd = (lp - lm) / (2 * h)
     print(f"dl/dlambda {lbar:.6e}, central difference {fd:.6e}")
     assert abs(lbar - fd) <= max(1e-4, 10.0 * fl) * abs(fd)
+    S.close()
+
+
+@pytest.mark.slow
+def test_full_size_deblur_refined_gradient(G):
+    """The 256 x 256 deblurring problem with its 2 refinement steps per iteration, 40 iterations,
+    FP64: the sweep runs back through 80 refinement steps.  The oracle against itself under
+    rounding-level perturbations differs by ~2e-7 in dl/db here (O(1) by 100 iterations, where the
+    unrolled derivative carries no digits); the GPU is held to 10 x that floor."""
+    P = make_problem("deblur2d")
+    P.iters = 40
+    S, b = recording_solver(G, P, "fp64", P.n_refine)
+    _, bbar, lbar = gpu_loss_grad(G, S, P, b, 40)
+    bb, lb, fb, fl = adjoint_floor(P, 40, n_refine=P.n_refine)
+    print(f"deblur refined 40 its: rel(bbar) = {rel(bbar, bb):.2e} (floor {fb:.2e}), "
+          f"rel(lambdabar) = {abs(lbar - lb) / abs(lb):.2e} (floor {fl:.2e})")
+    assert rel(bbar, bb) <= max(1e-6, 10.0 * fb)
+    assert abs(lbar - lb) <= max(1e-6, 10.0 * fl) * abs(lb)
     S.close()
