@@ -243,8 +243,18 @@ struct Engine : EngineBase {
         // W y^{r-1}, rho(W y^{r-1}) and the two rank-2 left vectors
         double *w = nullptr, *dl = nullptr, *td = nullptr;
         T *Ww = nullptr, *HWw = nullptr, *xp = nullptr, *rho = nullptr, *a1 = nullptr, *a2 = nullptr;
+        T *xin = nullptr, *bout = nullptr;   // the caller's xbar and the result bbar, copied in and out
         int* err = nullptr;
     } bw;
+    // The sweep for one (K, lambda) as a CUDA graph: the first call for a key runs the launches
+    // eagerly, the second captures them, later calls replay the graph.
+    cudaGraphExec_t bw_exec = nullptr;
+    int bw_key_K = -1;
+    double bw_key_lam = 0.0;
+    int64_t bw_graph_launches = 0;
+    ~Engine() override {
+        if (bw_exec) cudaGraphExecDestroy(bw_exec);
+    }
 
     template <typename P>
     cudaError_t bw_alloc(P** p, size_t count) {
@@ -265,7 +275,7 @@ struct Engine : EngineBase {
         A1(&bw.P, n); A1(&bw.Q, n); A1(&bw.tm, m); A1(&bw.tp, p); A1(&bw.Kv, ell * n); A1(&bw.Kb, ell * n);
         A1(&bw.uy, s); A1(&bw.uz, s); A1(&bw.vy, s); A1(&bw.vz, s); A1(&bw.cb, s); A1(&bw.st, s);
         A1(&bw.ybar, dm); A1(&bw.z, dm); A1(&bw.part, (size_t)nbS * dm); A1(&bw.acc, 2);
-        A1(&bw.R0, ell * ell); A1(&bw.Ri, ell * ell); A1(&bw.err, 1);
+        A1(&bw.R0, ell * ell); A1(&bw.Ri, ell * ell); A1(&bw.err, 1); A1(&bw.xin, n); A1(&bw.bout, m);
         if (n_refine > 0) {
             A1(&bw.w, dm); A1(&bw.dl, dm); A1(&bw.td, dm);
             A1(&bw.Ww, n); A1(&bw.HWw, n); A1(&bw.xp, n); A1(&bw.rho, n); A1(&bw.a1, n); A1(&bw.a2, n);
@@ -360,17 +370,59 @@ struct Engine : EngineBase {
         if (!yhist || !D.fast_small) return cudaErrorNotSupported;
         cudaError_t e = bw_prepare();
         if (e != cudaSuccess) return e;
+        auto L1 = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+        L1(cudaMemcpyAsync(bw.xin, xbar, sizeof(T) * D.n, cudaMemcpyDeviceToDevice, st));
+        const bool same = bw_key_K == K && bw_key_lam == D.lam;
+        if (e == cudaSuccess && same && bw_exec) {
+            L1(cudaGraphLaunch(bw_exec, st));
+            g_launches.fetch_add(bw_graph_launches);
+        } else if (e == cudaSuccess && same) {
+            L1(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+            if (e == cudaSuccess) {
+                const int64_t l0 = g_launches.load();
+                const cudaError_t e2 = bw_sweep(K);
+                bw_graph_launches = g_launches.load() - l0;
+                cudaGraph_t g = nullptr;
+                L1(cudaStreamEndCapture(st, &g));
+                L1(e2);
+                if (e == cudaSuccess) L1(cudaGraphInstantiate(&bw_exec, g, 0));
+                if (g) cudaGraphDestroy(g);
+                if (e == cudaSuccess) L1(cudaGraphLaunch(bw_exec, st));
+                if (e != cudaSuccess && bw_exec) {
+                    cudaGraphExecDestroy(bw_exec);
+                    bw_exec = nullptr;
+                }
+            }
+        } else if (e == cudaSuccess) {
+            if (bw_exec) cudaGraphExecDestroy(bw_exec);
+            bw_exec = nullptr;
+            bw_key_K = K;
+            bw_key_lam = D.lam;
+            L1(bw_sweep(K));
+        }
+        L1(cudaMemcpyAsync(bbar_v, bw.bout, sizeof(T) * D.m, cudaMemcpyDeviceToDevice, st));
+        int herr = 0;
+        L1(cudaMemcpyAsync(lbar_host, bw.acc, sizeof(double), cudaMemcpyDeviceToHost, st));
+        L1(cudaMemcpyAsync(&herr, bw.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        L1(cudaStreamSynchronize(st));
+        if (e == cudaSuccess && herr) e = cudaErrorInvalidValue;
+        return e;
+    }
+
+    // The launches of the sweep, reading bw.xin and writing bw.bout, bw.acc[0] and bw.err: no host
+    // synchronisation, so that the sequence can be captured.
+    cudaError_t bw_sweep(int K) {
         const int64_t n = D.n;
         const int ell = D.ell;
         const double lam = D.lam;
-        T* bbar = static_cast<T*>(bbar_v);
+        T* bbar = bw.bout;
         T* W = B.W;
-        e = cudaMemsetAsync(bw.Wb, 0, sizeof(T) * (size_t)(ell + K) * n, st);
+        cudaError_t e = cudaMemsetAsync(bw.Wb, 0, sizeof(T) * (size_t)(ell + K) * n, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(bw.cb, 0, sizeof(double) * D.s, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(bw.acc, 0, sizeof(double) * 2, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(bw.err, 0, sizeof(int), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(bbar, 0, sizeof(T) * D.m, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(bw.xb, xbar, sizeof(T) * n, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(bw.xb, bw.xin, sizeof(T) * n, cudaMemcpyDeviceToDevice, st);
         auto L1 = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
         const int NS = n_refine + 1;
         auto yrow = [&](int j, int r) { return yhist + ((size_t)j * NS + r) * D.dmax; };
@@ -452,11 +504,6 @@ struct Engine : EngineBase {
         L1(bw_sketch_adj(true, bw.cb, bw.tm));
         L1(launchd_axpby<T>(bbar, bbar, 1.0, bw.tm, 1.0, D.m, st));
         g_launches.fetch_add(2);
-        int herr = 0;
-        L1(cudaMemcpyAsync(lbar_host, bw.acc, sizeof(double), cudaMemcpyDeviceToHost, st));
-        L1(cudaMemcpyAsync(&herr, bw.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-        L1(cudaStreamSynchronize(st));
-        if (e == cudaSuccess && herr) e = cudaErrorInvalidValue;
         return e;
     }
 

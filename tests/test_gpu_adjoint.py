@@ -58,10 +58,22 @@ def test_backward_matches_oracle_fp64(G, kind, iters):
     assert abs(loss - L0) <= 1e-9 * L0
     assert rel(bbar, bb) < 1e-7
     assert abs(lbar - lb) <= 1e-7 * abs(lb)
-    # the call leaves the forward state as it was: a second call gives the same numbers
+    # the call leaves the forward state as it was: a second call (captured into a graph) and a
+    # third (a replay of it) give the same numbers; a replay with 2 xbar gives exactly twice them
+    # (scaling by 2 commutes with every rounding), so the graph reads the new xbar
     xt = torch.from_numpy(np.asarray(P.x_true)).cuda()
-    b2, l2 = S.backward((2.0 * (S.x() - xt)).contiguous())
+    xbar = (2.0 * (S.x() - xt)).contiguous()
+    b2, l2 = S.backward(xbar)
     assert np.array_equal(b2.cpu().numpy(), bbar) and l2 == lbar
+    b3, l3 = S.backward(xbar)
+    assert np.array_equal(b3.cpu().numpy(), bbar) and l3 == lbar
+    b4, l4 = S.backward((2.0 * xbar).contiguous())
+    assert np.array_equal(b4.cpu().numpy(), 2.0 * bbar) and l4 == 2.0 * lbar
+    # a new solve with the same K: the replayed graph reads the new forward state
+    S.reset(b)
+    S.solve(iters)
+    b5, l5 = S.backward(xbar)
+    assert np.array_equal(b5.cpu().numpy(), bbar) and l5 == lbar
     S.close()
 
 
@@ -106,6 +118,11 @@ def test_backward_with_refinement_matches_oracle(G, kind, iters, n_refine):
     assert abs(loss - L0) <= 1e-9 * L0
     assert rel(bbar, bb) < max(1e-7, 10.0 * fb)
     assert abs(lbar - lb) <= max(1e-7, 10.0 * fl) * abs(lb)
+    xt = torch.from_numpy(np.asarray(P.x_true)).cuda()
+    xbar = (2.0 * (S.x() - xt)).contiguous()
+    for _ in range(2):   # captured, then replayed
+        b2, l2 = S.backward(xbar)
+        assert np.array_equal(b2.cpu().numpy(), bbar) and l2 == lbar
     # the refinement steps change the derivative: the one without them is measurably different
     _, bb0, _ = loss_and_grad(P, iters, n_refine=0)
     assert rel(bb0, bb) > 1e3 * rel(bbar, bb)
