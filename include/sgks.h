@@ -325,7 +325,9 @@ int sgks_time_class(sgks_handle* h, int32_t cls, int32_t reps, double* us_out);
  * eq. (projected_sketched_bis) (the leading block of which serves every earlier step, since the
  * factors only grow by columns, eq. updqr).  Needs a handle created with SGKS_FLAG_RECORD.  The
  * forward state is unchanged, so the call may be repeated.  Device scratch is allocated at the
- * first call.  Synchronises.  Errors: SGKS_ERR_STATE (no SGKS_FLAG_RECORD, or no iteration
+ * first call.  Calls with the same K and lambda as the previous one capture the sweep's launches
+ * into a CUDA graph (second call) and then replay it; the results are bit-identical to the
+ * eager sweep.  Synchronises.  Errors: SGKS_ERR_STATE (no SGKS_FLAG_RECORD, or no iteration
  * recorded), SGKS_ERR_INVALID, SGKS_ERR_CUDA. */
 int sgks_backward(sgks_handle* h, const void* xbar, void* bbar, double* lambda_bar);
 
