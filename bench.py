@@ -36,6 +36,21 @@ WORKLOAD = ("deblur2d: 256x256 image, 9x9 Gaussian PSF sigma=2 zero boundary, gr
             "sparse-sign s=400 zeta=8, 100 iterations, FP32 + 2 refinement steps")
 
 
+def labels(name, P=None):
+    """(metric, workload) of the JSON line: the deblurring workload's fixed labels, or labels
+    built from the problem for another --config."""
+    if name == "deblur2d":
+        return METRIC, WORKLOAD
+    if P is None:
+        P = make_workload(name, seed=0)
+    A = P.A
+    op = f"CSR {A.m}x{A.n} nnz {len(A.col)}" if A.kind == "csr" else f"{A.kind} {A.m}x{A.n}"
+    form = P.precision.upper() + (f" + {P.n_refine} refinement steps" if P.n_refine else "")
+    wl = (f"{name}: A {op}, {P.L.kind} L (p = {P.p}), {P.sketch.kind} s={P.sketch.s}, {P.iters} iterations, "
+          f"{form}")
+    return f"sGKS iterations/s ({name}, {form})", wl
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -189,10 +204,30 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------------------- byte models
+def matrix_bytes(P, elem, rows):
+    """Bytes of one pass over the stored operator A (or its stored transpose, `rows` rows): CSR
+    column indices, values in the solve precision and row pointers; a dense matrix; nothing for
+    the matrix-free convolution."""
+    A = P.A
+    if A.kind == "csr":
+        return len(A.col) * (4 + elem) + (rows + 1) * 4
+    if A.kind == "dense":
+        return A.m * A.n * elem
+    return 0
+
+
 def bytes_model(P, cls, d, elem):
     """Algorithmic bytes of one launch of a kernel class at subspace size d (bytes each launch must move at minimum; per-kernel formulas below)."""
     n, m, p, s = P.n, P.m, P.p, P.sketch.s
     T = elem
+    if cls in ("gradient_append", "gradient_refine"):   # A^T e: one pass over the stored transpose
+        return _vector_bytes(n, m, s, d, T, cls) + matrix_bytes(P, elem, n)
+    if cls == "sketch_column":                           # A w: one pass over A
+        return _vector_bytes(n, m, s, d, T, cls) + matrix_bytes(P, elem, m)
+    return _vector_bytes(n, m, s, d, T, cls)
+
+
+def _vector_bytes(n, m, s, d, T, cls):
     if cls == "combine":
         return d * (n + m) * T + (n + 2 * m) * T + 3 * n * T
     if cls == "combine_refine":
@@ -259,10 +294,10 @@ def run_reference(args):
         tot += r["seconds"]
     value = args.steps * iters / tot
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": labels(name)[0], "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"setup + {iters} iterations per step, the setup inside the time"},
+        "config": {"workload": labels(name)[1], "sample": f"setup + {iters} iterations per step, the setup inside the time"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"NumPy FP64 oracle, setup + {iters} iterations of the workload per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -358,10 +393,11 @@ def main():
     elem = b_host.element_size()
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "metric": labels(args.config, P)[0], "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if P.precision == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "iterations_per_step": iters, "l2": "flushed (256 MiB write) before each step",
+        "config": {"workload": labels(args.config, P)[1], "iterations_per_step": iters, "l2": "flushed (256 MiB write) before each step",
                    "parallelism": "replicas" if ws > 1 else "single", "final_rre": rep["rre_last"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": P.m * elem, "d2h_bytes_per_step": P.n * elem},
         "gpu_launches": int(launches),
