@@ -25,7 +25,7 @@ constexpr int kGradCluster = 8;
 
 
 // Append variant: W[:, d] = r.
-template <typename T, typename V, bool WARPA, int LPR = 32>
+template <typename T, typename V, bool WARPA, int LPR = 32, bool SL = false>
 __global__ void __launch_bounds__(kThreads) k_gradient_append(Dims D, DevA<T, V> A, DevL L, Bulk<T> B, Small S) {
     pdl_wait();   // all global reads below depend on the previous kernel
     __shared__ T psf_s[128];
@@ -41,16 +41,26 @@ __global__ void __launch_bounds__(kThreads) k_gradient_append(Dims D, DevA<T, V>
     __syncthreads();
     T* out = B.W + (size_t)d * D.n;
     if (WARPA) {
-        // rows of A^T one per warp, dealt round-robin over every warp of the grid (a row is a
-        // chain of dependent loads, so the rows are spread as widely as the grid allows); a warp
-        // collects 32 of its rows, lane t holding row i0 + t GW, and the lanes then add the
-        // L^T L term of their own rows together (one warp instruction for 32 rows: in FP64 an
-        // instruction costs the FP64 pipe the same whether one lane or 32 are active)
+        // CSR with the interleaved slices of A^T: one slice per warp (lane t on row 32 g + t),
+        // dealt round-robin over the grid.  Otherwise rows of A^T one per warp (LPR lanes per
+        // CSR row), dealt round-robin over every warp of the grid (a row is a chain of dependent
+        // loads, so the rows are spread as widely as the grid allows); a warp collects 32 of its
+        // rows, lane t holding row i0 + t GW.  Either way the lanes then add the L^T L term of
+        // their own rows together (one warp instruction for 32 rows: in FP64 an instruction
+        // costs the FP64 pipe the same whether one lane or 32 are active).
         const int64_t GW = (int64_t)gridDim.x * kWarps;
         const int lane = lane_id();
+        if constexpr (SL) {
+            for (int64_t g = (int64_t)blockIdx.x * kWarps + warp_id(); g * 32 < D.n; g += GW) {
+                const T adj = sell_rows(A, B.e, g, D.n);
+                const int64_t my = g * 32 + lane;
+                if (my < D.n) out[my] = adj + (T)D.lam * ltl_row<T>(L, my, B.x);
+            }
+            return;
+        }
         for (int64_t i0 = (int64_t)blockIdx.x * kWarps + warp_id(); i0 < D.n; i0 += 32 * GW) {
             T adj = T(0);
-            if (A.kind == SGKS_OP_CSR) {   // LPR lanes per row of the stored transpose
+            if (A.kind == SGKS_OP_CSR) {
                 adj = csr_rows_rr<T, V, LPR>(A.trp, A.tci, A.tval, B.e, i0, GW, D.n);
             } else {
                 for (int t = 0; t < 32; ++t) {
@@ -158,6 +168,8 @@ cudaError_t launch_gradient(const Dims& D, const DevA<T, V>& A, const DevL& L, c
         const int64_t tiles = warpa ? (D.n + kWarps - 1) / kWarps : (D.n + kThreads - 1) / kThreads;
         const int blocks = (int)(tiles < 8 * 152 ? tiles : 8 * 152);
         if (warpa) {
+            if (A.kind == SGKS_OP_CSR && A.sl_off)
+                return launch_pdl(k_gradient_append<T, V, true, 32, true>, blocks, kThreads, 0, st, D, A, L, B, S);
             switch (A.kind == SGKS_OP_CSR ? csr_lanes_per_row(A.nnz, D.n) : 32) {
                 case 4: return launch_pdl(k_gradient_append<T, V, true, 4>, blocks, kThreads, 0, st, D, A, L, B, S);
                 case 8: return launch_pdl(k_gradient_append<T, V, true, 8>, blocks, kThreads, 0, st, D, A, L, B, S);

@@ -39,7 +39,7 @@ void carveout_once(const void* kernel) {
 }
 
 // ---------------------------------------------------------------------------- applies
-template <typename T, typename V, bool WARPA, int LPR = 32>
+template <typename T, typename V, bool WARPA, int LPR = 32, bool SL = false>
 __global__ void __launch_bounds__(kThreads) k_apply(DevA<T, V> A, DevL L, int which, const T* __restrict__ in,
                                                      T* __restrict__ out, int64_t rows) {
     __shared__ T psf_s[128];
@@ -51,6 +51,14 @@ __global__ void __launch_bounds__(kThreads) k_apply(DevA<T, V> A, DevL L, int wh
         // rows one per warp, dealt round-robin over the grid; lane t keeps row i0 + t GW
         const bool adj = which == SGKS_APPLY_AT;
         const int64_t GW = (int64_t)gridDim.x * kWarps;
+        if (SL && adj) {   // CSR slices of 32 rows of A^T, lane t on row 32 g + t
+            for (int64_t g = (int64_t)blockIdx.x * kWarps + warp_id(); g * 32 < rows; g += GW) {
+                const T v = sell_rows(A, in, g, rows);
+                const int64_t my = g * 32 + lane;
+                if (my < rows) out[my] = v;
+            }
+            return;
+        }
         for (int64_t i0 = (int64_t)blockIdx.x * kWarps + warp_id(); i0 < rows; i0 += 32 * GW) {
             T v = T(0);
             if (A.kind == SGKS_OP_CSR) {
@@ -114,7 +122,9 @@ cudaError_t launch_apply(const Dims& D, const DevA<T, V>& A, const DevL& L, int 
     }
     else {
         const int lpr = warp_rows && A.kind == SGKS_OP_CSR ? csr_lanes_per_row(A.nnz, rows) : 32;
-        if (lpr == 4) k_apply<T, V, true, 4><<<(int)blocks, kThreads, 0, st>>>(A, L, which, in, out, rows);
+        if (which == SGKS_APPLY_AT && A.kind == SGKS_OP_CSR && A.sl_off)
+            k_apply<T, V, true, 32, true><<<(int)blocks, kThreads, 0, st>>>(A, L, which, in, out, rows);
+        else if (lpr == 4) k_apply<T, V, true, 4><<<(int)blocks, kThreads, 0, st>>>(A, L, which, in, out, rows);
         else if (lpr == 8) k_apply<T, V, true, 8><<<(int)blocks, kThreads, 0, st>>>(A, L, which, in, out, rows);
         else if (lpr == 16) k_apply<T, V, true, 16><<<(int)blocks, kThreads, 0, st>>>(A, L, which, in, out, rows);
         else k_apply<T, V, true, 32><<<(int)blocks, kThreads, 0, st>>>(A, L, which, in, out, rows);
@@ -326,6 +336,60 @@ cudaError_t csr_transpose_device(int64_t m, int64_t n, int64_t nnz, const int32_
     if (vdt == SGKS_F32)
         return transpose_impl<float>(m, n, nnz, rp, ci, (const float*)val, trp, tci, (float*)tval, st);
     return transpose_impl<double>(m, n, nnz, rp, ci, (const double*)val, trp, tci, (double*)tval, st);
+}
+
+// ------------------------------------------------------- interleaved 32-row slices of a CSR
+// w[g] = 32 x the longest row among rows 32 g .. 32 g + 31 (the slice's stored entries)
+__global__ void __launch_bounds__(kThreads) k_slice_width(const int32_t* __restrict__ rp, int64_t rows, int64_t* w) {
+    const int64_t G = (rows + 31) / 32;
+    for (int64_t g = (int64_t)blockIdx.x * kWarps + warp_id(); g < G; g += (int64_t)gridDim.x * kWarps) {
+        const int64_t r = g * 32 + lane_id();
+        int len = r < rows ? rp[r + 1] - rp[r] : 0;
+        for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+        if (lane_id() == 0) w[g] = 32 * (int64_t)len;
+    }
+}
+
+// entry k of row 32 g + t -> position off[g] + 32 k + t; len[r] = entries of row r
+template <typename V>
+__global__ void __launch_bounds__(kThreads) k_slice_fill(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                         const V* __restrict__ val, int64_t rows,
+                                                         const int64_t* __restrict__ off, int32_t* len, int32_t* sci,
+                                                         V* sval) {
+    const int64_t G = (rows + 31) / 32;
+    for (int64_t g = (int64_t)blockIdx.x * kWarps + warp_id(); g < G; g += (int64_t)gridDim.x * kWarps) {
+        const int64_t r = g * 32 + lane_id();
+        if (r >= rows) continue;
+        const int b = rp[r], cnt = rp[r + 1] - b;
+        len[r] = cnt;
+        const int64_t o = off[g] + lane_id();
+        for (int k = 0; k < cnt; ++k) {
+            sci[o + 32 * (int64_t)k] = ci[b + k];
+            sval[o + 32 * (int64_t)k] = val[b + k];
+        }
+    }
+}
+
+static int slice_grid(int64_t rows) {
+    const int64_t warps = (rows + 31) / 32;
+    const int64_t b = (warps + kWarps - 1) / kWarps;
+    return (int)(b < 1 ? 1 : (b > 8 * 152 ? 8 * 152 : b));
+}
+
+cudaError_t slice_width_device(const int32_t* rp, int64_t rows, int64_t* w, cudaStream_t st) {
+    k_slice_width<<<slice_grid(rows), kThreads, 0, st>>>(rp, rows, w);
+    return cudaGetLastError();
+}
+
+cudaError_t slice_fill_device(const int32_t* rp, const int32_t* ci, const void* val, int vdt, int64_t rows,
+                              const int64_t* off, int32_t* len, int32_t* sci, void* sval, cudaStream_t st) {
+    if (vdt == SGKS_F32)
+        k_slice_fill<float><<<slice_grid(rows), kThreads, 0, st>>>(rp, ci, (const float*)val, rows, off, len, sci,
+                                                                   (float*)sval);
+    else
+        k_slice_fill<double><<<slice_grid(rows), kThreads, 0, st>>>(rp, ci, (const double*)val, rows, off, len, sci,
+                                                                    (double*)sval);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------- CSR transpose without allocation

@@ -824,7 +824,7 @@ static cudaError_t take_flag(int* d_err, cudaStream_t st, int* herr) {
 
 template <typename T, typename V>
 int prepare_operator(const sgks_op* op, DevA<T, V>& A, std::vector<void*>& allocs, int* d_err, cudaStream_t st,
-                     std::string* why) {
+                     std::string* why, bool slices) {
     cudaError_t e = cudaSuccess;
 #define AL(ptr, cnt)                                                   \
     do {                                                               \
@@ -886,6 +886,45 @@ int prepare_operator(const sgks_op* op, DevA<T, V>& A, std::vector<void*>& alloc
             A.trp = trp;
             A.tci = tci;
             A.tval = tv;
+        }
+        // The slices pay where a row's cross-lane sum is costly (FP64) or rows are short, and where
+        // there are enough of them to fill the GPU (a warp per 32 rows: at least 32 warps per SM of
+        // 152 needs n >= 155,648).  Measured on GB300: 512^2 CT (n = 262,144, A^T rows of ~229
+        // entries) FP64 1,078 -> 1,255 it/s, FP32 2,678 -> 2,161 it/s (kept on the CSR rows);
+        // dynamic CT (n = 524,288, ~38 entries) FP32 with 3 refinement steps 683 -> 1,198 it/s;
+        // seismic (n = 65,536, ~36 entries) FP32 forward 6.27 -> 6.66 ms (kept on the CSR rows).
+        const bool use_slices = slices && op->n >= 152 * 32 * 32 && (sizeof(T) == 8 || op->nnz < 96 * op->n);
+        if (use_slices && e == cudaSuccess) {
+            // A^T as interleaved 32-row slices (DevA::sl_*): slice sizes on the device, their prefix
+            // sums on the host (the total sizes the allocation), then the entries
+            const int64_t G = (op->n + 31) / 32;
+            int64_t* off = nullptr;
+            int32_t* len = nullptr;
+            AL(off, G + 1);
+            AL(len, op->n);
+            std::vector<int64_t> h((size_t)G + 1, 0);
+            if (e == cudaSuccess) e = slice_width_device(A.trp, op->n, off, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), off, sizeof(int64_t) * (size_t)G, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            int64_t tot = 0;
+            for (int64_t g = 0; g < G; ++g) {
+                const int64_t w = h[(size_t)g];
+                h[(size_t)g] = tot;
+                tot += w;
+            }
+            h[(size_t)G] = tot;
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(off, h.data(), sizeof(int64_t) * (size_t)(G + 1), cudaMemcpyHostToDevice, st);
+            int32_t* sci = nullptr;
+            V* sv = nullptr;
+            AL(sci, tot > 0 ? tot : 1);
+            AL(sv, tot > 0 ? tot : 1);
+            if (e == cudaSuccess) e = slice_fill_device(A.trp, A.tci, A.tval, vdt, op->n, off, len, sci, sv, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // h is read by the copy above
+            A.sl_off = off;
+            A.sl_len = len;
+            A.sl_ci = sci;
+            A.sl_val = sv;
         }
     } else if (op->kind == SGKS_OP_DENSE) {
         T* dd = nullptr;
@@ -963,11 +1002,11 @@ int prepare_sparse_sign(uint64_t keyA, uint64_t keyL, int64_t m, int64_t p, int 
 }
 
 template int prepare_operator<float, float>(const sgks_op*, DevA<float, float>&, std::vector<void*>&, int*,
-                                            cudaStream_t, std::string*);
+                                            cudaStream_t, std::string*, bool);
 template int prepare_operator<double, float>(const sgks_op*, DevA<double, float>&, std::vector<void*>&, int*,
-                                             cudaStream_t, std::string*);
+                                             cudaStream_t, std::string*, bool);
 template int prepare_operator<double, double>(const sgks_op*, DevA<double, double>&, std::vector<void*>&, int*,
-                                              cudaStream_t, std::string*);
+                                              cudaStream_t, std::string*, bool);
 
 }  // namespace sgks
 

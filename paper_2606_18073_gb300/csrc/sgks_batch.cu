@@ -357,7 +357,7 @@ int build_groups(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const st
     // operator, L and the sketches: prepared once, shared by the groups of this operator
     DevA<T, V> A{};
     std::string why;
-    int rc = prepare_operator<T, V>(op, A, h->allocs, h->d_err, h->st, &why);
+    int rc = prepare_operator<T, V>(op, A, h->allocs, h->d_err, h->st, &why, false);   // batched kernels read the CSR
     if (rc != SGKS_OK) return bfail(h, rc, why);
     const DevL L = make_devl(reg);
     SketchCSR SK{};

@@ -54,6 +54,18 @@ struct DevA {
     const int32_t* trp;  // CSR of A^T
     const int32_t* tci;
     const V* tval;
+    // A^T once more in 32-row slices with each slice's entries interleaved by row: entry k of row
+    // 32 g + t at sl_off[g] + 32 k + t (sl_len[i] entries in row i; the tail of a shorter row is
+    // padding that is never read).  A warp then reads the k-th entries of 32 consecutive rows
+    // together: for rows that are neighbouring pixels of a ray-based operator those entries are
+    // neighbouring rays, so the gathers of e fall on few cache lines, and no row needs a
+    // cross-lane sum.  Built when n >= 155,648 (enough slices to fill the GPU) for the FP64 form
+    // and for rows of fewer than 96 entries on average; sl_off = nullptr otherwise (long FP32
+    // rows run faster with 32 lanes per row, small operators with rows spread over every warp).
+    const int64_t* sl_off;   // [ceil(n / 32) + 1]
+    const int32_t* sl_len;   // [n]
+    const int32_t* sl_ci;
+    const V* sl_val;
     const T* dense;      // row-major m x ld
     int64_t ld;
     int nx, ny, kh, kw;  // conv2d
@@ -290,6 +302,40 @@ __device__ __forceinline__ T csr_rows_rr(const int32_t* __restrict__ rp, const i
         if (s >= 0 && s < RPW) mine = v;
     }
     return mine;
+}
+
+// Rows 32 g .. 32 g + 31 of A^T v from the interleaved slices: lane t returns row 32 g + t (0
+// past the last row).  Each lane runs its own row with eight entries in flight, entry k going to
+// accumulator k mod 8; the accumulators are summed pairwise at the end.
+template <typename T, typename V>
+__device__ __forceinline__ T sell_rows(const DevA<T, V>& A, const T* __restrict__ v, int64_t g, int64_t rows) {
+    constexpr int U = 8;
+    const int lane = lane_id();
+    const int64_t row = g * 32 + lane;
+    if (row >= rows) return T(0);
+    const int len = A.sl_len[row];
+    const int64_t o = A.sl_off[g] + lane;
+    const int32_t* ci = A.sl_ci + o;
+    const V* va = A.sl_val + o;
+    T acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = T(0);
+    int k = 0;
+    for (; k + U <= len; k += U) {
+        int c[U];
+        T w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            c[u] = ldg(ci + 32 * (k + u));
+            w[u] = (T)ldg(va + 32 * (k + u));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc[u] += w[u] * ldg(v + c[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U - 1; ++u)
+        if (k + u < len) acc[u] += (T)ldg(va + 32 * (k + u)) * ldg(v + ldg(ci + 32 * (k + u)));
+    return ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
 }
 
 // lanes per CSR row for rows of `avg` entries on average
@@ -593,7 +639,9 @@ __device__ __forceinline__ T grad_value(const DevA<T, V>& A, const DevL& L, cons
     const int lane = lane_id();
     const int64_t i = base + lane;
     T adj = T(0);
-    if (WARPA) {
+    if (WARPA && A.kind == SGKS_OP_CSR && A.sl_off) {   // base is a multiple of 32: one slice of A^T
+        adj = sell_rows(A, e, base >> 5, n);
+    } else if (WARPA) {
         for (int r = 0; r < 32; ++r) {
             const int64_t ii = base + r;
             if (ii >= n) break;
@@ -784,6 +832,11 @@ cudaError_t launch_sqnorm(const T* w, int64_t n, double* part, int nb, cudaStrea
 cudaError_t csr_transpose_device(int64_t m, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
                                  const void* val, int vdt, int32_t* trp, int32_t* tci, void* tval,
                                  cudaStream_t st);
+// interleaved 32-row slices of a CSR with `rows` rows (DevA::sl_*): the slice sizes w[g], then,
+// with off = their exclusive prefix sums, the row lengths and the interleaved entries
+cudaError_t slice_width_device(const int32_t* rp, int64_t rows, int64_t* w, cudaStream_t st);
+cudaError_t slice_fill_device(const int32_t* rp, const int32_t* ci, const void* val, int vdt, int64_t rows,
+                              const int64_t* off, int32_t* len, int32_t* sci, void* sval, cudaStream_t st);
 // ------------------------------------------------------------------- batched form
 // B instances of one problem shape (same A and L; their own b_i, lambda_i, x_true_i), all n-,
 // m- and p-vectors instance-interleaved: v[q * B + i].  B is a power of two, 1 <= B <= 256.
@@ -924,7 +977,7 @@ int validate_problem(const sgks_op* A, const sgks_reg* L, const void* b, double 
 DevL make_devl(const sgks_reg* reg);
 template <typename T, typename V>
 int prepare_operator(const sgks_op* op, DevA<T, V>& A, std::vector<void*>& allocs, int* d_err, cudaStream_t st,
-                     std::string* why);
+                     std::string* why, bool slices = true);
 int prepare_sparse_sign(uint64_t keyA, uint64_t keyL, int64_t m, int64_t p, int s, int zeta, SketchCSR& SK,
                         std::vector<void*>& allocs, int* d_err, cudaStream_t st, std::string* why);
 

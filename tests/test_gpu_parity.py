@@ -299,6 +299,31 @@ def test_csr_lanes_per_row(G, avg_row):
     S.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_csr_adjoint_paths(G, precision):
+    """A^T rows of ~146 entries (random 700 x 576 CSR, ~120 entries per row of A), read from the
+    CSR transpose with 32 lanes per row (the interleaved slices serve operators with n >= 155,648:
+    the full-size CT and dynamic-CT tests).  Against the oracle: the apply, and the iterates of a
+    solve with one refinement step (the append and the refinement gradients)."""
+    P = random_csr_problem(120, seed=3)
+    P.n_refine = 1
+    assert len(P.A.col) >= 96 * P.n
+    Aop, _ = O.make_operators(P)
+    S, xs = gpu_iterates(G, P, P.iters, precision)
+    v = np.random.default_rng(2).standard_normal(P.m)
+    if precision == "fp32":
+        v = v.astype(np.float32).astype(np.float64)
+    out = torch.empty(P.n, dtype=S.dtype, device="cuda")
+    S.apply(G._lib.SGKS_APPLY_AT, torch.from_numpy(v).to("cuda", S.dtype), out)
+    assert rel(out.cpu().numpy(), Aop.adjoint(v)) < (1e-13 if precision == "fp64" else 2e-6)
+    ref = O.sgks(P, record_x=True)
+    if precision == "fp64":
+        check_iterates(xs, ref["xs"], floor_curve(P, P.iters, EPS["fp64"])[0], TOL64, FACTOR64)
+    else:
+        check_fp32_early(P, xs, ref)
+    S.close()
+
+
 def test_programmatic_launch_changes_nothing(G, tmp_path):
     """The iteration's kernels launch with programmatic dependent launch; SGKS_PDL=0 launches them
     plainly.  Only the scheduling differs, so the solve is bit-identical (checked in a child
