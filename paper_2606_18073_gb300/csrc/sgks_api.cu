@@ -907,24 +907,28 @@ int prepare_operator(const sgks_op* op, DevA<T, V>& A, std::vector<void*>& alloc
             if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), off, sizeof(int64_t) * (size_t)G, cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             int64_t tot = 0;
+            bool narrow = true;   // the kernels index within a slice in 32-bit ints: 32 x longest row < 2^31
             for (int64_t g = 0; g < G; ++g) {
                 const int64_t w = h[(size_t)g];
+                narrow = narrow && w < ((int64_t)1 << 31);
                 h[(size_t)g] = tot;
                 tot += w;
             }
             h[(size_t)G] = tot;
-            if (e == cudaSuccess)
+            if (e == cudaSuccess && narrow)
                 e = cudaMemcpyAsync(off, h.data(), sizeof(int64_t) * (size_t)(G + 1), cudaMemcpyHostToDevice, st);
-            int32_t* sci = nullptr;
-            V* sv = nullptr;
-            AL(sci, tot > 0 ? tot : 1);
-            AL(sv, tot > 0 ? tot : 1);
-            if (e == cudaSuccess) e = slice_fill_device(A.trp, A.tci, A.tval, vdt, op->n, off, len, sci, sv, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // h is read by the copy above
-            A.sl_off = off;
-            A.sl_len = len;
-            A.sl_ci = sci;
-            A.sl_val = sv;
+            if (narrow) {
+                int32_t* sci = nullptr;
+                V* sv = nullptr;
+                AL(sci, tot > 0 ? tot : 1);
+                AL(sv, tot > 0 ? tot : 1);
+                if (e == cudaSuccess) e = slice_fill_device(A.trp, A.tci, A.tval, vdt, op->n, off, len, sci, sv, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // h is read by the copy above
+                A.sl_off = off;
+                A.sl_len = len;
+                A.sl_ci = sci;
+                A.sl_val = sv;
+            }
         }
     } else if (op->kind == SGKS_OP_DENSE) {
         T* dd = nullptr;
