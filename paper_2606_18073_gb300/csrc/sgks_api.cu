@@ -385,8 +385,10 @@ struct Engine : EngineBase {
                 cudaGraph_t g = nullptr;
                 L1(cudaStreamEndCapture(st, &g));
                 L1(e2);
-                if (e == cudaSuccess) L1(cudaGraphInstantiate(&bw_exec, g, 0));
+                cudaGraphExec_t x = nullptr;
+                if (e == cudaSuccess) L1(cudaGraphInstantiate(&x, g, 0));
                 if (g) cudaGraphDestroy(g);
+                if (e == cudaSuccess) bw_exec = x;   // only a successful instantiation is kept
                 if (e == cudaSuccess) L1(cudaGraphLaunch(bw_exec, st));
                 if (e != cudaSuccess && bw_exec) {
                     cudaGraphExecDestroy(bw_exec);
@@ -1406,10 +1408,18 @@ static cudaError_t ensure_graph(sgks_handle* h) {
     h->eng->host_d = hd;
     h->graph_launches = g_launches.load() - l0;
     g_launches.fetch_sub(h->graph_launches);
-    e = cudaStreamEndCapture(h->st, &h->graph);
-    if (e2 != cudaSuccess) return e2;
-    if (e != cudaSuccess) return e;
-    return cudaGraphInstantiate(&h->gexec, h->graph, 0);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->st, &g);
+    if (e2 != cudaSuccess) e = e2;
+    cudaGraphExec_t x = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {   // keep nothing: the next solve captures again
+        if (g) cudaGraphDestroy(g);
+        return e;
+    }
+    h->graph = g;
+    h->gexec = x;
+    return cudaSuccess;
 }
 
 int sgks_solve(sgks_handle* h, int32_t iters, double tol, void* x_out, sgks_report* rep) {

@@ -528,10 +528,18 @@ cudaError_t ensure_graph(sgks_batch* h) {
     cudaError_t e2 = for_groups(h, [](GroupBase* g) { return g->step(); });
     h->graph_launches = sgks_kernel_launches() - l0;
     add_launches(-h->graph_launches);
-    e = cudaStreamEndCapture(h->st, &h->graph);
-    if (e2 != cudaSuccess) return e2;
-    if (e != cudaSuccess) return e;
-    return cudaGraphInstantiate(&h->gexec, h->graph, 0);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->st, &g);
+    if (e2 != cudaSuccess) e = e2;
+    cudaGraphExec_t x = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {   // keep nothing: the next solve captures again
+        if (g) cudaGraphDestroy(g);
+        return e;
+    }
+    h->graph = g;
+    h->gexec = x;
+    return cudaSuccess;
 }
 
 cudaError_t read_scalars(sgks_batch* h) {
