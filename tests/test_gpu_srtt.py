@@ -71,6 +71,25 @@ def test_srtt_iterates_match_oracle(G, kind):
     S.close()
 
 
+@pytest.mark.parametrize("n_refine", [0, 2])
+def test_srtt_backward_matches_oracle(G, n_refine):
+    """The reverse sweep with the SRTT sketch (its adjoint is the dense S^T of the device rows),
+    without and with refinement steps, against the oracle's sweep, FP64, to 1e-7."""
+    from oracle.sgks_adjoint import loss_and_grad
+    P = srtt_problem("ct2d", iters=8)
+    kw = G.device_inputs(P, "fp64")
+    kw["n_refine"] = n_refine
+    S = G.Solver(**kw, record=True)
+    S.solve(8)
+    x = S.x()
+    xt = torch.from_numpy(np.asarray(P.x_true)).cuda()
+    bbar, lbar = S.backward((2.0 * (x - xt)).contiguous())
+    S.close()
+    _, bb, lb = loss_and_grad(P, 8, n_refine=n_refine)
+    assert rel(bbar.cpu().numpy(), bb) < 1e-7
+    assert abs(lbar - lb) <= 1e-7 * abs(lb)
+
+
 def test_srtt_rejects_missing_arrays(G):
     P = srtt_problem("deblur2d")
     kw = G.device_inputs(P, "fp64")

@@ -55,6 +55,17 @@ def test_adjoint_with_refinement_matches_central_differences(kind, iters, n_refi
         assert abs(an - fd) <= 1e-6 * abs(fd) + 1e-9, (kind, n_refine, an, fd)
 
 
+@pytest.mark.parametrize("n_refine", [0, 2])
+def test_adjoint_with_srtt_sketch_matches_central_differences(n_refine):
+    """The sweep with the subsampled randomized trigonometric transform (eq. sketching_trig) as
+    S_A and S_L, without and with refinement steps, against central differences."""
+    from workloads.configs import srtt_sketch
+    P = small_problem("ct2d", iters=8)
+    P.sketch = srtt_sketch(40, P.m, P.p, seed=2)
+    for an, fd in _fd(P, 8, n_refine=n_refine):
+        assert abs(an - fd) <= 1e-6 * abs(fd) + 1e-9, (n_refine, an, fd)
+
+
 def test_refinement_adjoint_terms_are_all_needed(monkeypatch):
     """A planted mistake: dropping the preconditioner's dependence on W and lambda (the G_j terms
     of the refinement adjoint) must fail the finite-difference pin, so the pin is not blind to
