@@ -59,8 +59,8 @@ struct DevA {
     // padding that is never read).  A warp then reads the k-th entries of 32 consecutive rows
     // together: for rows that are neighbouring pixels of a ray-based operator those entries are
     // neighbouring rays, so the gathers of e fall on few cache lines, and no row needs a
-    // cross-lane sum.  Built when n >= 155,648 (enough slices to fill the GPU) for the FP64 form
-    // and for rows of fewer than 96 entries on average; sl_off = nullptr otherwise (long FP32
+    // cross-lane sum.  Built when n >= 155,648 (enough slices to fill the GPU) and either the form
+    // is FP64 or rows hold fewer than 96 entries on average; sl_off = nullptr otherwise (long FP32
     // rows run faster with 32 lanes per row, small operators with rows spread over every warp).
     const int64_t* sl_off;   // [ceil(n / 32) + 1]
     const int32_t* sl_len;   // [n]
