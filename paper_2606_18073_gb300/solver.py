@@ -252,7 +252,9 @@ class Solver:
 
     def backward(self, xbar: torch.Tensor):
         """(dl/db, dl/dlambda) for xbar = dl/dx_K of the iterations since the last setup
-        (sgks_backward; the solver must have been created with record=True)."""
+        (sgks_backward; the solver must have been created with record=True).  The sweep runs
+        back through any refinement steps; repeated calls with the same K and lambda replay a
+        captured CUDA graph of it."""
         _need_cuda(xbar, "xbar")
         if xbar.dtype != self.dtype or xbar.numel() != self.n:
             raise ValueError(f"xbar must hold {self.n} values of {self.dtype}")
