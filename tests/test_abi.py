@@ -54,6 +54,25 @@ def test_invalid_create_fails_before_touching_the_device(lib):
     lib.sgks_destroy(None)
 
 
+def test_null_handles_are_rejected(lib):
+    """Every call that takes a handle returns SGKS_ERR_INVALID for a NULL one, without a device call."""
+    from paper_2606_18073_gb300 import _lib as L
+    calls = {
+        "sgks_reset": (None, None), "sgks_set_lambda": (None, 1.0), "sgks_backward": (None, None, None, None),
+        "sgks_step": (None,), "sgks_solve": (None, 1, 0.0, None, None), "sgks_status": (None, None),
+        "sgks_get_info": (None, None), "sgks_profile_steps": (None, 1, None, None, None),
+        "sgks_profile_graph": (None, 1, None, None, None), "sgks_time_class": (None, 0, 1, None),
+        "sgks_get_buffer": (None, 0, None, 0, None), "sgks_apply": (None, 0, None, None),
+        "sgks_batch_reset": (None, None), "sgks_batch_step": (None,), "sgks_batch_solve": (None, 1, 0.0, None, None),
+        "sgks_batch_get_x": (None, None), "sgks_batch_status": (None, None), "sgks_batch_layout": (None, None, None),
+        "sgks_batch_profile_steps": (None, 1, None, None),
+    }
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == L.SGKS_ERR_INVALID, name
+    assert lib.sgks_batch_config(None, 0) == b""
+    lib.sgks_batch_destroy(None)
+
+
 def test_binding_fails_loudly_without_library(tmp_path):
     from paper_2606_18073_gb300 import _lib as L
     with pytest.raises(RuntimeError, match="no CPU fallback"):
