@@ -48,7 +48,7 @@ enum { SGKS_F32 = 0, SGKS_F64 = 1 };
 enum { SGKS_OP_DENSE = 1, SGKS_OP_CSR = 2, SGKS_OP_CONV2D = 3 };
 enum { SGKS_REG_FD1 = 1, SGKS_REG_GRAD2D = 2, SGKS_REG_LAPLACE2D = 3, SGKS_REG_SPACETIME = 4 };
 enum { SGKS_SKETCH_SPARSE_SIGN = 0, SGKS_SKETCH_GAUSSIAN = 1, SGKS_SKETCH_SRTT = 2 };
-enum { SGKS_PREC_FP64 = 0, SGKS_PREC_FP32 = 1, SGKS_PREC_FP32X = 2 };
+enum { SGKS_PREC_FP64 = 0, SGKS_PREC_FP32 = 1, SGKS_PREC_FP32X = 2, SGKS_PREC_FP32_PLAIN = 3, SGKS_PREC_FF = 4 };
 enum { SGKS_FLAG_GLOBAL_SMALL = 1, SGKS_FLAG_RECORD = 2, SGKS_FLAG_GKS = 4, SGKS_FLAG_AUTOTUNE = 8 };
 
 /* Forward operator A (m x n).
@@ -96,14 +96,27 @@ typedef struct sgks_options {
     int32_t ell;          /* dimension of the initial Krylov basis W_0 [3]                          */
     int32_t n_refine;     /* refinement steps of the projected solve per iteration [0]              */
     int32_t precision;    /* SGKS_PREC_FP64: everything FP64.
-                             SGKS_PREC_FP32: FP32 operators, sketch and W with FP32 accumulation;
-                             FP64 sketched QR, projected solve and refinement reductions.
-                             SGKS_PREC_FP32X: FP32 storage of W, A and b; A W, x, e and every
-                             sum feeding the sketch or the gradient in compensated float-float
-                             arithmetic (TwoProd/TwoSum, Dot2); FP64 small phase.
-                             b, x_true and x_out are FP64 for FP64 and FP32 otherwise; for FP32X
-                             sgks_get_buffer(SGKS_BUF_X / SGKS_BUF_AW) returns (hi, lo) float
-                             pairs [FP64]                                                        */
+                             SGKS_PREC_FP32: the basis W, the operator values and b in FP32;
+                             the new column's A w and L w (the input of the sketched QR update),
+                             x = W y, e = A W y - b and the gradient (basis column and refinement
+                             residual) accumulated in compensated float-float arithmetic
+                             (TwoProd/TwoSum, Dot2) on the FP32 units, A W, x and e kept as
+                             float-float pairs; FP64 sketched QR, projected solve and refinement
+                             solve.  Iterates stay within the FP32-storage floor of the FP64
+                             ones.  SGKS_FLAG_GKS and SGKS_FLAG_RECORD run this form with the
+                             FP32-accumulation kernels of SGKS_PREC_FP32_PLAIN.
+                             SGKS_PREC_FP32X: the same form as SGKS_PREC_FP32.
+                             SGKS_PREC_FP32_PLAIN: FP32 operators, sketch, W, A W, x and e with
+                             FP32 accumulation; FP64 sketched QR, projected solve and refinement
+                             reductions (its iterates drift from the FP64 ones once the basis
+                             fills up).
+                             SGKS_PREC_FF (batches only): the basis and every vector as
+                             float-float pairs, compensated arithmetic on the FP32 units, FP64
+                             small phase: FP64-class results (48-bit significand, FP32 exponent
+                             range) at FP32-unit speed.
+                             b, x_true and x_out are FP64 for FP64 and FF, FP32 otherwise; for
+                             SGKS_PREC_FP32 sgks_get_buffer(SGKS_BUF_X / SGKS_BUF_AW) returns
+                             (hi, lo) float pairs [FP64]                                         */
     int32_t sketch_kind;  /* SGKS_SKETCH_SPARSE_SIGN, SGKS_SKETCH_GAUSSIAN or SGKS_SKETCH_SRTT
                              (eq. sketching_trig: S = sqrt(h/s) D F E, F the orthonormal DCT-II;
                              built as a dense FP64 matrix on the device at create) [sparse-sign] */
@@ -352,7 +365,8 @@ typedef struct sgks_batch sgks_batch;
  *  lambdas:  host array of `count` parameters, each > 0.
  *  x_true:   NULL, or a host array of `count` device pointers (n_i values each): RRE records.
  *  sketch_rows, seed, opt: as for sgks_create, shared by every instance; opt->x_true is ignored.
- *            Supported: precision SGKS_PREC_FP64 or SGKS_PREC_FP32, the sparse-sign sketch.
+ *            Supported: precision SGKS_PREC_FP64, SGKS_PREC_FP32 (= SGKS_PREC_FP32X),
+ *            SGKS_PREC_FP32_PLAIN or SGKS_PREC_FF; the sparse-sign sketch.
  * Errors as for sgks_create; SGKS_ERR_INVALID names the first bad instance. */
 int sgks_batch_create(sgks_batch** h, int32_t count, const sgks_op* A, const sgks_reg* L,
                       const void* const* b, const double* lambdas, const void* const* x_true,

@@ -5,10 +5,10 @@ method for Tikhonov regularization, as hand-written CUDA kernels for sm_103a beh
     from paper_2606_18073_gb300 import Solver, CSR, Dense, Conv2D, Reg
 """
 from . import _lib
-from .solver import (Batch, CSR, Conv2D, Dense, Reg, SGKSFunction, Solver, device_inputs, kernel_launches,
-                     solve_differentiable, sparse_sign_rows)
+from .solver import (PRECISIONS, Batch, CSR, Conv2D, Dense, Reg, SGKSFunction, Solver, device_inputs, io_dtype,
+                     kernel_launches, solve_differentiable, sparse_sign_rows)
 
-__all__ = ["Solver", "Batch", "SGKSFunction", "solve_differentiable", "CSR", "Dense", "Conv2D", "Reg", "device_inputs", "kernel_launches", "sparse_sign_rows", "_lib", "build"]
+__all__ = ["Solver", "Batch", "SGKSFunction", "solve_differentiable", "CSR", "Dense", "Conv2D", "Reg", "device_inputs", "kernel_launches", "sparse_sign_rows", "io_dtype", "PRECISIONS", "_lib", "build"]
 
 
 def build(force: bool = False) -> str:

@@ -19,7 +19,7 @@ SGKS_F32, SGKS_F64 = 0, 1
 SGKS_OP_DENSE, SGKS_OP_CSR, SGKS_OP_CONV2D = 1, 2, 3
 SGKS_REG_FD1, SGKS_REG_GRAD2D, SGKS_REG_LAPLACE2D, SGKS_REG_SPACETIME = 1, 2, 3, 4
 SGKS_SKETCH_SPARSE_SIGN, SGKS_SKETCH_GAUSSIAN, SGKS_SKETCH_SRTT = 0, 1, 2
-SGKS_PREC_FP64, SGKS_PREC_FP32, SGKS_PREC_FP32X = 0, 1, 2
+SGKS_PREC_FP64, SGKS_PREC_FP32, SGKS_PREC_FP32X, SGKS_PREC_FP32_PLAIN, SGKS_PREC_FF = 0, 1, 2, 3, 4
 (SGKS_BUF_X, SGKS_BUF_Y, SGKS_BUF_W, SGKS_BUF_QA, SGKS_BUF_RA, SGKS_BUF_QL, SGKS_BUF_RL,
  SGKS_BUF_DA, SGKS_BUF_SB, SGKS_BUF_T, SGKS_BUF_AW) = range(1, 12)
 (SGKS_APPLY_A, SGKS_APPLY_AT, SGKS_APPLY_L, SGKS_APPLY_LT, SGKS_APPLY_LTL, SGKS_APPLY_SA,

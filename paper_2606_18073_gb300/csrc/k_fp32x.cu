@@ -17,78 +17,12 @@
 // accurate arithmetic the deviation stays at the level of the FP32 storage rounding.
 #include <math.h>
 
+#include "ff.cuh"
 #include "sgks_internal.cuh"
 
 namespace sgks {
 
 constexpr int kXCluster = 8;
-
-// ------------------------------------------------------------------ error-free transforms
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-    p = __fmul_rn(a, b);
-    e = __fmaf_rn(a, b, -p);
-}
-
-// Dot2 accumulator: value = p + s.
-struct Dot2 {
-    float p = 0.f, s = 0.f;
-    __device__ __forceinline__ void add_prod(float a, float b) {
-        float h, r, q;
-        two_prod(a, b, h, r);
-        two_sum(p, h, p, q);
-        s = __fadd_rn(s, __fadd_rn(q, r));
-    }
-    // a * (bh + bl) with bh + bl a float-float value
-    __device__ __forceinline__ void add_prod2(float a, float bh, float bl) {
-        add_prod(a, bh);
-        s = __fmaf_rn(a, bl, s);
-    }
-    // (ah + al) * (bh + bl)
-    __device__ __forceinline__ void add_prod22(float ah, float al, float bh, float bl) {
-        add_prod(ah, bh);
-        s = __fmaf_rn(ah, bl, s);
-        s = __fmaf_rn(al, bh, s);
-    }
-    __device__ __forceinline__ void add(float a) {
-        float q;
-        two_sum(p, a, p, q);
-        s = __fadd_rn(s, q);
-    }
-    __device__ __forceinline__ void merge(const Dot2& o) {
-        float q;
-        two_sum(p, o.p, p, q);
-        s = __fadd_rn(s, __fadd_rn(q, o.s));
-    }
-    __device__ __forceinline__ float2 value() const {   // renormalised float-float pair
-        float hi, lo;
-        two_sum(p, s, hi, lo);
-        return make_float2(hi, lo);
-    }
-    __device__ __forceinline__ double to_double() const { return (double)p + (double)s; }
-};
-
-__device__ __forceinline__ double dval(float2 v) { return (double)v.x + (double)v.y; }
-__device__ __forceinline__ float2 dsplit(double v) {
-    const float h = (float)v;
-    return make_float2(h, (float)(v - (double)h));
-}
-
-// Warp-cooperative Dot2 reduction (lanes combine their accumulators in a fixed tree).
-__device__ __forceinline__ Dot2 warp_dot2(Dot2 a) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        Dot2 b;
-        b.p = __shfl_xor_sync(0xffffffffu, a.p, o);
-        b.s = __shfl_xor_sync(0xffffffffu, a.s, o);
-        a.merge(b);
-    }
-    return a;
-}
 
 // ------------------------------------------------------------------------- operator rows
 // A row j applied to an FP32 vector w (K1): CSR / dense warp-cooperative, conv per lane.

@@ -1020,7 +1020,7 @@ template <typename T, typename V>
 static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, const void* b, double lambda,
                         int s, uint64_t seed, const sgks_options& o, int cluster) {
     constexpr bool kF32 = std::is_same<T, float>::value && std::is_same<V, float>::value;
-    const bool xform = kF32 && o.precision == SGKS_PREC_FP32X;
+    const bool xform = kF32 && o.precision == SGKS_PREC_FP32;   // FP32_PLAIN: the FP32-accumulation kernels
     Engine<T, V>* E = nullptr;
     EngineX* EX = nullptr;
     if constexpr (kF32) {
@@ -1083,7 +1083,7 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
     D.nbG = (int)nbG;
     // k_gradient_refine2 (16-byte aligned columns of W, plain engine) leaves one partial per CTA,
     // the cluster kernels of the other cases one per cluster of 8
-    D.refine_np = (!(o.precision == SGKS_PREC_FP32X && std::is_same<T, float>::value) &&
+    D.refine_np = (!xform &&
                    (D.n * (int64_t)sizeof(T)) % 16 == 0) ? D.nbG : D.nbG / 8;
     D.nbX = (int)tiles;
     D.nbE = (int)((D.m + kThreads - 1) / kThreads);
@@ -1238,8 +1238,7 @@ int sgks::validate_problem(const sgks_op* A, const sgks_reg* L, const void* b, d
     if (o.max_iters < 1 || o.ell < 1 || o.ell > 8) return bad("need max_iters >= 1 and 1 <= ell <= 8");
     if (o.ell > A->n) return bad("ell must not exceed n");
     if (s > kMaxS || s < o.ell + o.max_iters) return bad("sketch_rows must satisfy ell + max_iters <= s <= 2048");
-    if (o.precision != SGKS_PREC_FP64 && o.precision != SGKS_PREC_FP32 && o.precision != SGKS_PREC_FP32X)
-        return bad("unknown precision");
+    if (o.precision < SGKS_PREC_FP64 || o.precision > SGKS_PREC_FF) return bad("unknown precision");
     if (o.sketch_kind == SGKS_SKETCH_SPARSE_SIGN) {
         if (o.zeta < 1 || o.zeta > kMaxZeta || o.zeta > s) return bad("zeta must satisfy 1 <= zeta <= min(16, s)");
     } else if (o.sketch_kind == SGKS_SKETCH_GAUSSIAN) {
@@ -1255,13 +1254,11 @@ int sgks::validate_problem(const sgks_op* A, const sgks_reg* L, const void* b, d
     if (o.n_refine < 0 || o.n_refine > 64) return bad("n_refine out of range");
     if (o.flags & SGKS_FLAG_GKS) {
         if (o.n_refine != 0) return bad("SGKS_FLAG_GKS (Algorithm 1) has no refinement: n_refine must be 0");
-        if (o.precision == SGKS_PREC_FP32X) return bad("SGKS_FLAG_GKS supports the FP64 and FP32 forms");
         if (o.flags & (SGKS_FLAG_RECORD | SGKS_FLAG_GLOBAL_SMALL))
             return bad("SGKS_FLAG_GKS cannot be combined with SGKS_FLAG_RECORD or SGKS_FLAG_GLOBAL_SMALL");
         if (o.ell + o.max_iters > 1024) return bad("SGKS_FLAG_GKS needs ell + max_iters <= 1024");
     }
     if (o.flags & SGKS_FLAG_RECORD) {
-        if (o.precision == SGKS_PREC_FP32X) return bad("SGKS_FLAG_RECORD supports the FP64 and FP32 forms");
         if (o.flags & SGKS_FLAG_GLOBAL_SMALL) return bad("SGKS_FLAG_RECORD needs the on-chip small kernels");
     }
     return SGKS_OK;
@@ -1282,6 +1279,12 @@ int sgks_create(sgks_handle** hp, const sgks_op* A, const sgks_reg* L, const voi
     std::string why;
     int rc = validate_problem(A, L, b, lambda, sketch_rows, o, &why);
     if (rc != SGKS_OK) return fail(nullptr, rc, why);
+    if (o.precision == SGKS_PREC_FF)
+        return fail(nullptr, SGKS_ERR_INVALID, "SGKS_PREC_FF is a batch form: use sgks_batch_create");
+    if (o.precision == SGKS_PREC_FP32X) o.precision = SGKS_PREC_FP32;
+    // GKS and the recorded (differentiable) solve have no compensated kernels: their FP32 form
+    // runs the FP32-accumulation kernels
+    if (o.precision == SGKS_PREC_FP32 && (o.flags & (SGKS_FLAG_GKS | SGKS_FLAG_RECORD))) o.precision = SGKS_PREC_FP32_PLAIN;
 
     sgks_handle* h = new (std::nothrow) sgks_handle();
     if (!h) return fail(nullptr, SGKS_ERR_NOMEM, "host allocation failed");
@@ -1304,7 +1307,7 @@ int sgks_create(sgks_handle** hp, const sgks_op* A, const sgks_reg* L, const voi
         return rc;
     }
     join_in(h);
-    if (o.precision == SGKS_PREC_FP32 || o.precision == SGKS_PREC_FP32X)
+    if (o.precision == SGKS_PREC_FP32 || o.precision == SGKS_PREC_FP32_PLAIN)
         rc = build_engine<float, float>(h, A, L, b, lambda, sketch_rows, seed, o, cluster);
     else if (A->kind == SGKS_OP_CSR && A->val_dtype == SGKS_F64)
         rc = build_engine<double, double>(h, A, L, b, lambda, sketch_rows, seed, o, cluster);

@@ -264,6 +264,180 @@ struct Group : GroupBase {
     }
 };
 
+// A group of the compensated forms (k_batchx.cu).  The setup builds W_0 in FP64 with the kernels
+// of the FP64 form (Xd, Ad) and rounds it to the basis type; every iteration then runs the
+// compensated kernels.
+template <typename TW>
+struct GroupX : GroupBase {
+    DevA<float, float> A{};
+    DevA<double, float> Ad{};   // the same operator for the FP64 setup kernels
+    DevL L{};
+    BBulkX<TW> X{};
+    BBulk<double> Xd{};         // setup: W = W_0 [ell][n][B], tm [m][B], b [m][B] in FP64
+    SketchCSR SK{};
+    int io_dt = SGKS_F32;       // element type of the caller's b, x_true and x_out
+
+    cudaError_t sketch_column() {
+        cudaError_t e = cudaSuccess;
+        RUNC(BK_APPLY, A.kind == SGKS_OP_CSR ? 2 : 1, launchbx_apply_column<TW>(D, A, L, X, S, st));
+        RUNC(BK_GATHER, 1, launchbx_sketch_gather<TW>(D, X, SK, S, nullptr, nullptr, st));
+        return e;
+    }
+
+    cudaError_t small_append() {
+        cudaError_t e = cudaSuccess;
+        RUNC(BK_QR_APPEND, 1, launch_qr_append(Ds, Small{}, st, Sarr, D.B));
+        RUNC(BK_STACKED_SOLVE, 1, launch_stacked_solve(Ds, Small{}, st, Sarr, D.B));
+        return e;
+    }
+
+    cudaError_t refine() {
+        cudaError_t e = cudaSuccess;
+        RUNC(BK_COMBINE_REFINE, 2, launchbx_combine<TW>(D, X, S, 0, st));
+        RUNC(BK_GRAD_REFINE, 1, launchbx_gradient<TW>(D, A, L, X, S, X.r, st));
+        RUNC(BK_GRAD_REFINE, 1, launchbx_wtr<TW>(D, X, S, X.r, st));
+        RUNC(BK_REFINE_SOLVE, 1, launch_refine_solve2(Ds, Small{}, st, Sarr, D.B, D.nb_refine));
+        return e;
+    }
+
+    cudaError_t normalize_d(double* w) {
+        cudaError_t e = cudaSuccess;
+        RUN(2, launchb_dots<double>(D, w, 1, w, S, st));
+        RUN(1, launchb_vec_update<double>(D, w, w, 0, S, 1, st));
+        return e;
+    }
+
+    // S_A b_i, ||x_true_i||^2, W_0 = orthonormal basis of K_l(A^T A, A^T b_i) by CGS2 in FP64
+    // (Sec. 2.1, Sec. 4), rounded to the basis type; the sketched QR of W_0, y_0, refinement, x_0
+    cudaError_t setup() override {
+        const int B = D.B;
+        const size_t nB = (size_t)D.n * B, mB = (size_t)D.m * B;
+        cudaError_t e = cudaMemsetAsync(S.sc, 0, sizeof(DevScalars) * B, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(S.ka_done, 0, sizeof(int), st);
+        RUN(1, launchbx_gather_in(bp, io_dt, X.b, D.m, B, st));
+        RUN(1, launchbx_to_double(X.b, Xd.b, (int64_t)mB, st));
+        RUN(1, launchbx_sketch_gather<TW>(D, X, SK, S, X.b, S.Sb, st));
+        double* W = Xd.W;
+        if (has_xt) {   // ||x_true||^2 from an FP64 copy (held in W_0's storage until W_0 is built)
+            RUN(1, launchbx_gather_in(xtp, io_dt, X.xtrue, D.n, B, st));
+            RUN(1, launchbx_to_double(X.xtrue, W, (int64_t)nB, st));
+            RUN(2, launchb_dots<double>(D, W, 1, W, S, st));
+            RUN(1, launchb_set_xt2(S, B, st));
+        }
+        RUN(1, (launchb_apply<double, float>(D, Ad, L, SGKS_APPLY_AT, Xd.b, W, st)));
+        if (e == cudaSuccess) e = normalize_d(W);
+        for (int j = 1; j < D.ell && e == cudaSuccess; ++j) {
+            double* wj = W + j * nB;
+            RUN(1, (launchb_apply<double, float>(D, Ad, L, SGKS_APPLY_A, W + (j - 1) * nB, Xd.tm, st)));
+            RUN(1, (launchb_apply<double, float>(D, Ad, L, SGKS_APPLY_AT, Xd.tm, wj, st)));
+            for (int pass = 0; pass < 2; ++pass) {
+                RUN(2, launchb_dots<double>(D, W, j, wj, S, st));
+                RUN(1, launchb_vec_update<double>(D, wj, W, j, S, 0, st));
+            }
+            if (e == cudaSuccess) e = normalize_d(wj);
+        }
+        RUN(1, launchbx_from_double<TW>(W, X.W, (int64_t)D.ell * nB, st));
+        for (int j = 0; j < D.ell && e == cudaSuccess; ++j) {
+            e = sketch_column();
+            if (e == cudaSuccess) e = small_append();
+        }
+        for (int r = 0; r < n_refine && e == cudaSuccess; ++r) e = refine();
+        RUN(2, launchbx_combine<TW>(D, X, S, 2, st));
+        return e;
+    }
+
+    cudaError_t step() override {
+        cudaError_t e = cudaSuccess;
+        RUNC(BK_GRAD_APPEND, 1, launchbx_gradient<TW>(D, A, L, X, S, nullptr, st));
+        if (e == cudaSuccess) e = sketch_column();
+        if (e == cudaSuccess) e = small_append();
+        for (int r = 0; r < n_refine && e == cudaSuccess; ++r) e = refine();
+        RUNC(BK_COMBINE, 2, launchbx_combine<TW>(D, X, S, 1, st));
+        return e;
+    }
+
+    // The tuner of Group: bulk-copy slice of the combine, lanes per CSR row of A and A^T.
+    cudaError_t tune() override {
+        const TuneKey key{D.m, D.n, D.p, A.kind == SGKS_OP_CSR ? nnz : 0, D.B, 100 + (int)sizeof(TW), A.kind};
+        {
+            std::lock_guard<std::mutex> g(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                D.slice_kb = it->second.slice_kb;
+                D.nl_a = it->second.nl_a;
+                D.nl_t = it->second.nl_t;
+                D.nb_combine = batchx_combine_grid(D, sizeof(TW));
+                tuned = "cached";
+                return cudaSuccess;
+            }
+        }
+        cudaEvent_t e0, e1;
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        if (e != cudaSuccess) return e;
+        auto time_it = [&](auto&& launch) -> float {
+            float best = 1e30f;
+            for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
+                cudaEventRecord(e0, st);
+                e = launch();
+                cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (r > 0 && ms < best) best = ms;
+            }
+            return best;
+        };
+        std::string log;
+        if (D.tma) {
+            float best = 1e30f;
+            int pick = D.slice_kb;
+            for (int kb : {16, 8}) {
+                D.slice_kb = kb;
+                D.nb_combine = batchx_combine_grid(D, sizeof(TW));
+                const float t = time_it([&] { return launchbx_combine<TW>(D, X, S, 0, st); });
+                log += " combine/" + std::to_string(kb) + "KB=" + std::to_string(t);
+                if (t < best) { best = t; pick = kb; }
+            }
+            D.slice_kb = pick;
+            D.nb_combine = batchx_combine_grid(D, sizeof(TW));
+        }
+        if (A.kind == SGKS_OP_CSR) {
+            for (int which = 0; which < 2; ++which) {
+                int* field = which == 0 ? &D.nl_a : &D.nl_t;
+                float best = 1e30f;
+                int pick = *field;
+                for (int nl : {1, 2, 4, 8, 16, 32}) {
+                    *field = nl;
+                    // the gradient is appended as column d, which the next step rewrites from
+                    // the same inputs
+                    const float t = time_it([&] {
+                        return which == 0 ? launchbx_apply_column<TW>(D, A, L, X, S, st)
+                                          : launchbx_gradient<TW>(D, A, L, X, S, nullptr, st);
+                    });
+                    log += std::string(which == 0 ? " A/" : " At/") + std::to_string(nl) + "=" + std::to_string(t);
+                    if (t < best) { best = t; pick = nl; }
+                }
+                *field = pick;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (e != cudaSuccess) return e;
+        tuned = "slice " + std::to_string(D.slice_kb) + " KB, lanes/row A " + std::to_string(D.nl_a) + ", A^T " +
+                std::to_string(D.nl_t) + " (ms:" + log + ")";
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune_cache[key] = TuneVal{D.slice_kb, D.nl_a, D.nl_t};
+        return cudaSuccess;
+    }
+
+    cudaError_t copy_x(const PtrPack& out, cudaStream_t s) override {
+        cudaError_t e = cudaSuccess;
+        RUN(1, launchbx_scatter_out(X.xs, out, io_dt, D.n, D.B, s));
+        return e;
+    }
+};
+
 int map_status(int dev) {
     switch (dev) {
         case ST_OK: return SGKS_OK;
@@ -350,6 +524,146 @@ int max_group_size(int dmax, int n_refine, size_t elem) {
     return B;
 }
 
+// Dimensions, FP64 per-instance state (sketched QR factors, projected solve, records) and the
+// scalars of one group of B instances; shared by both group kinds.  welem: bytes of a basis
+// value, velem: bytes of the other vectors' values; comb_grid(D): CTAs of the group's combine.
+template <typename CG>
+int init_group(sgks_batch* h, GroupBase* G, const sgks_op* op, const DevL& L, int B, int s, const sgks_options& o,
+               int cluster2, size_t welem, size_t velem, const double* lambdas, CG&& comb_grid) {
+    const int dmax = o.ell + o.max_iters;
+    G->nnz = op->kind == SGKS_OP_CSR ? op->nnz : 0;
+    G->n_refine = o.n_refine;
+    BDims& D = G->D;
+    D.n = op->n;
+    D.m = op->m;
+    D.p = L.p;
+    D.B = B;
+    D.s = s;
+    D.dmax = dmax;
+    D.ell = o.ell;
+    D.max_iters = o.max_iters;
+    D.sketch_scale = 1.0 / sqrt((double)o.zeta);
+    // the bulk-copy combine needs every column start of W and AW on a 16-byte boundary
+    D.tma = ((size_t)D.n * B * welem) % 16 == 0 && ((size_t)D.m * B * velem) % 16 == 0;
+    D.slice_kb = 16;
+    D.nl_a = 8;
+    D.nl_t = 8;
+    D.nb_combine = comb_grid(D);
+    int nb_comb_max = D.nb_combine;
+    if (D.tma) {   // the tuner may pick 8 KB slices: size the partials for the larger grid
+        BDims D8 = D;
+        D8.slice_kb = 8;
+        nb_comb_max = std::max(nb_comb_max, comb_grid(D8));
+    }
+    const int64_t rtiles = (D.n + 1024 / B - 1) / (1024 / B);
+    {   // enough CTAs to fill every SM at the residency the refinement's shared memory allows
+        const size_t sm = batch_refine_smem(dmax, B, velem) + 2048;
+        int64_t per_sm = (int64_t)((227 * 1024) / sm);
+        // at most two per SM: each CTA leaves one partial per instance for the solve to sum
+        per_sm = std::max<int64_t>(1, std::min<int64_t>(per_sm, 2));
+        const int64_t cap = std::max<int64_t>(8, 152 * per_sm / 8 * 8);
+        D.nb_refine = (int)std::min<int64_t>((rtiles + 7) / 8 * 8, cap);
+    }
+    D.nb_setup = (int)std::min<int64_t>((D.n * B + kThreads - 1) / kThreads, 304);
+    Dims& Ds = G->Ds;
+    Ds.n = D.n;
+    Ds.m = D.m;
+    Ds.p = D.p;
+    Ds.s = s;
+    Ds.zeta = o.zeta;
+    Ds.dmax = dmax;
+    Ds.ell = o.ell;
+    Ds.npA = 1;
+    Ds.npL = 1;
+    Ds.cluster2 = cluster2;
+    Ds.fast_small = 1;
+    Ds.sketch_kind = SGKS_SKETCH_SPARSE_SIGN;
+    Ds.sketch_scale = D.sketch_scale;
+    Ds.cgs_passes = o.cgs_passes;
+    Ds.max_iters = o.max_iters;
+
+    cudaError_t e = cudaSuccess;
+#define BA(ptr, cnt)                                              \
+    do {                                                          \
+        if (e == cudaSuccess) e = balloc(h, &(ptr), (size_t)(cnt)); \
+    } while (0)
+    BSmall& S = G->S;
+    BA(S.partA, (size_t)B * s);
+    BA(S.partL, (size_t)B * s);
+    BA(S.Sb, (size_t)B * s);
+    BA(S.gpart, (size_t)B * D.nb_refine * dmax);
+    BA(S.kapart, (size_t)nb_comb_max * B * 3);
+    BA(S.y, (size_t)B * dmax);
+    BA(S.lam, B);
+    BA(S.rc_hist, (size_t)B * o.max_iters);
+    BA(S.rre_hist, (size_t)B * o.max_iters);
+    BA(S.setup_part, (size_t)D.nb_setup * o.ell * B);
+    BA(S.setup_coef, (size_t)o.ell * B);
+    BA(S.sc, B);
+    BA(S.ka_done, 1);
+    // per-instance FP64 state of the sketched QR factors and the projected solve
+    const size_t dm2 = (size_t)dmax * dmax;
+    double *QA, *QL, *RA, *RL, *QT, *Xr, *z, *qo, *Xm, *Tm, *dA;
+    BA(QA, (size_t)B * s * dmax);
+    BA(QL, (size_t)B * s * dmax);
+    BA(RA, B * dm2);
+    BA(RL, B * dm2);
+    BA(QT, B * 2 * dm2);
+    BA(Xr, B * dm2);
+    BA(z, (size_t)B * dmax);
+    BA(qo, (size_t)B * 8);
+    BA(Xm, B * dm2);
+    BA(Tm, B * dm2);
+    BA(dA, (size_t)B * dmax);
+    BA(G->Sarr, B);
+#undef BA
+    if (e != cudaSuccess) return bfail(h, SGKS_ERR_NOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
+    std::vector<Small> sm((size_t)B);
+    std::vector<double> lam((size_t)B);
+    for (int i = 0; i < B; ++i) {
+        Small& q = sm[i];
+        q = Small{};
+        q.QA = QA + (size_t)i * s * dmax;
+        q.QL = QL + (size_t)i * s * dmax;
+        q.RA = RA + i * dm2;
+        q.RL = RL + i * dm2;
+        q.QT = QT + i * 2 * dm2;
+        q.Xr = Xr + i * dm2;
+        q.z = z + (size_t)i * dmax;
+        q.qr_out = qo + (size_t)i * 8;
+        q.X = Xm + i * dm2;
+        q.Tm = Tm + i * dm2;
+        q.dA = dA + (size_t)i * dmax;
+        q.y = S.y + (size_t)i * dmax;
+        q.Sb = S.Sb + (size_t)i * s;
+        q.partA = S.partA + (size_t)i * s;
+        q.partL = S.partL + (size_t)i * s;
+        q.gpart = S.gpart + (size_t)i * D.nb_refine * dmax;
+        q.sc = S.sc + i;
+        q.lam = lambdas[G->members[i]];
+        lam[i] = q.lam;
+    }
+    e = cudaMemcpy(G->Sarr, sm.data(), sizeof(Small) * B, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(S.lam, lam.data(), sizeof(double) * B, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.y, 0, sizeof(double) * B * dmax, h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.ka_done, 0, sizeof(int), h->st);   // also at every setup
+    if (e != cudaSuccess) return bcuda_fail(h, e, "batch workspace initialisation");
+    return SGKS_OK;
+}
+
+// group sizes: powers of two, largest first, each at most bcap
+std::vector<int> split_groups(size_t count, int bcap) {
+    std::vector<int> out;
+    size_t pos = 0;
+    while (pos < count) {
+        int B = bcap;
+        while ((size_t)B > count - pos) B >>= 1;
+        out.push_back(B);
+        pos += B;
+    }
+    return out;
+}
+
 template <typename T, typename V>
 int build_groups(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const std::vector<int>& inst,
                  const void* const* b, const double* lambdas, const void* const* x_true, int s, uint64_t seed,
@@ -366,13 +680,10 @@ int build_groups(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const st
     if (rc != SGKS_OK) return bfail(h, rc, why);
 
     const int dmax = o.ell + o.max_iters;
-    const int bcap = max_group_size(dmax, o.n_refine, sizeof(T));
     if (o.n_refine > 0 && batch_refine_smem(dmax, 1, sizeof(T)) > 200 * 1024)
         return bfail(h, SGKS_ERR_INVALID, "ell + max_iters too large for the batched refinement");
     size_t pos = 0;
-    while (pos < inst.size()) {
-        int B = bcap;
-        while ((size_t)B > inst.size() - pos) B >>= 1;
+    for (const int B : split_groups(inst.size(), max_group_size(dmax, o.n_refine, sizeof(T)))) {
         Group<T, V>* G = new (std::nothrow) Group<T, V>();
         if (!G) return bfail(h, SGKS_ERR_NOMEM, "host allocation failed");
         h->groups.push_back(G);
@@ -381,62 +692,15 @@ int build_groups(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const st
         G->A = A;
         G->L = L;
         G->SK = SK;
-        G->nnz = op->kind == SGKS_OP_CSR ? op->nnz : 0;
-        G->n_refine = o.n_refine;
         G->has_xt = x_true != nullptr;
         for (int i = 0; i < B; ++i) {
             G->bp.p[i] = b[G->members[i]];
             G->xtp.p[i] = x_true ? x_true[G->members[i]] : nullptr;
         }
-        BDims& D = G->D;
-        D.n = op->n;
-        D.m = op->m;
-        D.p = L.p;
-        D.B = B;
-        D.s = s;
-        D.dmax = dmax;
-        D.ell = o.ell;
-        D.max_iters = o.max_iters;
-        D.sketch_scale = 1.0 / sqrt((double)o.zeta);
-        // the bulk-copy combine needs every column start of W and AW on a 16-byte boundary
-        D.tma = ((size_t)D.n * B * sizeof(T)) % 16 == 0 && ((size_t)D.m * B * sizeof(T)) % 16 == 0;
-        D.slice_kb = 16;
-        D.nl_a = 8;
-        D.nl_t = 8;
-        D.nb_combine = batch_combine_grid(D, sizeof(T));
-        int nb_comb_max = D.nb_combine;
-        if (D.tma) {   // the tuner may pick 8 KB slices: size the partials for the larger grid
-            BDims D8 = D;
-            D8.slice_kb = 8;
-            nb_comb_max = std::max(nb_comb_max, batch_combine_grid(D8, sizeof(T)));
-        }
-        const int64_t rtiles = (D.n + 1024 / B - 1) / (1024 / B);
-        {   // enough CTAs to fill every SM at the residency the refinement's shared memory allows
-            const size_t sm = batch_refine_smem(dmax, B, sizeof(T)) + 2048;
-            int64_t per_sm = (int64_t)((227 * 1024) / sm);
-            // at most two per SM: each CTA leaves one partial per instance for the solve to sum
-            per_sm = std::max<int64_t>(1, std::min<int64_t>(per_sm, 2));
-            const int64_t cap = std::max<int64_t>(8, 152 * per_sm / 8 * 8);
-            D.nb_refine = (int)std::min<int64_t>((rtiles + 7) / 8 * 8, cap);
-        }
-        D.nb_setup = (int)std::min<int64_t>((D.n * B + kThreads - 1) / kThreads, 304);
-        Dims& Ds = G->Ds;
-        Ds.n = D.n;
-        Ds.m = D.m;
-        Ds.p = D.p;
-        Ds.s = s;
-        Ds.zeta = o.zeta;
-        Ds.dmax = dmax;
-        Ds.ell = o.ell;
-        Ds.npA = 1;
-        Ds.npL = 1;
-        Ds.cluster2 = cluster2;
-        Ds.fast_small = 1;
-        Ds.sketch_kind = SGKS_SKETCH_SPARSE_SIGN;
-        Ds.sketch_scale = D.sketch_scale;
-        Ds.cgs_passes = o.cgs_passes;
-        Ds.max_iters = o.max_iters;
-
+        rc = init_group(h, G, op, L, B, s, o, cluster2, sizeof(T), sizeof(T), lambdas,
+                        [](const BDims& D) { return batch_combine_grid(D, sizeof(T)); });
+        if (rc != SGKS_OK) return rc;
+        const BDims& D = G->D;
         cudaError_t e = cudaSuccess;
 #define BA(ptr, cnt)                                              \
     do {                                                          \
@@ -454,67 +718,103 @@ int build_groups(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const st
         BA(X.tp, pB);
         BA(X.tm, mB);
         if (o.n_refine > 0) BA(X.r, nB);
-        BSmall& S = G->S;
-        BA(S.partA, (size_t)B * s);
-        BA(S.partL, (size_t)B * s);
-        BA(S.Sb, (size_t)B * s);
-        BA(S.gpart, (size_t)B * D.nb_refine * dmax);
-        BA(S.kapart, (size_t)nb_comb_max * B * 3);
-        BA(S.y, (size_t)B * dmax);
-        BA(S.lam, B);
-        BA(S.rc_hist, (size_t)B * o.max_iters);
-        BA(S.rre_hist, (size_t)B * o.max_iters);
-        BA(S.setup_part, (size_t)D.nb_setup * o.ell * B);
-        BA(S.setup_coef, (size_t)o.ell * B);
-        BA(S.sc, B);
-        BA(S.ka_done, 1);
-        // per-instance FP64 state of the sketched QR factors and the projected solve
-        const size_t dm2 = (size_t)dmax * dmax;
-        double *QA, *QL, *RA, *RL, *QT, *Xr, *z, *qo, *Xm, *Tm, *dA;
-        BA(QA, (size_t)B * s * dmax);
-        BA(QL, (size_t)B * s * dmax);
-        BA(RA, B * dm2);
-        BA(RL, B * dm2);
-        BA(QT, B * 2 * dm2);
-        BA(Xr, B * dm2);
-        BA(z, (size_t)B * dmax);
-        BA(qo, (size_t)B * 8);
-        BA(Xm, B * dm2);
-        BA(Tm, B * dm2);
-        BA(dA, (size_t)B * dmax);
-        BA(G->Sarr, B);
 #undef BA
         if (e != cudaSuccess) return bfail(h, SGKS_ERR_NOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
-        std::vector<Small> sm((size_t)B);
-        std::vector<double> lam((size_t)B);
+        e = cudaMemsetAsync(X.xs, 0, sizeof(T) * nB, h->st);
+        if (e != cudaSuccess) return bcuda_fail(h, e, "batch workspace initialisation");
+    }
+    return SGKS_OK;
+}
+
+// Groups of the compensated forms (k_batchx.cu): basis in TW (float: FP32 form; float2: float-
+// float form); b, x_true and x_out in io_dt (SGKS_F32 or SGKS_F64) at the interface.
+template <typename TW>
+int build_groups_x(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const std::vector<int>& inst,
+                   const void* const* b, const double* lambdas, const void* const* x_true, int s, uint64_t seed,
+                   const sgks_options& o, int cluster2, int io_dt) {
+    DevA<float, float> A{};
+    DevA<double, float> Ad{};
+    std::string why;
+    int rc = prepare_operator<float, float>(op, A, h->allocs, h->d_err, h->st, &why, false);
+    if (rc != SGKS_OK) return bfail(h, rc, why);
+    if (op->kind == SGKS_OP_CSR) {   // the FP64 setup kernels read the same FP32 CSR arrays
+        Ad.kind = A.kind;
+        Ad.m = A.m;
+        Ad.n = A.n;
+        Ad.nnz = A.nnz;
+        Ad.rp = A.rp;
+        Ad.ci = A.ci;
+        Ad.val = A.val;
+        Ad.trp = A.trp;
+        Ad.tci = A.tci;
+        Ad.tval = A.tval;
+    } else {
+        rc = prepare_operator<double, float>(op, Ad, h->allocs, h->d_err, h->st, &why, false);
+        if (rc != SGKS_OK) return bfail(h, rc, why);
+    }
+    const DevL L = make_devl(reg);
+    SketchCSR SK{};
+    rc = prepare_sparse_sign(sketch_key_host_dev(seed, 0), sketch_key_host_dev(seed, 1), op->m, L.p, s, o.zeta, SK,
+                             h->allocs, h->d_err, h->st, &why);
+    if (rc != SGKS_OK) return bfail(h, rc, why);
+    const int dmax = o.ell + o.max_iters;
+    if (o.n_refine > 0 && batch_refine_smem(dmax, 1, sizeof(float2)) > 200 * 1024)
+        return bfail(h, SGKS_ERR_INVALID, "ell + max_iters too large for the batched refinement");
+    size_t pos = 0;
+    for (const int B : split_groups(inst.size(), max_group_size(dmax, o.n_refine, sizeof(float2)))) {
+        GroupX<TW>* G = new (std::nothrow) GroupX<TW>();
+        if (!G) return bfail(h, SGKS_ERR_NOMEM, "host allocation failed");
+        h->groups.push_back(G);
+        G->members.assign(inst.begin() + pos, inst.begin() + pos + B);
+        pos += B;
+        G->A = A;
+        G->Ad = Ad;
+        G->L = L;
+        G->SK = SK;
+        G->io_dt = io_dt;
+        G->has_xt = x_true != nullptr;
         for (int i = 0; i < B; ++i) {
-            Small& q = sm[i];
-            q = Small{};
-            q.QA = QA + (size_t)i * s * dmax;
-            q.QL = QL + (size_t)i * s * dmax;
-            q.RA = RA + i * dm2;
-            q.RL = RL + i * dm2;
-            q.QT = QT + i * 2 * dm2;
-            q.Xr = Xr + i * dm2;
-            q.z = z + (size_t)i * dmax;
-            q.qr_out = qo + (size_t)i * 8;
-            q.X = Xm + i * dm2;
-            q.Tm = Tm + i * dm2;
-            q.dA = dA + (size_t)i * dmax;
-            q.y = S.y + (size_t)i * dmax;
-            q.Sb = S.Sb + (size_t)i * s;
-            q.partA = S.partA + (size_t)i * s;
-            q.partL = S.partL + (size_t)i * s;
-            q.gpart = S.gpart + (size_t)i * D.nb_refine * dmax;
-            q.sc = S.sc + i;
-            q.lam = lambdas[G->members[i]];
-            lam[i] = q.lam;
+            G->bp.p[i] = b[G->members[i]];
+            G->xtp.p[i] = x_true ? x_true[G->members[i]] : nullptr;
         }
-        e = cudaMemcpy(G->Sarr, sm.data(), sizeof(Small) * B, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(S.lam, lam.data(), sizeof(double) * B, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemsetAsync(S.y, 0, sizeof(double) * B * dmax, h->st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(X.xs, 0, sizeof(T) * nB, h->st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(S.ka_done, 0, sizeof(int), h->st);   // also at every setup
+        rc = init_group(h, G, op, L, B, s, o, cluster2, sizeof(TW), sizeof(float2), lambdas,
+                        [](const BDims& D) { return batchx_combine_grid(D, sizeof(TW)); });
+        if (rc != SGKS_OK) return rc;
+        const BDims& D = G->D;
+        cudaError_t e = cudaSuccess;
+#define BA(ptr, cnt)                                              \
+    do {                                                          \
+        if (e == cudaSuccess) e = balloc(h, &(ptr), (size_t)(cnt)); \
+    } while (0)
+        BBulkX<TW>& X = G->X;
+        const size_t nB = (size_t)D.n * B, mB = (size_t)D.m * B, pB = (size_t)D.p * B;
+        float2 *lam2 = nullptr;
+        BA(X.W, (size_t)dmax * nB);
+        BA(X.AW, (size_t)dmax * mB);
+        BA(X.x, nB);
+        BA(X.xs, nB);
+        BA(X.e, mB);
+        BA(X.b, mB);
+        if (G->has_xt) BA(X.xtrue, nB);
+        BA(X.tp, pB);
+        if (o.n_refine > 0) BA(X.r, nB);
+        BA(lam2, B);
+        BA(X.y2, (size_t)B * dmax);
+        // the FP64 setup of W_0 (Krylov basis, CGS2): its ell columns, a temporary and b
+        BA(G->Xd.W, (size_t)D.ell * nB);
+        BA(G->Xd.tm, mB);
+        BA(G->Xd.b, mB);
+#undef BA
+        if (e != cudaSuccess) return bfail(h, SGKS_ERR_NOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
+        X.lam2 = lam2;
+        std::vector<float2> l2((size_t)B);
+        for (int i = 0; i < B; ++i) {
+            const double lam = lambdas[G->members[i]];
+            const float hi = (float)lam;
+            l2[i] = make_float2(hi, (float)(lam - (double)hi));
+        }
+        e = cudaMemcpy(lam2, l2.data(), sizeof(float2) * B, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemsetAsync(X.xs, 0, sizeof(float2) * nB, h->st);
         if (e != cudaSuccess) return bcuda_fail(h, e, "batch workspace initialisation");
     }
     return SGKS_OK;
@@ -570,8 +870,10 @@ int sgks_batch_create(sgks_batch** hp, int32_t count, const sgks_op* A, const sg
     if (o.ell == 0) o.ell = 3;
     if (o.zeta == 0) o.zeta = 8;
     if (o.cgs_passes == 0) o.cgs_passes = 2;
-    if (o.precision != SGKS_PREC_FP64 && o.precision != SGKS_PREC_FP32)
-        return bfail(nullptr, SGKS_ERR_INVALID, "batches support SGKS_PREC_FP64 and SGKS_PREC_FP32");
+    if (o.precision == SGKS_PREC_FP32X) o.precision = SGKS_PREC_FP32;
+    if (o.precision != SGKS_PREC_FP64 && o.precision != SGKS_PREC_FP32 && o.precision != SGKS_PREC_FP32_PLAIN &&
+        o.precision != SGKS_PREC_FF)
+        return bfail(nullptr, SGKS_ERR_INVALID, "unknown precision");
     if (o.sketch_kind != SGKS_SKETCH_SPARSE_SIGN)
         return bfail(nullptr, SGKS_ERR_INVALID, "batches support the sparse-sign sketch only");
     if (o.flags & (SGKS_FLAG_GKS | SGKS_FLAG_RECORD | SGKS_FLAG_GLOBAL_SMALL))
@@ -631,6 +933,12 @@ int sgks_batch_create(sgks_batch** hp, int32_t count, const sgks_op* A, const sg
         const sgks_op* op = &A[rep[k]];
         const sgks_reg* reg = &L[rep[k]];
         if (o.precision == SGKS_PREC_FP32)
+            rc = build_groups_x<float>(h, op, reg, members[k], b, lambdas, x_true, sketch_rows, seed, o, cluster2,
+                                       SGKS_F32);
+        else if (o.precision == SGKS_PREC_FF)
+            rc = build_groups_x<float2>(h, op, reg, members[k], b, lambdas, x_true, sketch_rows, seed, o, cluster2,
+                                        SGKS_F64);
+        else if (o.precision == SGKS_PREC_FP32_PLAIN)
             rc = build_groups<float, float>(h, op, reg, members[k], b, lambdas, x_true, sketch_rows, seed, o, cluster2);
         else if (op->kind == SGKS_OP_CSR && op->val_dtype == SGKS_F64)
             rc = build_groups<double, double>(h, op, reg, members[k], b, lambdas, x_true, sketch_rows, seed, o,

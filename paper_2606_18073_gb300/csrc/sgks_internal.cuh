@@ -865,6 +865,22 @@ struct BBulk {
     T* r;                     // [n][B] gradient r(y) inside the refinement
 };
 
+// Batched compensated forms (k_batchx.cu): the basis W in TW (float for the FP32 form, float2
+// for the float-float form), every other vector as float-float pairs (hi, lo).
+template <typename TW>
+struct BBulkX {
+    TW* W;                    // [dmax][n][B]
+    float2* AW;               // [dmax][m][B]
+    float2 *x, *xs;           // [n][B]
+    float2* e;                // [m][B] A x - b
+    float2* b;                // [m][B]
+    float2* xtrue;            // [n][B] or nullptr
+    float2* tp;               // [p][B] L w of the newest column
+    float2* r;                // [n][B] gradient r(y) inside the refinement
+    const float2* lam2;       // [B] lambda_i split into (hi, lo)
+    float2* y2;               // [B][dmax] y_i split into (hi, lo) for the combine
+};
+
 struct BSmall {
     double *partA, *partL;    // [B][s] sketched newest column (one partial)
     double* Sb;               // [B][s] S_A b_i
@@ -909,6 +925,31 @@ template <typename T>
 cudaError_t launchb_gather_in(const PtrPack& P, T* out, int64_t len, int B, cudaStream_t st);
 template <typename T>
 cudaError_t launchb_scatter_out(const T* in, const PtrPack& P, int64_t len, int B, cudaStream_t st);
+// compensated batched kernels (k_batchx.cu); TW = float or float2
+template <typename TW>
+cudaError_t launchbx_apply_column(const BDims& D, const DevA<float, float>& A, const DevL& L, const BBulkX<TW>& X,
+                                  const BSmall& S, cudaStream_t st);
+template <typename TW>
+cudaError_t launchbx_sketch_gather(const BDims& D, const BBulkX<TW>& X, const SketchCSR& SK, const BSmall& S,
+                                   const float2* vec, double* out_vec, cudaStream_t st);
+template <typename TW>
+cudaError_t launchbx_combine(const BDims& D, const BBulkX<TW>& X, const BSmall& S, int mode, cudaStream_t st);
+template <typename TW>
+cudaError_t launchbx_gradient(const BDims& D, const DevA<float, float>& A, const DevL& L, const BBulkX<TW>& X,
+                              const BSmall& S, float2* out, cudaStream_t st);
+template <typename TW>
+cudaError_t launchbx_wtr(const BDims& D, const BBulkX<TW>& X, const BSmall& S, const float2* r, cudaStream_t st);
+// in: float (in_dt SGKS_F32) or double values per instance -> float-float [len][B]
+cudaError_t launchbx_gather_in(const PtrPack& P, int in_dt, float2* out, int64_t len, int B, cudaStream_t st);
+// float-float [len][B] -> float (rounded) or double per instance (null pointers skipped)
+cudaError_t launchbx_scatter_out(const float2* in, const PtrPack& P, int out_dt, int64_t len, int B, cudaStream_t st);
+// out[i] = in[i] rounded to TW (float: nearest float; float2: split)
+template <typename TW>
+cudaError_t launchbx_from_double(const double* in, TW* out, int64_t len, cudaStream_t st);
+// double copy of a float-float vector
+cudaError_t launchbx_to_double(const float2* in, double* out, int64_t len, cudaStream_t st);
+size_t batchx_combine_smem(size_t welem, int slice_kb);
+int batchx_combine_grid(const BDims& D, size_t welem);
 cudaError_t launchb_set_xt2(const BSmall& S, int B, cudaStream_t st);
 cudaError_t launchb_set_tol(DevScalars* sc, int B, double tol, cudaStream_t st);
 size_t batch_refine_smem(int dmax, int B, size_t elem);

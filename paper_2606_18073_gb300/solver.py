@@ -14,6 +14,25 @@ import torch
 from . import _lib as L
 
 
+# Precision forms (the precision field of sgks_options):
+#   "fp64"       everything FP64;
+#   "fp32"       FP32 basis, operator values and b; the sketch inputs, x, e and the gradient in
+#                compensated float-float arithmetic on the FP32 units; FP64 small phase
+#                ("fp32x" is the same form);
+#   "fp32plain"  FP32 arithmetic with FP32 accumulation in the operator passes (drifts from the
+#                FP64 iterates; kept for comparison);
+#   "ff"         batches only: the basis and every vector in float-float, FP64-class results.
+PRECISIONS = {"fp64": L.SGKS_PREC_FP64, "fp32": L.SGKS_PREC_FP32, "fp32x": L.SGKS_PREC_FP32X,
+              "fp32plain": L.SGKS_PREC_FP32_PLAIN, "ff": L.SGKS_PREC_FF}
+
+
+def io_dtype(precision):
+    """Element type of b, x_true and x at the interface for a precision form."""
+    if precision not in PRECISIONS:
+        raise ValueError(f"unknown precision {precision!r}")
+    return torch.float32 if precision in ("fp32", "fp32x", "fp32plain") else torch.float64
+
+
 def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
@@ -131,7 +150,7 @@ class Solver:
                  method: str = "sgks", srtt=None):
         self._lib = L.load()
         self.precision = precision
-        self.dtype = torch.float32 if precision in ("fp32", "fp32x") else torch.float64
+        self.dtype = io_dtype(precision)
         for nm, t in (("b", b), ("x_true", x_true)):
             _need_cuda(t, nm)
             if t is not None and t.dtype != self.dtype:
@@ -148,7 +167,7 @@ class Solver:
         self.max_iters = max_iters
         o = L.sgks_options()
         o.max_iters, o.ell, o.n_refine, o.zeta, o.cgs_passes = max_iters, ell, n_refine, zeta, cgs_passes
-        o.precision = {"fp64": L.SGKS_PREC_FP64, "fp32": L.SGKS_PREC_FP32, "fp32x": L.SGKS_PREC_FP32X}[precision]
+        o.precision = PRECISIONS[precision]
         o.sketch_kind = {"gaussian": L.SGKS_SKETCH_GAUSSIAN, "srtt": L.SGKS_SKETCH_SRTT}.get(
             sketch, L.SGKS_SKETCH_SPARSE_SIGN)
         o.gauss_SA, o.gauss_SL, o.x_true = _ptr(gauss_SA), _ptr(gauss_SL), _ptr(x_true)
@@ -216,10 +235,14 @@ class Solver:
         return out[: n.value // out.element_size()]
 
     def x(self):
-        """Current iterate x_k; for fp32x the float-float pairs are summed in float64."""
-        if self.precision == "fp32x":
-            v = self.buffer(L.SGKS_BUF_X, 2 * self.n, torch.float32).view(self.n, 2).double()
-            return v[:, 0] + v[:, 1]
+        """Current iterate x_k.  The compensated FP32 form keeps x as float-float pairs, which are
+        summed in float64 here."""
+        if self.dtype == torch.float32:
+            v = self.buffer(L.SGKS_BUF_X, 2 * self.n, torch.float32)
+            if v.numel() == 2 * self.n:
+                v = v.view(self.n, 2).double()
+                return v[:, 0] + v[:, 1]
+            return v
         return self.buffer(L.SGKS_BUF_X, self.n, self.dtype)
 
     def apply(self, which: int, x: torch.Tensor, out: torch.Tensor):
@@ -290,7 +313,7 @@ class Batch:
                  autotune: bool = False):
         self._lib = L.load()
         self.precision = precision
-        self.dtype = torch.float32 if precision in ("fp32", "fp32x") else torch.float64
+        self.dtype = io_dtype(precision)
         k = len(instances)
         if k < 1:
             raise ValueError("a batch needs at least one instance")
@@ -311,7 +334,7 @@ class Batch:
         self._xt = (C.c_void_p * k)(*[inst["x_true"].data_ptr() for inst in instances]) if has_xt else None
         o = L.sgks_options()
         o.max_iters, o.ell, o.n_refine, o.zeta, o.cgs_passes = max_iters, ell, n_refine, zeta, cgs_passes
-        o.precision = {"fp64": L.SGKS_PREC_FP64, "fp32": L.SGKS_PREC_FP32, "fp32x": L.SGKS_PREC_FP32X}[precision]
+        o.precision = PRECISIONS[precision]
         o.sketch_kind = L.SGKS_SKETCH_SPARSE_SIGN
         o.flags = L.SGKS_FLAG_AUTOTUNE if autotune else 0
         self.max_iters = max_iters
@@ -466,7 +489,7 @@ def device_inputs(problem, precision: Optional[str] = None, device="cuda", trans
     import numpy as np
 
     prec = precision or problem.precision
-    dt = torch.float32 if prec in ("fp32", "fp32x") else torch.float64
+    dt = io_dtype(prec)
     A = problem.A
     if A.kind == "csr":
         op = CSR(torch.from_numpy(np.ascontiguousarray(A.row_ptr)).to(device),

@@ -15,6 +15,7 @@ import pytest
 import torch
 
 import oracle as O
+import parity_log
 from workloads import small_problem
 from workloads.problem import SketchDesc
 
@@ -66,7 +67,7 @@ def share_operators(problems, s, zeta=8, seed=0):
 
 
 def batch_inputs(G, problems, prec):
-    dt = torch.float32 if prec == "fp32" else torch.float64
+    dt = G.io_dtype(prec)
     ops = {}
     insts = []
     for P in problems:
@@ -97,12 +98,19 @@ def batch_iterates(G, problems, prec, iters, **over):
     return Bt, xs
 
 
+FORM_BAR = {  # precision -> (floor eps, strict bar, factor on the floor)
+    "fp64": (EPS["fp64"], TOL64, FACTOR64),
+    "ff": (EPS["ff"], TOL64, FACTOR64),
+    "fp32": (EPS["fp32"], TOL32, FACTOR32),
+}
+
+
 def check_instance(xs, P, prec):
     ref = O.sgks(P, iters=len(xs) - 1, record_x=True)
-    eps = EPS["fp64" if prec == "fp64" else "fp32"]
+    eps, tol, fac = FORM_BAR[prec]
     fl = floor_curve(P, len(xs) - 1, eps)[0]
-    tol, fac = (TOL64, FACTOR64) if prec == "fp64" else (TOL32, FACTOR32)
     errs = [rel(a, b) for a, b in zip(xs, ref["xs"])]
+    parity_log.record(f"batch[{prec}] {P.name}", errs, fl, tol, fac)
     bad = [(k, e, fl[k]) for k, e in enumerate(errs) if e > max(tol, fac * fl[k])]
     assert not bad, f"{P.name}: iterates above max(tol, {fac} x floor): {bad[:4]}"
     return ref
@@ -117,19 +125,22 @@ def ct_instances(count, iters=15):
 
 # --------------------------------------------------------------------------------- parity
 
-def test_batch_ct_instances_split_into_groups_match_oracle(G):
-    """Five CT instances (own noise and lambda_i = 10^(-4 + 3i/63)) sharing one CSR: groups 4 + 1."""
+@pytest.mark.parametrize("prec", ["fp64", "ff", "fp32"])
+def test_batch_ct_instances_split_into_groups_match_oracle(G, prec):
+    """Five CT instances (own noise and lambda_i = 10^(-4 + 3i/63)) sharing one CSR: groups 4 + 1;
+    the FP64 form and the two compensated forms."""
     probs = ct_instances(5)
-    Bt, xs = batch_iterates(G, probs, "fp64", probs[0].iters)
+    Bt, xs = batch_iterates(G, probs, prec, probs[0].iters)
     ng, grp, size = Bt.layout()
     assert ng == 2 and sorted(size) == [1, 4, 4, 4, 4]
     for P, x in zip(probs, xs):
-        check_instance(x, P, "fp64")
+        check_instance(x, P, prec)
     Bt.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "ff", "fp32"])
 @pytest.mark.parametrize("kind", ["deblur2d", "seismic2d", "deconv1d"])
-def test_batch_operator_families_match_oracle(G, kind):
+def test_batch_operator_families_match_oracle(G, kind, prec):
     """Convolution + grad2d with refinement, CSR + Laplacian, dense + fd1: four instances each."""
     if kind == "deblur2d":
         probs = [small_problem("deblur2d", seed=i, precision="fp64", n_refine=2, iters=12) for i in range(4)]
@@ -141,31 +152,44 @@ def test_batch_operator_families_match_oracle(G, kind):
         probs = [small_problem("deconv1d", seed=i, iters=10) for i in range(4)]
     share_operators(probs, s=probs[0].sketch.s)
     assert all(P.A is probs[0].A for P in probs)
-    Bt, xs = batch_iterates(G, probs, "fp64", probs[0].iters)
+    Bt, xs = batch_iterates(G, probs, prec, probs[0].iters)
     assert Bt.layout()[0] == 1
     for P, x in zip(probs, xs):
-        check_instance(x, P, "fp64")
+        check_instance(x, P, prec)
     Bt.close()
 
 
-def test_batch_ragged_frames_run_as_concurrent_groups(G):
+@pytest.mark.parametrize("prec", ["fp64", "ff", "fp32"])
+def test_batch_ragged_frames_run_as_concurrent_groups(G, prec):
     """Space-time instances with 2, 3, 4 and 4 frames: three groups on their own streams."""
     probs = [small_problem("dynct", frames=F, seed=i, iters=12) for i, F in enumerate((2, 3, 4, 4))]
     share_operators(probs, s=100)
-    Bt, xs = batch_iterates(G, probs, "fp64", probs[0].iters)
+    Bt, xs = batch_iterates(G, probs, prec, probs[0].iters)
     ng, grp, size = Bt.layout()
     assert ng == 3 and grp[2] == grp[3] and len({grp[0], grp[1], grp[2]}) == 3
     for P, x in zip(probs, xs):
-        check_instance(x, P, "fp64")
+        check_instance(x, P, prec)
     Bt.close()
 
 
 def test_batch_fp32_form(G):
+    """The FP32 form (FP32 basis, compensated sums) with two refinement steps: every iterate of
+    every instance within max(1e-4, F x floor) of the oracle."""
+    probs = [small_problem("deblur2d", seed=i, iters=20) for i in range(4)]
+    share_operators(probs, s=80)
+    Bt, xs = batch_iterates(G, probs, "fp32", probs[0].iters)
+    for P, x in zip(probs, xs):
+        check_instance(x, P, "fp32")
+        assert abs(rel(x[-1], P.x_true) - O.sgks(P)["rre"][-1]) < 0.05 * O.sgks(P)["rre"][-1]
+    Bt.close()
+
+
+def test_batch_fp32plain_form(G):
     """FP32 operators and accumulation: early iterates within 1e-4 of the oracle while the
     method's FP32 floor is below 1e-6, final RRE within 5 % (as for the single handle)."""
     probs = [small_problem("deblur2d", seed=i, iters=20) for i in range(4)]
     share_operators(probs, s=80)
-    Bt, xs = batch_iterates(G, probs, "fp32", probs[0].iters)
+    Bt, xs = batch_iterates(G, probs, "fp32plain", probs[0].iters)
     for P, x in zip(probs, xs):
         ref = O.sgks(P, record_x=True)
         fl = floor_curve(P, P.iters, EPS["fp32"])[0]
@@ -257,9 +281,8 @@ def test_batch_nonfinite_instance_does_not_disturb_the_others(G):
 def test_batch_invalid_arguments(G):
     probs = ct_instances(2, iters=5)
     insts = batch_inputs(G, probs, "fp64")
-    insts32 = batch_inputs(G, probs, "fp32")
-    with pytest.raises(G._lib.SGKSError) as ei:
-        G.Batch(insts32, 80, 0, max_iters=5, precision="fp32x")     # no batched compensated form
+    with pytest.raises(G._lib.SGKSError) as ei:    # the float-float form exists for batches only
+        G.Solver(**G.device_inputs(probs[0], "ff"))
     assert ei.value.code == G._lib.SGKS_ERR_INVALID
     insts[1]["lam"] = 0.0
     with pytest.raises(G._lib.SGKSError) as ei:
@@ -286,11 +309,14 @@ def test_batch_autotune_keeps_parity_and_caches(G):
     B2.close()
 
 
-@pytest.mark.parametrize("count,prec,tol", [(33, "fp64", 1e-10), (128, "fp64", 1e-10), (64, "fp32", 1e-4)])
+@pytest.mark.parametrize("count,prec,tol", [(33, "fp64", 1e-10), (128, "fp64", 1e-10), (64, "fp32", 1e-4),
+                                            (64, "fp32plain", 1e-4), (128, "ff", 1e-10), (3, "ff", 1e-10),
+                                            (2, "fp32", 1e-4)])
 def test_batch_large_groups(G, count, prec, tol):
-    """Wide groups: 32 + 1 and 128 instances in FP64 (two instance passes per warp at 128) and 64
-    in FP32; final iterate of every instance after 8 iterations against the oracle (at 8
-    iterations the method's floor is far below the bar)."""
+    """Wide and narrow groups: 32 + 1 and 128 instances in FP64 (two instance passes per warp at
+    128), 64 in each FP32 form, 128 and 2 + 1 in float-float, 2 in FP32; final iterate of every
+    instance after 8 iterations against the oracle (at 8 iterations the method's floor is far
+    below the bar)."""
     A0 = small_problem("ct2d").A
     rng = np.random.default_rng(11)
     probs = [small_problem("ct2d", instance=int(i), A=A0, iters=8) for i in rng.integers(0, 64, size=count)]
