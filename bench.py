@@ -1,20 +1,20 @@
 #!/usr/bin/env python
 """Benchmark of the sGKS hot path on one GB300 (or N independent replicas under torchrun).
 
-Workload (default): the 256 x 256 image-deblurring problem -- 9x9 Gaussian PSF (sigma 2),
-zero boundary, 2D gradient regularizer, lambda = 5e-3, 1% noise, sparse-sign sketch with
-s = 400 rows and 8 nonzeros per column, FP32 operators with FP64 sketched QR / projected
-solve and 2 refinement steps, 100 iterations.  One step = one whole solve of one right-hand
-side: sgks_reset (setup: S_A b, W_0, sketched QR of W_0, y_0, x_0) + 100 iterations.
-Metric: sGKS iterations per second (whole job, all replicas).  L2 is flushed (a 256 MiB
-write) before every step, outside the timed interval of the step.
+Headline workload (default, --config ct2d_batch): parallel-beam CT, 512 x 512 image, 180 angles x
+725 bins (CSR of ray-pixel intersection lengths, FP32 values, 60 M nonzeros), 2D gradient L, 2%
+noise; 64 right-hand sides (noise seed i) x lambda_i = 10^(-4 + 3i/63) solved as one batch
+(sgks_batch_*), 150 iterations each, sparse-sign sketch s = 600, zeta = 8.  Form: float-float
+("ff": the basis and every vector as (hi, lo) float pairs, compensated sums on the FP32 units,
+FP64 sketched QR and projected solve), FP64-class results.  One step = one batch solve:
+sgks_batch_reset (setup of all 64 instances) + 150 iterations.  Metric: sGKS instance-iterations
+per second (whole job, all replicas).  The working set (basis 20.5 GB) is far larger than L2.
 
-Extra keys: the plain FP64 GPU form on the same problem (iterations/s, final RRE and the
-time to reach 1.01 x its final RRE, for the FP32+refinement form too), the per-kernel profile
-and the roofline of the dominant kernel, nvidia-smi clocks during the timed region, the
-FP64 CPU oracle timed on the host cores on a bounded sample, and the batched form on the CT
-(64 right-hand sides x lambdas sharing one CSR) and ragged dynamic-CT (16 instances of 8 to
-32 frames) workloads, each next to plain FP64 GPU sGKS on one of its instances.
+The line also carries the roofline of the step's largest-share kernel, the CPU oracle on the
+host cores (one thread, and one process per core over different instances), an end-to-end
+figure through the public API with host buffers, and a compact comparison: plain FP64 GPU sGKS
+on the same batch and on one instance alone, with the time to reach the FP64 run's RRE targets.
+--config deblur2d|ct2d|seismic2d|dynct|deconv1d runs one right-hand side of that workload instead.
 """
 from __future__ import annotations
 
@@ -58,10 +58,20 @@ def parse():
                     help="timed steps (default 100: about 1 s of GPU work; 20 for --impl reference)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="deblur2d")
+    ap.add_argument("--config", default=BATCH_CONFIG)
+    ap.add_argument("--precision", default="ff", choices=["ff", "fp32", "fp64", "fp32plain"],
+                    help="form of the batched headline (ct2d_batch)")
+    ap.add_argument("--compare", default="fp64,fp32", type=lambda v: [x for x in v.split(",") if x],
+                    help="other forms timed on the same batch for the comparison block")
+    ap.add_argument("--compare-dynct", default="fp32", help="form of the ragged dynamic-CT batch extra")
+    ap.add_argument("--cpu-instance", type=int, default=42, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-opfile", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-seed", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--ct-size", type=int, default=512, help=argparse.SUPPRESS)   # image side of the CT batch (tests)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, profile and CPU baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched CT and dynamic-CT measurements")
-    ap.add_argument("--cpu-sample-iters", type=int, default=25)
+    ap.add_argument("--cpu-sample-iters", type=int, default=None,
+                    help="iterations of the oracle sample (default 20 for the CT batch, 25 otherwise)")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--profile-batch", default=None, choices=["ct2d", "dynct"],
                     help="run one batched solve of a reduced CT / dynamic-CT batch (for profiler captures) and exit")
@@ -69,7 +79,12 @@ def parse():
     ap.add_argument("--batch-iters", type=int, default=40)
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = 20 if args.impl == "reference" else 100
+        if args.config == BATCH_CONFIG:
+            args.steps = 3 if args.impl == "reference" else 10
+        else:
+            args.steps = 20 if args.impl == "reference" else 100
+    if args.cpu_sample_iters is None:
+        args.cpu_sample_iters = 20 if args.config == BATCH_CONFIG else 25
     return args
 
 
@@ -280,9 +295,58 @@ def flops_fp64(P, cls, d):
 
 
 # --------------------------------------------------------------------------- reference
+def run_reference_batch(args):
+    """The oracle arm on the CT batch: each step runs one single-threaded oracle process per host
+    core, each on its own instance (setup + --cpu-sample-iters // 4 iterations, at least 3), all
+    together; instance-iterations/s over the steps."""
+    import tempfile
+
+    import numpy as np
+    A0 = ct_batch_operator(args.ct_size)
+    cores = os.cpu_count() or 1
+    iters = max(3, args.cpu_sample_iters // 4)
+    tot = 0.0
+    with tempfile.TemporaryDirectory() as td:
+        opfile = os.path.join(td, "ctop.npz")
+        np.savez(opfile, rp=A0.row_ptr, col=A0.col, val=A0.val, m=A0.m, n=A0.n)
+
+        def one_step(k):
+            procs = [run_cpu_batch_sample(opfile, (k * cores + i) % BATCH_COUNT, iters, 1, 0, args.ct_size)
+                     for i in range(cores)]
+            secs = []
+            for q in procs:
+                so, se = q.communicate(timeout=3600)
+                if q.returncode != 0:
+                    raise RuntimeError(se[-2000:])
+                secs.append(json.loads(so.strip().splitlines()[-1])["seconds"])
+            return max(secs)
+
+        for k in range(args.warmup):
+            one_step(k)
+        for k in range(args.steps):
+            tot += one_step(args.warmup + k)
+    value = args.steps * cores * iters / tot
+    prec = args.precision
+    line = {
+        "impl": "reference", "metric": batch_metric(prec), "value": value, "unit": "instance-iterations/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": batch_workload(len(A0.col), prec, args.ct_size),
+                   "sample": f"per step: {cores} single-threaded oracle processes (one per host core), each "
+                             f"setup + {iters} of 150 iterations of its own instance, run together; setup included"},
+        "cpu_baseline": {"value": value, "unit": "instance-iterations/s", "cores": cores, "kind": "oracle",
+                         "sample": f"NumPy FP64 oracle, {cores} processes x (setup + {iters} iterations) per step"},
+        "e2e": {"value": value, "unit": "instance-iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
+        return
+    if args.config == BATCH_CONFIG:
+        run_reference_batch(args)
         return
     name = args.config
     iters = args.cpu_sample_iters   # the same sample as the cpu_baseline of the GPU arm's line
@@ -305,17 +369,412 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------------- batched headline
+BATCH_CONFIG = "ct2d_batch"
+BATCH_COUNT = 64
+BATCH_FORM_LABEL = {"ff": "float-float (hi, lo) pairs on the FP32 units + FP64 sketched QR / projected solve",
+                    "fp32": "FP32 basis, compensated float-float sums + FP64 sketched QR / projected solve",
+                    "fp64": "plain FP64", "fp32plain": "FP32 arithmetic with FP32 accumulation"}
+BATCH_DTYPE = {"ff": "ff32x2+f64", "fp32": "f32+ff32x2+f64", "fp64": "f64", "fp32plain": "f32+f64"}
+
+
+def batch_metric(prec):
+    return f"sGKS instance-iterations/s (512^2 CT, 64 RHS x lambda batch, 150 iterations, {prec})"
+
+
+def batch_workload(nnz, prec, N=512):
+    return (f"ct2d_batch: {N}x{N} parallel-beam CT, 180 angles x {int(math.ceil(math.sqrt(2.0) * N))} bins, "
+            f"CSR FP32 (nnz {nnz}), grad2d L, "
+            f"2% noise, 64 right-hand sides (noise seed i) x lambda_i = 10^(-4+3i/63), sparse-sign s=600 zeta=8, "
+            f"150 iterations each, one batch (sgks_batch), form {prec}: {BATCH_FORM_LABEL.get(prec, prec)}")
+
+
+def ct_batch_operator(N):
+    """The CT operator of the batch: N x N image, 180 angles, ceil(sqrt(2) N) bins (725 at N = 512)."""
+    import numpy as np
+    from workloads.configs import ct_op
+    return ct_op(N, np.arange(180) * 1.0, int(math.ceil(math.sqrt(2.0) * N)))
+
+
+def ct_batch_problems(A0, count, seed=0, prec="ff"):
+    from workloads.configs import make_ct2d
+    return [make_ct2d(instance=i, seed=seed, N=A0.nx, A=A0, precision=prec) for i in range(count)]
+
+
+def ct_batch_inputs(G, probs, prec, dev):
+    dt = G.io_dtype(prec)
+    kw = G.device_inputs(probs[0], prec, device=dev)
+    insts = [dict(A=kw["A"], reg=kw["reg"], lam=P.lam, b=_dev_tensor(P.b, dt, dev),
+                  x_true=_dev_tensor(P.x_true, dt, dev)) for P in probs]
+    return insts
+
+
+def make_batch(G, insts, P0, prec, iters, n_refine=0):
+    return G.Batch(insts, P0.sketch.s, P0.sketch.seed, max_iters=iters, n_refine=n_refine, precision=prec,
+                   zeta=P0.sketch.zeta, autotune=True)
+
+
+def batch_bytes(kind, B, n, m, nnz, d, prec):
+    """Algorithmic bytes of one launch of a batched kernel class (all B instances): the CSR arrays
+    once (4-byte indices and values, row pointers), each instance vector read or written once, and
+    for the combine the d columns of W and A W.  Basis values take 8 bytes in the FP64 and
+    float-float forms and 4 in the FP32 forms; the other vectors 8 (float-float or FP64) or 4."""
+    tw = 8 if prec in ("ff", "fp64") else 4
+    tv = 4 if prec == "fp32plain" else 8
+    if kind == "apply_column":      # u = A w -> AW column (L w is a stencil: n in, p out, not counted)
+        return nnz * 8 + (m + 1) * 4 + B * (n * tw + m * tv)
+    if kind == "gradient_append":   # A^T e + lambda L^T L x -> W column
+        return nnz * 8 + (n + 1) * 4 + B * (m * tv + n * tv + n * tw)
+    if kind == "combine":           # x = W y, e = AW y - b, RC / RRE statistics
+        return B * (d * (n * tw + m * tv) + n * tv * 3 + n * tv + m * tv * 2)
+    if kind == "sketch_gather":
+        return 0
+    return 0
+
+
+def timed_batch_steps(Bt, bs, iters, steps, dev, flush=None):
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    rep = None
+    for k in range(steps):
+        if flush is not None:
+            flush.zero_()
+        evs[k][0].record(stream)
+        Bt.reset(bs)
+        rep = Bt.solve(iters, history=(k == steps - 1))
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    return sum(a.elapsed_time(b) for a, b in evs), rep
+
+
+def rre_targets(rre_hist):
+    """Targets for time-to-tolerance: 1.01 x the final RRE and 1.01 x the minimum RRE of a run (the
+    CT batch is semi-convergent: its RRE bottoms out early and then rises), with the iteration of
+    the minimum."""
+    k_min = int(min(range(len(rre_hist)), key=lambda k: rre_hist[k]))
+    return {"final": 1.01 * rre_hist[-1], "min": 1.01 * rre_hist[k_min], "k_min": k_min + 1}
+
+
+def run_cpu_batch_sample(opfile, instance, iters, threads=1, seed=0, ct_size=512):
+    env = dict(os.environ, OPENBLAS_NUM_THREADS=str(threads), OMP_NUM_THREADS=str(threads),
+               MKL_NUM_THREADS=str(threads))
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--config", BATCH_CONFIG,
+           "--cpu-sample-iters", str(iters), "--cpu-instance", str(instance), "--cpu-opfile", opfile,
+           "--cpu-seed", str(seed), "--ct-size", str(ct_size)]
+    return subprocess.Popen(cmd, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+
+
+def cpu_batch_worker(args):
+    """One oracle solve (setup + --cpu-sample-iters iterations) of CT instance --cpu-instance, with
+    the operator read from --cpu-opfile; prints the seconds."""
+    import numpy as np
+    import oracle as O
+    from workloads.configs import make_ct2d
+    from workloads.problem import OperatorDesc
+    z = np.load(args.cpu_opfile)
+    A0 = OperatorDesc("csr", int(z["m"]), int(z["n"]), row_ptr=z["rp"], col=z["col"], val=z["val"],
+                      nx=args.ct_size, ny=args.ct_size)
+    P = make_ct2d(instance=args.cpu_instance, seed=args.cpu_seed, N=args.ct_size, A=A0)
+    t0 = time.perf_counter()
+    O.sgks(P, iters=args.cpu_sample_iters)
+    print(json.dumps({"seconds": time.perf_counter() - t0, "iters": args.cpu_sample_iters,
+                      "instance": args.cpu_instance}))
+
+
+def cpu_batch_baseline(A0, iters, seed=0):
+    N = A0.nx
+    """The oracle as it stands on the batch workload, bounded sample (setup + `iters` iterations of
+    an instance per process): one process with one thread, then one single-threaded process per
+    host core (instances 0, 1, ...) running together.  Instance-iterations/s for each."""
+    import tempfile
+
+    import numpy as np
+    cores = os.cpu_count() or 1
+    with tempfile.TemporaryDirectory() as td:
+        opfile = os.path.join(td, "ctop.npz")
+        np.savez(opfile, rp=A0.row_ptr, col=A0.col, val=A0.val, m=A0.m, n=A0.n)
+        out = {}
+        p = run_cpu_batch_sample(opfile, 42, iters, 1, seed, N)
+        so, se = p.communicate(timeout=1800)
+        if p.returncode != 0:
+            raise RuntimeError(se[-2000:])
+        r1 = json.loads(so.strip().splitlines()[-1])
+        out["one_thread"] = {"value": iters / r1["seconds"], "seconds": r1["seconds"], "cores": 1}
+        t0 = time.perf_counter()
+        procs = [run_cpu_batch_sample(opfile, i % BATCH_COUNT, iters, 1, seed, N) for i in range(cores)]
+        secs = []
+        for q in procs:
+            so, se = q.communicate(timeout=3600)
+            if q.returncode != 0:
+                raise RuntimeError(se[-2000:])
+            secs.append(json.loads(so.strip().splitlines()[-1])["seconds"])
+        wall = time.perf_counter() - t0
+        out["all_cores"] = {"value": cores * iters / max(secs), "seconds": max(secs), "cores": cores,
+                            "wall_s": wall}
+    return out
+
+
+def bench_batch_form(G, probs, prec, dev, iters, steps=2):
+    """One timed batch solve (best of `steps` after a warm-up) of the CT batch in form `prec`, and
+    the RRE record of instance 42."""
+    import torch
+    insts = ct_batch_inputs(G, probs, prec, dev)
+    Bt = make_batch(G, insts, probs[0], prec, iters)
+    bs = [i["b"] for i in insts]
+    Bt.reset(bs)
+    Bt.solve(iters)
+    best, rep = None, None
+    for _ in range(steps):
+        ms, r = timed_batch_steps(Bt, bs, iters, 1, dev)
+        if best is None or ms < best:
+            best, rep = ms, r
+    Bt.close()
+    del insts
+    torch.cuda.empty_cache()
+    return best, rep
+
+
+def main_batch(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2606_18073_gb300 as G
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    G.build()
+    prec = args.precision
+    iters = 150
+    A0 = ct_batch_operator(args.ct_size)
+    nnz = len(A0.col)
+    probs = ct_batch_problems(A0, BATCH_COUNT, seed=rank, prec=prec)
+    n, m = probs[0].n, probs[0].m
+    insts = ct_batch_inputs(G, probs, prec, dev)
+    bs = [i["b"] for i in insts]
+    Bt = make_batch(G, insts, probs[0], prec, iters)
+    tuned = Bt.config(0)
+    for _ in range(args.warmup):
+        Bt.reset(bs)
+        Bt.solve(iters)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        dist.barrier()
+    clk = ClockSampler(dev.index)
+    clk.start()
+    launches0 = G.kernel_launches()
+    torch.cuda.synchronize(dev)
+    clk.begin()
+    ms, rep = timed_batch_steps(Bt, bs, iters, args.steps, dev)
+    clk.end()
+    launches = G.kernel_launches() - launches0
+    if ws > 1:
+        dist.barrier()
+    ms = max_over_ranks(ms, dev)
+    clocks = clk.stop()
+    units = BATCH_COUNT * iters
+    value = job_throughput(args.steps * units, ms, ws)
+
+    # ---- e2e through the public API: every instance's b host -> device (pinned) before the
+    # reset, every instance's x device -> host after the solve, inside the timed step
+    dt = G.io_dtype(prec)
+    b_host = [torch.from_numpy(np.asarray(P.b)).to(dt).pin_memory() for P in probs]
+    x_host = [torch.empty(n, dtype=dt).pin_memory() for _ in probs]
+    b_dev = [torch.empty(m, dtype=dt, device=dev) for _ in probs]
+    x_dev = [torch.empty(n, dtype=dt, device=dev) for _ in probs]
+    stream = torch.cuda.current_stream(dev)
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for bd, bh in zip(b_dev, b_host):
+            bd.copy_(bh, non_blocking=True)
+        Bt.reset(b_dev)
+        Bt.solve(iters, x_out=x_dev)
+        for xh, xd in zip(x_host, x_dev):
+            xh.copy_(xd, non_blocking=True)
+        c.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms += a.elapsed_time(c)
+    e2e_ms = max_over_ranks(e2e_ms, dev)
+    e2e_value = job_throughput(args.steps * units, e2e_ms, ws)
+    elem = torch.empty(0, dtype=dt).element_size()
+    rre = [r["rre_last"] for r in rep]
+    line = {
+        "metric": batch_metric(prec), "value": value, "unit": "instance-iterations/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": BATCH_DTYPE.get(prec, prec), "data": "synthetic",
+        "config": {"workload": batch_workload(nnz, prec, args.ct_size), "instances": BATCH_COUNT, "iterations_per_step": iters,
+                   "l2": "inputs larger than L2 (basis %.1f GB)" % (BATCH_COUNT * n * (iters + 3) * (8 if prec in ("ff", "fp64") else 4) / 1e9),
+                   "parallelism": "replicas" if ws > 1 else "single", "autotuned": tuned,
+                   "final_rre": {"instance_42": rre[42], "median": float(np.median(rre))}},
+        "e2e": {"value": e2e_value, "unit": "instance-iterations/s",
+                "h2d_bytes_per_step": BATCH_COUNT * m * elem, "d2h_bytes_per_step": BATCH_COUNT * n * elem},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_extras:
+        # ---- roofline of the step's largest-share kernel: one eager solve with an event pair
+        # around every launch (launches are milliseconds long, so the pair adds little)
+        Bt.reset(bs)
+        prof = Bt.profile(iters)
+        tot = sum(v["ms"] for v in prof.values())
+        d_avg = 3 + (iters + 1) / 2.0
+        kern = {}
+        for k, v in prof.items():
+            if not v["launches"]:
+                continue
+            us = 1e3 * v["ms"] / v["launches"]
+            bts = batch_bytes(k, BATCH_COUNT, n, m, nnz, d_avg, prec)
+            kern[k] = {"share": v["ms"] / tot, "launches": v["launches"], "us_per_launch": us,
+                       "alg_bytes_per_launch": bts, "gbps": bts / (us * 1e-6) / 1e9 if bts else None}
+        dom = max(kern, key=lambda k: kern[k]["share"])
+        hbm = measured_hbm()
+        ach = kern[dom]["gbps"] or 0.0
+        line["roofline"] = {"kernel": BATCH_KERNEL_NAMES.get(dom, dom), "class": dom, "bound": "hbm",
+                            "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                            "traffic": traffic_record_batch(BATCH_KERNEL_NAMES.get(dom, dom), prec),
+                            "alg_bytes_per_launch": kern[dom]["alg_bytes_per_launch"],
+                            "us_per_launch": kern[dom]["us_per_launch"], "share": kern[dom]["share"],
+                            "duration": "CUDA event pair around each launch of one eager solve (150 iterations)",
+                            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"}
+        line["kernels"] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                           for k, v in kern.items()}
+        # ---- plain FP64 GPU sGKS: the same batch, and instance 42 alone; time to the RRE targets
+        tg = rre_targets(rep[42]["rre"])
+        cmp = {"form": prec, "instance": 42, "rre_targets": tg}
+        ours_ms = ms / args.steps
+        cmp[prec] = {"ms_per_solve": ours_ms, "instance_iters_per_s": units / (ours_ms / 1e3),
+                     "time_to_min_target_ms": time_to_rre(ours_ms, rep[42]["rre"], tg["min"], iters),
+                     "time_to_final_target_ms": time_to_rre(ours_ms, rep[42]["rre"], tg["final"], iters),
+                     "rre_42_final": rep[42]["rre_last"], "rre_42_min": min(rep[42]["rre"])}
+        Bt.close()
+        del insts, bs
+        torch.cuda.empty_cache()
+        for other in args.compare:
+            if other == prec:
+                continue
+            try:
+                t, r = bench_batch_form(G, probs, other, dev, iters)
+                cmp[other] = {"ms_per_solve": t, "instance_iters_per_s": units / (t / 1e3),
+                              "time_to_min_target_ms": time_to_rre(t, r[42]["rre"], tg["min"], iters),
+                              "time_to_final_target_ms": time_to_rre(t, r[42]["rre"], tg["final"], iters),
+                              "rre_42_final": r[42]["rre_last"], "rre_42_min": min(r[42]["rre"])}
+            except Exception as exc:   # the headline stands without it
+                cmp[other] = {"error": repr(exc)[:300]}
+        P42 = probs[42]
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+        kw64 = G.device_inputs(P42, "fp64", device=dev)
+        S64 = G.Solver(**kw64)
+        t64, h64 = time_solve(G, S64, kw64["b"], iters, flush, dev)
+        S64.close()
+        cmp["fp64_single_instance_42"] = {
+            "ms_per_solve": t64, "iters_per_s": iters / (t64 / 1e3),
+            "time_to_min_target_ms": time_to_rre(t64, h64["rre"], tg["min"], iters),
+            "time_to_final_target_ms": time_to_rre(t64, h64["rre"], tg["final"], iters),
+            "rre_final": h64["rre_last"], "rre_min": min(h64["rre"])}
+        line["compare"] = cmp
+        # ---- the oracle on the host cores (bounded sample)
+        try:
+            cb = cpu_batch_baseline(A0, args.cpu_sample_iters)
+            ac, one = cb["all_cores"], cb["one_thread"]
+            line["cpu_baseline"] = {
+                "value": ac["value"], "unit": "instance-iterations/s", "cores": ac["cores"], "kind": "oracle",
+                "sample": f"NumPy FP64 oracle, setup + {args.cpu_sample_iters} of {iters} iterations per instance, "
+                          f"one single-threaded process per core ({ac['cores']} cores, instances 0..{ac['cores'] - 1}), "
+                          f"{ac['seconds']:.1f} s; setup included",
+                "one_thread": {"value": one["value"], "cores": 1, "seconds": one["seconds"], "instance": 42}}
+        except Exception as exc:
+            line["cpu_baseline"] = {"value": None, "unit": "instance-iterations/s", "cores": os.cpu_count(),
+                                    "kind": "oracle", "sample": f"failed: {exc}"[:300]}
+        if not args.no_batch:
+            extras_path = os.environ.get("SGKS_BENCH_EXTRAS")
+            ex = {"dynct_ragged16": bench_dynct_batch(G, dev, flush, args.compare_dynct)}
+            ex["single_instance"] = bench_singles(G, dev, flush)
+            line["dynct_ragged16"] = compact_dynct(ex["dynct_ragged16"])
+            if extras_path:
+                with open(extras_path, "w") as f:
+                    json.dump(ex, f, indent=1)
+    else:
+        Bt.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+BATCH_KERNEL_NAMES = {"apply_column": "kbx_csr_apply", "gradient_append": "kbx_csr_gradient",
+                      "combine": "kbx_combine_tma", "sketch_gather": "kbx_sketch_gather",
+                      "qr_append": "k_qr_append", "stacked_solve": "k_stacked_solve"}
+
+
+def traffic_record_batch(kernel, prec):
+    """DRAM bytes per launch of a batched kernel at the full workload size, from the committed ncu
+    summary of that kernel and form (profiles/*.md lines 'traffic-record-batch: <kernel> <form>
+    <source file> <sha12> <bytes>'), or None when absent or when the source changed since."""
+    import glob
+    import hashlib
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for line in open(path):
+            f = line.split()
+            if len(f) == 6 and f[0] == "traffic-record-batch:" and f[1] == kernel and f[2] == prec:
+                src = os.path.join(ROOT, "paper_2606_18073_gb300", "csrc", f[3])
+                try:
+                    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+                except OSError:
+                    return None
+                return float(f[5]) if sha == f[4] else None
+    return None
+
+
+def compact_dynct(rec):
+    keep = ("instances", "iterations", "ms_per_solve", "instance_iters_per_s", "final_rre", "fp64_plain_single",
+            "batched_instance_final_rre", "time_to_target_ms", "form", "compare")
+    return {k: rec[k] for k in keep if k in rec}
+
+
+def bench_singles(G, dev, flush):
+    """One right-hand side of the deblurring, CT and dynamic-CT workloads alone: the FP32 form
+    (compensated sums, the workload's refinement steps) and plain FP64 (no refinement)."""
+    out = {}
+    for name in ("deblur2d", "ct2d", "dynct"):
+        rec = {}
+        for prec in ("fp32", "fp64"):
+            P = make_workload(name, seed=0)
+            if prec == "fp64":
+                P.n_refine = 0
+            kw = G.device_inputs(P, prec, device=dev)
+            S = G.Solver(**kw)
+            t, h = time_solve(G, S, kw["b"], P.iters, flush, dev)
+            S.close()
+            rec[prec] = {"iters_per_s": P.iters / (t / 1e3), "ms_per_solve": t, "final_rre": h["rre_last"],
+                         "n_refine": P.n_refine}
+        out[name] = rec
+    return out
+
+
 # --------------------------------------------------------------------------------- ours
 def main():
     args = parse()
     if args.cpu_worker:
-        print(json.dumps(cpu_oracle_sample(args.config, args.cpu_sample_iters)))
+        if args.config == BATCH_CONFIG:
+            cpu_batch_worker(args)
+        else:
+            print(json.dumps(cpu_oracle_sample(args.config, args.cpu_sample_iters)))
         return
     if args.impl == "reference":
         run_reference(args)
         return
     if args.profile_batch:
         profile_batch(args)
+        return
+    if args.config == BATCH_CONFIG:
+        main_batch(args)
         return
     import numpy as np
     import torch
@@ -623,15 +1082,19 @@ def batch_report(ms, reps, iters, count, P64, ref_idx, G, dev, flush):
     t64, h64 = time_solve(G, S64, kw64["b"], iters, flush, dev)
     S64.close()
     rre = [r["rre_last"] for r in reps]
-    target = 1.01 * h64["rre_last"]
+    tg = rre_targets(h64["rre"])
     return {"instances": count, "iterations": iters, "ms_per_solve": ms,
             "instance_iters_per_s": count * iters / (ms / 1e3),
             "final_rre": {"min": float(np.min(rre)), "median": float(np.median(rre)), "max": float(np.max(rre))},
             "fp64_plain_single": {"instance": ref_idx, "iters_per_s": iters / (t64 / 1e3), "ms_per_solve": t64,
-                                  "final_rre": h64["rre_last"]},
+                                  "final_rre": h64["rre_last"], "min_rre": min(h64["rre"])},
             "batched_instance_final_rre": rre[ref_idx],
-            "batched_instance_time_to_target_ms": time_to_rre(ms, reps[ref_idx]["rre"], target, iters),
-            "fp64_time_to_target_ms": time_to_rre(t64, h64["rre"], target, iters)}
+            "rre_targets_from_fp64": tg,
+            "time_to_target_ms": {
+                "batched": {"min": time_to_rre(ms, reps[ref_idx]["rre"], tg["min"], iters),
+                            "final": time_to_rre(ms, reps[ref_idx]["rre"], tg["final"], iters)},
+                "fp64_single": {"min": time_to_rre(t64, h64["rre"], tg["min"], iters),
+                                "final": time_to_rre(t64, h64["rre"], tg["final"], iters)}}}
 
 
 def bench_ct_batch(G, dev, flush, count=64):
@@ -672,9 +1135,9 @@ def bench_ct_batch(G, dev, flush, count=64):
     return out
 
 
-def bench_dynct_batch(G, dev, flush):
+def bench_dynct_batch(G, dev, flush, prec="fp32"):
     """Dynamic CT 128 x 128 x F frames, 16 instances, F in {8, 16, 24, 32} (4 each, seeds 0..15):
-    ragged sizes in four groups, FP32 + 3 refinement steps, 200 iterations, s = 800."""
+    ragged sizes in four groups, 3 refinement steps, 200 iterations, s = 800, form `prec`."""
     import torch
     from workloads.configs import dynct_frame_ops, make_dynct
     ops = dynct_frame_ops(128, 32)
@@ -686,15 +1149,16 @@ def bench_dynct_batch(G, dev, flush):
         probs.append(P)
     dev_ops = {}
     insts = []
+    dt = G.io_dtype(prec)
     for P in probs:
         if id(P.A) not in dev_ops:
-            kw = G.device_inputs(P, "fp32", device=dev)
+            kw = G.device_inputs(P, prec, device=dev)
             dev_ops[id(P.A)] = (kw["A"], kw["reg"])
         A, reg = dev_ops[id(P.A)]
-        insts.append(dict(A=A, reg=reg, lam=P.lam, b=_dev_tensor(P.b, torch.float32, dev),
-                          x_true=_dev_tensor(P.x_true, torch.float32, dev)))
+        insts.append(dict(A=A, reg=reg, lam=P.lam, b=_dev_tensor(P.b, dt, dev),
+                          x_true=_dev_tensor(P.x_true, dt, dev)))
     P0 = probs[0]
-    Bt = G.Batch(insts, P0.sketch.s, P0.sketch.seed, max_iters=P0.iters, n_refine=P0.n_refine, precision="fp32",
+    Bt = G.Batch(insts, P0.sketch.s, P0.sketch.seed, max_iters=P0.iters, n_refine=P0.n_refine, precision=prec,
                  zeta=P0.sketch.zeta, autotune=True)
     groups = Bt.layout()[0]
     tuned = [Bt.config(g) for g in range(groups)]
@@ -712,8 +1176,9 @@ def bench_dynct_batch(G, dev, flush):
     out["roofline"] = batch_roofline(prof, [(P.n, P.m) for P in probs], nnz_groups, 3, P0.iters, measured_hbm(),
                                      groups=groups)
     out["autotuned"] = tuned
+    out["form"] = prec
     out["workload"] = ("dynct: 128x128 x F frames, F in {8,16,24,32} x 4 instances, 30 angles/frame x 185 bins, "
-                       "space-time L, 1% noise, sparse-sign s=800 zeta=8, 200 iterations, FP32 + 3 refinement steps")
+                       f"space-time L, 1% noise, sparse-sign s=800 zeta=8, 200 iterations, {prec} + 3 refinement steps")
     return out
 
 
@@ -747,8 +1212,8 @@ def bench_gks(G, name, dev, flush):
 
 def profile_batch(args):
     """One reset + solve of a reduced batch, for profiler captures: the 512^2 CT operator with
-    --batch-size right-hand sides (FP32, sparse-sign s = 600), or --batch-size space-time
-    instances of 8 frames (FP32, 3 refinement steps, s = 800), --batch-iters iterations."""
+    --batch-size right-hand sides (sparse-sign s = 600), or --batch-size space-time instances of 8
+    frames (3 refinement steps, s = 800), --batch-iters iterations, form --precision."""
     import numpy as np
     import torch
     import paper_2606_18073_gb300 as G
@@ -758,23 +1223,25 @@ def profile_batch(args):
     if args.profile_batch == "ct2d":
         from workloads.configs import ct_op, make_ct2d
         A0 = ct_op(512, np.arange(180) * 1.0, 725)
-        probs = [make_ct2d(instance=i, A=A0, precision="fp32", iters=iters) for i in range(B)]
+        probs = [make_ct2d(instance=i, A=A0, precision=args.precision, iters=iters) for i in range(B)]
     else:
         from workloads.configs import dynct_frame_ops, make_dynct
         ops = dynct_frame_ops(128, 8)
         probs = [make_dynct(seed=i, frames=8, frame_ops=ops, iters=iters) for i in range(B)]
         for P in probs[1:]:
             P.A = probs[0].A
-    kw = G.device_inputs(probs[0], "fp32", device=dev)
-    insts = [dict(A=kw["A"], reg=kw["reg"], lam=P.lam, b=torch.from_numpy(np.asarray(P.b)).to(dev, torch.float32),
-                  x_true=torch.from_numpy(np.asarray(P.x_true)).to(dev, torch.float32)) for P in probs]
+    dt = G.io_dtype(args.precision)
+    kw = G.device_inputs(probs[0], args.precision, device=dev)
+    insts = [dict(A=kw["A"], reg=kw["reg"], lam=P.lam, b=torch.from_numpy(np.asarray(P.b)).to(dev, dt),
+                  x_true=torch.from_numpy(np.asarray(P.x_true)).to(dev, dt)) for P in probs]
     P0 = probs[0]
-    Bt = G.Batch(insts, P0.sketch.s, P0.sketch.seed, max_iters=iters, n_refine=P0.n_refine, precision="fp32",
+    Bt = G.Batch(insts, P0.sketch.s, P0.sketch.seed, max_iters=iters, n_refine=P0.n_refine, precision=args.precision,
                  zeta=P0.sketch.zeta)
     Bt.reset([i["b"] for i in insts])
     out = Bt.solve(iters)
     torch.cuda.synchronize(dev)
-    print(json.dumps({"profile_batch": args.profile_batch, "instances": B, "iterations": iters,
+    print(json.dumps({"profile_batch": args.profile_batch, "precision": args.precision, "instances": B,
+                      "iterations": iters,
                       "median_final_rre": float(np.median([o["rre_last"] for o in out]))}))
     Bt.close()
 

@@ -83,7 +83,7 @@ typedef struct sgks_op {
  *  SGKS_REG_FD1:       D_n (rows [-1 1]), n = nx, p = nx-1               (Sec. 4, eq. reg_matrix)
  *  SGKS_REG_GRAD2D:    [I_ny (x) D_nx ; D_ny (x) I_nx], p = ny(nx-1)+(ny-1)nx (eq. reg_matrix)
  *  SGKS_REG_LAPLACE2D: 5-point Laplacian 4x_p - sum of the 4 neighbours, zero outside, p = nx ny
- *  SGKS_REG_SPACETIME: Psi of eq. spacetime_tik (Sec. 4.4), nt frames of ny x nx,
+ *  SGKS_REG_SPACETIME: Psi of eq. spacetime_tik (Sec. 4.3), nt frames of ny x nx,
  *                      p = nt(ny(nx-1)+(ny-1)nx) + (nt-1)nx ny */
 typedef struct sgks_reg {
     int32_t kind;

@@ -23,7 +23,7 @@ What each function follows, and what pins it (tests/test_oracle_*.py):
   projected_solve      eq. (projected_sketched_bis): Householder QR of [R_A; sqrt(lam) R_L],
                        rebuilt from scratch each call, then back substitution.
   refine_step          one sketch-preconditioned refinement step of the projected problem,
-                       the q = 0 setting of Sec. 4.4 (no inner iteration).  Pinned by
+                       the q = 0 setting of Sec. 4.3 (no inner iteration).  Pinned by
                        convergence to the unsketched projected solution (eq. sGKS_noSASL).
   sgks                 Algorithm 2 (sGKS), optionally with S = I (sGKS_0 of eq. sGKS_noSASL).
   gks                  Algorithm 1 (GKS) with the loss-ratio test of eq. (loss_criterion).

@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(kThreads) kb_combine_tma(BDims D, BBulk<T> X, 
             __syncthreads();
         }
         const int st = k % NS;
-        const bool ok = mbar_wait(&full[st], (k / NS) & 1);
+        const bool ok = mbar_wait_n(&full[st], (k / NS) & 1, D.wait_tries);
         if (ok && j < db) {
             const T yv = ys[(j % JC) * B + b];
             const T* sl = stg + (size_t)st * kSlice + t;

@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(kThreads) kbx_combine_tma(BDims D, BBulkX<TW> 
             __syncthreads();
         }
         const int st = k % NS;
-        const bool ok = mbar_wait(&full[st], (k / NS) & 1);
+        const bool ok = mbar_wait_n(&full[st], (k / NS) & 1, D.wait_tries);
         if (ok && j < db) {
             const float h = yh[(j % JC) * B + b], l = yl[(j % JC) * B + b];
             if (isx) {

@@ -8,6 +8,7 @@
 // separate groups.  Every group runs on its own stream, forked from and joined back to the
 // handle's stream, and one captured CUDA graph holds one iteration of every group.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -549,6 +550,13 @@ int init_group(sgks_batch* h, GroupBase* G, const sgks_op* op, const DevL& L, in
     D.nl_a = 8;
     D.nl_t = 8;
     D.nb_combine = comb_grid(D);
+    // SGKS_TEST_TIMEOUT_GROUP=g (read at create) gives group g's bulk-copy combine a wait limit of
+    // zero rounds: its first wait reports a timeout, the CTA drains its own copies with the full
+    // limit and stops the group's instances with ST_TIMEOUT.  This exercises the timeout path of
+    // the ring without stalling the GPU (every copy that was issued still lands).
+    D.wait_tries = kWaitTries;
+    if (const char* tg = getenv("SGKS_TEST_TIMEOUT_GROUP"))
+        if (atoi(tg) == (int)h->groups.size() - 1) D.wait_tries = 0;
     int nb_comb_max = D.nb_combine;
     if (D.tma) {   // the tuner may pick 8 KB slices: size the partials for the larger grid
         BDims D8 = D;

@@ -133,6 +133,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
+// the same with a caller-chosen number of rounds (0: report failure without waiting)
+__device__ __forceinline__ bool mbar_wait_n(uint64_t* bar, uint32_t parity, int tries) {
+    for (int i = 0; i < tries; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
 // ----------------------------------------------------- programmatic dependent launch (PDL)
 // The kernels of one iteration follow each other on one stream.  Launched with the
 // programmatic-serialization attribute (launch_pdl), a kernel is launched as soon as every CTA of
@@ -852,6 +859,8 @@ struct BDims {
     int nl_a, nl_t;           // CSR rows: lanes per row of A and of A^T (powers of two <= 32, tuned)
     int nb_refine;            // CTAs of kb_wtr (each leaves one partial per instance)
     int nb_setup;             // CTAs of the setup reductions
+    int wait_tries;           // bounded waits of the bulk-copy combine's ring (kWaitTries; 0 in the
+                              // timeout test of SGKS_TEST_TIMEOUT_GROUP, see sgks_batch.cu)
     double sketch_scale;      // 1/sqrt(zeta)
 };
 

@@ -388,10 +388,13 @@ class Batch:
             out.append(d)
         return out
 
-    def x(self):
-        """Current iterates x_k of all instances (list of device tensors)."""
-        xs = [torch.empty(n, dtype=self.dtype, device=self.device) for n in self.n]
-        arr = (C.c_void_p * self.count)(*[t.data_ptr() for t in xs])
+    def x(self, which=None):
+        """Current iterates x_k (list of device tensors): of every instance, or of the instances
+        listed in `which` (None in the other places of the list)."""
+        pick = set(range(self.count)) if which is None else set(which)
+        xs = [torch.empty(n, dtype=self.dtype, device=self.device) if i in pick else None
+              for i, n in enumerate(self.n)]
+        arr = (C.c_void_p * self.count)(*[t.data_ptr() if t is not None else None for t in xs])
         L.check_batch(self._lib.sgks_batch_get_x(self._h, arr), self._h)
         return xs
 

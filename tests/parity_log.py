@@ -11,12 +11,14 @@ RECORDS = []
 
 def record(name, errs, floor, tol, factor):
     errs = [float(e) for e in errs]
-    ratios = [e / f for e, f in zip(errs, floor) if f > 0 and e > tol]
+    fl = [float(f) for f in floor[:len(errs)]]
+    ratios = [e / f for e, f in zip(errs, fl) if f > 0 and e > tol]
     k_strict = max([k for k, e in enumerate(errs) if e < tol] + [0])
     RECORDS.append({"name": name, "iters": len(errs) - 1, "max_err": max(errs), "final_err": errs[-1],
                     "max_ratio_to_floor_above_tol": max(ratios) if ratios else 0.0, "tol": tol,
                     "factor": factor, "strict_through": k_strict,
-                    "floor_final": float(floor[len(errs) - 1]) if len(floor) >= len(errs) else None})
+                    "floor_final": fl[-1] if len(fl) == len(errs) else None,
+                    "errs": errs if len(errs) > 40 else None, "floor": fl if len(errs) > 40 else None})
     return errs
 
 

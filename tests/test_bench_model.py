@@ -35,3 +35,17 @@ def test_labels_follow_the_config():
     metric, wl = bench.labels("ct2d", P)
     assert "ct2d" in metric and wl.startswith("ct2d: A CSR")
     assert bench.labels("deblur2d") == (bench.METRIC, bench.WORKLOAD)
+
+
+def test_batch_byte_model():
+    """Batched passes: the CSR arrays once per pass for all B instances, the instance vectors once
+    each; basis values 8 bytes in the FP64 and float-float forms, 4 in the FP32 forms."""
+    B, n, m, nnz, d = 64, 1000, 700, 50000, 20.0
+    a_ff = bench.batch_bytes("apply_column", B, n, m, nnz, d, "ff")
+    a_32 = bench.batch_bytes("apply_column", B, n, m, nnz, d, "fp32")
+    assert a_ff == nnz * 8 + (m + 1) * 4 + B * (n * 8 + m * 8)
+    assert a_ff - a_32 == B * n * 4
+    g = bench.batch_bytes("gradient_append", B, n, m, nnz, d, "fp64")
+    assert g == nnz * 8 + (n + 1) * 4 + B * (m * 8 + n * 8 + n * 8)
+    c = bench.batch_bytes("combine", B, n, m, nnz, d, "ff")
+    assert c == B * (d * (n + m) * 8 + n * 8 * 4 + m * 8 * 2)

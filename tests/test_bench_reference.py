@@ -37,3 +37,17 @@ def test_reference_arm_other_ranks_are_silent():
              "--cpu-sample-iters", "3"], RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_reference_arm_batch_line():
+    """The CT batch's oracle arm: one single-threaded process per host core, each on its own
+    instance, instance-iterations/s with the GPU arm's metric (a 48 x 48 image keeps it short)."""
+    r = run(["--impl", "reference", "--ct-size", "48", "--steps", "1", "--warmup", "1",
+             "--cpu-sample-iters", "12"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "instance-iterations/s" and line["value"] > 0
+    assert line["config"]["workload"].startswith("ct2d_batch: 48x48")
+    cb = line["cpu_baseline"]
+    assert cb["cores"] == (os.cpu_count() or 1) and cb["value"] == line["value"] and "3 iterations" in cb["sample"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0

@@ -327,3 +327,141 @@ def test_batch_large_groups(G, count, prec, tol):
     worst = max(rel(x.double().cpu().numpy(), O.sgks(P, iters=8)["x"]) for x, P in zip(xs, probs))
     assert worst < tol, worst
     Bt.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "ff"])
+def test_batch_combine_timeout_stops_only_its_group(G, prec, monkeypatch):
+    """The bounded waits of the bulk-copy combine: with SGKS_TEST_TIMEOUT_GROUP=0 the first group's
+    ring reports a timeout at its first wait (a wait limit of zero rounds; every copy already
+    issued still lands and is drained).  That group's instances stop with the timeout status,
+    which the solve reports as a CUDA error; the other group's instances are unharmed."""
+    probs = [small_problem("dynct", frames=F, seed=i, iters=6) for i, F in enumerate((2, 2, 3, 3))]
+    share_operators(probs, s=100)
+    monkeypatch.setenv("SGKS_TEST_TIMEOUT_GROUP", "0")
+    Bt = make_batch(G, probs, prec)
+    monkeypatch.delenv("SGKS_TEST_TIMEOUT_GROUP")
+    ng, grp, _ = Bt.layout()
+    assert ng == 2 and grp[0] == grp[1] == 0 and grp[2] == grp[3] == 1
+    with pytest.raises(G._lib.SGKSError) as ei:
+        Bt.solve(6)
+    assert ei.value.code == G._lib.SGKS_ERR_CUDA
+    st = Bt.status()
+    assert st[0] == st[1] == G._lib.SGKS_ERR_CUDA and st[2] == st[3] == G._lib.SGKS_OK
+    xs = Bt.x()
+    for i in (2, 3):
+        ref = O.sgks(probs[i], iters=6)
+        assert rel(xs[i].double().cpu().numpy(), ref["x"]) < 1e-9
+    Bt.close()
+    # a batch created without the variable runs every group
+    B2 = make_batch(G, probs, prec)
+    B2.solve(6)
+    assert all(c == G._lib.SGKS_OK for c in B2.status())
+    B2.close()
+
+
+# ------------------------------------------------------------------------- full-size batches
+# The two batched workloads at full size, launched as bench.py launches them (one captured graph
+# replayed per iteration), against the oracle run on single instances alone.  The GPU iterates are
+# collected first and saved; the oracle runs afterwards in spawned processes (one per instance),
+# each comparing its own iterates and returning the error curve.
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load_floor(tag):
+    import json
+    path = os.path.join(GOLDEN, f"floor_{tag}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"missing {path}: run tests/golden/make_floors.py")
+    with open(path) as f:
+        return json.load(f)["floor"]
+
+
+def _oracle_errors(args):
+    """Spawned worker: oracle iterates of one instance against the saved GPU iterates."""
+    kind, kw, path = args
+    import numpy as np
+    import oracle as O
+    from workloads import make_problem
+    P = make_problem(kind, **kw)
+    if kind == "ct2d":
+        P.n_refine = 0
+    ref = O.sgks(P, record_x=True)
+    xs = np.load(path)
+    return [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(xs, ref["xs"])]
+
+
+def _compare_in_workers(cases):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(cases)) as pool:
+        return pool.map(_oracle_errors, cases)
+
+
+def _graph_iterates(Bt, iters, which):
+    xs = {i: [] for i in which}
+    for k in range(iters + 1):
+        if k:
+            Bt.solve(1)
+        for i, x in enumerate(Bt.x(which)):
+            if x is not None:
+                xs[i].append(x.double().cpu().numpy())
+    return {i: np.stack(v) for i, v in xs.items()}
+
+
+@pytest.mark.slow
+def test_full_size_ct_batch_ff(G, tmp_path):
+    """512^2 CT, 64 right-hand sides x lambda_i, 150 iterations, float-float form (the bench's
+    headline workload): instances 0, 21, 42 and 63 against the oracle at every iteration,
+    max(1e-10, 10 x floor_k) with the instance's float-float floor."""
+    from workloads.configs import ct_op, make_ct2d
+    A0 = ct_op(512, np.arange(180) * 1.0, 725)
+    probs = [make_ct2d(instance=i, A=A0, precision="ff") for i in range(64)]
+    Bt = make_batch(G, probs, "ff", autotune=True)
+    which = (0, 21, 42, 63)
+    xs = _graph_iterates(Bt, 150, which)
+    Bt.close()
+    cases = []
+    for i in which:
+        path = str(tmp_path / f"x{i}.npy")
+        np.save(path, xs[i])
+        cases.append(("ct2d", {"instance": i, "A": A0}, path))
+    del xs
+    errs = _compare_in_workers(cases)
+    for i, e in zip(which, errs):
+        fl = _load_floor(f"ct2d_ff" if i == 42 else f"ct2d_instance{i}_ff")
+        parity_log.record(f"full_size_ct_batch_ff[{i}]", e, fl, TOL64, FACTOR64)
+        bad = [(k, v, fl[k]) for k, v in enumerate(e) if v > max(TOL64, FACTOR64 * fl[k])]
+        assert not bad, f"instance {i}: {bad[:4]}"
+
+
+@pytest.mark.slow
+def test_full_size_dynct_batch_fp32(G, tmp_path):
+    """Dynamic CT, 16 ragged instances (frames 8, 16, 24, 32; seeds 0..15), 200 iterations with 3
+    refinement steps, FP32 form: one instance per frame count (seeds 0..3) against the oracle at
+    every iteration, max(1e-4, 10 x floor_k) with the instance's FP32 floor."""
+    from workloads.configs import dynct_frame_ops, make_dynct
+    ops = dynct_frame_ops(128, 32)
+    frames = [8, 16, 24, 32] * 4
+    probs, shared = [], {}
+    for i, F in enumerate(frames):
+        P = make_dynct(seed=i, frames=F, frame_ops=ops)
+        P.A = shared.setdefault(F, P.A)
+        probs.append(P)
+    Bt = make_batch(G, probs, "fp32", autotune=True)
+    assert Bt.layout()[0] == 4
+    which = (0, 1, 2, 3)
+    xs = _graph_iterates(Bt, 200, which)
+    Bt.close()
+    cases = []
+    for i in which:
+        path = str(tmp_path / f"x{i}.npy")
+        np.save(path, xs[i])
+        cases.append(("dynct", {"seed": i, "frames": frames[i]}, path))
+    del xs
+    errs = _compare_in_workers(cases)
+    for i, e in zip(which, errs):
+        fl = _load_floor(f"dynct_seed{i}_frames{frames[i]}_fp32")
+        parity_log.record(f"full_size_dynct_batch_fp32[{i}]", e, fl, TOL32, FACTOR32)
+        bad = [(k, v, fl[k]) for k, v in enumerate(e) if v > max(TOL32, FACTOR32 * fl[k])]
+        assert not bad, f"instance {i} ({frames[i]} frames): {bad[:4]}"

@@ -4,10 +4,11 @@ Iterates x_k are compared in relative 2-norm.  The bar is 1e-10 for the FP64 for
 for the FP32 form, raised where the method's own sensitivity makes that impossible: sGKS
 never re-orthogonalises its basis, so rounding-level differences between two correct
 implementations grow from iteration to iteration.  The floor of iteration k is measured with
-the oracle alone (oracle vs oracle with every gradient perturbed by (1 + eps N(0,1)), eps =
-2^-53 for FP64, 2^-24 for FP32; tests/golden/make_floors.py) and an iterate passes when its
-error is below max(tolerance, FACTOR * floor_k), the floor being the largest deviation over five
-perturbation seeds.  The FP32 form ("fp32": FP32 basis, compensated sums) is gated at every
+the oracle alone: the oracle against itself with every gradient, every sketched column entering
+the QR update and the inputs of every projected solve perturbed by (1 + eps N(0,1)) -- the
+backward errors of those steps -- eps = 2^-53 for FP64, 2^-48 for float-float, 2^-24 for FP32
+(tests/golden/make_floors.py), the largest deviation over five seeds.  An iterate passes when its
+error is below max(tolerance, FACTOR * floor_k).  The FP32 form ("fp32": FP32 basis, compensated sums) is gated at every
 iteration; the FP32-accumulation kernels ("fp32plain") drift from the FP64 iterates by design and
 are gated only while the FP32 floor is below 1e-6.  Sparse-sign indices, CSR transposes and
 integer state are compared bit-exactly."""
@@ -22,7 +23,6 @@ import torch
 
 import oracle as O
 import parity_log
-from oracle import sgks_oracle as OS
 from workloads import make_problem, small_problem
 
 sys.path.insert(0, os.path.join(os.path.dirname(__file__), "golden"))
@@ -178,16 +178,8 @@ def test_fp64_iterates_cgs1_and_gaussian(G):
 
 
 def floor_curve_cgs1(P):
-    """Floor of the single-projection variant (oracle with cgs_passes = 1 on both runs)."""
-    rng = np.random.default_rng(0)
-    ref = O.sgks(P, record_x=True, cgs_passes=1)
-    orig = OS.gradient
-    OS.gradient = lambda A, L, b, lam, x: orig(A, L, b, lam, x) * (1 + EPS["fp64"] * rng.standard_normal(P.n))
-    try:
-        p = O.sgks(P, record_x=True, cgs_passes=1)
-    finally:
-        OS.gradient = orig
-    return [rel(a, b) for a, b in zip(p["xs"], ref["xs"])]
+    """Floor of the single-projection variant (oracle with cgs_passes = 1 on every run)."""
+    return floor_curve(P, P.iters, EPS["fp64"], cgs_passes=1)[0]
 
 
 @pytest.mark.parametrize("kind", ["deblur2d", "dynct"])

@@ -269,7 +269,7 @@ def test_gradient_orthogonal_to_basis():
 
 
 def test_refinement_converges_to_unsketched_solution():
-    """The refinement's fixed point is y_sGKS0 over the same W (Sec. 3.1, Sec. 4.4)."""
+    """The refinement's fixed point is y_sGKS0 over the same W (Sec. 3.1, Sec. 4.3)."""
     P = small_problem("deblur2d", precision="fp64", n_refine=0, s=300)
     out = O.sgks(P, iters=8, record_state=True)
     Aop, Lop = O.make_operators(P)

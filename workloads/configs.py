@@ -7,22 +7,22 @@ deconv1d  (1D deconvolution, plain FP64): n = m = 256; A dense Toeplitz Gaussian
           L = D_256 (255 x 256); x_true piecewise constant with 5 pieces (4 sorted
           breakpoints uniform in [1, 255], values U[0,1]); 1% noise; lambda = 1e-2;
           30 iterations; Gaussian sketch with s = 120 rows; seed 0.
-deblur2d  (image deblurring, after Sec. 4.1): 256 x 256 image; A = 2D convolution with a
+deblur2d  (image deblurring, after Experiment 1, Sec. 4.1): 256 x 256 image; A = 2D convolution with a
           9x9 Gaussian PSF, sigma = 2, zero boundary; L = 2D forward-difference gradient;
           x_true = 20 axis-aligned rectangles (later ones overwrite), intensities U[0,1];
           1% noise; lambda = 5e-3; 100 iterations; sparse-sign sketch, zeta = 8, s = 400;
           FP32 operators with 2 refinement steps.
-ct2d      (parallel-beam X-ray CT, after Sec. 4.2): 512 x 512 image; 180 angles j*1 deg,
+ct2d      (parallel-beam X-ray CT, after Experiment 2, Sec. 4.2.1): 512 x 512 image; 180 angles j*1 deg,
           725 detector bins of 1 px; A = CSR of ray-pixel intersection lengths (float32
           values, int32 indices); phantom = 10 random ellipses, densities U[0,1], added;
           L = grad2d; 2% noise; instance i of the 64-instance batch has noise seed i and
           lambda_i = 10^(-4 + 3 i / 63); 150 iterations; sparse-sign, zeta = 8, s = 600.
-seismic2d (travel-time tomography, after Sec. 4.3): 256 x 256 slowness grid; 64 sources on
+seismic2d (travel-time tomography, after Experiment 3, Sec. 4.2.2): 256 x 256 slowness grid; 64 sources on
           the left edge, 128 receivers (64 on the right edge, 64 on the top edge), m = 8192
           straight rays; x_true = 1 + 0.1 * (Gaussian random field, correlation length 20
           cells, unit std); L = 5-point Laplacian; 1% noise; 80 iterations; sparse-sign,
           zeta = 8, s = 400.
-dynct     (dynamic CT, after Sec. 4.4): 128 x 128 x F frames (F = 32 by default); frame t
+dynct     (dynamic CT, after Experiment 4, Sec. 4.3): 128 x 128 x F frames (F = 32 by default); frame t
           sees 30 angles (6 t + 0.2 j) deg mod 180, j = 0..29, 185 bins; A = block-diagonal
           CSR; L = Psi (eq. spacetime_tik); 4 ellipses moving 1 or 2 px per frame; 1% noise;
           200 iterations; sparse-sign, zeta = 8, s = 800; FP32 operators with 3 refinement

@@ -60,7 +60,7 @@ class RegDesc:
     kind = "grad2d":    [I_ny (x) D_nx ; D_ny (x) I_nx], p = ny(nx-1) + (ny-1)nx (eq. reg_matrix).
     kind = "laplace2d": 5-point Laplacian, zero Dirichlet values outside the grid, p = nx*ny.
     kind = "spacetime": Psi = [I_t (x) I_y (x) D_x ; I_t (x) D_y (x) I_x ; D_t (x) I_y (x) I_x]
-                        (Sec. 4.4, eq. spacetime_tik), p = nt(ny(nx-1) + (ny-1)nx) + (nt-1)nx ny.
+                        (Sec. 4.3, eq. spacetime_tik), p = nt(ny(nx-1) + (ny-1)nx) + (nt-1)nx ny.
     """
     kind: str
     nx: int = 0
