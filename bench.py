@@ -696,6 +696,11 @@ def main_batch(args):
             extras_path = os.environ.get("SGKS_BENCH_EXTRAS")
             ex = {"dynct_ragged16": bench_dynct_batch(G, dev, flush, args.compare_dynct)}
             ex["single_instance"] = bench_singles(G, dev, flush)
+            ex["srtt_sketch_sweep"] = {"deblur2d": bench_srtt_sweep(G, dev, flush),
+                                       "ct2d": bench_srtt_sweep(G, dev, flush, "ct2d", (300, 600), "fp64")}
+            ex["differentiable"] = bench_differentiable(G, dev, flush)
+            ex["gks"] = {nm: bench_gks(G, nm, dev, flush) for nm in ("deblur2d", "ct2d")}
+            line["srtt_ct2d"] = {k: v for k, v in ex["srtt_sketch_sweep"]["ct2d"].items()}
             line["dynct_ragged16"] = compact_dynct(ex["dynct_ragged16"])
             if extras_path:
                 with open(extras_path, "w") as f:
@@ -1246,26 +1251,30 @@ def profile_batch(args):
     Bt.close()
 
 
-def bench_srtt_sweep(G, dev, flush, sizes=(200, 400, 800)):
-    """The deblurring workload with the paper's SRTT sketch (eq. sketching_trig, dense on the
-    device) at several sketch sizes s, next to the sparse-sign sketch at the workload's s."""
+def bench_srtt_sweep(G, dev, flush, name="deblur2d", sizes=(200, 400, 800), precision=None):
+    """A workload with the paper's SRTT sketch (eq. sketching_trig, dense on the device) at several
+    sketch sizes s, next to the sparse-sign sketch at the workload's s (the paper's sketch-size
+    sweeps: deblurring in Sec. 4.1, CT in Sec. 4.2.1)."""
     from workloads.configs import srtt_sketch
     out = {}
-    base = make_workload("deblur2d", seed=0)
+    base = make_workload(name, seed=0)
+    prec = precision or base.precision
     iters = base.iters
     for s in sizes:
-        P = make_workload("deblur2d", seed=0)
+        P = make_workload(name, seed=0)
         P.sketch = srtt_sketch(s, P.m, P.p, seed=0)
-        kw = G.device_inputs(P, P.precision, device=dev)
+        kw = G.device_inputs(P, prec, device=dev)
         S = G.Solver(**kw)
         t, h = time_solve(G, S, kw["b"], iters, flush, dev)
         S.close()
-        out[f"srtt_s{s}"] = {"iters_per_s": iters / (t / 1e3), "final_rre": h["rre_last"]}
-    kw = G.device_inputs(base, base.precision, device=dev)
+        out[f"srtt_s{s}"] = {"iters_per_s": iters / (t / 1e3), "final_rre": h["rre_last"], "min_rre": min(h["rre"])}
+    kw = G.device_inputs(base, prec, device=dev)
     S = G.Solver(**kw)
     t, h = time_solve(G, S, kw["b"], iters, flush, dev)
     S.close()
-    out[f"sparse_sign_s{base.sketch.s}"] = {"iters_per_s": iters / (t / 1e3), "final_rre": h["rre_last"]}
+    out[f"sparse_sign_s{base.sketch.s}"] = {"iters_per_s": iters / (t / 1e3), "final_rre": h["rre_last"],
+                                            "min_rre": min(h["rre"])}
+    out["form"] = prec
     return out
 
 

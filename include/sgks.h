@@ -49,7 +49,8 @@ enum { SGKS_OP_DENSE = 1, SGKS_OP_CSR = 2, SGKS_OP_CONV2D = 3 };
 enum { SGKS_REG_FD1 = 1, SGKS_REG_GRAD2D = 2, SGKS_REG_LAPLACE2D = 3, SGKS_REG_SPACETIME = 4 };
 enum { SGKS_SKETCH_SPARSE_SIGN = 0, SGKS_SKETCH_GAUSSIAN = 1, SGKS_SKETCH_SRTT = 2 };
 enum { SGKS_PREC_FP64 = 0, SGKS_PREC_FP32 = 1, SGKS_PREC_FP32X = 2, SGKS_PREC_FP32_PLAIN = 3, SGKS_PREC_FF = 4 };
-enum { SGKS_FLAG_GLOBAL_SMALL = 1, SGKS_FLAG_RECORD = 2, SGKS_FLAG_GKS = 4, SGKS_FLAG_AUTOTUNE = 8 };
+enum { SGKS_FLAG_GLOBAL_SMALL = 1, SGKS_FLAG_RECORD = 2, SGKS_FLAG_GKS = 4, SGKS_FLAG_AUTOTUNE = 8,
+       SGKS_FLAG_NO_TILES = 16, SGKS_FLAG_BW_HOST = 32 };
 
 /* Forward operator A (m x n).
  *  SGKS_OP_CSR:    row_ptr[m+1], col[nnz] (int32, 0-based), val[nnz] of val_dtype.  Optional
@@ -140,7 +141,19 @@ typedef struct sgks_options {
                              candidate tile choices of each group on its own data and keep the
                              fastest (bulk-copy slice 8 or 16 KB; lanes per CSR row of A and A^T);
                              results are cached per shape for the process.  Without it the
-                             defaults are used (16 KB, 8, 8) and results are reproducible [0] */
+                             defaults are used (16 KB, 8, 8) and results are reproducible.
+                             bit 4 (SGKS_FLAG_NO_TILES, batches only): the compensated forms
+                             (FP32, FF) compute A w of a CSR operator whose regularizer gives an
+                             image geometry (2D stencils, space-time) through pixel tiles: each
+                             tile of w is staged once in shared memory and the rays crossing it
+                             leave one partial sum per (ray, tile), summed per ray in entry
+                             order.  This flag keeps the CSR-row kernel instead.
+                             bit 5 (SGKS_FLAG_BW_HOST, with SGKS_FLAG_RECORD): sgks_backward keeps
+                             the adjoint of the basis (d_max x n values, the sweep's largest
+                             array, as large as W itself) in pinned host memory mapped into the
+                             device's address space, reached over the CPU-GPU link, for when the
+                             device memory cannot hold a second basis-sized array; the result is
+                             the same, bit for bit, as with device memory [0] */
     const double* gauss_SA; /* Gaussian sketch only: S_A, sketch_rows x m, row-major, FP64, device */
     const double* gauss_SL; /* Gaussian sketch only: S_L, sketch_rows x p, row-major, FP64, device */
     const void* x_true;     /* optional, n values of the solver precision: enables RRE records    */
@@ -259,7 +272,10 @@ int sgks_sparse_sign_rows(uint64_t seed, int32_t stream_id, int64_t h_cols, int3
 /* Build the transpose of a CSR matrix on the device: the column-major storage of A, with
  * row indices ascending within each column (deterministic).  Inputs row_ptr[m+1], col[nnz],
  * val[nnz] (val_dtype); outputs t_row_ptr[n+1], t_col[nnz], t_val[nnz] (same dtype), all
- * device, caller-allocated.  Temporary device memory is allocated and freed inside.
+ * device, caller-allocated.  Preconditions: 0 = row_ptr[0] <= row_ptr[1] <= ... <= row_ptr[m]
+ * = nnz and every col[k] in [0, n).  Entries that break them are skipped by the kernels (nothing
+ * is written outside the output and temporary arrays) and the call returns SGKS_ERR_INVALID;
+ * the output is then not a transpose.  Temporary device memory is allocated and freed inside.
  * Synchronises `stream`. */
 int sgks_csr_transpose(int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr,
                        const int32_t* col, const void* val, int32_t val_dtype,
@@ -273,11 +289,19 @@ int sgks_csr_transpose(int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr
  * fail or stall in the middle of a request.
  *
  * Its temporaries live in a fixed scratch array of 16 MiB (16,777,216 bytes) inside the
- * library.  Every GPU that loads the library holds that array until the process exits.  The
+ * library.  With CUDA's lazy module loading the array is reserved on a device the first time
+ * the library's kernels are used there, which may be this call: if the device memory is
+ * already full that first use returns an allocation error (SGKS_ERR_CUDA), so make one warm-up
+ * call at start-up, while memory is still free.  From then on the device holds the array until
+ * the process exits.  The
  * array must hold 4*(n+1) + 4*nnz + es*nnz bytes, each of the three parts rounded up to 256
  * bytes, where es = 4 for SGKS_F32 values and 8 for SGKS_F64.  For example, n = 65,536 with
  * FP32 values fits nnz up to about 2.06 million.  Larger sizes return SGKS_ERR_INVALID, with
  * the sizes in sgks_last_error(NULL); use sgks_csr_transpose for those.
+ *
+ * The preconditions on row_ptr and col are those of sgks_csr_transpose, with the same
+ * SGKS_ERR_INVALID when they do not hold (the error flag is a second, 4-byte array of the
+ * library, so a malformed input cannot write into the scratch's neighbours).
  *
  * The first call on a device looks up the array's device address on the current device, which
  * must be the device of `stream` and of the buffers.  Make that first call before any stream

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libsgks.so")
 SOURCES = ["k_sketch.cu", "k_small.cu", "k_small2.cu", "k_fp32x.cu", "k_bulk.cu", "k_setup.cu", "k_batch.cu",
-           "k_adjoint.cu", "k_gks.cu", "k_conv.cu", "k_batchx.cu", "sgks_api.cu", "sgks_batch.cu"]
+           "k_adjoint.cu", "k_gks.cu", "k_conv.cu", "k_batchx.cu", "k_tiles.cu", "sgks_api.cu", "sgks_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include")]

@@ -827,10 +827,11 @@ static cudaError_t x_csr_apply_vv(const BDims& D, const DevA<float, float>& A, c
 
 template <typename TW>
 cudaError_t launchbx_apply_column(const BDims& D, const DevA<float, float>& A, const DevL& L, const BBulkX<TW>& X,
-                                  const BSmall& S, cudaStream_t st) {
+                                  const BSmall& S, cudaStream_t st, bool a_rows) {
     if (A.kind == SGKS_OP_CSR) {
         constexpr int VW = wvec<TW>();
-        cudaError_t e = D.B >= VW ? x_csr_apply_vv<TW, VW>(D, A, X, S, st)
+        cudaError_t e = !a_rows ? cudaSuccess
+                        : D.B >= VW ? x_csr_apply_vv<TW, VW>(D, A, X, S, st)
                         : (VW == 4 && D.B == 2) ? x_csr_apply_vv<TW, 2>(D, A, X, S, st)
                                                 : x_csr_apply_vv<TW, 1>(D, A, X, S, st);
         if (e != cudaSuccess) return e;
@@ -945,7 +946,7 @@ cudaError_t launchbx_to_double(const float2* in, double* out, int64_t len, cudaS
 
 #define SGKS_INST_BX(TW)                                                                                          \
     template cudaError_t launchbx_apply_column<TW>(const BDims&, const DevA<float, float>&, const DevL&,           \
-                                                   const BBulkX<TW>&, const BSmall&, cudaStream_t);               \
+                                                   const BBulkX<TW>&, const BSmall&, cudaStream_t, bool);         \
     template cudaError_t launchbx_sketch_gather<TW>(const BDims&, const BBulkX<TW>&, const SketchCSR&,             \
                                                     const BSmall&, const float2*, double*, cudaStream_t);          \
     template cudaError_t launchbx_combine<TW>(const BDims&, const BBulkX<TW>&, const BSmall&, int, cudaStream_t);  \

@@ -235,9 +235,17 @@ cudaError_t sparse_sign_rows_device(uint64_t key, int64_t h, int s, int zeta, in
 }
 
 // ---------------------------------------------------------------------------- transpose
-__global__ void k_col_count(const int32_t* __restrict__ ci, int64_t nnz, int32_t* cnt) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(cnt + ci[k], 1);
+// Column indices outside [0, n) are skipped and raise *err (when err is given), so a malformed
+// input cannot make the count or the fill write outside their arrays.
+__global__ void k_col_count(const int32_t* __restrict__ ci, int64_t nnz, int64_t n, int32_t* cnt, int* err) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = ci[k];
+        if (c < 0 || c >= n) {
+            if (err) *err = 1;
+            continue;
+        }
+        atomicAdd(cnt + c, 1);
+    }
 }
 
 // Exclusive scan of cnt[0..n) into ptr[0..n]; one CTA of 1024 threads, contiguous chunks.
@@ -264,13 +272,22 @@ __global__ void __launch_bounds__(1024) k_scan(const int32_t* __restrict__ cnt, 
     if (t == 1023) ptr[n] = (int32_t)sums[1023];
 }
 
+// A row whose pointers are not 0 <= row_ptr[r] <= row_ptr[r+1] <= nnz, or an entry with a column
+// outside [0, n), is skipped and raises *err.
 template <typename V>
 __global__ void k_fill(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const V* __restrict__ val,
-                       int64_t m, const int32_t* __restrict__ tp, int32_t* fill, int32_t* trow, V* tval) {
+                       int64_t m, int64_t n, int64_t nnz, const int32_t* __restrict__ tp, int32_t* fill,
+                       int32_t* trow, V* tval, int* err) {
     const int64_t r = (int64_t)blockIdx.x * kWarps + warp_id();
     if (r >= m) return;
-    for (int k = rp[r] + lane_id(); k < rp[r + 1]; k += 32) {
+    const int32_t b = rp[r], e = rp[r + 1];
+    if (b < 0 || e < b || e > nnz) {
+        if (err && lane_id() == 0) *err = 1;
+        return;
+    }
+    for (int k = b + lane_id(); k < e; k += 32) {
         const int c = ci[k];
+        if (c < 0 || c >= n) continue;
         const int pos = tp[c] + atomicAdd(fill + c, 1);
         trow[pos] = (int32_t)r;
         tval[pos] = val[k];
@@ -296,7 +313,7 @@ __global__ void k_rank_sort(const int32_t* __restrict__ tp, int64_t n, const int
 
 template <typename V>
 static cudaError_t transpose_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
-                                  const V* val, int32_t* trp, int32_t* tci, V* tval, cudaStream_t st) {
+                                  const V* val, int32_t* trp, int32_t* tci, V* tval, int* err, cudaStream_t st) {
     int32_t *cnt = nullptr, *rowtmp = nullptr;
     V* valtmp = nullptr;
     cudaError_t e = cudaMallocAsync(&cnt, sizeof(int32_t) * (size_t)(n + 1), st);
@@ -306,7 +323,7 @@ static cudaError_t transpose_impl(int64_t m, int64_t n, int64_t nnz, const int32
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)(n + 1), st);
     if (e == cudaSuccess && nnz > 0) {
         carveout_once((const void*)k_col_count);
-        k_col_count<<<1216, 256, 0, st>>>(ci, nnz, cnt);
+        k_col_count<<<1216, 256, 0, st>>>(ci, nnz, n, cnt, err);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
@@ -317,7 +334,8 @@ static cudaError_t transpose_impl(int64_t m, int64_t n, int64_t nnz, const int32
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)(n + 1), st);
     if (e == cudaSuccess && m > 0) {
         carveout_once((const void*)k_fill<V>);
-        k_fill<V><<<(unsigned)((m + kWarps - 1) / kWarps), kThreads, 0, st>>>(rp, ci, val, m, trp, cnt, rowtmp, valtmp);
+        k_fill<V><<<(unsigned)((m + kWarps - 1) / kWarps), kThreads, 0, st>>>(rp, ci, val, m, n, nnz, trp, cnt, rowtmp,
+                                                                            valtmp, err);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && n > 0) {
@@ -332,10 +350,11 @@ static cudaError_t transpose_impl(int64_t m, int64_t n, int64_t nnz, const int32
 }
 
 cudaError_t csr_transpose_device(int64_t m, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
-                                 const void* val, int vdt, int32_t* trp, int32_t* tci, void* tval, cudaStream_t st) {
+                                 const void* val, int vdt, int32_t* trp, int32_t* tci, void* tval, cudaStream_t st,
+                                 int* err) {
     if (vdt == SGKS_F32)
-        return transpose_impl<float>(m, n, nnz, rp, ci, (const float*)val, trp, tci, (float*)tval, st);
-    return transpose_impl<double>(m, n, nnz, rp, ci, (const double*)val, trp, tci, (double*)tval, st);
+        return transpose_impl<float>(m, n, nnz, rp, ci, (const float*)val, trp, tci, (float*)tval, err, st);
+    return transpose_impl<double>(m, n, nnz, rp, ci, (const double*)val, trp, tci, (double*)tval, err, st);
 }
 
 // ------------------------------------------------------- interleaved 32-row slices of a CSR
@@ -398,6 +417,8 @@ cudaError_t slice_fill_device(const int32_t* rp, const int32_t* ci, const void* 
 // 256-byte boundary.  The array belongs to the module, so every GPU that loads the library holds
 // kNoAllocScratchBytes of it until the process exits, and every call shares it.
 static __device__ __align__(256) unsigned char g_transpose_scratch[kNoAllocScratchBytes];
+// Malformed-input flag of the allocation-free transpose (col outside [0, n) or bad row pointers).
+static __device__ int g_transpose_err;
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -407,11 +428,13 @@ size_t transpose_noalloc_need(int64_t n, int64_t nnz, int vdt) {
            align256(es * (size_t)nnz);
 }
 
-// Device address of the scratch on the current device, looked up once per device.
-static cudaError_t transpose_scratch_ptr(unsigned char** out) {
+// Device addresses of the scratch and of the error flag on the current device, looked up once
+// per device.
+static cudaError_t transpose_scratch_ptr(unsigned char** out, int** err) {
     constexpr int kMaxDevices = 64;
     static std::mutex mu;
     static unsigned char* ptrs[kMaxDevices] = {nullptr};
+    static int* errs[kMaxDevices] = {nullptr};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -419,19 +442,28 @@ static cudaError_t transpose_scratch_ptr(unsigned char** out) {
     std::lock_guard<std::mutex> g(mu);
     if (!ptrs[dev]) {
         void* p = nullptr;
+        void* q = nullptr;
         e = cudaGetSymbolAddress(&p, g_transpose_scratch);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, g_transpose_err);
         if (e != cudaSuccess) return e;
         ptrs[dev] = static_cast<unsigned char*>(p);
+        errs[dev] = static_cast<int*>(q);
     }
     *out = ptrs[dev];
+    *err = errs[dev];
     return cudaSuccess;
 }
 
 template <typename V>
 static cudaError_t transpose_noalloc_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
-                                          const V* val, int32_t* trp, int32_t* tci, V* tval, cudaStream_t st) {
+                                          const V* val, int32_t* trp, int32_t* tci, V* tval, cudaStream_t st,
+                                          int** err_out) {
     unsigned char* base = nullptr;
-    cudaError_t e = transpose_scratch_ptr(&base);
+    int* err = nullptr;
+    cudaError_t e = transpose_scratch_ptr(&base, &err);
+    if (e != cudaSuccess) return e;
+    *err_out = err;
+    e = cudaMemsetAsync(err, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     int32_t* cnt = reinterpret_cast<int32_t*>(base);
     int32_t* rowtmp = reinterpret_cast<int32_t*>(base + align256(sizeof(int32_t) * (size_t)(n + 1)));
@@ -439,7 +471,7 @@ static cudaError_t transpose_noalloc_impl(int64_t m, int64_t n, int64_t nnz, con
     // the counts are the only part read before it is written; the previous call left its own there
     e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)(n + 1), st);
     if (e == cudaSuccess && nnz > 0) {
-        k_col_count<<<1216, 256, 0, st>>>(ci, nnz, cnt);
+        k_col_count<<<1216, 256, 0, st>>>(ci, nnz, n, cnt, err);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
@@ -448,7 +480,8 @@ static cudaError_t transpose_noalloc_impl(int64_t m, int64_t n, int64_t nnz, con
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)(n + 1), st);
     if (e == cudaSuccess && m > 0) {
-        k_fill<V><<<(unsigned)((m + kWarps - 1) / kWarps), kThreads, 0, st>>>(rp, ci, val, m, trp, cnt, rowtmp, valtmp);
+        k_fill<V><<<(unsigned)((m + kWarps - 1) / kWarps), kThreads, 0, st>>>(rp, ci, val, m, n, nnz, trp, cnt, rowtmp,
+                                                                            valtmp, err);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && n > 0) {
@@ -460,10 +493,10 @@ static cudaError_t transpose_noalloc_impl(int64_t m, int64_t n, int64_t nnz, con
 
 cudaError_t csr_transpose_noalloc_device(int64_t m, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
                                          const void* val, int vdt, int32_t* trp, int32_t* tci, void* tval,
-                                         cudaStream_t st) {
+                                         cudaStream_t st, int** err) {
     if (vdt == SGKS_F32)
-        return transpose_noalloc_impl<float>(m, n, nnz, rp, ci, (const float*)val, trp, tci, (float*)tval, st);
-    return transpose_noalloc_impl<double>(m, n, nnz, rp, ci, (const double*)val, trp, tci, (double*)tval, st);
+        return transpose_noalloc_impl<float>(m, n, nnz, rp, ci, (const float*)val, trp, tci, (float*)tval, st, err);
+    return transpose_noalloc_impl<double>(m, n, nnz, rp, ci, (const double*)val, trp, tci, (double*)tval, st, err);
 }
 
 // ------------------------------------------------------------------------- SRTT sketch

@@ -97,6 +97,8 @@ struct EngineBase {
     // reverse sweep (sgks_backward): y_k of every iteration, recorded when SGKS_FLAG_RECORD is set
     double* yhist = nullptr;
     std::vector<void*>* allocs = nullptr;   // the handle's device allocations
+    std::vector<void*>* host_allocs = nullptr;   // the handle's mapped host allocations
+    bool bw_host = false;   // SGKS_FLAG_BW_HOST: the reverse sweep's basis adjoint in mapped host memory
     virtual cudaError_t backward(const void* xbar, void* bbar, double* lbar_host, int K) {
         (void)xbar; (void)bbar; (void)lbar_host; (void)K;
         return cudaErrorNotSupported;
@@ -271,7 +273,26 @@ struct Engine : EngineBase {
         const size_t n = D.n, m = D.m, p = D.p, s = D.s, dm = D.dmax, ell = D.ell;
         cudaError_t e = cudaSuccess;
         auto A1 = [&](auto** ptr, size_t c) { if (e == cudaSuccess) e = bw_alloc(ptr, c); };
-        A1(&bw.Wb, dm * n); A1(&bw.xb, n); A1(&bw.t1, n); A1(&bw.t2, n);
+        if (bw_host) {
+            // the adjoint of the basis (the sweep's one d_max x n array) in pinned host memory
+            // mapped into the device's address space: the kernels read and write it over the
+            // CPU-GPU link (NVLink-C2C on GB300) instead of holding it in device memory
+            void* hp = nullptr;
+            void* dp = nullptr;
+            e = cudaHostAlloc(&hp, sizeof(T) * dm * n + 16, cudaHostAllocMapped);
+            if (e == cudaSuccess) {
+                host_allocs->push_back(hp);
+                e = cudaHostGetDevicePointer(&dp, hp, 0);
+            }
+            if (e == cudaSuccess) bw.Wb = (T*)dp;
+            if (e != cudaSuccess) {
+                bw.Wb = nullptr;
+                return e;
+            }
+        } else {
+            A1(&bw.Wb, dm * n);
+        }
+        A1(&bw.xb, n); A1(&bw.t1, n); A1(&bw.t2, n);
         A1(&bw.P, n); A1(&bw.Q, n); A1(&bw.tm, m); A1(&bw.tp, p); A1(&bw.Kv, ell * n); A1(&bw.Kb, ell * n);
         A1(&bw.uy, s); A1(&bw.uz, s); A1(&bw.vy, s); A1(&bw.vz, s); A1(&bw.cb, s); A1(&bw.st, s);
         A1(&bw.ybar, dm); A1(&bw.z, dm); A1(&bw.part, (size_t)nbS * dm); A1(&bw.acc, 2);
@@ -744,6 +765,7 @@ struct sgks_handle {
     cudaStream_t user = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::vector<void*> allocs;
+    std::vector<void*> host_allocs;   // mapped pinned host memory (cudaFreeHost)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     std::string err;
@@ -1160,6 +1182,8 @@ static int build_engine(sgks_handle* h, const sgks_op* op, const sgks_reg* reg, 
         AL(EG->flag, 1);
     }
     E->allocs = &h->allocs;
+    E->host_allocs = &h->host_allocs;
+    E->bw_host = (o.flags & SGKS_FLAG_BW_HOST) != 0;
     S.lam = lambda;
     AL(E->d_err, 1);
     if (e != cudaSuccess) return fail(h, SGKS_ERR_NOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
@@ -1261,6 +1285,8 @@ int sgks::validate_problem(const sgks_op* A, const sgks_reg* L, const void* b, d
     if (o.flags & SGKS_FLAG_RECORD) {
         if (o.flags & SGKS_FLAG_GLOBAL_SMALL) return bad("SGKS_FLAG_RECORD needs the on-chip small kernels");
     }
+    if ((o.flags & SGKS_FLAG_BW_HOST) && !(o.flags & SGKS_FLAG_RECORD))
+        return bad("SGKS_FLAG_BW_HOST applies to the reverse sweep: it needs SGKS_FLAG_RECORD");
     return SGKS_OK;
 }
 
@@ -1497,6 +1523,7 @@ void sgks_destroy(sgks_handle* h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
     for (void* p : h->allocs) cudaFree(p);
+    for (void* p : h->host_allocs) cudaFreeHost(p);
     if (h->sc_host) cudaFreeHost(h->sc_host);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
@@ -1686,9 +1713,18 @@ int sgks_csr_transpose(int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr
         (val_dtype != SGKS_F32 && val_dtype != SGKS_F64))
         return fail(nullptr, SGKS_ERR_INVALID, "bad sgks_csr_transpose arguments");
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = csr_transpose_device(m, n, nnz, row_ptr, col, val, val_dtype, t_row_ptr, t_col, t_val, st);
+    int* derr = nullptr;
+    int herr = 0;
+    cudaError_t e = cudaMallocAsync(&derr, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = csr_transpose_device(m, n, nnz, row_ptr, col, val, val_dtype, t_row_ptr, t_col, t_val, st, derr);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (derr) cudaFreeAsync(derr, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "sgks_csr_transpose");
+    if (herr) return fail(nullptr, SGKS_ERR_INVALID, "sgks_csr_transpose: a column index outside [0, n) or row "
+                                                     "pointers outside [0, nnz]; the output is not a transpose");
     return SGKS_OK;
 }
 
@@ -1705,10 +1741,15 @@ int sgks_csr_transpose_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t*
                         " needs more than its fixed scratch of " + std::to_string(kNoAllocScratchBytes) +
                         " bytes; use sgks_csr_transpose");
     cudaStream_t st = (cudaStream_t)stream;
+    int* derr = nullptr;
+    int herr = 0;
     cudaError_t e =
-        csr_transpose_noalloc_device(m, n, nnz, row_ptr, col, val, val_dtype, t_row_ptr, t_col, t_val, st);
+        csr_transpose_noalloc_device(m, n, nnz, row_ptr, col, val, val_dtype, t_row_ptr, t_col, t_val, st, &derr);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "sgks_csr_transpose_noalloc");
+    if (herr) return fail(nullptr, SGKS_ERR_INVALID, "sgks_csr_transpose_noalloc: a column index outside [0, n) or "
+                                                     "row pointers outside [0, nnz]; the output is not a transpose");
     return SGKS_OK;
 }
 

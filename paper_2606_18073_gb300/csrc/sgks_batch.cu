@@ -277,10 +277,17 @@ struct GroupX : GroupBase {
     BBulk<double> Xd{};         // setup: W = W_0 [ell][n][B], tm [m][B], b [m][B] in FP64
     SketchCSR SK{};
     int io_dt = SGKS_F32;       // element type of the caller's b, x_true and x_out
+    TiledA T{};                 // pixel tiles of a CSR A (ntiles = 0: the CSR-row kernel)
+    float2* part = nullptr;     // [nseg][B] partial sums of the tiled forward pass
 
     cudaError_t sketch_column() {
         cudaError_t e = cudaSuccess;
-        RUNC(BK_APPLY, A.kind == SGKS_OP_CSR ? 2 : 1, launchbx_apply_column<TW>(D, A, L, X, S, st));
+        if (T.ntiles) {
+            RUNC(BK_APPLY, 2, launchbx_tile_apply<TW>(D, T, X, S, part, st));
+            RUNC(BK_APPLY, 1, launchbx_apply_column<TW>(D, A, L, X, S, st, false));
+        } else {
+            RUNC(BK_APPLY, A.kind == SGKS_OP_CSR ? 2 : 1, launchbx_apply_column<TW>(D, A, L, X, S, st));
+        }
         RUNC(BK_GATHER, 1, launchbx_sketch_gather<TW>(D, X, SK, S, nullptr, nullptr, st));
         return e;
     }
@@ -404,7 +411,7 @@ struct GroupX : GroupBase {
             D.nb_combine = batchx_combine_grid(D, sizeof(TW));
         }
         if (A.kind == SGKS_OP_CSR) {
-            for (int which = 0; which < 2; ++which) {
+            for (int which = T.ntiles ? 1 : 0; which < 2; ++which) {   // tiled: A w has no lanes to tune
                 int* field = which == 0 ? &D.nl_a : &D.nl_t;
                 float best = 1e30f;
                 int pick = *field;
@@ -765,6 +772,15 @@ int build_groups_x(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const 
     rc = prepare_sparse_sign(sketch_key_host_dev(seed, 0), sketch_key_host_dev(seed, 1), op->m, L.p, s, o.zeta, SK,
                              h->allocs, h->d_err, h->st, &why);
     if (rc != SGKS_OK) return bfail(h, rc, why);
+    // pixel tiles for the forward pass of a CSR operator on an image geometry (the regularizer's)
+    TiledA T{};
+    if (op->kind == SGKS_OP_CSR && !(o.flags & SGKS_FLAG_NO_TILES) &&
+        (reg->kind == SGKS_REG_GRAD2D || reg->kind == SGKS_REG_LAPLACE2D || reg->kind == SGKS_REG_SPACETIME)) {
+        const int nt = reg->kind == SGKS_REG_SPACETIME ? reg->nt : 1;
+        rc = build_tiles(A.rp, A.ci, A.val, op->m, op->n, op->nnz, reg->nx, reg->ny, nt, 32, 16, T, h->allocs, h->st,
+                         &why);
+        if (rc != SGKS_OK) return bfail(h, rc, why);
+    }
     const int dmax = o.ell + o.max_iters;
     if (o.n_refine > 0 && batch_refine_smem(dmax, 1, sizeof(float2)) > 200 * 1024)
         return bfail(h, SGKS_ERR_INVALID, "ell + max_iters too large for the batched refinement");
@@ -779,6 +795,7 @@ int build_groups_x(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const 
         G->Ad = Ad;
         G->L = L;
         G->SK = SK;
+        G->T = T;
         G->io_dt = io_dt;
         G->has_xt = x_true != nullptr;
         for (int i = 0; i < B; ++i) {
@@ -808,6 +825,7 @@ int build_groups_x(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const 
         if (o.n_refine > 0) BA(X.r, nB);
         BA(lam2, B);
         BA(X.y2, (size_t)B * dmax);
+        if (T.ntiles) BA(G->part, (size_t)T.nseg * B);
         // the FP64 setup of W_0 (Krylov basis, CGS2): its ell columns, a temporary and b
         BA(G->Xd.W, (size_t)D.ell * nB);
         BA(G->Xd.tm, mB);
@@ -885,7 +903,7 @@ int sgks_batch_create(sgks_batch** hp, int32_t count, const sgks_op* A, const sg
     if (o.sketch_kind != SGKS_SKETCH_SPARSE_SIGN)
         return bfail(nullptr, SGKS_ERR_INVALID, "batches support the sparse-sign sketch only");
     if (o.flags & (SGKS_FLAG_GKS | SGKS_FLAG_RECORD | SGKS_FLAG_GLOBAL_SMALL))
-        return bfail(nullptr, SGKS_ERR_INVALID, "batches take SGKS_FLAG_AUTOTUNE only");
+        return bfail(nullptr, SGKS_ERR_INVALID, "batches take SGKS_FLAG_AUTOTUNE and SGKS_FLAG_NO_TILES only");
     o.x_true = nullptr;
     for (int i = 0; i < count; ++i) {
         std::string why;

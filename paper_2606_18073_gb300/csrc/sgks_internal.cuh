@@ -837,8 +837,8 @@ cudaError_t launch_sqnorm(const T* w, int64_t n, double* part, int nb, cudaStrea
 
 // transpose and sketch rows (sgks_util.cu)
 cudaError_t csr_transpose_device(int64_t m, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
-                                 const void* val, int vdt, int32_t* trp, int32_t* tci, void* tval,
-                                 cudaStream_t st);
+                                 const void* val, int vdt, int32_t* trp, int32_t* tci, void* tval, cudaStream_t st,
+                                 int* err = nullptr);
 // interleaved 32-row slices of a CSR with `rows` rows (DevA::sl_*): the slice sizes w[g], then,
 // with off = their exclusive prefix sums, the row lengths and the interleaved entries
 cudaError_t slice_width_device(const int32_t* rp, int64_t rows, int64_t* w, cudaStream_t st);
@@ -934,10 +934,35 @@ template <typename T>
 cudaError_t launchb_gather_in(const PtrPack& P, T* out, int64_t len, int B, cudaStream_t st);
 template <typename T>
 cudaError_t launchb_scatter_out(const T* in, const PtrPack& P, int64_t len, int B, cudaStream_t st);
+// A CSR operator re-blocked by pixel tiles for the batched forward pass (k_tiles.cu): the image
+// (nt frames of ny x nx) cut into TX x TY tiles; a segment is the run of one row's entries that
+// falls in one tile.  Segments are stored tile-major (the segments of tile t are
+// [tile_seg[t], tile_seg[t+1]), in row order), each with its entries (local pixel index within
+// the tile, value) and the slot of its partial sum; the slots of row r are
+// [ray_slot[r], ray_slot[r+1]), in the order of the row's entries.
+struct TiledA {
+    int TX, TY, nx, ny, nt, ntx, nty, ntiles;
+    int64_t nseg;
+    const int32_t* tile_seg;   // [ntiles + 1]
+    const int32_t* seg_ent;    // [nseg + 1]
+    const int32_t* seg_slot;   // [nseg]
+    const int32_t* ray_slot;   // [m + 1]
+    const uint2* ent;          // [nnz] (local pixel index within the tile, value bits)
+};
+int build_tiles(const int32_t* d_rp, const int32_t* d_ci, const float* d_val, int64_t m, int64_t n, int64_t nnz,
+                int nx, int ny, int nt, int TX, int TY, TiledA& T, std::vector<void*>& allocs, cudaStream_t st,
+                std::string* why);
+size_t tile_smem(const TiledA& T, int B, size_t welem);
+// u_i = A w_i into column d_i of AW through the tiles (partials in part, nseg x B float-float)
+template <typename TW>
+cudaError_t launchbx_tile_apply(const BDims& D, const TiledA& T, const BBulkX<TW>& X, const BSmall& S, float2* part,
+                                cudaStream_t st);
+
 // compensated batched kernels (k_batchx.cu); TW = float or float2
+// a_rows = false: the L rows only (the A rows come from launchbx_tile_apply)
 template <typename TW>
 cudaError_t launchbx_apply_column(const BDims& D, const DevA<float, float>& A, const DevL& L, const BBulkX<TW>& X,
-                                  const BSmall& S, cudaStream_t st);
+                                  const BSmall& S, cudaStream_t st, bool a_rows = true);
 template <typename TW>
 cudaError_t launchbx_sketch_gather(const BDims& D, const BBulkX<TW>& X, const SketchCSR& SK, const BSmall& S,
                                    const float2* vec, double* out_vec, cudaStream_t st);
@@ -1034,9 +1059,10 @@ int prepare_sparse_sign(uint64_t keyA, uint64_t keyL, int64_t m, int64_t p, int 
 // Scratch size of the allocation-free CSR transpose and the bytes a given size needs of it.
 constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;
 size_t transpose_noalloc_need(int64_t n, int64_t nnz, int vdt);
+// *err receives the device address of the call's malformed-input flag (read it after the stream)
 cudaError_t csr_transpose_noalloc_device(int64_t m, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
                                          const void* val, int vdt, int32_t* trp, int32_t* tci, void* tval,
-                                         cudaStream_t st);
+                                         cudaStream_t st, int** err);
 cudaError_t sparse_sign_rows_device(uint64_t key, int64_t h, int s, int zeta, int32_t* rows, uint8_t* neg,
                                     int* err, cudaStream_t st);
 cudaError_t convert_values(const void* in, int in_dt, void* out, int out_dt, int64_t count, cudaStream_t st);

@@ -310,7 +310,7 @@ class Batch:
 
     def __init__(self, instances, sketch_rows: int, seed: int = 0, *, max_iters: int = 100, ell: int = 3,
                  n_refine: int = 0, precision: str = "fp64", zeta: int = 8, cgs_passes: int = 2, stream=None,
-                 autotune: bool = False):
+                 autotune: bool = False, tiles: bool = True):
         self._lib = L.load()
         self.precision = precision
         self.dtype = io_dtype(precision)
@@ -336,7 +336,7 @@ class Batch:
         o.max_iters, o.ell, o.n_refine, o.zeta, o.cgs_passes = max_iters, ell, n_refine, zeta, cgs_passes
         o.precision = PRECISIONS[precision]
         o.sketch_kind = L.SGKS_SKETCH_SPARSE_SIGN
-        o.flags = L.SGKS_FLAG_AUTOTUNE if autotune else 0
+        o.flags = (L.SGKS_FLAG_AUTOTUNE if autotune else 0) | (0 if tiles else L.SGKS_FLAG_NO_TILES)
         self.max_iters = max_iters
         dev = instances[0]["b"].device
         self.device = dev

@@ -95,16 +95,22 @@ def _suffix(params):
 
 
 def _run(task):
-    """One oracle run of (config, form) with the gradients perturbed by `seed` (None: unperturbed)."""
+    """One target (config, parameters, form) in one process: the unperturbed oracle run, then one
+    perturbed run per seed, keeping only the deviation curves (the iterates of one run at a time)."""
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-    name, params, form, seed = task
+    name, params, form, seeds = task
     import oracle as O
     P = _problem(name, form, params)
-    if seed is None:
-        ref = O.sgks(P, iters=P.iters, record_x=True)
-        return task, [np.asarray(x) for x in ref["xs"]], [float(v) for v in ref["rre"]]
-    p = _perturbed(P, P.iters, EPS[form], seed)
-    return task, [np.asarray(x) for x in p["xs"]], None
+    ref = O.sgks(P, iters=P.iters, record_x=True)
+    xs = [np.asarray(x) for x in ref["xs"]]
+    rre = [float(v) for v in ref["rre"]]
+    del ref
+    curves = []
+    for sd in range(seeds):
+        p = _perturbed(P, P.iters, EPS[form], sd)
+        curves.append([float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(p["xs"], xs)])
+        del p
+    return task, curves, rre
 
 
 def main(argv):
@@ -118,27 +124,19 @@ def main(argv):
         name, params, form = _parse(t)
         for f in ([form] if form else FORMS[name][0]):
             targets.append((name, params, f))
-    tasks = [(n, pr, f, s) for n, pr, f in targets for s in [None] + list(range(a.seeds))]
+    tasks = [(n, pr, f, a.seeds) for n, pr, f in targets]
     ctx = mp.get_context("spawn")
-    results = {}
-    with ctx.Pool(a.jobs) as pool:
-        for task, xs, rre in pool.imap_unordered(_run, tasks):
-            results[task] = (xs, rre)
-    for name, params, form in targets:
-        ref, rre = results[(name, params, form, None)]
-        curves = []
-        for s in range(a.seeds):
-            xs = results[(name, params, form, s)][0]
-            curves.append([float(np.linalg.norm(x - r) / np.linalg.norm(r)) for x, r in zip(xs, ref)])
-        floor = [max(c[k] for c in curves) for k in range(len(ref))]
-        P = _problem(name, form, params)
-        out = {"config": name, "params": dict(params), "form": form, "eps": EPS[form], "n_refine": P.n_refine,
-               "iters": P.iters, "seeds": a.seeds, "floor": floor, "per_seed": curves, "oracle_rre": rre,
-               "note": "max over seeds of oracle vs oracle with gradients, sketched QR inputs and projected-solve "
-                       "inputs perturbed by (1 + eps*N(0,1)); written by make_floors.py"}
-        with open(os.path.join(HERE, f"floor_{name}{_suffix(params)}_{form}.json"), "w") as f:
-            json.dump(out, f)
-        print(name + _suffix(params), form, f"floor at k={P.iters}: {floor[-1]:.2e}", flush=True)
+    with ctx.Pool(min(a.jobs, len(tasks))) as pool:
+        for (name, params, form, seeds), curves, rre in pool.imap_unordered(_run, tasks):
+            floor = [max(c[k] for c in curves) for k in range(len(rre))]
+            P = _problem(name, form, params)
+            out = {"config": name, "params": dict(params), "form": form, "eps": EPS[form], "n_refine": P.n_refine,
+                   "iters": P.iters, "seeds": seeds, "floor": floor, "per_seed": curves, "oracle_rre": rre,
+                   "note": "max over seeds of oracle vs oracle with gradients, sketched QR inputs and projected-solve "
+                           "inputs perturbed by (1 + eps*N(0,1)); written by make_floors.py"}
+            with open(os.path.join(HERE, f"floor_{name}{_suffix(params)}_{form}.json"), "w") as f:
+                json.dump(out, f)
+            print(name + _suffix(params), form, f"floor at k={P.iters}: {floor[-1]:.2e}", flush=True)
 
 
 if __name__ == "__main__":

@@ -211,9 +211,8 @@ def test_backward_errors(G):
         S.backward(torch.zeros(P.n, dtype=torch.float64, device="cuda"))
     assert ei.value.code == G._lib.SGKS_ERR_STATE
     S.close()
-    kx = G.device_inputs(P, "fp32x")        # the recorded forward keeps W in the solve precision
-    with pytest.raises(G._lib.SGKSError) as ei:
-        G.Solver(**kx, record=True)
+    with pytest.raises(G._lib.SGKSError) as ei:   # float-float is a batch form
+        G.Solver(**G.device_inputs(P, "ff"), record=True)
     assert ei.value.code == G._lib.SGKS_ERR_INVALID
     S = G.Solver(**kw, record=True)
     S.solve(4)
@@ -287,3 +286,38 @@ def test_full_size_deblur_refined_gradient(G):
     assert rel(bbar, bb) <= max(1e-6, 10.0 * fb)
     assert abs(lbar - lb) <= max(1e-6, 10.0 * fl) * abs(lb)
     S.close()
+
+
+@pytest.mark.parametrize("n_refine", [0, 1])
+def test_backward_basis_adjoint_in_host_memory_is_bit_identical(G, n_refine):
+    """SGKS_FLAG_BW_HOST keeps the reverse sweep's basis adjoint (as large as W) in pinned host
+    memory that the kernels reach over the CPU-GPU link: dl/db and dl/dlambda are the same, bit
+    for bit, as with the adjoint in device memory -- seismic 256^2 at K = 80 (and K = 20 with a
+    refinement step), eager and replayed."""
+    P = make_problem("seismic2d")
+    K = 80 if n_refine == 0 else 20
+    out = []
+    for flags in (0, G._lib.SGKS_FLAG_BW_HOST):
+        kw = G.device_inputs(P, "fp64")
+        kw["n_refine"] = n_refine
+        kw["max_iters"] = K
+        S = G.Solver(**kw, record=True, flags=flags)
+        S.solve(K)
+        x = S.x()
+        xt = torch.from_numpy(np.asarray(P.x_true)).to(x.device, x.dtype)
+        xbar = (2.0 * (x - xt)).contiguous()
+        r1 = S.backward(xbar)
+        r2 = S.backward(xbar)
+        r3 = S.backward(xbar)   # replayed from the captured graph
+        S.close()
+        for r in (r2, r3):
+            assert torch.equal(r[0], r1[0]) and r[1] == r1[1]
+        out.append((r1[0].cpu().numpy(), r1[1]))
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
+def test_backward_host_flag_needs_record(G):
+    P = small_problem("seismic2d", iters=4)
+    with pytest.raises(G._lib.SGKSError) as ei:
+        G.Solver(**G.device_inputs(P, "fp64"), flags=G._lib.SGKS_FLAG_BW_HOST)
+    assert ei.value.code == G._lib.SGKS_ERR_INVALID

@@ -465,3 +465,28 @@ def test_full_size_dynct_batch_fp32(G, tmp_path):
         parity_log.record(f"full_size_dynct_batch_fp32[{i}]", e, fl, TOL32, FACTOR32)
         bad = [(k, v, fl[k]) for k, v in enumerate(e) if v > max(TOL32, FACTOR32 * fl[k])]
         assert not bad, f"instance {i} ({frames[i]} frames): {bad[:4]}"
+
+
+@pytest.mark.parametrize("prec", ["ff", "fp32"])
+def test_batch_tiled_and_row_forward_passes_agree(G, prec):
+    """A w through pixel tiles (partials per ray and tile, summed in entry order) and through the
+    CSR-row kernel (SGKS_FLAG_NO_TILES): both match the oracle, on CT instances and on the
+    space-time operator of two frames (tiles per frame), and the tiled solve is reproducible."""
+    probs = ct_instances(4, iters=12) + []
+    Bt, xs = batch_iterates(G, probs, prec, probs[0].iters)
+    Bt.close()
+    Bn, xn = batch_iterates(G, probs, prec, probs[0].iters, tiles=False)
+    Bn.close()
+    for P, a, b in zip(probs, xs, xn):
+        check_instance(a, P, prec)
+        check_instance(b, P, prec)
+    B2, x2 = batch_iterates(G, probs, prec, probs[0].iters)
+    B2.close()
+    for a, b in zip(xs, x2):
+        assert np.array_equal(a[-1], b[-1])
+    dyn = [small_problem("dynct", frames=2, seed=i, iters=10) for i in range(2)]
+    share_operators(dyn, s=100)
+    Bd, xd = batch_iterates(G, dyn, prec, dyn[0].iters)
+    Bd.close()
+    for P, a in zip(dyn, xd):
+        check_instance(a, P, prec)

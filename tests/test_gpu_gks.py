@@ -80,13 +80,10 @@ def test_gks_graph_replay_equals_steps(G):
 def test_gks_rejects_unsupported_options(G):
     P = small_problem("seismic2d")
     kw = G.device_inputs(P, "fp64")
-    for bad in (dict(n_refine=1), dict(record=True), dict(precision="fp32x")):
+    for bad in (dict(n_refine=1), dict(record=True), dict(precision="ff")):
         k2 = dict(kw)
         k2["n_refine"] = 0
         k2.update(bad)
-        if bad.get("precision") == "fp32x":
-            k2["b"] = kw["b"].float()
-            k2["x_true"] = kw["x_true"].float()
         with pytest.raises(G._lib.SGKSError) as ei:
             G.Solver(**k2, method="gks")
         assert ei.value.code == G._lib.SGKS_ERR_INVALID

@@ -89,6 +89,48 @@ def test_noalloc_transpose_matches_allocating_one_twice_in_a_row(lib):
         assert np.array_equal(g, w)
 
 
+def test_noalloc_transpose_leaves_device_memory_unchanged(lib):
+    """After a warm-up call (which may make the library's module resident on the device), a second
+    call changes neither the device's free memory nor torch's allocator state: nothing is
+    allocated, not even temporarily from a pool that would keep it reserved."""
+    from paper_2606_18073_gb300 import _lib as L
+    m, n = 20000, 30000
+    rp, ci, val = _random_csr(m, n, 30, torch.float32, seed=5)
+    _transpose(lib, "sgks_csr_transpose_noalloc", m, n, rp, ci, val)          # warm-up
+    out = [torch.empty(n + 1, dtype=torch.int32, device="cuda"), torch.empty_like(ci), torch.empty_like(val)]
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    st = torch.cuda.current_stream().cuda_stream
+    rc = lib.sgks_csr_transpose_noalloc(m, n, int(ci.numel()), _p(rp), _p(ci), _p(val), L.SGKS_F32, _p(out[0]),
+                                        _p(out[1]), _p(out[2]), C.c_void_p(st))
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+
+
+@pytest.mark.parametrize("fn", ["sgks_csr_transpose", "sgks_csr_transpose_noalloc"])
+def test_transposes_reject_a_column_outside_the_matrix(lib, fn):
+    """A column index outside [0, n) is skipped by the kernels' bounds checks and reported."""
+    from paper_2606_18073_gb300 import _lib as L
+    m, n = 500, 400
+    rp, ci, val = _random_csr(m, n, 6, torch.float64, seed=9)
+    orig = int(ci[7])
+    ci[7] = n + 3
+    trp = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    tci, tv = torch.zeros_like(ci), torch.zeros_like(val)
+    st = torch.cuda.current_stream().cuda_stream
+    rc = getattr(lib, fn)(m, n, int(ci.numel()), _p(rp), _p(ci), _p(val), L.SGKS_F64, _p(trp), _p(tci), _p(tv),
+                          C.c_void_p(st))
+    assert rc == L.SGKS_ERR_INVALID
+    assert b"outside" in lib.sgks_last_error(None)
+    ci[7] = orig   # the flag does not outlive the call: the valid matrix transposes cleanly
+    rc = getattr(lib, fn)(m, n, int(ci.numel()), _p(rp), _p(ci), _p(val), L.SGKS_F64, _p(trp), _p(tci), _p(tv),
+                          C.c_void_p(st))
+    assert rc == 0
+
+
 def test_noalloc_transpose_rejects_sizes_beyond_its_scratch(lib):
     from paper_2606_18073_gb300 import _lib as L
     n = 65536
