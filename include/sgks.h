@@ -139,7 +139,8 @@ typedef struct sgks_options {
                              1024; sgks_solve's tol applies the relative-change test of eq. RC.
                              bit 3 (SGKS_FLAG_AUTOTUNE, batches only): after the setup, time the
                              candidate tile choices of each group on its own data and keep the
-                             fastest (bulk-copy slice 8 or 16 KB; lanes per CSR row of A and A^T);
+                             fastest (bulk-copy slice 8 or 16 KB; lanes per CSR row of A and A^T),
+                             a candidate replacing the default only when at least 5% faster;
                              results are cached per shape for the process.  Without it the
                              defaults are used (16 KB, 8, 8) and results are reproducible.
                              bit 4 (SGKS_FLAG_NO_TILES, batches only): the compensated forms

@@ -71,9 +71,11 @@ __device__ __forceinline__ void combine_finish(const BDims& D, bool has_xt, cons
             t2 += __ldcg(pp + 2);
         }
         __syncthreads();
-        red[0][threadIdx.x] = t0;
-        red[1][threadIdx.x] = t1;
-        red[2][threadIdx.x] = t2;
+        if (threadIdx.x < kThreads) {   // a block may carry extra (producer) threads
+            red[0][threadIdx.x] = t0;
+            red[1][threadIdx.x] = t1;
+            red[2][threadIdx.x] = t2;
+        }
         __syncthreads();
         for (int h = SUB / 2; h > 0; h >>= 1) {
             if (u < h)

@@ -25,8 +25,6 @@
 
 namespace sgks {
 
-constexpr int kYStageX = 4096;   // y values (as hi and lo planes) staged per chunk in the combine
-
 __device__ __forceinline__ float2 ff_zero() { return make_float2(0.f, 0.f); }
 __device__ __forceinline__ float2 ff_neg(float2 v) { return make_float2(-v.x, -v.y); }
 
@@ -330,163 +328,202 @@ __global__ void __launch_bounds__(kThreads) kbx_sketch_gather(BDims D, BBulkX<TW
 }
 
 // ------------------------------------------------------------------- a5 + a6: combine
-// x_i = W_i y_i and e_i = (A W_i) y_i - b_i with Dot2 (y_i split into float-float in shared
-// memory).  The bulk-copy ring of kb_combine_tma: tiles of one SB-byte slice per column stream
-// through NS stages filled by cp.async.bulk from one thread, one mbarrier per stage, every wait
-// bounded (a timeout stops every instance of the group with ST_TIMEOUT).  x tiles hold SB /
-// sizeof(TW) values per column slice, e tiles SB / 8 (A W is float-float).  Thread t owns slice
-// positions t + kThreads r.  mode 1 also forms ||x_k - x_{k-1}||^2, ||x_{k-1}||^2 and
-// ||x_k - x_true||^2 per instance (eq. RC, RRE) from the leading parts, in FP32 per element.
+// x_i = W_i y_i and e_i = (A W_i) y_i - b_i with Dot2, y_i as float-float pairs laid out [j][B]
+// (kbx_split_y).  The items of a CTA are (tile, column) pairs: one SB-byte slice of one column
+// of W (x tiles, SB / sizeof(TW) values) or of A W (e tiles, SB / 8 values), streamed through an
+// NS-stage ring filled by cp.async.bulk.  Stage s has two mbarriers: full[s] (the copy landed)
+// and empty[s] (every consumer warp has read it; one arrival per warp).  kCombConsumers threads
+// (8 warps) consume; one extra warp produces: its first thread refills stage s with item k as
+// soon as item k - NS has been released, so the ring never waits on a consumer's epilogue and
+// no CTA-wide barrier sits in the column loop.  Every wait is bounded: a wait that gives up sets
+// a shared flag, every thread leaves its loop, the producer waits for its copies in flight and
+// stops every instance of the group with ST_TIMEOUT.  Consumer thread t owns slice positions
+// t + kThreads r.  mode 1 also forms ||x_k - x_{k-1}||^2, ||x_{k-1}||^2 and ||x_k - x_true||^2
+// per instance (eq. RC, RRE) from the leading parts, in FP32 per element.
+constexpr int kCombThreads = kThreads + 32;   // kThreads consumers + one producer warp
+
 template <typename TW, int NS, int SB>
-__global__ void __launch_bounds__(kThreads) kbx_combine_tma(BDims D, BBulkX<TW> X, BSmall S, int mode) {
+__global__ void __launch_bounds__(kCombThreads, 3) kbx_combine_tma(BDims D, BBulkX<TW> X, BSmall S, int mode) {
     constexpr int kSX = SB / (int)sizeof(TW);   // values per x slice
     constexpr int kSE = SB / 8;                  // values per e slice
-    constexpr int RPX = kSX / kThreads, RPE = kSE / kThreads;
+    constexpr int RPX = kSX / kThreads, RPE = kSE / kThreads, RPM = RPX > RPE ? RPX : RPE;
+    constexpr int EC = 2;                        // epilogue loads issued together
+    static_assert(RPM % EC == 0, "epilogue chunks");
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char* stg = smem_raw;                                       // [NS][SB]
-    float* yh = reinterpret_cast<float*>(smem_raw + (size_t)NS * SB);    // [kYStageX]
-    float* yl = yh + kYStageX;                                           // [kYStageX]
+    unsigned char* stg = smem_raw;   // [NS][SB]
     __shared__ __align__(8) uint64_t full[NS];
-    __shared__ int sd[kMaxBatch];
-    __shared__ int s_dlive;
+    __shared__ __align__(8) uint64_t empty[NS];
+    __shared__ int s_dlive, s_err;
     __shared__ double red[3][kThreads];
     __shared__ int am_last;
     const int B = D.B, G = kThreads / B;
-    const int t = threadIdx.x, b = t & (B - 1), g = t / B;
-    const int JC = kYStageX / B;
+    const int t = threadIdx.x, b = t & (B - 1), g = t / B, lane = t & 31;
     if (t == 0) {
         int mx = 0;
         for (int i = 0; i < B; ++i) {
             const int di = S.sc[i].stop ? 0 : S.sc[i].d;
-            sd[i] = di;
             mx = di > mx ? di : mx;
         }
         s_dlive = mx;
-        for (int q = 0; q < NS; ++q) mbar_init(&full[q], 1);
+        s_err = 0;
+        for (int q = 0; q < NS; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], kWarps);
+        }
         fence_mbar_init();
     }
     __syncthreads();
-    const int db = sd[b], dlive = s_dlive;
-    const bool live = !S.sc[b].stop;
+    const int dlive = s_dlive;
     const int TRX = kSX / B, TRE = kSE / B;
     const int64_t ntx = (D.n + TRX - 1) / TRX, nte = (D.m + TRE - 1) / TRE;
     const int64_t ntiles = ntx + nte;
     const int my_tiles = ntiles > blockIdx.x ? (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x) : 0;
     const int nitems = my_tiles * dlive;
-    auto item = [&](int k, uint32_t* bytes) -> const void* {
-        const int64_t tile = blockIdx.x + (int64_t)(k / dlive) * gridDim.x;
-        const int j = k % dlive;
-        if (tile < ntx) {
-            const int64_t r0 = tile * TRX;
-            const int64_t vrows = min((int64_t)TRX, D.n - r0);
-            *bytes = (uint32_t)(((size_t)vrows * B * sizeof(TW) + 15) & ~(size_t)15);
-            return X.W + ((size_t)j * D.n + r0) * B;
-        }
-        const int64_t r0 = (tile - ntx) * TRE;
-        const int64_t vrows = min((int64_t)TRE, D.m - r0);
-        *bytes = (uint32_t)(((size_t)vrows * B * 8 + 15) & ~(size_t)15);
-        return X.AW + ((size_t)j * D.m + r0) * B;
-    };
-    if (t == 0) {
-        const int pre = min(NS, nitems);
-        for (int q = 0; q < pre; ++q) {
-            uint32_t bytes;
-            const void* src = item(q, &bytes);
-            mbar_expect_tx(&full[q], bytes);
-            bulk_g2s(stg + (size_t)q * SB, src, bytes, &full[q]);
-        }
-    }
+    volatile int* err_flag = &s_err;
     float q0 = 0.f, q1 = 0.f, q2 = 0.f;
-    Dot2 acc[RPX];
-    float2 pa[RPX];   // x tile: x_{k-1}; e tile: b
-    float2 pb[RPX];   // x tile: x_true
-    int err = 0, k = 0;
-    bool isx = true;
-    int64_t row0 = 0;
-    int nv = 0;
-    for (; k < nitems; ++k) {
-        const int j = k % dlive;
-        if (j == 0) {
-            const int64_t tile = blockIdx.x + (int64_t)(k / dlive) * gridDim.x;
-            isx = tile < ntx;
-            const int64_t rows = isx ? D.n : D.m;
-            row0 = (isx ? tile * TRX : (tile - ntx) * TRE) + g;
-            const int rp = isx ? RPX : RPE;
-            nv = row0 < rows ? (int)min((int64_t)rp, (rows - row0 + G - 1) / G) : 0;
-            const size_t o0 = (size_t)row0 * B + b;
-#pragma unroll
-            for (int r = 0; r < RPX; ++r) {
-                acc[r] = Dot2{};
-                const size_t o = o0 + (size_t)kThreads * r;
-                const bool in = live && r < nv;
-                pa[r] = in && isx && mode >= 1 ? X.xs[o] : (in && !isx ? X.b[o] : ff_zero());
-                pb[r] = in && isx && mode >= 1 && X.xtrue ? X.xtrue[o] : ff_zero();
-            }
-        }
-        if (j % JC == 0 && (k == 0 || dlive > JC)) {   // y chunk [j, j + JC) as [jj][B], split
-            __syncthreads();
-            for (int q = t; q < JC * B; q += kThreads) {
-                const int jj = q / B, i = q & (B - 1), jg = j + jj;
-                const float2 yv = jg < sd[i] ? X.y2[(size_t)i * D.dmax + jg] : ff_zero();
-                yh[q] = yv.x;
-                yl[q] = yv.y;
-            }
-            __syncthreads();
-        }
-        const int st = k % NS;
-        const bool ok = mbar_wait_n(&full[st], (k / NS) & 1, D.wait_tries);
-        if (ok && j < db) {
-            const float h = yh[(j % JC) * B + b], l = yl[(j % JC) * B + b];
-            if (isx) {
-                const TW* sl = reinterpret_cast<const TW*>(stg + (size_t)st * SB) + t;
-#pragma unroll
-                for (int r = 0; r < RPX; ++r)
-                    if (r < nv) acc_wy(acc[r], sl[kThreads * r], h, l);
-            } else {
-                const float2* sl = reinterpret_cast<const float2*>(stg + (size_t)st * SB) + t;
-#pragma unroll
-                for (int r = 0; r < RPE; ++r)
-                    if (r < nv) acc_wy(acc[r], sl[kThreads * r], h, l);
-            }
-        }
-        err = __syncthreads_or(!ok);   // every reader of stage st is done; err is uniform
-        if (err) break;
-        if (t == 0 && k + NS < nitems) {
-            uint32_t bytes;
-            const void* src = item(k + NS, &bytes);
-            fence_proxy_async();
-            mbar_expect_tx(&full[st], bytes);
-            bulk_g2s(stg + (size_t)st * SB, src, bytes, &full[st]);
-        }
-        if (j != dlive - 1 || !live) continue;
-#pragma unroll
-        for (int r = 0; r < RPX; ++r) {
-            if (r >= nv) continue;
-            const size_t o = (size_t)row0 * B + b + (size_t)kThreads * r;
-            if (isx) {
-                const float2 xv = acc[r].value();
-                X.x[o] = xv;
-                if (mode >= 1) {
-                    const float2 old = pa[r];
-                    const float df = (xv.x - old.x) + (xv.y - old.y);
-                    q0 += df * df;
-                    q1 += old.x * old.x;
-                    if (X.xtrue) {
-                        const float er = (xv.x - pb[r].x) + (xv.y - pb[r].y);
-                        q2 += er * er;
-                    }
-                    X.xs[o] = xv;
+    int issued = 0;   // producer: items whose copies were started
+    if (t >= kThreads) {
+        // ------------------------------------------------------------ producer warp
+        if (t == kThreads) {
+            int st = 0, tl = 0, j = 0;
+            uint32_t ph = 0;
+            for (; issued < nitems; ++issued) {
+                if (issued >= NS && !mbar_wait_n(&empty[st], ph ^ 1u, D.wait_tries)) {
+                    *err_flag = 1;
+                    break;
                 }
-            } else {
-                acc[r].add2(-pa[r].x, -pa[r].y);
-                X.e[o] = acc[r].value();
+                if (*err_flag) break;
+                const int64_t tile = blockIdx.x + (int64_t)tl * gridDim.x;
+                const void* src;
+                uint32_t bytes;
+                if (tile < ntx) {
+                    const int64_t r0 = tile * TRX;
+                    const int64_t vrows = min((int64_t)TRX, D.n - r0);
+                    bytes = (uint32_t)(((size_t)vrows * B * sizeof(TW) + 15) & ~(size_t)15);
+                    src = X.W + ((size_t)j * D.n + r0) * B;
+                } else {
+                    const int64_t r0 = (tile - ntx) * TRE;
+                    const int64_t vrows = min((int64_t)TRE, D.m - r0);
+                    bytes = (uint32_t)(((size_t)vrows * B * 8 + 15) & ~(size_t)15);
+                    src = X.AW + ((size_t)j * D.m + r0) * B;
+                }
+                fence_proxy_async();
+                mbar_expect_tx(&full[st], bytes);
+                bulk_g2s(stg + (size_t)st * SB, src, bytes, &full[st]);
+                if (++j == dlive) {
+                    j = 0;
+                    ++tl;
+                }
+                if (++st == NS) {
+                    st = 0;
+                    ph ^= 1u;
+                }
+            }
+        }
+    } else {
+        // ---------------------------------------------------------- consumer warps
+        const bool live = !S.sc[b].stop;
+        const int db = live ? S.sc[b].d : 0;
+        Dot2 acc[RPM];
+        bool isx = true;
+        int64_t row0 = 0;
+        int nv = 0, tl = 0, j = 0, st = 0;
+        uint32_t ph = 0;
+        // y of the next item is loaded one item ahead, so its latency hides behind the current one
+        float2 ynext = nitems > 0 && 0 < db ? __ldg(X.y2 + b) : ff_zero();
+        for (int k = 0; k < nitems; ++k) {
+            if (j == 0) {
+                const int64_t tile = blockIdx.x + (int64_t)tl * gridDim.x;
+                isx = tile < ntx;
+                const int64_t rows = isx ? D.n : D.m;
+                row0 = (isx ? tile * TRX : (tile - ntx) * TRE) + g;
+                const int rp = isx ? RPX : RPE;
+                nv = row0 < rows ? (int)min((int64_t)rp, (rows - row0 + G - 1) / G) : 0;
+#pragma unroll
+                for (int r = 0; r < RPM; ++r) acc[r] = Dot2{};
+            }
+            const bool use = j < db;
+            const float2 yv = ynext;
+            {
+                const int jn = j + 1 == dlive ? 0 : j + 1;
+                ynext = k + 1 < nitems && jn < db ? __ldg(X.y2 + (size_t)jn * B + b) : ff_zero();
+            }
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_n(&full[st], ph, D.wait_tries));
+            if (!ok) *err_flag = 1;
+            if (ok && use) {
+                if (isx) {
+                    const TW* sl = reinterpret_cast<const TW*>(stg + (size_t)st * SB) + t;
+#pragma unroll
+                    for (int r = 0; r < RPX; ++r)
+                        if (r < nv) acc_wy(acc[r], sl[kThreads * r], yv.x, yv.y);
+                } else {
+                    const float2* sl = reinterpret_cast<const float2*>(stg + (size_t)st * SB) + t;
+#pragma unroll
+                    for (int r = 0; r < RPE; ++r)
+                        if (r < nv) acc_wy(acc[r], sl[kThreads * r], yv.x, yv.y);
+                }
+            }
+            __syncwarp();
+            if (lane == 0 && ok) mbar_arrive(&empty[st]);
+            if (__any_sync(0xffffffffu, *err_flag != 0)) break;   // warp-uniform exit
+            if (j == dlive - 1 && live) {
+                // epilogue: EC loads issued together, then the stores
+#pragma unroll
+                for (int r0 = 0; r0 < RPM; r0 += EC) {
+                    float2 l0[EC], l1[EC];
+#pragma unroll
+                    for (int c = 0; c < EC; ++c) {
+                        const int r = r0 + c;
+                        const size_t o = (size_t)row0 * B + b + (size_t)kThreads * r;
+                        l0[c] = l1[c] = ff_zero();
+                        if (r < nv) {
+                            if (!isx) l0[c] = X.b[o];
+                            else if (mode >= 1) {
+                                l0[c] = X.xs[o];
+                                if (X.xtrue) l1[c] = X.xtrue[o];
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < EC; ++c) {
+                        const int r = r0 + c;
+                        if (r >= nv) continue;
+                        const size_t o = (size_t)row0 * B + b + (size_t)kThreads * r;
+                        if (isx) {
+                            const float2 xv = acc[r].value();
+                            X.x[o] = xv;
+                            if (mode >= 1) {
+                                const float2 old = l0[c];
+                                const float df = (xv.x - old.x) + (xv.y - old.y);
+                                q0 += df * df;
+                                q1 += old.x * old.x;
+                                if (X.xtrue) {
+                                    const float er = (xv.x - l1[c].x) + (xv.y - l1[c].y);
+                                    q2 += er * er;
+                                }
+                                X.xs[o] = xv;
+                            }
+                        } else {
+                            acc[r].add2(-l0[c].x, -l0[c].y);
+                            X.e[o] = acc[r].value();
+                        }
+                    }
+                }
+            }
+            if (++j == dlive) {
+                j = 0;
+                ++tl;
+            }
+            if (++st == NS) {
+                st = 0;
+                ph ^= 1u;
             }
         }
     }
-    if (err) {
-        if (t == 0) {
-            const int last = min(nitems, k + NS);
-            for (int q = k; q < last; ++q) mbar_wait(&full[q % NS], (q / NS) & 1);
+    __syncthreads();
+    if (s_err) {   // every consumer has left its loop: wait for the copies in flight, then stop
+        if (t == kThreads) {
+            for (int q = max(0, issued - NS); q < issued; ++q) mbar_wait(&full[q % NS], (uint32_t)(q / NS) & 1u);
             for (int i = 0; i < B; ++i) {
                 S.sc[i].status = ST_TIMEOUT;
                 S.sc[i].stop = 1;
@@ -495,11 +532,13 @@ __global__ void __launch_bounds__(kThreads) kbx_combine_tma(BDims D, BBulkX<TW> 
         return;
     }
     if (mode == 0) return;
-    red[0][t] = (double)q0;
-    red[1][t] = (double)q1;
-    red[2][t] = (double)q2;
+    if (t < kThreads) {
+        red[0][t] = (double)q0;
+        red[1][t] = (double)q1;
+        red[2][t] = (double)q2;
+    }
     __syncthreads();
-    for (int h = G / 2; h > 0; h >>= 1) {
+    for (int h = G / 2; h > 0; h >>= 1) {   // the producer warp has g >= G and takes no part
         if (g < h)
             for (int q = 0; q < 3; ++q) red[q][t] += red[q][t + h * B];
         __syncthreads();
@@ -526,14 +565,14 @@ __global__ void __launch_bounds__(kThreads) kbx_combine(BDims D, BBulkX<TW> X, B
     const DevScalars& sc = S.sc[b];
     const bool live = !sc.stop;
     const int d = live ? sc.d : 0;
-    const float2* y = X.y2 + (size_t)b * D.dmax;
+    const float2* y = X.y2 + b;   // y2[j * B + b]
     float q0 = 0.f, q1 = 0.f, q2 = 0.f;
     const int64_t tot = (D.n + D.m) * B;
     for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < tot && live; t += gstride()) {
         Dot2 a;
         if (t < D.n * B) {
             for (int j = 0; j < d; ++j) {
-                const float2 yv = y[j];
+                const float2 yv = y[(size_t)j * B];
                 acc_wy(a, X.W[(size_t)j * D.n * B + t], yv.x, yv.y);
             }
             const float2 xv = a.value();
@@ -552,7 +591,7 @@ __global__ void __launch_bounds__(kThreads) kbx_combine(BDims D, BBulkX<TW> X, B
         } else {
             const int64_t te = t - D.n * B;
             for (int j = 0; j < d; ++j) {
-                const float2 yv = y[j];
+                const float2 yv = y[(size_t)j * B];
                 acc_wy(a, X.AW[(size_t)j * D.m * B + te], yv.x, yv.y);
             }
             a.add2(-X.b[te].x, -X.b[te].y);
@@ -763,9 +802,14 @@ __global__ void __launch_bounds__(kThreads, 2) kbx_wtr(BDims D, BBulkX<TW> X, BS
 }
 
 // ------------------------------------------------------------------------ conversions
-// y_i (FP64, from the small phase) split into float-float once per combine
-__global__ void kbx_split_y(const double* __restrict__ y, float2* __restrict__ y2, int len) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < len; t += gridDim.x * blockDim.x) y2[t] = dsplit(y[t]);
+// y_i (FP64 from the small phase, y[i * dmax + j]) split into float-float once per combine and
+// transposed to y2[j * B + i], so that the B threads of one column read consecutive pairs
+__global__ void kbx_split_y(const double* __restrict__ y, float2* __restrict__ y2, int B, int dmax) {
+    const int len = B * dmax;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < len; t += gridDim.x * blockDim.x) {
+        const int j = t / B, i = t - j * B;
+        y2[t] = dsplit(y[(size_t)i * dmax + j]);
+    }
 }
 
 __global__ void kbx_gather_in(PtrPack P, int in_dt, float2* __restrict__ out, int64_t len, int B) {
@@ -853,14 +897,28 @@ static int xcomb_stages(int slice_kb) { return slice_kb == 8 ? 6 : 4; }
 
 size_t batchx_combine_smem(size_t welem, int slice_kb) {
     (void)welem;
-    return (size_t)xcomb_stages(slice_kb) * slice_kb * 1024 + (size_t)2 * kYStageX * sizeof(float);
+    return (size_t)xcomb_stages(slice_kb) * slice_kb * 1024;
+}
+
+// resident CTAs of the bulk-copy combine per SM (registers and shared memory), from the runtime
+template <typename TW>
+static int xcomb_per_sm(int slice_kb) {
+    auto k = slice_kb == 8 ? kbx_combine_tma<TW, 6, 8192> : kbx_combine_tma<TW, 4, 16384>;
+    const size_t smem = batchx_combine_smem(sizeof(TW), slice_kb);
+    int nb = 0;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kCombThreads, smem) != cudaSuccess || nb < 1) {
+        (void)cudaGetLastError();
+        nb = 1;
+    }
+    return nb;
 }
 
 int batchx_combine_grid(const BDims& D, size_t welem) {
     if (D.tma) {
         const int64_t TRX = (int64_t)(D.slice_kb * 1024 / welem) / D.B, TRE = (int64_t)(D.slice_kb * 1024 / 8) / D.B;
         const int64_t tiles = (D.n + TRX - 1) / TRX + (D.m + TRE - 1) / TRE;
-        const int per_sm = (int)std::max<size_t>(1, (227 * 1024) / (batchx_combine_smem(welem, D.slice_kb) + 8192));
+        const int per_sm = welem == 4 ? xcomb_per_sm<float>(D.slice_kb) : xcomb_per_sm<float2>(D.slice_kb);
         return (int)std::min<int64_t>(tiles, 152 * per_sm);
     }
     return xgrid((D.n + D.m) * D.B);
@@ -869,7 +927,7 @@ int batchx_combine_grid(const BDims& D, size_t welem) {
 template <typename TW>
 cudaError_t launchbx_combine(const BDims& D, const BBulkX<TW>& X, const BSmall& S, int mode, cudaStream_t st) {
     const int ylen = D.B * D.dmax;
-    kbx_split_y<<<(ylen + kThreads - 1) / kThreads, kThreads, 0, st>>>(S.y, X.y2, ylen);
+    kbx_split_y<<<(ylen + kThreads - 1) / kThreads, kThreads, 0, st>>>(S.y, X.y2, D.B, D.dmax);
     cudaError_t e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;
     if (D.tma) {
@@ -877,7 +935,7 @@ cudaError_t launchbx_combine(const BDims& D, const BBulkX<TW>& X, const BSmall& 
         auto k = D.slice_kb == 8 ? kbx_combine_tma<TW, 6, 8192> : kbx_combine_tma<TW, 4, 16384>;
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k<<<D.nb_combine, kThreads, smem, st>>>(D, X, S, mode);
+        k<<<D.nb_combine, kCombThreads, smem, st>>>(D, X, S, mode);
         return cudaGetLastError();
     }
     kbx_combine<TW><<<D.nb_combine, kThreads, 0, st>>>(D, X, S, mode);

@@ -76,6 +76,13 @@ struct TuneVal {
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
 
+// A candidate replaces the default only when it is at least 5% faster: candidates within
+// timing noise of each other (or timings inflated by a profiler's per-launch overhead) keep
+// the default, so the choice is stable from run to run.
+int tune_pick(float best, int pick, float t_def, int def) {
+    return (t_def > 0.f && best < 0.95f * t_def) ? pick : def;
+}
+
 // one launcher call: counted, and timed with an event pair when profiling
 template <typename F>
 cudaError_t run_timed(GroupBase* g, int cls, int nl, F&& f) {
@@ -219,23 +226,26 @@ struct Group : GroupBase {
         };
         std::string log;
         if (D.tma) {
-            float best = 1e30f;
+            float best = 1e30f, t_def = 0.f;
             int pick = D.slice_kb;
+            const int def = D.slice_kb;
             for (int kb : {16, 8}) {
                 D.slice_kb = kb;
                 D.nb_combine = batch_combine_grid(D, sizeof(T));
                 const float t = time_it([&] { return launchb_combine<T>(D, X, S, 0, st); });
                 log += " combine/" + std::to_string(kb) + "KB=" + std::to_string(t);
+                if (kb == def) t_def = t;
                 if (t < best) { best = t; pick = kb; }
             }
-            D.slice_kb = pick;
+            D.slice_kb = tune_pick(best, pick, t_def, def);
             D.nb_combine = batch_combine_grid(D, sizeof(T));
         }
         if (A.kind == SGKS_OP_CSR) {
             for (int which = 0; which < 2; ++which) {
                 int* field = which == 0 ? &D.nl_a : &D.nl_t;
-                float best = 1e30f;
+                float best = 1e30f, t_def = 0.f;
                 int pick = *field;
+                const int def = *field;
                 for (int nl : {1, 2, 4, 8, 16, 32}) {
                     *field = nl;
                     const float t = time_it([&] {
@@ -243,9 +253,10 @@ struct Group : GroupBase {
                                           : launchb_gradient<T, V>(D, A, L, X, S, nullptr, st);
                     });
                     log += std::string(which == 0 ? " A/" : " At/") + std::to_string(nl) + "=" + std::to_string(t);
+                    if (nl == def) t_def = t;
                     if (t < best) { best = t; pick = nl; }
                 }
-                *field = pick;
+                *field = tune_pick(best, pick, t_def, def);
             }
         }
         cudaEventDestroy(e0);
@@ -398,23 +409,26 @@ struct GroupX : GroupBase {
         };
         std::string log;
         if (D.tma) {
-            float best = 1e30f;
+            float best = 1e30f, t_def = 0.f;
             int pick = D.slice_kb;
+            const int def = D.slice_kb;
             for (int kb : {16, 8}) {
                 D.slice_kb = kb;
                 D.nb_combine = batchx_combine_grid(D, sizeof(TW));
                 const float t = time_it([&] { return launchbx_combine<TW>(D, X, S, 0, st); });
                 log += " combine/" + std::to_string(kb) + "KB=" + std::to_string(t);
+                if (kb == def) t_def = t;
                 if (t < best) { best = t; pick = kb; }
             }
-            D.slice_kb = pick;
+            D.slice_kb = tune_pick(best, pick, t_def, def);
             D.nb_combine = batchx_combine_grid(D, sizeof(TW));
         }
         if (A.kind == SGKS_OP_CSR) {
             for (int which = T.ntiles ? 1 : 0; which < 2; ++which) {   // tiled: A w has no lanes to tune
                 int* field = which == 0 ? &D.nl_a : &D.nl_t;
-                float best = 1e30f;
+                float best = 1e30f, t_def = 0.f;
                 int pick = *field;
+                const int def = *field;
                 for (int nl : {1, 2, 4, 8, 16, 32}) {
                     *field = nl;
                     // the gradient is appended as column d, which the next step rewrites from
@@ -424,9 +438,10 @@ struct GroupX : GroupBase {
                                           : launchbx_gradient<TW>(D, A, L, X, S, nullptr, st);
                     });
                     log += std::string(which == 0 ? " A/" : " At/") + std::to_string(nl) + "=" + std::to_string(t);
+                    if (nl == def) t_def = t;
                     if (t < best) { best = t; pick = nl; }
                 }
-                *field = pick;
+                *field = tune_pick(best, pick, t_def, def);
             }
         }
         cudaEventDestroy(e0);

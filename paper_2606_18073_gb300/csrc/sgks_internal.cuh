@@ -117,6 +117,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 
+// one arrival (release at CTA scope) on a barrier counting thread arrivals
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -887,7 +892,7 @@ struct BBulkX {
     float2* tp;               // [p][B] L w of the newest column
     float2* r;                // [n][B] gradient r(y) inside the refinement
     const float2* lam2;       // [B] lambda_i split into (hi, lo)
-    float2* y2;               // [B][dmax] y_i split into (hi, lo) for the combine
+    float2* y2;               // [dmax][B] y_i split into (hi, lo) for the combine: y2[j * B + i]
 };
 
 struct BSmall {
