@@ -113,17 +113,19 @@ __global__ void __launch_bounds__(kThreads) kbx_seg_reduce(BDims D, TiledA T, BB
     }
 }
 
-int tile_instances(int B, size_t welem) { return std::min(B, welem == 4 ? 32 : 16); }
+int tile_instances(const BDims& D, size_t welem) {
+    return std::min(D.B, D.tile_ic > 0 ? D.tile_ic : (welem == 4 ? 32 : 16));
+}
 
-size_t tile_smem(const TiledA& T, int B, size_t welem) {
-    return (size_t)T.TX * T.TY * tile_instances(B, welem) * welem;
+size_t tile_smem(const TiledA& T, const BDims& D, size_t welem) {
+    return (size_t)T.TX * T.TY * tile_instances(D, welem) * welem;
 }
 
 template <typename TW, int VV>
 static cudaError_t tile_apply_vv(const BDims& D, const TiledA& T, const BBulkX<TW>& X, const BSmall& S, float2* part,
                                  cudaStream_t st) {
-    const int IC = tile_instances(D.B, sizeof(TW));
-    const size_t smem = tile_smem(T, D.B, sizeof(TW));
+    const int IC = tile_instances(D, sizeof(TW));
+    const size_t smem = tile_smem(T, D, sizeof(TW));
     auto k = kbx_tile_apply<TW, VV>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -138,7 +140,7 @@ template <typename TW>
 cudaError_t launchbx_tile_apply(const BDims& D, const TiledA& T, const BBulkX<TW>& X, const BSmall& S, float2* part,
                                 cudaStream_t st) {
     constexpr int VW = 16 / (int)sizeof(TW);
-    const int IC = tile_instances(D.B, sizeof(TW));
+    const int IC = tile_instances(D, sizeof(TW));
     cudaError_t e = IC >= VW ? tile_apply_vv<TW, VW>(D, T, X, S, part, st) : tile_apply_vv<TW, 1>(D, T, X, S, part, st);
     if (e != cudaSuccess) return e;
     int64_t rb = (D.m * D.B + kThreads - 1) / kThreads;

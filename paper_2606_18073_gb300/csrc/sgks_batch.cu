@@ -71,7 +71,7 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int slice_kb, nl_a, nl_t;
+    int slice_kb, nl_a, nl_t, tile_ic;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
@@ -202,6 +202,7 @@ struct Group : GroupBase {
                 D.slice_kb = it->second.slice_kb;
                 D.nl_a = it->second.nl_a;
                 D.nl_t = it->second.nl_t;
+                D.tile_ic = it->second.tile_ic;
                 D.nb_combine = batch_combine_grid(D, sizeof(T));
                 tuned = "cached";
                 return cudaSuccess;
@@ -265,7 +266,7 @@ struct Group : GroupBase {
         tuned = "slice " + std::to_string(D.slice_kb) + " KB, lanes/row A " + std::to_string(D.nl_a) + ", A^T " +
                 std::to_string(D.nl_t) + " (ms:" + log + ")";
         std::lock_guard<std::mutex> g(g_tune_mu);
-        g_tune_cache[key] = TuneVal{D.slice_kb, D.nl_a, D.nl_t};
+        g_tune_cache[key] = TuneVal{D.slice_kb, D.nl_a, D.nl_t, D.tile_ic};
         return cudaSuccess;
     }
 
@@ -385,6 +386,7 @@ struct GroupX : GroupBase {
                 D.slice_kb = it->second.slice_kb;
                 D.nl_a = it->second.nl_a;
                 D.nl_t = it->second.nl_t;
+                D.tile_ic = it->second.tile_ic;
                 D.nb_combine = batchx_combine_grid(D, sizeof(TW));
                 tuned = "cached";
                 return cudaSuccess;
@@ -423,6 +425,19 @@ struct GroupX : GroupBase {
             D.slice_kb = tune_pick(best, pick, t_def, def);
             D.nb_combine = batchx_combine_grid(D, sizeof(TW));
         }
+        if (T.ntiles) {   // instances per CTA of the tiled forward pass: the default or half of it
+            const int half = (sizeof(TW) == 4 ? 32 : 16) / 2;
+            float best = 1e30f, t_def = 0.f;
+            int pick = 0;
+            for (int ic : {0, half}) {
+                D.tile_ic = ic;
+                const float t = time_it([&] { return launchbx_tile_apply<TW>(D, T, X, S, part, st); });
+                log += " tile/" + std::to_string(ic ? ic : 2 * half) + "=" + std::to_string(t);
+                if (ic == 0) t_def = t;
+                if (t < best) { best = t; pick = ic; }
+            }
+            D.tile_ic = tune_pick(best, pick, t_def, 0);
+        }
         if (A.kind == SGKS_OP_CSR) {
             for (int which = T.ntiles ? 1 : 0; which < 2; ++which) {   // tiled: A w has no lanes to tune
                 int* field = which == 0 ? &D.nl_a : &D.nl_t;
@@ -448,9 +463,12 @@ struct GroupX : GroupBase {
         cudaEventDestroy(e1);
         if (e != cudaSuccess) return e;
         tuned = "slice " + std::to_string(D.slice_kb) + " KB, lanes/row A " + std::to_string(D.nl_a) + ", A^T " +
-                std::to_string(D.nl_t) + " (ms:" + log + ")";
+                std::to_string(D.nl_t) +
+                (T.ntiles ? ", tile instances " + std::to_string(D.tile_ic ? D.tile_ic : (sizeof(TW) == 4 ? 32 : 16))
+                          : std::string()) +
+                " (ms:" + log + ")";
         std::lock_guard<std::mutex> g(g_tune_mu);
-        g_tune_cache[key] = TuneVal{D.slice_kb, D.nl_a, D.nl_t};
+        g_tune_cache[key] = TuneVal{D.slice_kb, D.nl_a, D.nl_t, D.tile_ic};
         return cudaSuccess;
     }
 
@@ -571,6 +589,7 @@ int init_group(sgks_batch* h, GroupBase* G, const sgks_op* op, const DevL& L, in
     D.slice_kb = 16;
     D.nl_a = 8;
     D.nl_t = 8;
+    D.tile_ic = 0;
     D.nb_combine = comb_grid(D);
     // SGKS_TEST_TIMEOUT_GROUP=g (read at create) gives group g's bulk-copy combine a wait limit of
     // zero rounds: its first wait reports a timeout, the CTA drains its own copies with the full

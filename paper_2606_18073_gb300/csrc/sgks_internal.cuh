@@ -864,6 +864,8 @@ struct BDims {
     int nl_a, nl_t;           // CSR rows: lanes per row of A and of A^T (powers of two <= 32, tuned)
     int nb_refine;            // CTAs of kb_wtr (each leaves one partial per instance)
     int nb_setup;             // CTAs of the setup reductions
+    int tile_ic;              // tiled forward pass: instances per CTA (0: 32 for an FP32 basis, 16
+                              // for a float-float one; tuned)
     int wait_tries;           // bounded waits of the bulk-copy combine's ring (kWaitTries; 0 in the
                               // timeout test of SGKS_TEST_TIMEOUT_GROUP, see sgks_batch.cu)
     double sketch_scale;      // 1/sqrt(zeta)
@@ -957,7 +959,7 @@ struct TiledA {
 int build_tiles(const int32_t* d_rp, const int32_t* d_ci, const float* d_val, int64_t m, int64_t n, int64_t nnz,
                 int nx, int ny, int nt, int TX, int TY, TiledA& T, std::vector<void*>& allocs, cudaStream_t st,
                 std::string* why);
-size_t tile_smem(const TiledA& T, int B, size_t welem);
+size_t tile_smem(const TiledA& T, const BDims& D, size_t welem);
 // u_i = A w_i into column d_i of AW through the tiles (partials in part, nseg x B float-float)
 template <typename TW>
 cudaError_t launchbx_tile_apply(const BDims& D, const TiledA& T, const BBulkX<TW>& X, const BSmall& S, float2* part,
