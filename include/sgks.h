@@ -426,8 +426,9 @@ int sgks_batch_layout(sgks_batch* h, int32_t* group_of, int32_t* group_size);
  * launch timed with a CUDA event pair and synchronised: for measurement only).  Host arrays of
  * SGKS_BATCH_PROFILE_CLASSES entries receive the total milliseconds and the launch count per
  * kernel class: the classes of sgks_profile_steps, except that class 1 is the operator apply
- * alone and class 8 the sketch gather. */
-#define SGKS_BATCH_PROFILE_CLASSES 9
+ * alone (A w through pixel tiles: the tile pass and the per-ray sums), class 8 the sketch gather
+ * and class 9 the L w column when A w runs through pixel tiles (otherwise part of class 1). */
+#define SGKS_BATCH_PROFILE_CLASSES 10
 int sgks_batch_profile_steps(sgks_batch* h, int32_t iters, double* ms_out, int64_t* count_out);
 
 /* Description of the tile configuration of group `group` chosen by SGKS_FLAG_AUTOTUNE ("" when

@@ -117,9 +117,9 @@ SGKS_FLAG_GKS = 4
 SGKS_FLAG_AUTOTUNE = 8
 SGKS_FLAG_NO_TILES = 16
 SGKS_FLAG_BW_HOST = 32
-SGKS_BATCH_PROFILE_CLASSES = 9
+SGKS_BATCH_PROFILE_CLASSES = 10
 BATCH_PROFILE_CLASS_NAMES = ["gradient_append", "apply_column", "qr_append", "stacked_solve", "combine_refine",
-                             "gradient_refine", "refine_solve", "combine", "sketch_gather"]
+                             "gradient_refine", "refine_solve", "combine", "sketch_gather", "apply_l"]
 
 _lib = None
 

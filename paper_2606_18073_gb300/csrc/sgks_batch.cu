@@ -28,7 +28,8 @@ thread_local std::string g_batch_error;
 
 // Per-kernel timing of eager steps (sgks_batch_profile_steps): the classes of sgks_profile_steps.
 enum { BK_GRAD_APPEND = 0, BK_APPLY = 1, BK_QR_APPEND = 2, BK_STACKED_SOLVE = 3, BK_COMBINE_REFINE = 4,
-       BK_GRAD_REFINE = 5, BK_REFINE_SOLVE = 6, BK_COMBINE = 7, BK_GATHER = 8, BK_COUNT = 9, BK_NONE = -1 };
+       BK_GRAD_REFINE = 5, BK_REFINE_SOLVE = 6, BK_COMBINE = 7, BK_GATHER = 8, BK_APPLY_L = 9, BK_COUNT = 10,
+       BK_NONE = -1 };
 
 struct BProf {
     cudaEvent_t ev[2];
@@ -296,7 +297,7 @@ struct GroupX : GroupBase {
         cudaError_t e = cudaSuccess;
         if (T.ntiles) {
             RUNC(BK_APPLY, 2, launchbx_tile_apply<TW>(D, T, X, S, part, st));
-            RUNC(BK_APPLY, 1, launchbx_apply_column<TW>(D, A, L, X, S, st, false));
+            RUNC(BK_APPLY_L, 1, launchbx_apply_column<TW>(D, A, L, X, S, st, false));
         } else {
             RUNC(BK_APPLY, A.kind == SGKS_OP_CSR ? 2 : 1, launchbx_apply_column<TW>(D, A, L, X, S, st));
         }

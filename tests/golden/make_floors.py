@@ -4,12 +4,22 @@ sGKS builds its basis from gradients at earlier iterates and never re-orthogonal
 perturbation at the level of rounding grows from one iteration to the next.  Two correct
 implementations that differ only in the order of floating-point operations therefore drift
 apart.  This script measures that drift with the FP64 oracle alone: it runs the oracle once
-unperturbed and then once per seed with every gradient (eq. gradient), every sketched column
-entering the QR update (eq. updqr) and the inputs of every projected solve multiplied entrywise
-by (1 + eps * N(0,1)) -- the backward errors of those steps -- and records, for every k, the
-largest ||x_k - x'_k|| / ||x'_k|| over the seeds (five by default).  eps = 2^-53 models FP64 arithmetic, eps = 2^-48 float-float
-arithmetic (a 48-bit significand), eps = 2^-24 FP32 storage of the basis.  The per-seed curves are kept too.  The parity tests accept a CUDA iterate when its error
-against the oracle is below max(tolerance, FACTOR * floor_k).
+unperturbed and then once per seed with the output of every step that rounds multiplied
+entrywise by (1 + eps * N(0,1)) -- the backward errors of those steps -- and records, for every
+k, the largest ||x_k - x'_k|| / ||x'_k|| over the seeds (five by default).  The steps are the
+initial basis W_0 and every gradient (eq. gradient; each becomes a basis column, stored in the
+form's basis precision), every sketched column entering the
+QR update (eq. updqr), the inputs R_A, R_L, d_A of every projected solve and the gradient r(y)
+inside every refinement step, each with the unit roundoff of the arithmetic a form uses for it:
+
+    form        basis column          sketched column   projected solve   refinement residual
+    fp64        2^-53                 2^-53             2^-53             2^-53
+    ff          2^-48 (float-float)   2^-48             2^-53 (FP64)      2^-48
+    fp32        2^-24 (FP32 basis)    2^-48             2^-53             2^-48
+    fp32plain   2^-24                 2^-24             2^-24             2^-24 (FP32 sums)
+
+The per-seed curves are kept too.  The parity tests accept a CUDA iterate when its error against
+the oracle is below max(tolerance, FACTOR * floor_k).
 
 Only oracle/ and workloads/ are used.  Run:
     python tests/golden/make_floors.py [config[@key=value,...][:form] ...] [--seeds N] [--jobs J]
@@ -27,7 +37,13 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
-EPS = {"fp64": 2.0 ** -53, "ff": 2.0 ** -48, "fp32": 2.0 ** -24}
+U53, U48, U24 = 2.0 ** -53, 2.0 ** -48, 2.0 ** -24
+EPS = {  # form -> unit roundoff of each step that rounds
+    "fp64": {"gradient": U53, "column": U53, "solve": U53, "refine": U53},
+    "ff": {"gradient": U48, "column": U48, "solve": U53, "refine": U48},
+    "fp32": {"gradient": U24, "column": U48, "solve": U53, "refine": U48},
+    "fp32plain": {"gradient": U24, "column": U24, "solve": U24, "refine": U24},
+}
 FORMS = {  # config -> (forms, n_refine used with the FP64 and float-float forms)
     "deconv1d": (["fp64"], 0),
     "deblur2d": (["fp64", "fp32"], 0),
@@ -37,28 +53,52 @@ FORMS = {  # config -> (forms, n_refine used with the FP64 and float-float forms
 }
 
 
+def _steps(eps):
+    """eps as a dict of the steps' unit roundoffs (a number applies to every step)."""
+    if isinstance(eps, dict):
+        return eps
+    return {"gradient": eps, "column": eps, "solve": eps, "refine": eps}
+
+
 def _perturbed(P, iters, eps, seed, **kw):
-    """Oracle iterates of a nearby computation: every gradient (eq. gradient), every sketched
-    column entering the QR update (eq. updqr) and the inputs R_A, R_L, d_A of each projected
-    solve (eq. projected_sketched_bis) multiplied entrywise by (1 + eps N(0,1)), seeded.  Each of
-    these steps is backward stable, so a correct implementation computes the exact result of
-    such a nearby input; the perturbation models the rounding of every one of them."""
+    """Oracle iterates of a nearby computation: the initial basis and every gradient
+    (eq. gradient), every sketched column entering the QR update (eq. updqr), the inputs R_A,
+    R_L, d_A of each projected solve (eq. projected_sketched_bis) and the gradient r(y) of each
+    refinement step multiplied entrywise by (1 + u N(0,1)), seeded, u the step's unit roundoff
+    from eps.  Each of these steps is backward stable, so a correct implementation computes the
+    exact result of such a nearby input; the perturbation models the rounding of every one of
+    them."""
     import oracle as O
     from oracle import sgks_oracle as OS
     rng = np.random.default_rng(seed)
-    orig_g, orig_qr, orig_ps = OS.gradient, OS.qr_append, OS.projected_solve
+    u = _steps(eps)
+    orig_g, orig_qr, orig_ps, orig_rs = OS.gradient, OS.qr_append, OS.projected_solve, OS.refine_step
 
-    def pert(v):
+    def pert(v, e):
         v = np.asarray(v, dtype=np.float64)
-        return v * (1.0 + eps * rng.standard_normal(v.shape))
+        return v * (1.0 + e * rng.standard_normal(v.shape))
 
-    OS.gradient = lambda A, L, b, lam, x: pert(orig_g(A, L, b, lam, x))
-    OS.qr_append = lambda Q, R, u, passes=2, breakdown_tol=1e-13: orig_qr(Q, R, pert(u), passes, breakdown_tol)
-    OS.projected_solve = lambda RA, RL, dA, lam: orig_ps(pert(RA), pert(RL), pert(dA), lam)
+    ug, uc, us, ur = u["gradient"], u["column"], u["solve"], u["refine"]
+    basis_gradient = lambda A, L, b, lam, x: pert(orig_g(A, L, b, lam, x), ug)  # noqa: E731
+
+    def refine_step(*a, **k):   # the refinement's r(y) with its own unit roundoff
+        OS.gradient = lambda A, L, b, lam, x: pert(orig_g(A, L, b, lam, x), ur)
+        try:
+            return orig_rs(*a, **k)
+        finally:
+            OS.gradient = basis_gradient
+
+    if kw.get("W0") is None:   # the initial basis, stored in the basis precision
+        Aop, _ = OS.make_operators(P)
+        kw["W0"] = pert(OS.initial_basis(Aop, np.asarray(P.b, dtype=np.float64), P.ell), ug)
+    OS.gradient = basis_gradient
+    OS.refine_step = refine_step
+    OS.qr_append = lambda Q, R, v, passes=2, breakdown_tol=1e-13: orig_qr(Q, R, pert(v, uc), passes, breakdown_tol)
+    OS.projected_solve = lambda RA, RL, dA, lam: orig_ps(pert(RA, us), pert(RL, us), pert(dA, us), lam)
     try:
         return O.sgks(P, iters=iters, record_x=True, **kw)
     finally:
-        OS.gradient, OS.qr_append, OS.projected_solve = orig_g, orig_qr, orig_ps
+        OS.gradient, OS.qr_append, OS.projected_solve, OS.refine_step = orig_g, orig_qr, orig_ps, orig_rs
 
 
 def floor_curve(P, iters, eps, seeds=5, **kw):
@@ -130,10 +170,10 @@ def main(argv):
         for (name, params, form, seeds), curves, rre in pool.imap_unordered(_run, tasks):
             floor = [max(c[k] for c in curves) for k in range(len(rre))]
             P = _problem(name, form, params)
-            out = {"config": name, "params": dict(params), "form": form, "eps": EPS[form], "n_refine": P.n_refine,
+            out = {"config": name, "params": dict(params), "form": form, "eps": _steps(EPS[form]), "n_refine": P.n_refine,
                    "iters": P.iters, "seeds": seeds, "floor": floor, "per_seed": curves, "oracle_rre": rre,
                    "note": "max over seeds of oracle vs oracle with gradients, sketched QR inputs and projected-solve "
-                           "inputs perturbed by (1 + eps*N(0,1)); written by make_floors.py"}
+                           "inputs perturbed by (1 + u*N(0,1)), u per step in eps; written by make_floors.py"}
             with open(os.path.join(HERE, f"floor_{name}{_suffix(params)}_{form}.json"), "w") as f:
                 json.dump(out, f)
             print(name + _suffix(params), form, f"floor at k={P.iters}: {floor[-1]:.2e}", flush=True)

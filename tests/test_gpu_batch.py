@@ -186,13 +186,13 @@ def test_batch_fp32_form(G):
 
 def test_batch_fp32plain_form(G):
     """FP32 operators and accumulation: early iterates within 1e-4 of the oracle while the
-    method's FP32 floor is below 1e-6, final RRE within 5 % (as for the single handle)."""
+    plain-FP32 floor is below 1e-6, final RRE within 5 % (as for the single handle)."""
     probs = [small_problem("deblur2d", seed=i, iters=20) for i in range(4)]
     share_operators(probs, s=80)
     Bt, xs = batch_iterates(G, probs, "fp32plain", probs[0].iters)
     for P, x in zip(probs, xs):
         ref = O.sgks(P, record_x=True)
-        fl = floor_curve(P, P.iters, EPS["fp32"])[0]
+        fl = floor_curve(P, P.iters, EPS["fp32plain"])[0]
         errs = [rel(a, b) for a, b in zip(x, ref["xs"])]
         early = [k for k in range(len(errs)) if max(fl[:k + 1]) < 1e-6]
         assert early and max(errs[k] for k in early) < TOL32, errs
