@@ -751,7 +751,7 @@ def main_batch(args):
 BATCH_KERNEL_NAMES = {"apply_column": "kbx_csr_apply", "gradient_append": "kbx_csr_gradient",
                       "combine": "kbx_combine_tma", "sketch_gather": "kbx_sketch_gather",
                       "qr_append": "k_qr_append", "stacked_solve": "k_stacked_solve",
-                      "apply_l": "kbx_apply_column"}
+                      "sketch_l": "kbx_sketch_l_chunks+kbx_sketch_l_reduce"}
 
 
 def batch_kernel_name(kind, prec):

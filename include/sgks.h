@@ -427,7 +427,7 @@ int sgks_batch_layout(sgks_batch* h, int32_t* group_of, int32_t* group_size);
  * SGKS_BATCH_PROFILE_CLASSES entries receive the total milliseconds and the launch count per
  * kernel class: the classes of sgks_profile_steps, except that class 1 is the operator apply
  * alone (A w through pixel tiles: the tile pass and the per-ray sums), class 8 the sketch gather
- * and class 9 the L w column when A w runs through pixel tiles (otherwise part of class 1). */
+ * (S_A A w) and class 9 S_L L w (L w formed and sketched in column chunks, never stored). */
 #define SGKS_BATCH_PROFILE_CLASSES 10
 int sgks_batch_profile_steps(sgks_batch* h, int32_t iters, double* ms_out, int64_t* count_out);
 

@@ -119,7 +119,7 @@ SGKS_FLAG_NO_TILES = 16
 SGKS_FLAG_BW_HOST = 32
 SGKS_BATCH_PROFILE_CLASSES = 10
 BATCH_PROFILE_CLASS_NAMES = ["gradient_append", "apply_column", "qr_append", "stacked_solve", "combine_refine",
-                             "gradient_refine", "refine_solve", "combine", "sketch_gather", "apply_l"]
+                             "gradient_refine", "refine_solve", "combine", "sketch_gather", "sketch_l"]
 
 _lib = None
 

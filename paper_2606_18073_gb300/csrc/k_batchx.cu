@@ -234,10 +234,11 @@ __global__ void __launch_bounds__(kThreads) kbx_csr_apply(BDims D, DevA<float, f
 }
 
 // a1 for the other rows: t_i = L w_i -> tp (float-float), and u_i = A w_i for a convolution or
-// dense A (rows t < t0 skipped: done by kbx_csr_apply).  One thread per (row, instance).
+// dense A, rows t in [t0, tot) of the (A rows, L rows) range (A rows of a CSR A come from
+// kbx_csr_apply or the tiled pass).  One thread per (row, instance).
 template <typename TW>
 __global__ void __launch_bounds__(kThreads) kbx_apply_column(BDims D, DevA<float, float> A, DevL L, BBulkX<TW> X,
-                                                             BSmall S, int64_t t0) {
+                                                             BSmall S, int64_t t0, int64_t tot) {
     __shared__ float psf_s[128];
     if (A.kind == SGKS_OP_CONV2D)
         for (int i = threadIdx.x; i < A.kh * A.kw; i += blockDim.x) psf_s[i] = A.psf[i];
@@ -250,7 +251,6 @@ __global__ void __launch_bounds__(kThreads) kbx_apply_column(BDims D, DevA<float
     if (d >= D.dmax) return;
     const TW* w = X.W + (size_t)d * D.n * B + b;
     const StridedW<TW> wv{w, B};
-    const int64_t tot = (D.m + D.p) * B;
     for (int64_t t = t0 + (int64_t)blockIdx.x * kThreads + threadIdx.x; t < tot; t += gstride()) {
         if (t < D.m * B) {
             const int64_t j = qdiv(t, B);
@@ -324,6 +324,75 @@ __global__ void __launch_bounds__(kThreads) kbx_sketch_gather(BDims D, BBulkX<TW
     if (g == 0 && live) {
         if (vec) out_vec[(size_t)b * D.s + r] = D.sketch_scale * red[b];
         else (isA ? S.partA : S.partL)[(size_t)b * D.s + r] = red[b];
+    }
+}
+
+// ------------------------------------------------------- a1: S_L L w through column chunks
+// Chunk c of t = L w (kLChunk rows) is formed once in shared memory for kLInst instances, from
+// the newest basis column (the stencil of eq. reg_matrix / eq. spacetime_tik in float-float),
+// and every sketch row's entries in the chunk are summed by Dot2 from there: t is never stored,
+// and each of its values is read from on-chip memory by its zeta sketch rows.  One partial per
+// (chunk, row, instance); kbx_sketch_l_reduce sums them over the chunks in order.
+constexpr int kLInst = 4;
+
+size_t sketch_l_smem(int B) { return (size_t)kLChunk * std::min(B, kLInst) * sizeof(float2); }
+
+template <typename TW>
+__global__ void __launch_bounds__(kThreads) kbx_sketch_l_chunks(BDims D, DevL L, BBulkX<TW> X, SketchLChunks LC,
+                                                                BSmall S, float2* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* t = reinterpret_cast<float2*>(smem_raw);   // [C][IC]
+    const int B = D.B, IC = B < kLInst ? B : kLInst, nig = B / IC, s = D.s;
+    const int c = (int)(blockIdx.x / nig), ig = (int)(blockIdx.x % nig);
+    const int64_t q0 = (int64_t)c * LC.C;
+    const int nq = (int)min((int64_t)LC.C, D.p - q0);
+    constexpr int KU = 4;   // rows formed together, so that their loads are in flight together
+    for (int u0 = threadIdx.x; u0 < nq * IC; u0 += KU * kThreads) {
+        float2 v[KU];
+#pragma unroll
+        for (int j = 0; j < KU; ++j) {
+            const int u = u0 + j * kThreads;
+            v[j] = ff_zero();
+            if (u < nq * IC) {
+                const int ql = u / IC, i = u - ql * IC, b = ig * IC + i;
+                const DevScalars& sc = S.sc[b];
+                if (!sc.stop && sc.d < D.dmax)
+                    v[j] = ff_l_row<TW>(L, q0 + ql, StridedW<TW>{X.W + (size_t)sc.d * D.n * B + b, B});
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < KU; ++j)
+            if (u0 + j * kThreads < nq * IC) t[u0 + j * kThreads] = v[j];
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < s * IC; u += kThreads) {
+        const int r = u / IC, i = u - r * IC;
+        const int e0 = LC.seg[(size_t)c * s + r], e1 = LC.seg[(size_t)c * s + r + 1];
+        Dot2 a;
+        for (int k = e0; k < e1; ++k) {
+            const uint32_t en = __ldg(LC.ent + k);
+            const float2 v = t[(int)(en & 0x7fffffffu) * IC + i];
+            const float sg = (en >> 31) ? -1.f : 1.f;
+            a.add2(sg * v.x, sg * v.y);
+        }
+        part[((size_t)c * s + r) * B + ig * IC + i] = a.value();
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) kbx_sketch_l_reduce(BDims D, SketchLChunks LC, BSmall S,
+                                                                const float2* __restrict__ part) {
+    const int B = D.B, s = D.s;
+    for (int64_t u = (int64_t)blockIdx.x * kThreads + threadIdx.x; u < (int64_t)s * B; u += gstride()) {
+        const int r = (int)(u / B), b = (int)(u - (int64_t)r * B);
+        const DevScalars& sc = S.sc[b];
+        if (sc.stop || sc.d >= D.dmax) continue;
+        Dot2 a;
+#pragma unroll 8
+        for (int c = 0; c < LC.nchunks; ++c) {
+            const float2 v = __ldcg(part + ((size_t)c * s + r) * B + b);
+            a.add2(v.x, v.y);
+        }
+        S.partL[(size_t)b * s + r] = a.to_double();
     }
 }
 
@@ -871,26 +940,106 @@ static cudaError_t x_csr_apply_vv(const BDims& D, const DevA<float, float>& A, c
 
 template <typename TW>
 cudaError_t launchbx_apply_column(const BDims& D, const DevA<float, float>& A, const DevL& L, const BBulkX<TW>& X,
-                                  const BSmall& S, cudaStream_t st, bool a_rows) {
+                                  const BSmall& S, cudaStream_t st, bool a_rows, bool l_rows) {
+    const int64_t mB = D.m * D.B, tot = (D.m + (l_rows ? D.p : 0)) * D.B;
     if (A.kind == SGKS_OP_CSR) {
         constexpr int VW = wvec<TW>();
         cudaError_t e = !a_rows ? cudaSuccess
                         : D.B >= VW ? x_csr_apply_vv<TW, VW>(D, A, X, S, st)
                         : (VW == 4 && D.B == 2) ? x_csr_apply_vv<TW, 2>(D, A, X, S, st)
                                                 : x_csr_apply_vv<TW, 1>(D, A, X, S, st);
-        if (e != cudaSuccess) return e;
-        kbx_apply_column<TW><<<xgrid(D.p * D.B), kThreads, 0, st>>>(D, A, L, X, S, D.m * D.B);
+        if (e != cudaSuccess || !l_rows) return e;
+        kbx_apply_column<TW><<<xgrid(D.p * D.B), kThreads, 0, st>>>(D, A, L, X, S, mB, tot);
         return cudaGetLastError();
     }
-    kbx_apply_column<TW><<<xgrid((D.m + D.p) * D.B), kThreads, 0, st>>>(D, A, L, X, S, 0);
+    const int64_t t0 = a_rows ? 0 : mB;
+    if (tot <= t0) return cudaSuccess;
+    kbx_apply_column<TW><<<xgrid(tot - t0), kThreads, 0, st>>>(D, A, L, X, S, t0, tot);
     return cudaGetLastError();
 }
 
 template <typename TW>
 cudaError_t launchbx_sketch_gather(const BDims& D, const BBulkX<TW>& X, const SketchCSR& SK, const BSmall& S,
-                                   const float2* vec, double* out_vec, cudaStream_t st) {
-    kbx_sketch_gather<TW><<<vec ? D.s : 2 * D.s, kThreads, 0, st>>>(D, X, SK, S, vec, out_vec);
+                                   const float2* vec, double* out_vec, cudaStream_t st, bool l_rows) {
+    kbx_sketch_gather<TW><<<vec || !l_rows ? D.s : 2 * D.s, kThreads, 0, st>>>(D, X, SK, S, vec, out_vec);
     return cudaGetLastError();
+}
+
+template <typename TW>
+cudaError_t launchbx_sketch_l(const BDims& D, const DevL& L, const BBulkX<TW>& X, const SketchLChunks& LC,
+                              const BSmall& S, float2* part, cudaStream_t st) {
+    const size_t smem = sketch_l_smem(D.B);
+    auto k = kbx_sketch_l_chunks<TW>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int IC = std::min(D.B, kLInst);
+    k<<<(unsigned)((int64_t)LC.nchunks * (D.B / IC)), kThreads, smem, st>>>(D, L, X, LC, S, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    kbx_sketch_l_reduce<<<xgrid((int64_t)D.s * D.B), kThreads, 0, st>>>(D, LC, S, part);
+    return cudaGetLastError();
+}
+
+int build_sketch_l_chunks(const SketchCSR& SK, int64_t p, int s, int C, SketchLChunks& LC,
+                          std::vector<void*>& allocs, cudaStream_t st, std::string* why) {
+    std::vector<int32_t> ptr((size_t)s + 1);
+    cudaError_t e = cudaMemcpyAsync(ptr.data(), SK.ptrL, sizeof(int32_t) * (s + 1), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        *why = std::string("sketch chunks: ") + cudaGetErrorString(e);
+        return SGKS_ERR_CUDA;
+    }
+    const int64_t nnz = ptr[s];
+    std::vector<uint32_t> idx((size_t)nnz);
+    if (nnz) e = cudaMemcpyAsync(idx.data(), SK.idxL, sizeof(uint32_t) * nnz, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        *why = std::string("sketch chunks: ") + cudaGetErrorString(e);
+        return SGKS_ERR_CUDA;
+    }
+    const int nch = (int)((p + C - 1) / C);
+    // counts per (chunk, row), then a stable placement in the row's own order
+    std::vector<int32_t> seg((size_t)nch * s + 1, 0);
+    for (int r = 0; r < s; ++r)
+        for (int64_t k = ptr[r]; k < ptr[r + 1]; ++k) {
+            const int64_t q = idx[k] & 0x7fffffffu;
+            if (q >= p) {
+                *why = "sketch chunks: a column index outside [0, p)";
+                return SGKS_ERR_STATE;
+            }
+            ++seg[(size_t)(q / C) * s + r + 1];
+        }
+    for (size_t i = 1; i < seg.size(); ++i) seg[i] += seg[i - 1];
+    std::vector<int32_t> pos(seg.begin(), seg.end() - 1);
+    std::vector<uint32_t> ent((size_t)nnz);
+    for (int r = 0; r < s; ++r)
+        for (int64_t k = ptr[r]; k < ptr[r + 1]; ++k) {
+            const uint32_t u = idx[k];
+            const int64_t q = u & 0x7fffffffu, c = q / C;
+            ent[pos[(size_t)c * s + r]++] = (uint32_t)(q - c * C) | (u & 0x80000000u);
+        }
+    int32_t* d_seg = nullptr;
+    uint32_t* d_ent = nullptr;
+    e = cudaMalloc(&d_seg, sizeof(int32_t) * seg.size());
+    if (e == cudaSuccess) allocs.push_back(d_seg);
+    if (e == cudaSuccess) e = cudaMalloc(&d_ent, sizeof(uint32_t) * std::max<int64_t>(nnz, 1));
+    if (e == cudaSuccess) allocs.push_back(d_ent);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_seg, seg.data(), sizeof(int32_t) * seg.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nnz)
+        e = cudaMemcpyAsync(d_ent, ent.data(), sizeof(uint32_t) * nnz, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        *why = std::string("sketch chunks: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? SGKS_ERR_NOMEM : SGKS_ERR_CUDA;
+    }
+    LC.C = C;
+    LC.nchunks = nch;
+    LC.seg = d_seg;
+    LC.ent = d_ent;
+    return SGKS_OK;
 }
 
 static int xcomb_stages(int slice_kb) { return slice_kb == 8 ? 6 : 4; }
@@ -1004,9 +1153,11 @@ cudaError_t launchbx_to_double(const float2* in, double* out, int64_t len, cudaS
 
 #define SGKS_INST_BX(TW)                                                                                          \
     template cudaError_t launchbx_apply_column<TW>(const BDims&, const DevA<float, float>&, const DevL&,           \
-                                                   const BBulkX<TW>&, const BSmall&, cudaStream_t, bool);         \
+                                                   const BBulkX<TW>&, const BSmall&, cudaStream_t, bool, bool);   \
     template cudaError_t launchbx_sketch_gather<TW>(const BDims&, const BBulkX<TW>&, const SketchCSR&,             \
-                                                    const BSmall&, const float2*, double*, cudaStream_t);          \
+                                                    const BSmall&, const float2*, double*, cudaStream_t, bool);    \
+    template cudaError_t launchbx_sketch_l<TW>(const BDims&, const DevL&, const BBulkX<TW>&, const SketchLChunks&, \
+                                               const BSmall&, float2*, cudaStream_t);                             \
     template cudaError_t launchbx_combine<TW>(const BDims&, const BBulkX<TW>&, const BSmall&, int, cudaStream_t);  \
     template cudaError_t launchbx_gradient<TW>(const BDims&, const DevA<float, float>&, const DevL&,               \
                                                const BBulkX<TW>&, const BSmall&, float2*, cudaStream_t);          \

@@ -28,7 +28,7 @@ thread_local std::string g_batch_error;
 
 // Per-kernel timing of eager steps (sgks_batch_profile_steps): the classes of sgks_profile_steps.
 enum { BK_GRAD_APPEND = 0, BK_APPLY = 1, BK_QR_APPEND = 2, BK_STACKED_SOLVE = 3, BK_COMBINE_REFINE = 4,
-       BK_GRAD_REFINE = 5, BK_REFINE_SOLVE = 6, BK_COMBINE = 7, BK_GATHER = 8, BK_APPLY_L = 9, BK_COUNT = 10,
+       BK_GRAD_REFINE = 5, BK_REFINE_SOLVE = 6, BK_COMBINE = 7, BK_GATHER = 8, BK_SKETCH_L = 9, BK_COUNT = 10,
        BK_NONE = -1 };
 
 struct BProf {
@@ -292,16 +292,15 @@ struct GroupX : GroupBase {
     int io_dt = SGKS_F32;       // element type of the caller's b, x_true and x_out
     TiledA T{};                 // pixel tiles of a CSR A (ntiles = 0: the CSR-row kernel)
     float2* part = nullptr;     // [nseg][B] partial sums of the tiled forward pass
+    SketchLChunks LC{};         // S_L in column chunks of L w
+    float2* lpart = nullptr;    // [nchunks][s][B] partial sums of S_L L w
 
     cudaError_t sketch_column() {
         cudaError_t e = cudaSuccess;
-        if (T.ntiles) {
-            RUNC(BK_APPLY, 2, launchbx_tile_apply<TW>(D, T, X, S, part, st));
-            RUNC(BK_APPLY_L, 1, launchbx_apply_column<TW>(D, A, L, X, S, st, false));
-        } else {
-            RUNC(BK_APPLY, A.kind == SGKS_OP_CSR ? 2 : 1, launchbx_apply_column<TW>(D, A, L, X, S, st));
-        }
-        RUNC(BK_GATHER, 1, launchbx_sketch_gather<TW>(D, X, SK, S, nullptr, nullptr, st));
+        if (T.ntiles) RUNC(BK_APPLY, 2, launchbx_tile_apply<TW>(D, T, X, S, part, st));
+        else RUNC(BK_APPLY, 1, launchbx_apply_column<TW>(D, A, L, X, S, st, true, false));
+        RUNC(BK_SKETCH_L, 2, launchbx_sketch_l<TW>(D, L, X, LC, S, lpart, st));
+        RUNC(BK_GATHER, 1, launchbx_sketch_gather<TW>(D, X, SK, S, nullptr, nullptr, st, false));
         return e;
     }
 
@@ -450,7 +449,7 @@ struct GroupX : GroupBase {
                     // the gradient is appended as column d, which the next step rewrites from
                     // the same inputs
                     const float t = time_it([&] {
-                        return which == 0 ? launchbx_apply_column<TW>(D, A, L, X, S, st)
+                        return which == 0 ? launchbx_apply_column<TW>(D, A, L, X, S, st, true, false)
                                           : launchbx_gradient<TW>(D, A, L, X, S, nullptr, st);
                     });
                     log += std::string(which == 0 ? " A/" : " At/") + std::to_string(nl) + "=" + std::to_string(t);
@@ -807,6 +806,9 @@ int build_groups_x(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const 
     rc = prepare_sparse_sign(sketch_key_host_dev(seed, 0), sketch_key_host_dev(seed, 1), op->m, L.p, s, o.zeta, SK,
                              h->allocs, h->d_err, h->st, &why);
     if (rc != SGKS_OK) return bfail(h, rc, why);
+    SketchLChunks LC{};   // S_L L w without storing L w
+    rc = build_sketch_l_chunks(SK, L.p, s, kLChunk, LC, h->allocs, h->st, &why);
+    if (rc != SGKS_OK) return bfail(h, rc, why);
     // pixel tiles for the forward pass of a CSR operator on an image geometry (the regularizer's)
     TiledA T{};
     if (op->kind == SGKS_OP_CSR && !(o.flags & SGKS_FLAG_NO_TILES) &&
@@ -831,6 +833,7 @@ int build_groups_x(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const 
         G->L = L;
         G->SK = SK;
         G->T = T;
+        G->LC = LC;
         G->io_dt = io_dt;
         G->has_xt = x_true != nullptr;
         for (int i = 0; i < B; ++i) {
@@ -847,7 +850,7 @@ int build_groups_x(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const 
         if (e == cudaSuccess) e = balloc(h, &(ptr), (size_t)(cnt)); \
     } while (0)
         BBulkX<TW>& X = G->X;
-        const size_t nB = (size_t)D.n * B, mB = (size_t)D.m * B, pB = (size_t)D.p * B;
+        const size_t nB = (size_t)D.n * B, mB = (size_t)D.m * B;
         float2 *lam2 = nullptr;
         BA(X.W, (size_t)dmax * nB);
         BA(X.AW, (size_t)dmax * mB);
@@ -856,7 +859,7 @@ int build_groups_x(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const 
         BA(X.e, mB);
         BA(X.b, mB);
         if (G->has_xt) BA(X.xtrue, nB);
-        BA(X.tp, pB);
+        BA(G->lpart, (size_t)LC.nchunks * s * B);
         if (o.n_refine > 0) BA(X.r, nB);
         BA(lam2, B);
         BA(X.y2, (size_t)B * dmax);

@@ -716,6 +716,15 @@ struct SketchCSR {
     const uint32_t* idxL;
 };
 
+// S_L re-blocked by column chunks of t = L w (batched compensated forms): chunk c covers the
+// columns q in [c C, c C + C); the entries of sketch row r in chunk c are ent[seg[c s + r] ..
+// seg[c s + r + 1]), each (q - c C) | sign << 31, in the row's own order.  nchunks = 0: not built.
+struct SketchLChunks {
+    int C, nchunks;
+    const int32_t* seg;
+    const uint32_t* ent;
+};
+
 // ------------------------------------------------------------------------ launchers
 struct Dims {
     int64_t n, m, p;
@@ -966,13 +975,25 @@ cudaError_t launchbx_tile_apply(const BDims& D, const TiledA& T, const BBulkX<TW
                                 cudaStream_t st);
 
 // compensated batched kernels (k_batchx.cu); TW = float or float2
-// a_rows = false: the L rows only (the A rows come from launchbx_tile_apply)
+// a_rows = false: no A rows (they come from launchbx_tile_apply); l_rows = false: no t = L w
+// column (S_L L w comes from launchbx_sketch_l)
 template <typename TW>
 cudaError_t launchbx_apply_column(const BDims& D, const DevA<float, float>& A, const DevL& L, const BBulkX<TW>& X,
-                                  const BSmall& S, cudaStream_t st, bool a_rows = true);
+                                  const BSmall& S, cudaStream_t st, bool a_rows = true, bool l_rows = true);
+// l_rows = false: the S_A rows only
 template <typename TW>
 cudaError_t launchbx_sketch_gather(const BDims& D, const BBulkX<TW>& X, const SketchCSR& SK, const BSmall& S,
-                                   const float2* vec, double* out_vec, cudaStream_t st);
+                                   const float2* vec, double* out_vec, cudaStream_t st, bool l_rows = true);
+// S_L L w_i for the newest column of every live instance through the column chunks of S_L, without
+// storing L w: part[nchunks][s][B] per-chunk partial sums, then S.partL.
+template <typename TW>
+cudaError_t launchbx_sketch_l(const BDims& D, const DevL& L, const BBulkX<TW>& X, const SketchLChunks& LC,
+                              const BSmall& S, float2* part, cudaStream_t st);
+// column chunks of S_L (device arrays to allocs); chunk length C
+int build_sketch_l_chunks(const SketchCSR& SK, int64_t p, int s, int C, SketchLChunks& LC,
+                          std::vector<void*>& allocs, cudaStream_t st, std::string* why);
+size_t sketch_l_smem(int B);
+constexpr int kLChunk = 2048;   // columns of L w per chunk of S_L
 template <typename TW>
 cudaError_t launchbx_combine(const BDims& D, const BBulkX<TW>& X, const BSmall& S, int mode, cudaStream_t st);
 template <typename TW>
