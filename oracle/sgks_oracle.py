@@ -22,6 +22,7 @@ What each function follows, and what pins it (tests/test_oracle_*.py):
                        applied twice (CGS2) by default.  Pinned by QR = M and Q^T Q = I.
   projected_solve      eq. (projected_sketched_bis): Householder QR of [R_A; sqrt(lam) R_L],
                        rebuilt from scratch each call, then back substitution.
+  combine              x = W y (a matmul).
   refine_step          one sketch-preconditioned refinement step of the projected problem,
                        the q = 0 setting of Sec. 4.3 (no inner iteration).  Pinned by
                        convergence to the unsketched projected solution (eq. sGKS_noSASL).
@@ -364,6 +365,12 @@ def projected_solve(RA, RL, dA, lam):
     return y, T
 
 
+def combine(W, y):
+    """x = W y, the iterate of Algorithm 2 from its projected coefficients (a matmul).  A
+    module-level step so that the floor model of the parity tests can perturb its terms."""
+    return W @ y
+
+
 def refine_step(Aop, Lop, b, lam, W, y, T):
     """One refinement step of the projected problem, sketched preconditioner, no inner solve.
 
@@ -373,7 +380,7 @@ def refine_step(Aop, Lop, b, lam, W, y, T):
     triangular factor of the sketched problem.  Its fixed point is the unsketched
     projected solution of eq. (sGKS_noSASL).
     """
-    x = W @ y
+    x = combine(W, y)
     g = W.T @ gradient(Aop, Lop, b, lam, x)
     t = scipy.linalg.solve_triangular(T, g, trans="T", lower=False)
     return y - scipy.linalg.solve_triangular(T, t, lower=False)
@@ -438,7 +445,7 @@ def sgks(problem, iters=None, n_refine=None, sketched=True, cgs_passes=2, tol=0.
     xt = np.asarray(P.x_true, dtype=np.float64)
     nxt = np.linalg.norm(xt)
     y, chain = solve()
-    x = W @ y
+    x = combine(W, y)
     rc, rre, xs = [], [np.linalg.norm(x - xt) / nxt], [x.copy()] if record_x else None
     ys = [y.copy()] if record_x else None
     yrs = [[c.copy() for c in chain]] if record_x else None
@@ -447,7 +454,7 @@ def sgks(problem, iters=None, n_refine=None, sketched=True, cgs_passes=2, tol=0.
         W = np.concatenate([W, r[:, None]], axis=1)
         append(r)
         y, chain = solve()
-        x_new = W @ y
+        x_new = combine(W, y)
         rc.append(np.linalg.norm(x_new - x) / np.linalg.norm(x))
         rre.append(np.linalg.norm(x_new - xt) / nxt)
         x = x_new

@@ -4,19 +4,28 @@ sGKS builds its basis from gradients at earlier iterates and never re-orthogonal
 perturbation at the level of rounding grows from one iteration to the next.  Two correct
 implementations that differ only in the order of floating-point operations therefore drift
 apart.  This script measures that drift with the FP64 oracle alone: it runs the oracle once
-unperturbed and then once per seed with the output of every step that rounds multiplied
-entrywise by (1 + eps * N(0,1)) -- the backward errors of those steps -- and records, for every
-k, the largest ||x_k - x'_k|| / ||x'_k|| over the seeds (five by default).  The steps are the
-initial basis W_0 and every gradient (eq. gradient; each becomes a basis column, stored in the
-form's basis precision), every sketched column entering the
-QR update (eq. updqr), the inputs R_A, R_L, d_A of every projected solve and the gradient r(y)
-inside every refinement step, each with the unit roundoff of the arithmetic a form uses for it:
+unperturbed and then once per seed with every step that rounds given the backward error of
+that step -- each term or entry multiplied by (1 + u * N(0,1)), u the unit roundoff the form uses
+for it -- and records, for every k, the largest ||x_k - x'_k|| / ||x'_k|| over the seeds (five
+by default).  The steps:
+  basis      the initial basis W_0 and every gradient (eq. gradient) as stored in the basis;
+  sum        one rounding per term of the sums: the terms W_j y_j of x = W y (which reach
+             e = A W y - b through A), the b term of the residual, the residual entering A^T,
+             and the two terms A^T e and lam L^T L x of every gradient (eq. gradient), in the
+             basis gradient and in every refinement residual;
+  column     every sketched column entering the QR update (eq. updqr);
+  solve      the inputs R_A, R_L, d_A of every projected solve (eq. projected_sketched_bis);
+  refine     the refinement residual r(y) as stored.
+Per term, not per output: the residual is near the noise level and the gradient tends to zero
+as the iterates converge, so their rounding errors are set by their terms, not their values.
 
-    form        basis column          sketched column   projected solve   refinement residual
-    fp64        2^-53                 2^-53             2^-53             2^-53
-    ff          2^-48 (float-float)   2^-48             2^-53 (FP64)      2^-48
-    fp32        2^-24 (FP32 basis)    2^-48             2^-53             2^-48
-    fp32plain   2^-24                 2^-24             2^-24             2^-24 (FP32 sums)
+    form        basis      sum        column     solve      refine
+    fp64        2^-53      2^-53      2^-53      2^-53      2^-53
+    ff          2^-48      2^-48      2^-48      2^-53      2^-48   (float-float, FP64 small phase)
+    fp32        2^-24      2^-48      2^-48      2^-53      2^-48   (FP32 basis, compensated sums)
+    fp32plain   2^-24      2^-24      2^-24      2^-24      2^-24   (FP32 sums everywhere)
+
+(In EPS below, "gradient" is the basis column, and "combine" the sum x = W y.)
 
 The per-seed curves are kept too.  The parity tests accept a CUDA iterate when its error against
 the oracle is below max(tolerance, FACTOR * floor_k).
@@ -39,10 +48,10 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 U53, U48, U24 = 2.0 ** -53, 2.0 ** -48, 2.0 ** -24
 EPS = {  # form -> unit roundoff of each step that rounds
-    "fp64": {"gradient": U53, "column": U53, "solve": U53, "refine": U53},
-    "ff": {"gradient": U48, "column": U48, "solve": U53, "refine": U48},
-    "fp32": {"gradient": U24, "column": U48, "solve": U53, "refine": U48},
-    "fp32plain": {"gradient": U24, "column": U24, "solve": U24, "refine": U24},
+    "fp64": {"gradient": U53, "column": U53, "solve": U53, "refine": U53, "combine": U53, "sum": U53},
+    "ff": {"gradient": U48, "column": U48, "solve": U53, "refine": U48, "combine": U48, "sum": U48},
+    "fp32": {"gradient": U24, "column": U48, "solve": U53, "refine": U48, "combine": U48, "sum": U48},
+    "fp32plain": {"gradient": U24, "column": U24, "solve": U24, "refine": U24, "combine": U24, "sum": U24},
 }
 FORMS = {  # config -> (forms, n_refine used with the FP64 and float-float forms)
     "deconv1d": (["fp64"], 0),
@@ -57,7 +66,7 @@ def _steps(eps):
     """eps as a dict of the steps' unit roundoffs (a number applies to every step)."""
     if isinstance(eps, dict):
         return eps
-    return {"gradient": eps, "column": eps, "solve": eps, "refine": eps}
+    return {"gradient": eps, "column": eps, "solve": eps, "refine": eps, "combine": eps, "sum": eps}
 
 
 def _perturbed(P, iters, eps, seed, **kw):
@@ -72,17 +81,26 @@ def _perturbed(P, iters, eps, seed, **kw):
     from oracle import sgks_oracle as OS
     rng = np.random.default_rng(seed)
     u = _steps(eps)
-    orig_g, orig_qr, orig_ps, orig_rs = OS.gradient, OS.qr_append, OS.projected_solve, OS.refine_step
+    orig_g, orig_qr, orig_ps, orig_rs, orig_c = (OS.gradient, OS.qr_append, OS.projected_solve, OS.refine_step,
+                                                 OS.combine)
 
     def pert(v, e):
         v = np.asarray(v, dtype=np.float64)
         return v * (1.0 + e * rng.standard_normal(v.shape))
 
-    ug, uc, us, ur = u["gradient"], u["column"], u["solve"], u["refine"]
-    basis_gradient = lambda A, L, b, lam, x: pert(orig_g(A, L, b, lam, x), ug)  # noqa: E731
+    ug, uc, us, ur, ux, um = u["gradient"], u["column"], u["solve"], u["refine"], u["combine"], u["sum"]
+
+    def term_gradient(A, L, b, lam, x, u_out):
+        # eq. gradient with one rounding per term of its sums: the b term of the residual, the
+        # residual entering A^T, the two terms A^T e and lam L^T L x, and the stored result (the
+        # terms of A x are those of x = W y, perturbed in combine)
+        e = A.apply(x) - pert(b, um)
+        return pert(pert(A.adjoint(pert(e, um)), um) + pert(lam * L.adjoint(L.apply(x)), um), u_out)
+
+    basis_gradient = lambda A, L, b, lam, x: term_gradient(A, L, b, lam, x, ug)  # noqa: E731
 
     def refine_step(*a, **k):   # the refinement's r(y) with its own unit roundoff
-        OS.gradient = lambda A, L, b, lam, x: pert(orig_g(A, L, b, lam, x), ur)
+        OS.gradient = lambda A, L, b, lam, x: term_gradient(A, L, b, lam, x, ur)
         try:
             return orig_rs(*a, **k)
         finally:
@@ -93,12 +111,14 @@ def _perturbed(P, iters, eps, seed, **kw):
         kw["W0"] = pert(OS.initial_basis(Aop, np.asarray(P.b, dtype=np.float64), P.ell), ug)
     OS.gradient = basis_gradient
     OS.refine_step = refine_step
+    OS.combine = lambda W, y: orig_c(W, pert(y, ux))   # one rounding per term W_j y_j of x = W y
     OS.qr_append = lambda Q, R, v, passes=2, breakdown_tol=1e-13: orig_qr(Q, R, pert(v, uc), passes, breakdown_tol)
     OS.projected_solve = lambda RA, RL, dA, lam: orig_ps(pert(RA, us), pert(RL, us), pert(dA, us), lam)
     try:
         return O.sgks(P, iters=iters, record_x=True, **kw)
     finally:
         OS.gradient, OS.qr_append, OS.projected_solve, OS.refine_step = orig_g, orig_qr, orig_ps, orig_rs
+        OS.combine = orig_c
 
 
 def floor_curve(P, iters, eps, seeds=5, **kw):
