@@ -209,19 +209,25 @@ __global__ void __launch_bounds__(kThreads) kbx_csr_apply(BDims D, DevA<float, f
         if (!__any_sync(0xffffffffu, any)) continue;
         Dot2 acc[VV];
         const int beg = rl.valid ? A.rp[rl.row] : 0, end = rl.valid ? A.rp[rl.row + 1] : 0;
+        for (int kb = beg + rl.nl; kb < end; kb += kDot2Block * rl.NL) {   // blocked Dot2 (ff.cuh)
+            const int ke = min(end, kb + kDot2Block * rl.NL);
+            Dot2 blk[VV];
 #pragma unroll 4
-        for (int kk = beg + rl.nl; kk < end; kk += rl.NL) {
-            const int64_t c = (int64_t)__ldg(A.ci + kk) * B;
-            const float a = __ldg(A.val + kk);
-            TW xv[VV];
-            if (same) {
-                ldw<TW, VV>(xb[0] + c, xv);
-            } else {
+            for (int kk = kb; kk < ke; kk += rl.NL) {
+                const int64_t c = (int64_t)__ldg(A.ci + kk) * B;
+                const float a = __ldg(A.val + kk);
+                TW xv[VV];
+                if (same) {
+                    ldw<TW, VV>(xb[0] + c, xv);
+                } else {
 #pragma unroll
-                for (int v = 0; v < VV; ++v) xv[v] = xb[v] ? __ldcg(xb[v] + c) : wzero<TW>();
+                    for (int v = 0; v < VV; ++v) xv[v] = xb[v] ? __ldcg(xb[v] + c) : wzero<TW>();
+                }
+#pragma unroll
+                for (int v = 0; v < VV; ++v) acc_w(blk[v], a, xv[v]);
             }
 #pragma unroll
-            for (int v = 0; v < VV; ++v) acc_w(acc[v], a, xv[v]);
+            for (int v = 0; v < VV; ++v) acc[v].merge(blk[v]);
         }
         for (int off = 1; off < rl.NL; off <<= 1)
 #pragma unroll
@@ -254,21 +260,28 @@ __global__ void __launch_bounds__(kThreads) kbx_apply_column(BDims D, DevA<float
     for (int64_t t = t0 + (int64_t)blockIdx.x * kThreads + threadIdx.x; t < tot; t += gstride()) {
         if (t < D.m * B) {
             const int64_t j = qdiv(t, B);
-            Dot2 a;
+            Dot2 a;   // blocked Dot2 (ff.cuh): one block per row of the psf, or of kDot2Block values
             if (A.kind == SGKS_OP_CONV2D) {
                 const int nx = A.nx, ny = A.ny, kh = A.kh, kw = A.kw;
                 const int iy = (int)qdiv(j, nx), ix = (int)(j - (int64_t)iy * nx);
                 for (int aa = 0; aa < kh; ++aa) {
                     const int yy = iy - aa + kh / 2;
                     if (yy < 0 || yy >= ny) continue;
+                    Dot2 blk;
                     for (int c = 0; c < kw; ++c) {
                         const int xx = ix - c + kw / 2;
-                        if (xx >= 0 && xx < nx) acc_w(a, psf_s[aa * kw + c], wv((int64_t)yy * nx + xx));
+                        if (xx >= 0 && xx < nx) acc_w(blk, psf_s[aa * kw + c], wv((int64_t)yy * nx + xx));
                     }
+                    a.merge(blk);
                 }
             } else {
                 const float* row = A.dense + j * A.ld;
-                for (int64_t k = 0; k < A.n; ++k) acc_w(a, __ldg(row + k), wv(k));
+                for (int64_t k0 = 0; k0 < A.n; k0 += kDot2Block) {
+                    Dot2 blk;
+                    const int64_t k1 = k0 + kDot2Block < A.n ? k0 + kDot2Block : A.n;
+                    for (int64_t k = k0; k < k1; ++k) acc_w(blk, __ldg(row + k), wv(k));
+                    a.merge(blk);
+                }
             }
             X.AW[((size_t)d * D.m + j) * B + b] = a.value();
         } else {
@@ -310,9 +323,11 @@ __global__ void __launch_bounds__(kThreads) kbx_sketch_gather(BDims D, BBulkX<TW
 #pragma unroll
             for (int q = 0; q < 16; ++q)
                 val[q] = k0 + q * G < e ? __ldcg(v + (int64_t)(u[q] & 0x7fffffffu) * B + b) : ff_zero();
+            Dot2 blk;   // blocked Dot2 (ff.cuh): one block per round of 16 entries
 #pragma unroll
             for (int q = 0; q < 16; ++q)
-                if (k0 + q * G < e) acc_add(a, (u[q] >> 31) ? -1.f : 1.f, val[q]);
+                if (k0 + q * G < e) acc_add(blk, (u[q] >> 31) ? -1.f : 1.f, val[q]);
+            a.merge(blk);
         }
     }
     red[threadIdx.x] = a.to_double();
@@ -369,11 +384,16 @@ __global__ void __launch_bounds__(kThreads) kbx_sketch_l_chunks(BDims D, DevL L,
         const int r = u / IC, i = u - r * IC;
         const int e0 = LC.seg[(size_t)c * s + r], e1 = LC.seg[(size_t)c * s + r + 1];
         Dot2 a;
-        for (int k = e0; k < e1; ++k) {
-            const uint32_t en = __ldg(LC.ent + k);
-            const float2 v = t[(int)(en & 0x7fffffffu) * IC + i];
-            const float sg = (en >> 31) ? -1.f : 1.f;
-            a.add2(sg * v.x, sg * v.y);
+        for (int kb = e0; kb < e1; kb += kDot2Block) {   // blocked Dot2 (ff.cuh)
+            const int ke = min(e1, kb + kDot2Block);
+            Dot2 blk;
+            for (int k = kb; k < ke; ++k) {
+                const uint32_t en = __ldg(LC.ent + k);
+                const float2 v = t[(int)(en & 0x7fffffffu) * IC + i];
+                const float sg = (en >> 31) ? -1.f : 1.f;
+                blk.add2(sg * v.x, sg * v.y);
+            }
+            a.merge(blk);
         }
         part[((size_t)c * s + r) * B + ig * IC + i] = a.value();
     }
@@ -387,10 +407,15 @@ __global__ void __launch_bounds__(kThreads) kbx_sketch_l_reduce(BDims D, SketchL
         const DevScalars& sc = S.sc[b];
         if (sc.stop || sc.d >= D.dmax) continue;
         Dot2 a;
+        for (int c0 = 0; c0 < LC.nchunks; c0 += kDot2Block) {   // blocked Dot2 (ff.cuh)
+            const int c1 = min(LC.nchunks, c0 + kDot2Block);
+            Dot2 blk;
 #pragma unroll 8
-        for (int c = 0; c < LC.nchunks; ++c) {
-            const float2 v = __ldcg(part + ((size_t)c * s + r) * B + b);
-            a.add2(v.x, v.y);
+            for (int c = c0; c < c1; ++c) {
+                const float2 v = __ldcg(part + ((size_t)c * s + r) * B + b);
+                blk.add2(v.x, v.y);
+            }
+            a.merge(blk);
         }
         S.partL[(size_t)b * s + r] = a.to_double();
     }
@@ -535,6 +560,9 @@ __global__ void __launch_bounds__(kCombThreads, 3) kbx_combine_tma(BDims D, BBul
             __syncwarp();
             if (lane == 0 && ok) mbar_arrive(&empty[st]);
             if (__any_sync(0xffffffffu, *err_flag != 0)) break;   // warp-uniform exit
+            if ((j & 3) == 3)   // the collected errors folded back every 4 columns (ff.cuh)
+#pragma unroll
+                for (int r = 0; r < RPM; ++r) acc[r].renorm();
             if (j == dlive - 1 && live) {
                 // epilogue: EC loads issued together, then the stores
 #pragma unroll
@@ -638,11 +666,15 @@ __global__ void __launch_bounds__(kThreads) kbx_combine(BDims D, BBulkX<TW> X, B
     float q0 = 0.f, q1 = 0.f, q2 = 0.f;
     const int64_t tot = (D.n + D.m) * B;
     for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < tot && live; t += gstride()) {
-        Dot2 a;
+        Dot2 a;   // blocked Dot2 over the columns (ff.cuh)
         if (t < D.n * B) {
-            for (int j = 0; j < d; ++j) {
-                const float2 yv = y[(size_t)j * B];
-                acc_wy(a, X.W[(size_t)j * D.n * B + t], yv.x, yv.y);
+            for (int j0 = 0; j0 < d; j0 += kDot2Block) {
+                Dot2 blk;
+                for (int j = j0; j < min(d, j0 + kDot2Block); ++j) {
+                    const float2 yv = y[(size_t)j * B];
+                    acc_wy(blk, X.W[(size_t)j * D.n * B + t], yv.x, yv.y);
+                }
+                a.merge(blk);
             }
             const float2 xv = a.value();
             X.x[t] = xv;
@@ -659,9 +691,13 @@ __global__ void __launch_bounds__(kThreads) kbx_combine(BDims D, BBulkX<TW> X, B
             }
         } else {
             const int64_t te = t - D.n * B;
-            for (int j = 0; j < d; ++j) {
-                const float2 yv = y[(size_t)j * B];
-                acc_wy(a, X.AW[(size_t)j * D.m * B + te], yv.x, yv.y);
+            for (int j0 = 0; j0 < d; j0 += kDot2Block) {
+                Dot2 blk;
+                for (int j = j0; j < min(d, j0 + kDot2Block); ++j) {
+                    const float2 yv = y[(size_t)j * B];
+                    acc_wy(blk, X.AW[(size_t)j * D.m * B + te], yv.x, yv.y);
+                }
+                a.merge(blk);
             }
             a.add2(-X.b[te].x, -X.b[te].y);
             X.e[te] = a.value();
@@ -694,7 +730,7 @@ __global__ void __launch_bounds__(kThreads) kbx_combine(BDims D, BBulkX<TW> X, B
 // 16-byte load), then the stencil and lambda_i (hi, lo) on the row's leading lane.  out ==
 // nullptr: appended as column d_i of W_i (rounded to TW); otherwise written to out (float-float).
 template <typename TW, int VV>
-__global__ void __launch_bounds__(kThreads) kbx_csr_gradient(BDims D, DevA<float, float> A, DevL L, BBulkX<TW> X,
+__global__ void __launch_bounds__(kThreads, 3) kbx_csr_gradient(BDims D, DevA<float, float> A, DevL L, BBulkX<TW> X,
                                                              BSmall S, float2* out) {
     const int B = D.B;
     const int64_t items = rl_items(D.n, B, VV, D.nl_t);
@@ -724,14 +760,20 @@ __global__ void __launch_bounds__(kThreads) kbx_csr_gradient(BDims D, DevA<float
         Dot2 acc[VV];
         const int beg = rl.valid ? A.trp[rl.row] : 0, end = rl.valid ? A.trp[rl.row + 1] : 0;
         const float2* eb = X.e + rl.b0;
+        for (int kb = beg + rl.nl; kb < end; kb += kDot2Block * rl.NL) {   // blocked Dot2 (ff.cuh)
+            const int ke = min(end, kb + kDot2Block * rl.NL);
+            Dot2 blk[VV];
 #pragma unroll 4
-        for (int kk = beg + rl.nl; kk < end; kk += rl.NL) {
-            const int64_t c = (int64_t)__ldg(A.tci + kk) * B;
-            const float a = __ldg(A.tval + kk);
-            float2 ev[VV];
-            ldw<float2, VV>(eb + c, ev);
+            for (int kk = kb; kk < ke; kk += rl.NL) {
+                const int64_t c = (int64_t)__ldg(A.tci + kk) * B;
+                const float a = __ldg(A.tval + kk);
+                float2 ev[VV];
+                ldw<float2, VV>(eb + c, ev);
 #pragma unroll
-            for (int v = 0; v < VV; ++v) acc[v].add_prod2(a, ev[v].x, ev[v].y);
+                for (int v = 0; v < VV; ++v) blk[v].add_prod2(a, ev[v].x, ev[v].y);
+            }
+#pragma unroll
+            for (int v = 0; v < VV; ++v) acc[v].merge(blk[v]);
         }
         for (int off = 1; off < rl.NL; off <<= 1)
 #pragma unroll
@@ -780,25 +822,32 @@ __global__ void __launch_bounds__(kThreads) kbx_gradient(BDims D, DevA<float, fl
     const StridedW<float2> ev{X.e + b, B}, xv{X.x + b, B};
     for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < D.n * B; t += gstride()) {
         const int64_t i = qdiv(t, B);
-        Dot2 a;
+        Dot2 a;   // blocked Dot2 (ff.cuh): one block per row of the psf, or of kDot2Block values
         if (A.kind == SGKS_OP_CONV2D) {
             const int nx = A.nx, ny = A.ny, kh = A.kh, kw = A.kw;
             const int iy = (int)qdiv(i, nx), ix = (int)(i - (int64_t)iy * nx);
             for (int aa = 0; aa < kh; ++aa) {
                 const int yy = iy + aa - kh / 2;
                 if (yy < 0 || yy >= ny) continue;
+                Dot2 blk;
                 for (int c = 0; c < kw; ++c) {
                     const int xx = ix + c - kw / 2;
                     if (xx >= 0 && xx < nx) {
                         const float2 e = ev((int64_t)yy * nx + xx);
-                        a.add_prod2(psf_s[aa * kw + c], e.x, e.y);
+                        blk.add_prod2(psf_s[aa * kw + c], e.x, e.y);
                     }
                 }
+                a.merge(blk);
             }
         } else {
-            for (int64_t k = 0; k < A.m; ++k) {
-                const float2 e = ev(k);
-                a.add_prod2(__ldg(A.dense + k * A.ld + i), e.x, e.y);
+            for (int64_t k0 = 0; k0 < A.m; k0 += kDot2Block) {
+                Dot2 blk;
+                const int64_t k1 = k0 + kDot2Block < A.m ? k0 + kDot2Block : A.m;
+                for (int64_t k = k0; k < k1; ++k) {
+                    const float2 e = ev(k);
+                    blk.add_prod2(__ldg(A.dense + k * A.ld + i), e.x, e.y);
+                }
+                a.merge(blk);
             }
         }
         Dot2 lt;

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kThreads) kbx_seg_reduce(BDims D, TiledA T, BB
 }
 
 int tile_instances(const BDims& D, size_t welem) {
-    return std::min(D.B, D.tile_ic > 0 ? D.tile_ic : (welem == 4 ? 32 : 16));
+    return std::min(D.B, D.tile_ic > 0 ? D.tile_ic : (welem == 4 ? 16 : 8));
 }
 
 size_t tile_smem(const TiledA& T, const BDims& D, size_t welem) {

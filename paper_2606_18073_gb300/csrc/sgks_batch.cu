@@ -425,14 +425,14 @@ struct GroupX : GroupBase {
             D.slice_kb = tune_pick(best, pick, t_def, def);
             D.nb_combine = batchx_combine_grid(D, sizeof(TW));
         }
-        if (T.ntiles) {   // instances per CTA of the tiled forward pass: the default or half of it
-            const int half = (sizeof(TW) == 4 ? 32 : 16) / 2;
+        if (T.ntiles) {   // instances per CTA of the tiled forward pass: the default or twice it
+            const int def_ic = sizeof(TW) == 4 ? 16 : 8;
             float best = 1e30f, t_def = 0.f;
             int pick = 0;
-            for (int ic : {0, half}) {
+            for (int ic : {0, 2 * def_ic}) {
                 D.tile_ic = ic;
                 const float t = time_it([&] { return launchbx_tile_apply<TW>(D, T, X, S, part, st); });
-                log += " tile/" + std::to_string(ic ? ic : 2 * half) + "=" + std::to_string(t);
+                log += " tile/" + std::to_string(ic ? ic : def_ic) + "=" + std::to_string(t);
                 if (ic == 0) t_def = t;
                 if (t < best) { best = t; pick = ic; }
             }
@@ -464,7 +464,7 @@ struct GroupX : GroupBase {
         if (e != cudaSuccess) return e;
         tuned = "slice " + std::to_string(D.slice_kb) + " KB, lanes/row A " + std::to_string(D.nl_a) + ", A^T " +
                 std::to_string(D.nl_t) +
-                (T.ntiles ? ", tile instances " + std::to_string(D.tile_ic ? D.tile_ic : (sizeof(TW) == 4 ? 32 : 16))
+                (T.ntiles ? ", tile instances " + std::to_string(D.tile_ic ? D.tile_ic : (sizeof(TW) == 4 ? 16 : 8))
                           : std::string()) +
                 " (ms:" + log + ")";
         std::lock_guard<std::mutex> g(g_tune_mu);

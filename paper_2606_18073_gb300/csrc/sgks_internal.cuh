@@ -873,7 +873,7 @@ struct BDims {
     int nl_a, nl_t;           // CSR rows: lanes per row of A and of A^T (powers of two <= 32, tuned)
     int nb_refine;            // CTAs of kb_wtr (each leaves one partial per instance)
     int nb_setup;             // CTAs of the setup reductions
-    int tile_ic;              // tiled forward pass: instances per CTA (0: 32 for an FP32 basis, 16
+    int tile_ic;              // tiled forward pass: instances per CTA (0: 16 for an FP32 basis, 8
                               // for a float-float one; tuned)
     int wait_tries;           // bounded waits of the bulk-copy combine's ring (kWaitTries; 0 in the
                               // timeout test of SGKS_TEST_TIMEOUT_GROUP, see sgks_batch.cu)

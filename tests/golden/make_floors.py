@@ -135,8 +135,14 @@ def floor_curve(P, iters, eps, seeds=5, **kw):
 
 
 def _problem(name, form, params=()):
+    """The workload; params may hold sketch_seed, which replaces the sketch seed (a batch shares
+    the sketch of its first instance)."""
     from workloads import make_problem
-    P = make_problem(name, **dict(params))
+    kw = dict(params)
+    sketch_seed = kw.pop("sketch_seed", None)
+    P = make_problem(name, **kw)
+    if sketch_seed is not None:
+        P.sketch.seed = sketch_seed
     if form in ("fp64", "ff"):
         P.n_refine = FORMS[name][1]
     return P
@@ -154,26 +160,30 @@ def _suffix(params):
     return "".join(f"_{k}{v}" for k, v in params)
 
 
-def _run(task):
-    """One target (config, parameters, form) in one process: the unperturbed oracle run, then one
-    perturbed run per seed, keeping only the deviation curves (the iterates of one run at a time)."""
+def _reference(task):
+    """The unperturbed oracle run of one target; its iterates go to a scratch file."""
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-    name, params, form, seeds = task
+    name, params, form, scratch = task
     import oracle as O
     P = _problem(name, form, params)
     ref = O.sgks(P, iters=P.iters, record_x=True)
-    xs = [np.asarray(x) for x in ref["xs"]]
-    rre = [float(v) for v in ref["rre"]]
-    del ref
-    curves = []
-    for sd in range(seeds):
-        p = _perturbed(P, P.iters, EPS[form], sd)
-        curves.append([float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(p["xs"], xs)])
-        del p
-    return task, curves, rre
+    np.save(scratch, np.stack([np.asarray(x) for x in ref["xs"]]))
+    return [float(v) for v in ref["rre"]]
+
+
+def _seed(task):
+    """One perturbed run of one target against its reference iterates (read from the scratch
+    file): the deviation curve."""
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    name, params, form, scratch, seed = task
+    P = _problem(name, form, params)
+    p = _perturbed(P, P.iters, EPS[form], seed)
+    xs = np.load(scratch, mmap_mode="r")
+    return [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(p["xs"], xs)]
 
 
 def main(argv):
+    import tempfile
     ap = argparse.ArgumentParser()
     ap.add_argument("targets", nargs="*")
     ap.add_argument("--seeds", type=int, default=5)
@@ -184,19 +194,24 @@ def main(argv):
         name, params, form = _parse(t)
         for f in ([form] if form else FORMS[name][0]):
             targets.append((name, params, f))
-    tasks = [(n, pr, f, a.seeds) for n, pr, f in targets]
     ctx = mp.get_context("spawn")
-    with ctx.Pool(min(a.jobs, len(tasks))) as pool:
-        for (name, params, form, seeds), curves, rre in pool.imap_unordered(_run, tasks):
-            floor = [max(c[k] for c in curves) for k in range(len(rre))]
-            P = _problem(name, form, params)
-            out = {"config": name, "params": dict(params), "form": form, "eps": _steps(EPS[form]), "n_refine": P.n_refine,
-                   "iters": P.iters, "seeds": seeds, "floor": floor, "per_seed": curves, "oracle_rre": rre,
-                   "note": "max over seeds of oracle vs oracle with gradients, sketched QR inputs and projected-solve "
-                           "inputs perturbed by (1 + u*N(0,1)), u per step in eps; written by make_floors.py"}
-            with open(os.path.join(HERE, f"floor_{name}{_suffix(params)}_{form}.json"), "w") as f:
-                json.dump(out, f)
-            print(name + _suffix(params), form, f"floor at k={P.iters}: {floor[-1]:.2e}", flush=True)
+    with tempfile.TemporaryDirectory() as tmp, ctx.Pool(a.jobs) as pool:
+        scratch = [os.path.join(tmp, f"ref{i}.npy") for i in range(len(targets))]
+        rres = pool.map(_reference, [(n, pr, f, sc) for (n, pr, f), sc in zip(targets, scratch)])
+        # every (target, seed) pair is one task, so that the seeds of one target run in parallel
+        tasks = [(n, pr, f, sc, sd) for (n, pr, f), sc in zip(targets, scratch) for sd in range(a.seeds)]
+        curves = pool.map(_seed, tasks)
+    for i, ((name, params, form), rre) in enumerate(zip(targets, rres)):
+        per_seed = curves[i * a.seeds:(i + 1) * a.seeds]
+        floor = [max(c[k] for c in per_seed) for k in range(len(rre))]
+        P = _problem(name, form, params)
+        out = {"config": name, "params": dict(params), "form": form, "eps": _steps(EPS[form]), "n_refine": P.n_refine,
+               "iters": P.iters, "seeds": a.seeds, "floor": floor, "per_seed": per_seed, "oracle_rre": rre,
+               "note": "max over seeds of oracle vs oracle with every rounding step perturbed by (1 + u*N(0,1)), "
+                       "u per step in eps; written by make_floors.py"}
+        with open(os.path.join(HERE, f"floor_{name}{_suffix(params)}_{form}.json"), "w") as f:
+            json.dump(out, f)
+        print(name + _suffix(params), form, f"floor at k={P.iters}: {floor[-1]:.2e}", flush=True)
 
 
 if __name__ == "__main__":
