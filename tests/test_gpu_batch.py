@@ -20,12 +20,12 @@ from workloads import small_problem
 from workloads.problem import SketchDesc
 
 sys.path.insert(0, os.path.join(os.path.dirname(__file__), "golden"))
-from make_floors import EPS, floor_curve  # noqa: E402
+from make_floors import EPS, FF_SCALE, floor_curve  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
 TOL64, TOL32 = 1e-10, 1e-4
-FACTOR64, FACTOR32 = 100.0, 10.0
+FACTOR64, FACTOR32 = 10.0, 10.0
 
 
 @pytest.fixture(scope="module")
@@ -98,17 +98,17 @@ def batch_iterates(G, problems, prec, iters, **over):
     return Bt, xs
 
 
-FORM_BAR = {  # precision -> (floor eps, strict bar, factor on the floor)
-    "fp64": (EPS["fp64"], TOL64, FACTOR64),
-    "ff": (EPS["ff"], TOL64, FACTOR64),
-    "fp32": (EPS["fp32"], TOL32, FACTOR32),
+FORM_BAR = {  # precision -> (floor model, scale of the floor, strict bar, factor on the floor)
+    "fp64": (EPS["fp64"], 1.0, TOL64, FACTOR64),
+    "ff": (EPS["fp64"], FF_SCALE, TOL64, FACTOR64),   # the FP64 floor scaled by 2^-48 / 2^-53
+    "fp32": (EPS["fp32"], 1.0, TOL32, FACTOR32),
 }
 
 
 def check_instance(xs, P, prec):
     ref = O.sgks(P, iters=len(xs) - 1, record_x=True)
-    eps, tol, fac = FORM_BAR[prec]
-    fl = floor_curve(P, len(xs) - 1, eps)[0]
+    eps, scale, tol, fac = FORM_BAR[prec]
+    fl = [scale * v for v in floor_curve(P, len(xs) - 1, eps)[0]]
     errs = [rel(a, b) for a, b in zip(xs, ref["xs"])]
     parity_log.record(f"batch[{prec}] {P.name}", errs, fl, tol, fac)
     bad = [(k, e, fl[k]) for k, e in enumerate(errs) if e > max(tol, fac * fl[k])]
@@ -383,7 +383,11 @@ def _oracle_errors(args):
     import numpy as np
     import oracle as O
     from workloads import make_problem
+    kw = dict(kw)
+    sketch_seed = kw.pop("sketch_seed", None)
     P = make_problem(kind, **kw)
+    if sketch_seed is not None:   # a batch shares one sketch: the seed of its first instance
+        P.sketch.seed = sketch_seed
     if kind == "ct2d":
         P.n_refine = 0
     ref = O.sgks(P, record_x=True)
@@ -413,7 +417,7 @@ def _graph_iterates(Bt, iters, which):
 def test_full_size_ct_batch_ff(G, tmp_path):
     """512^2 CT, 64 right-hand sides x lambda_i, 150 iterations, float-float form (the bench's
     headline workload): instances 0, 21, 42 and 63 against the oracle at every iteration,
-    max(1e-10, 10 x floor_k) with the instance's float-float floor."""
+    max(1e-10, 10 x floor_k), floor_k the instance's FP64 floor scaled by 2^-48 / 2^-53."""
     from workloads.configs import ct_op, make_ct2d
     A0 = ct_op(512, np.arange(180) * 1.0, 725)
     probs = [make_ct2d(instance=i, A=A0, precision="ff") for i in range(64)]
@@ -429,7 +433,7 @@ def test_full_size_ct_batch_ff(G, tmp_path):
     del xs
     errs = _compare_in_workers(cases)
     for i, e in zip(which, errs):
-        fl = _load_floor(f"ct2d_ff" if i == 42 else f"ct2d_instance{i}_ff")
+        fl = [FF_SCALE * v for v in _load_floor("ct2d_fp64" if i == 42 else f"ct2d_instance{i}_fp64")]
         parity_log.record(f"full_size_ct_batch_ff[{i}]", e, fl, TOL64, FACTOR64)
         bad = [(k, v, fl[k]) for k, v in enumerate(e) if v > max(TOL64, FACTOR64 * fl[k])]
         assert not bad, f"instance {i}: {bad[:4]}"
@@ -439,7 +443,8 @@ def test_full_size_ct_batch_ff(G, tmp_path):
 def test_full_size_dynct_batch_fp32(G, tmp_path):
     """Dynamic CT, 16 ragged instances (frames 8, 16, 24, 32; seeds 0..15), 200 iterations with 3
     refinement steps, FP32 form: one instance per frame count (seeds 0..3) against the oracle at
-    every iteration, max(1e-4, 10 x floor_k) with the instance's FP32 floor."""
+    every iteration, max(1e-4, 10 x floor_k) with the instance's FP32 floor.  The batch shares one
+    sketch (the seed of instance 0), so the oracle and the floors use sketch seed 0 throughout."""
     from workloads.configs import dynct_frame_ops, make_dynct
     ops = dynct_frame_ops(128, 32)
     frames = [8, 16, 24, 32] * 4
@@ -457,11 +462,11 @@ def test_full_size_dynct_batch_fp32(G, tmp_path):
     for i in which:
         path = str(tmp_path / f"x{i}.npy")
         np.save(path, xs[i])
-        cases.append(("dynct", {"seed": i, "frames": frames[i]}, path))
+        cases.append(("dynct", {"seed": i, "frames": frames[i], "sketch_seed": probs[0].sketch.seed}, path))
     del xs
     errs = _compare_in_workers(cases)
     for i, e in zip(which, errs):
-        fl = _load_floor(f"dynct_seed{i}_frames{frames[i]}_fp32")
+        fl = _load_floor(f"dynct_seed{i}_frames{frames[i]}_sketch_seed0_fp32" if i else "dynct_seed0_frames8_fp32")
         parity_log.record(f"full_size_dynct_batch_fp32[{i}]", e, fl, TOL32, FACTOR32)
         bad = [(k, v, fl[k]) for k, v in enumerate(e) if v > max(TOL32, FACTOR32 * fl[k])]
         assert not bad, f"instance {i} ({frames[i]} frames): {bad[:4]}"

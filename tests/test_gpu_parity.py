@@ -35,7 +35,7 @@ pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-10
 TOL32 = 1e-4
-FACTOR64 = 100.0
+FACTOR64 = 10.0
 FACTOR32 = 10.0
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
