@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--cpu-sample-iters", type=int, default=None,
                     help="iterations of the oracle sample (default 20 for the CT batch, 25 otherwise)")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--profile-single", default=None, choices=["deblur2d", "ct2d", "dynct"],
+                    help="one solve of one instance of the workload alone in --precision (fp64 or fp32), "
+                         "for profiler captures")
     ap.add_argument("--profile-batch", default=None, choices=["ct2d", "dynct"],
                     help="run one batched solve of a reduced CT / dynamic-CT batch (for profiler captures) and exit")
     ap.add_argument("--batch-size", type=int, default=16)
@@ -822,6 +825,9 @@ def main():
     if args.profile_batch:
         profile_batch(args)
         return
+    if args.profile_single:
+        profile_single(args)
+        return
     if args.config == BATCH_CONFIG:
         main_batch(args)
         return
@@ -1257,6 +1263,24 @@ def bench_gks(G, name, dev, flush):
         out[method] = rec
     out["gks_over_sgks_time"] = out["gks"]["ms_per_solve"] / out["sgks"]["ms_per_solve"]
     return out
+
+
+def profile_single(args):
+    """One solve of instance 0 of a workload on a single handle (FP64 without refinement, or the
+    FP32 form with the workload's refinement steps), for profiler captures."""
+    import torch
+    import paper_2606_18073_gb300 as G
+    G.build()
+    dev = torch.device("cuda", 0)
+    prec = args.precision if args.precision in ("fp64", "fp32") else "fp64"
+    P = make_workload(args.profile_single, seed=0)
+    if prec == "fp64":
+        P.n_refine = 0
+    S = G.Solver(**G.device_inputs(P, prec, device=dev))
+    out = S.solve(P.iters)
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"profile_single": args.profile_single, "precision": prec, "iterations": out["iters_done"]}))
+    S.close()
 
 
 def profile_batch(args):
