@@ -320,6 +320,35 @@ struct GroupX : GroupBase {
         return e;
     }
 
+    // Setup of the float-float form (the Krylov basis W_0, Sec. 2.1): its FP64 vectors pass
+    // through A and A^T in float-float, with the compensated kernels of the iteration on views
+    // of the group's buffers (S.sc is zero during the setup, so column 0 of each view is used):
+    // A^T v -> out (FP64) from the m-vector v (float2) with lambda = 0 and x = 0.
+    float2* ff_tmp = nullptr;   // [n][B] float-float scratch of the setup (float-float form only)
+    float2* zlam = nullptr;     // [B] zero lambda for the setup's A^T passes
+    cudaError_t ff_apply_at(const float2* v, double* out) {
+        cudaError_t e = cudaSuccess;
+        BBulkX<TW> Xs = X;
+        Xs.e = const_cast<float2*>(v);
+        Xs.lam2 = zlam;
+        RUN(1, launchbx_gradient<TW>(D, A, L, Xs, S, ff_tmp, st));
+        RUN(1, launchbx_to_double(ff_tmp, out, (int64_t)D.n * D.B, st));
+        return e;
+    }
+    // A w -> X.e (float-float) for the FP64 n-vector w
+    cudaError_t ff_apply_a(const double* w) {
+        cudaError_t e = cudaSuccess;
+        if constexpr (sizeof(TW) == sizeof(float2)) {
+            BBulkX<TW> Xs = X;
+            RUN(1, launchbx_from_double<TW>(w, reinterpret_cast<TW*>(ff_tmp), (int64_t)D.n * D.B, st));
+            Xs.W = reinterpret_cast<TW*>(ff_tmp);
+            Xs.AW = X.e;
+            if (T.ntiles) RUN(2, launchbx_tile_apply<TW>(D, T, Xs, S, part, st));
+            else RUN(1, launchbx_apply_column<TW>(D, A, L, Xs, S, st, true, false));
+        }
+        return e;
+    }
+
     cudaError_t normalize_d(double* w) {
         cudaError_t e = cudaSuccess;
         RUN(2, launchb_dots<double>(D, w, 1, w, S, st));
@@ -344,12 +373,22 @@ struct GroupX : GroupBase {
             RUN(2, launchb_dots<double>(D, W, 1, W, S, st));
             RUN(1, launchb_set_xt2(S, B, st));
         }
-        RUN(1, (launchb_apply<double, float>(D, Ad, L, SGKS_APPLY_AT, Xd.b, W, st)));
+        if (ff_tmp) {   // float-float form: the Krylov vectors' operator passes in float-float
+            if (e == cudaSuccess) e = cudaMemsetAsync(X.x, 0, sizeof(float2) * nB, st);
+            e = e == cudaSuccess ? ff_apply_at(X.b, W) : e;
+        } else {
+            RUN(1, (launchb_apply<double, float>(D, Ad, L, SGKS_APPLY_AT, Xd.b, W, st)));
+        }
         if (e == cudaSuccess) e = normalize_d(W);
         for (int j = 1; j < D.ell && e == cudaSuccess; ++j) {
             double* wj = W + j * nB;
-            RUN(1, (launchb_apply<double, float>(D, Ad, L, SGKS_APPLY_A, W + (j - 1) * nB, Xd.tm, st)));
-            RUN(1, (launchb_apply<double, float>(D, Ad, L, SGKS_APPLY_AT, Xd.tm, wj, st)));
+            if (ff_tmp) {
+                e = ff_apply_a(W + (j - 1) * nB);
+                if (e == cudaSuccess) e = ff_apply_at(X.e, wj);
+            } else {
+                RUN(1, (launchb_apply<double, float>(D, Ad, L, SGKS_APPLY_A, W + (j - 1) * nB, Xd.tm, st)));
+                RUN(1, (launchb_apply<double, float>(D, Ad, L, SGKS_APPLY_AT, Xd.tm, wj, st)));
+            }
             for (int pass = 0; pass < 2; ++pass) {
                 RUN(2, launchb_dots<double>(D, W, j, wj, S, st));
                 RUN(1, launchb_vec_update<double>(D, wj, W, j, S, 0, st));
@@ -868,6 +907,10 @@ int build_groups_x(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const 
         BA(G->Xd.W, (size_t)D.ell * nB);
         BA(G->Xd.tm, mB);
         BA(G->Xd.b, mB);
+        if (sizeof(TW) == sizeof(float2)) {   // the float-float form's setup passes
+            BA(G->ff_tmp, nB);
+            BA(G->zlam, B);
+        }
 #undef BA
         if (e != cudaSuccess) return bfail(h, SGKS_ERR_NOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
         X.lam2 = lam2;
@@ -879,6 +922,7 @@ int build_groups_x(sgks_batch* h, const sgks_op* op, const sgks_reg* reg, const 
         }
         e = cudaMemcpy(lam2, l2.data(), sizeof(float2) * B, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemsetAsync(X.xs, 0, sizeof(float2) * nB, h->st);
+        if (e == cudaSuccess && G->zlam) e = cudaMemsetAsync(G->zlam, 0, sizeof(float2) * B, h->st);
         if (e != cudaSuccess) return bcuda_fail(h, e, "batch workspace initialisation");
     }
     return SGKS_OK;
