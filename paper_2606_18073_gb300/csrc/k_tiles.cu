@@ -31,6 +31,13 @@ __device__ __forceinline__ TW tzero() { return TW{}; }
 // Partials of the segments of one tile for IC instances.  grid: ntiles * (B / IC) CTAs of
 // kThreads threads; thread (ig, sl) takes VV consecutive instances c IC + ig VV + [0, VV) (one
 // 16-byte shared-memory load per entry serves all VV) and segments sl, sl + NSL, ... of the tile.
+// Shared-memory slot of local pixel q (row-major in a tile of width TX, TX even): pixel rows
+// swap neighbouring slots on odd rows.  A 16-byte shared load phase serves the pixels of two
+// neighbouring segments, which on rays running along x lie one pixel row apart: with 8 float-float
+// instances a pixel takes 64 bytes, half of a bank line, and the swap puts such pairs in different
+// halves (as for pixels one column apart) instead of in the same one.
+__host__ __device__ inline int tile_slot(int q, int TX) { return q ^ ((q / TX) & 1); }
+
 template <typename TW, int VV>
 __global__ void __launch_bounds__(kThreads) kbx_tile_apply(BDims D, TiledA T, BBulkX<TW> X, BSmall S, int IC,
                                                            float2* __restrict__ part) {
@@ -65,8 +72,9 @@ __global__ void __launch_bounds__(kThreads) kbx_tile_apply(BDims D, TiledA T, BB
 #pragma unroll
             for (int k = 0; k < VV; ++k) v[k] = (in && wb[k]) ? __ldcg(wb[k] + off) : tzero<TW>();
         }
+        const int qs = tile_slot(q, T.TX);
 #pragma unroll
-        for (int k = 0; k < VV; ++k) ws[q * IC + ig * VV + k] = v[k];
+        for (int k = 0; k < VV; ++k) ws[qs * IC + ig * VV + k] = v[k];
     }
     __syncthreads();
     const int s0 = T.tile_seg[t], s1 = T.tile_seg[t + 1];
@@ -160,7 +168,7 @@ template cudaError_t launchbx_tile_apply<float2>(const BDims&, const TiledA&, co
 int build_tiles(const int32_t* d_rp, const int32_t* d_ci, const float* d_val, int64_t m, int64_t n, int64_t nnz,
                 int nx, int ny, int nt, int TX, int TY, TiledA& T, std::vector<void*>& allocs, cudaStream_t st,
                 std::string* why) {
-    if ((int64_t)nx * ny * nt != n || TX * TY > 65536 || nnz >= ((int64_t)1 << 31)) {
+    if ((int64_t)nx * ny * nt != n || TX * TY > 65536 || TX % 2 != 0 || nnz >= ((int64_t)1 << 31)) {
         *why = "tiled operator: geometry does not match the unknowns";
         return SGKS_ERR_INVALID;
     }
@@ -188,7 +196,9 @@ int build_tiles(const int32_t* d_rp, const int32_t* d_ci, const float* d_val, in
         const int64_t col = ci[(size_t)k];
         const int64_t f = col / fr, r = col - f * fr, iy = r / nx, ix = r - iy * nx;
         tile_of[(size_t)k] = (int32_t)(f * tpf + (iy / TY) * ntx + ix / TX);
-        loc_of[(size_t)k] = (int32_t)((iy % TY) * TX + ix % TX);
+        // staged w is laid out in checkerboard order (tile_slot): neighbouring pixels in x and
+        // in y fall in different halves of the 128-byte bank line
+        loc_of[(size_t)k] = tile_slot((iy % TY) * TX + ix % TX, TX);
     }
     // pass 1: per row, entries stably ordered by tile; segments are the runs; count per tile
     std::vector<int32_t> order((size_t)nnz);
