@@ -139,10 +139,14 @@ typedef struct sgks_options {
                              1024; sgks_solve's tol applies the relative-change test of eq. RC.
                              bit 3 (SGKS_FLAG_AUTOTUNE, batches only): after the setup, time the
                              candidate tile choices of each group on its own data and keep the
-                             fastest (bulk-copy slice 8 or 16 KB; lanes per CSR row of A and A^T),
+                             fastest (bulk-copy slice 8 or 16 KB; lanes per CSR row of A and A^T;
+                             instances per CTA of the tiled forward pass, the default or twice it),
                              a candidate replacing the default only when at least 5% faster;
                              results are cached per shape for the process.  Without it the
-                             defaults are used (16 KB, 8, 8) and results are reproducible.
+                             defaults are used (16 KB, 8, 8; 8 float-float or 16 FP32 instances
+                             per tile CTA) and results are reproducible from run to run; the slice
+                             and the tile instances keep every sum's order, the lanes per CSR row
+                             change it (at the level of rounding).
                              bit 4 (SGKS_FLAG_NO_TILES, batches only): the compensated forms
                              (FP32, FF) compute A w of a CSR operator whose regularizer gives an
                              image geometry (2D stencils, space-time) through pixel tiles: each
